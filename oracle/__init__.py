@@ -1,0 +1,193 @@
+"""ORACLE -- test infrastructure only.
+
+A plain, slow CPU statement of the multi-receiver spectral-kurtosis RFI
+detector of Taylor et al., "Spectral Kurtosis Based RFI Mitigation for CHIME"
+(arXiv:1808.10365).  Only `tests/`, `__graft_entry__.smoke()` and the CPU
+baseline leg of `bench.py` may import it.  It shares no code with the CUDA
+library and never calls it; its inputs come from the `synth` generator or
+from the tests themselves.
+
+Notation: M samples per input per estimate (the paper's n), N inputs (the
+paper's N), N_eff the inputs with non-zero power.
+
+Pieces and the passages they follow (every function cites its own):
+  * `power_sums`         Eq. 1 / Eq. (singlesums)            [sk_oracle.c]
+  * `sk_f64`             Eqs. (discreteMean)-(normedSum2), (final)  fp64
+  * `sk_spec`            Eq. (final) via Avg(SK^_i) in the CUDA path's declared
+                         precision (int64 D_i, one fp32 divide, 2^32 fixed
+                         point sum) so Q and masks compare bit for bit
+  * `thresholds`, `mask` Sec. 3.2: flag outside mean +- a*sqrt(var), with
+                         var = 4/(n N) (Eq. final moments) and the mean shifted
+                         by the digitisation offset (App. B)
+  * `digitisation`       App. B: mean offset of SK for clipped 4-bit data
+  * `served_flags`       running per-input power state feeding the App. B offset
+  * `brute`              exact rational arithmetic on tiny inputs
+
+Parity status: S1, S2, Q, N_eff, SK and the static mask are pinned (closed
+forms, brute force, moments; tests/test_oracle_pins.py).  The integer
+threshold recipe and the digitisation-offset table are pinned only by
+Monte-Carlo false-alarm rates and by limits of the model (the paper prints no
+threshold numbers): parity for those is "partial" in the strict sense.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "liboracle.so")
+TWO32 = 4294967296.0
+
+_lib = None
+
+
+def build():
+    """Compile the C part of the oracle (plain gcc, no FMA contraction)."""
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                    "-fno-fast-math", "-std=c11", "-o", LIB,
+                    os.path.join(HERE, "sk_oracle.c"), "-lm"], check=True)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        src = os.path.join(HERE, "sk_oracle.c")
+        if not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(src):
+            build()
+        lib = ctypes.CDLL(LIB)
+        P = ctypes.c_void_p
+        i64, i32 = ctypes.c_int64, ctypes.c_int32
+        lib.oracle_power_sums.argtypes = [P, i64, i32, i32, i32, P, P]
+        lib.oracle_sk_f64.argtypes = [P, P, i64, i32, i32, P, P, P]
+        lib.oracle_sk_spec.argtypes = [P, P, i64, i32, i32, P, P, P]
+        lib.oracle_sk_single_f64.argtypes = [P, P, i64, i32, P]
+        lib.oracle_max_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def power_sums(x: np.ndarray, M: int, N: int, layout: int = 0):
+    """S1, S2 (int64 [frames, N]) of Eq. 1 for bytes x ([frames, M*N] uint8)."""
+    x = np.ascontiguousarray(x, dtype=np.uint8).reshape(-1, M * N)
+    F = x.shape[0]
+    S1 = np.zeros((F, N), dtype=np.int64)
+    S2 = np.zeros((F, N), dtype=np.int64)
+    _load().oracle_power_sums(_p(x), F, M, N, layout, _p(S1), _p(S2))
+    return S1, S2
+
+
+def sk_f64(S1: np.ndarray, S2: np.ndarray, M: int):
+    """(SK~ fp64, S1bar, N_eff) per frame from Eqs. discreteMean..final in fp64."""
+    S1 = np.ascontiguousarray(S1, dtype=np.int64)
+    S2 = np.ascontiguousarray(S2, dtype=np.int64)
+    F, N = S1.shape
+    sk = np.zeros(F, dtype=np.float64)
+    sb1 = np.zeros(F, dtype=np.float64)
+    ne = np.zeros(F, dtype=np.int32)
+    _load().oracle_sk_f64(_p(S1), _p(S2), F, M, N, _p(sk), _p(sb1), _p(ne))
+    return sk, sb1, ne
+
+
+def sk_spec(S1: np.ndarray, S2: np.ndarray, M: int):
+    """(Q int64, N_eff int32, SK~ fp32) per frame in the CUDA path's declared precision."""
+    S1 = np.ascontiguousarray(S1, dtype=np.int64)
+    S2 = np.ascontiguousarray(S2, dtype=np.int64)
+    F, N = S1.shape
+    Q = np.zeros(F, dtype=np.int64)
+    ne = np.zeros(F, dtype=np.int32)
+    sk = np.zeros(F, dtype=np.float32)
+    _load().oracle_sk_spec(_p(S1), _p(S2), F, M, N, _p(Q), _p(ne), _p(sk))
+    return Q, ne, sk
+
+
+def sk_single_f64(S1: np.ndarray, S2: np.ndarray, M: int) -> np.ndarray:
+    """Per-input SK^_i (Eq. originalSK) in fp64, NaN where S1_i = 0."""
+    S1 = np.ascontiguousarray(S1, dtype=np.int64)
+    S2 = np.ascontiguousarray(S2, dtype=np.int64)
+    out = np.zeros(S1.shape, dtype=np.float64)
+    _load().oracle_sk_single_f64(_p(S1), _p(S2), S1.size, M, _p(out))
+    return out
+
+
+def sk_from_complex(x: np.ndarray) -> np.ndarray:
+    """SK~ per frame for float complex samples x [frames, M, N] (the non-digitised path of App. B).
+
+    Follows Eqs. (singlesums), (discreteMean), (normedSum2), (final) in fp64.
+    """
+    p = (x.real ** 2 + x.imag ** 2)
+    M = x.shape[1]
+    N = x.shape[2]
+    S1 = p.sum(axis=1)
+    S2 = (p * p).sum(axis=1)
+    mu = S1 / M
+    s2bar = (S2 / (mu * mu)).sum(axis=1)
+    return (M + 1.0) / (M - 1.0) * (s2bar / (M * N) - 1.0)
+
+
+# ----------------------------------------------------------------------------
+# thresholds and mask (Sec. 3.2, Eq. final moments, App. B)
+# ----------------------------------------------------------------------------
+
+def thresholds(M: int, N: int, n_sigma: float, mean_offset: float = 0.0):
+    """Integer thresholds on Q for N_eff = 0..N (entry 0 unused).
+
+    The centre is mean(SK~) = 1 (Eq. final moments) plus the digitisation offset
+    delta (App. B); the half-width a*sqrt(var) with var = 4/(n N_eff).  In Q units
+    SK~ = (n+1)/((n-1) N_eff) * Q / 2^32, so SK~ > X  <=>  Q > X (n-1) N_eff 2^32/(n+1).
+    Evaluated in double in exactly this order:
+      X_hi = ((1+delta) + a*s) * (n-1) * N_eff * 2^32 / (n+1),  T_hi = floor(X_hi)
+      X_lo = ((1+delta) - a*s) * (n-1) * N_eff * 2^32 / (n+1),  T_lo = ceil(X_lo)
+    with s = 2 / sqrt(n * N_eff).
+    """
+    t_lo = np.zeros(N + 1, dtype=np.int64)
+    t_hi = np.zeros(N + 1, dtype=np.int64)
+    centre = 1.0 + float(mean_offset)
+    a = float(n_sigma)
+    for ne in range(1, N + 1):
+        s = 2.0 / math.sqrt(float(M * ne))
+        x_hi = (centre + a * s) * float(M - 1) * float(ne) * TWO32 / float(M + 1)
+        x_lo = (centre - a * s) * float(M - 1) * float(ne) * TWO32 / float(M + 1)
+        t_hi[ne] = math.floor(x_hi)
+        t_lo[ne] = math.ceil(x_lo)
+    return t_lo, t_hi
+
+
+def mask(Q: np.ndarray, neff: np.ndarray, t_lo: np.ndarray, t_hi: np.ndarray,
+         shift: np.ndarray | None = None) -> np.ndarray:
+    """1 where SK~ lies strictly outside [lo, hi] or no input had power (Sec. 3.2)."""
+    ne = np.asarray(neff, dtype=np.int64)
+    lo = t_lo[ne].copy()
+    hi = t_hi[ne].copy()
+    if shift is not None:
+        lo = lo + shift
+        hi = hi + shift
+    m = (Q > hi) | (Q < lo) | (ne == 0)
+    return m.astype(np.uint8)
+
+
+def flag(x: np.ndarray, M: int, N: int, n_sigma: float = 3.0, mean_offset: float = 0.0,
+         layout: int = 0):
+    """Whole plain path on bytes x: dict with S1, S2, Q, neff, sk (fp32), mask, sk64."""
+    S1, S2 = power_sums(x, M, N, layout)
+    Q, ne, sk = sk_spec(S1, S2, M)
+    sk64, _, _ = sk_f64(S1, S2, M)
+    t_lo, t_hi = thresholds(M, N, n_sigma, mean_offset)
+    return dict(S1=S1, S2=S2, Q=Q, neff=ne, sk=sk, sk64=sk64,
+                mask=mask(Q, ne, t_lo, t_hi), t_lo=t_lo, t_hi=t_hi)
+
+
+from . import digitisation  # noqa: E402
+from .served import served_flags  # noqa: E402,F401

@@ -1,0 +1,106 @@
+"""The input generator (published Philox vectors, level distribution, regenerability)
+and invariants of the oracle's served-state path."""
+
+import numpy as np
+
+import oracle
+import synth
+from oracle import digitisation as dg
+from oracle import served
+
+
+def test_philox_known_answers():
+    """Philox4x32-10 known-answer vectors published with the generator (Salmon et al. 2011)."""
+    assert list(synth.philox_block([0, 0, 0, 0], [0, 0])) == [
+        0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+    assert list(synth.philox_block([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2)) == [
+        0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]
+    assert list(synth.philox_block([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344],
+                                   [0xA4093822, 0x299F31D0])) == [
+        0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
+
+
+def test_level_distribution_matches_model():
+    N, M = 4, 256
+    ds = synth.Dataset(n_frames=200, M=M, N=N, seed=42, sigma=np.array([1.52, 2.5, 3.0, 3.5]))
+    x = ds.generate_cpu().reshape(200, M, N)
+    re = (x >> 4).astype(int) - 8
+    for i, s in enumerate(ds.sigma):
+        _, p = dg.level_probs(s)
+        counts = np.bincount(re[:, :, i].ravel() + 7, minlength=15)
+        n = counts.sum()
+        # chi-square over the populated levels
+        e = np.asarray(p).reshape(-1) * n
+        m = e > 20
+        chi2 = (((counts[m] - e[m]) ** 2) / e[m]).sum()
+        assert chi2 < 60, (s, chi2)
+
+
+def test_frames_regenerate_alone_and_layouts_transpose():
+    ds = synth.pathfinder_config()
+    full = ds.generate_cpu()
+    part = ds.generate_cpu(frame0=37, n=5)
+    assert (full[37:42] == part).all()
+    dt = synth.Dataset(n_frames=3, M=16, N=10, seed=5, layout=0)
+    di = synth.Dataset(n_frames=3, M=16, N=10, seed=5, layout=1, sigma=dt.sigma)
+    a = dt.generate_cpu().reshape(3, 16, 10)
+    b = di.generate_cpu().reshape(3, 10, 16)
+    assert (a.transpose(0, 2, 1) == b).all()
+
+
+def test_rfi_plan_disjoint_and_sized():
+    r = synth.rfi_plan(synth.sub_seed(1, 0), 1525)
+    frames = [x.frame for x in r]
+    assert len(frames) == len(set(frames)) == 30 + 15
+    assert sum(1 for x in r if x.kind == "cw") == 30
+    assert all(1.0 <= x.amp <= 5.0 for x in r)
+
+
+def test_cw_lowers_and_pulse_raises_sk():
+    """CW tones drive SK below 1, a short-duty pulse above 1 (spec RFI checks)."""
+    ds = synth.pathfinder_config(duty=0.25)
+    r = oracle.flag(ds.generate_cpu(), 256, 256, 3.0, float(np.mean(dg.delta_of_sigma(ds.sigma))))
+    clean = np.r_[0:10, 20:40, 45:64]
+    base = np.median(r["sk64"][clean])
+    assert (r["sk64"][10:20] < base - 0.1).all()
+    assert (r["sk64"][40:45] > base + 0.05).all()
+    assert (r["mask"][10:20] == 1).all() and (r["mask"][40:45] == 1).all()
+    assert r["mask"][clean].sum() <= 2
+
+
+def _served_setup(T=40, N=32, M=256):
+    ds = synth.Dataset(n_frames=T, M=M, N=N, seed=77,
+                       rfi=[synth.RFI(5, "cw", 4.0), synth.RFI(6, "cw", 4.0)])
+    return ds, ds.generate_cpu(), dg.offset_table(M, B=4096)
+
+
+def test_served_state_flagged_frames_leave_state():
+    ds, x, e = _served_setup()
+    M, N = ds.M, ds.N
+    full = served.served_flags(x, M, N, e)
+    assert full["mask"][5] == 1 and full["mask"][6] == 1
+    # dropping the flagged frames changes nothing for the others' state evolution
+    keep = [f for f in range(ds.n_frames) if f not in (5, 6)]
+    sub = served.served_flags(x[keep], M, N, e)
+    assert (sub["P"] == full["P"]).all()
+    assert (sub["E"] == full["E"][keep]).all()
+
+
+def test_served_state_checkpoint_resume():
+    ds, x, e = _served_setup()
+    M, N = ds.M, ds.N
+    full = served.served_flags(x, M, N, e)
+    a = served.served_flags(x[:17], M, N, e)
+    b = served.served_flags(x[17:], M, N, e, P0=a["P"])
+    assert (np.concatenate([a["mask"], b["mask"]]) == full["mask"]).all()
+    assert (b["P"] == full["P"]).all()
+
+
+def test_served_offset_tracks_per_input_sigma():
+    """The running state's shift E approaches sum_i delta(sigma_i) in Q units (App. B)."""
+    ds, x, e = _served_setup(T=60)
+    M, N = ds.M, ds.N
+    full = served.served_flags(x, M, N, e)
+    want = float(np.sum(dg.delta_of_sigma(ds.sigma))) * 2 ** 32 * (M - 1) / (M + 1)
+    got = float(full["E"][-1])
+    assert abs(got - want) < 0.05 * abs(want) + 0.002 * 2 ** 32 * N
