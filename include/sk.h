@@ -1,0 +1,248 @@
+/*
+ * sk.h -- C ABI of the B300 spectral-kurtosis RFI detector.
+ *
+ * Method: Taylor et al., "Spectral Kurtosis Based RFI Mitigation for CHIME"
+ * (arXiv:1808.10365).  Notation: M samples per input per estimate (the
+ * paper's n), N inputs (receivers), N_eff the inputs with non-zero power in
+ * a frame.  A frame is one estimate: M time samples of all N inputs of one
+ * frequency channel.
+ *
+ * Input bytes: one complex sample per byte, 4+4-bit offset binary, real part
+ * in the high nibble and imaginary part in the low nibble, each value
+ * v + 8 with v in [-8, 7] (the generator never writes -8; the library decodes
+ * it as -8).
+ *
+ * Layouts:
+ *   SK_LAYOUT_TIME_MAJOR  uint8 [frame][t = 0..M-1][input = 0..N-1]
+ *   SK_LAYOUT_INPUT_MAJOR uint8 [frame][input][t]
+ * Several frequencies of the same (N, M) are simply more frames.
+ *
+ * Ownership: the caller owns every buffer and CUDA stream it passes.  A plan
+ * owns its threshold tables and device copies of them.  No C++ exception or
+ * abort crosses this interface: every call returns an sk_status_t and
+ * sk_last_error() gives a message for the calling thread's last failure.
+ * Calls taking a stream enqueue work and return without synchronising
+ * unless stated otherwise.
+ */
+#ifndef SK_H
+#define SK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SK_OK = 0,
+    SK_ERR_INVALID_ARG = 1, /* null pointer, size out of range, misaligned */
+    SK_ERR_UNSUPPORTED = 2, /* valid request this build does not serve     */
+    SK_ERR_OOM = 3,         /* device or host allocation failed            */
+    SK_ERR_CUDA = 4,        /* a CUDA runtime call failed                  */
+    SK_ERR_BUSY = 5,        /* admission refused: ring full or over budget */
+    SK_ERR_TIMEOUT = 6,     /* a bounded wait ran out                      */
+    SK_ERR_NOT_READY = 7,   /* result not yet available                    */
+    SK_ERR_CLOSED = 8       /* stream or server already closed             */
+} sk_status_t;
+
+typedef enum {
+    SK_LAYOUT_TIME_MAJOR = 0,
+    SK_LAYOUT_INPUT_MAJOR = 1
+} sk_layout_t;
+
+/* sk_params_t.flags */
+#define SK_RUNNING_OFFSET 0x1u /* served streams: per-input power state sets the
+                                  digitisation offset of the threshold centre */
+
+#define SK_MAX_INPUTS 4096
+#define SK_MAX_TIME 4096
+#define SK_OFFSET_BUCKETS 4096 /* power buckets of the running-offset table */
+#define SK_STATE_SHIFT 6       /* leaky-integrator gain 2^-6 of the state   */
+
+typedef struct {
+    int32_t n_inputs;   /* N, 1..SK_MAX_INPUTS                              */
+    int32_t n_time;     /* M (the paper's n), 2..SK_MAX_TIME                */
+    int32_t layout;     /* sk_layout_t                                      */
+    uint32_t flags;     /* SK_RUNNING_OFFSET                                */
+    double n_sigma;     /* a: flag outside centre +- a*sqrt(4/(M N_eff))    */
+    double mean_offset; /* static delta added to the centre 1 (App. B)     */
+    /* optional host table [SK_OFFSET_BUCKETS] of per-input offsets in Q
+       units for SK_RUNNING_OFFSET; NULL builds it from the App. B model */
+    const int64_t *offset_table;
+} sk_params_t;
+
+typedef struct sk_plan_s *sk_plan_t;
+typedef struct sk_batch_s *sk_batch_t;
+typedef struct sk_server_s *sk_server_t;
+typedef void *sk_cuda_stream_t; /* a cudaStream_t; NULL = legacy default */
+typedef int32_t sk_stream_id;
+typedef int64_t sk_ticket_t;
+
+/* ---------------------------------------------------------------- plans */
+
+/*
+ * Validate params and build the plan for one (N, M, layout): integer
+ * thresholds on Q for N_eff = 1..N (Sec. 3.2: outside mean +- a*sqrt(var),
+ * var = 4/(M N_eff) from the moments below Eq. final; mean 1 + delta, App.
+ * B), the fp32 scale (M+1)/((M-1) N_eff) of Eq. final, and, with
+ * SK_RUNNING_OFFSET, the offset table.  Copies them to `device`.  Tile
+ * choice (rows per register batch) comes from the autotune cache file named
+ * by the environment variable SK_AUTOTUNE_CACHE when it has an entry for
+ * (N, M, layout), else from the built-in default.
+ * Errors: INVALID_ARG (null, N or M out of range, bad layout, n_sigma < 0),
+ * CUDA, OOM.  *out is NULL on error.
+ */
+sk_status_t sk_plan_create(const sk_params_t *params, int device,
+                           sk_plan_t *out);
+sk_status_t sk_plan_destroy(sk_plan_t plan);
+
+/* Host copies of the threshold tables, N+1 entries each (entry 0 unused). */
+sk_status_t sk_plan_thresholds(sk_plan_t plan, int64_t *t_lo, int64_t *t_hi);
+/* Host copy of the offset table (SK_OFFSET_BUCKETS entries). */
+sk_status_t sk_plan_offset_table(sk_plan_t plan, int64_t *e);
+
+/*
+ * Tile choice of the fused kernel for this plan: rows_per_batch (8 or 16)
+ * rows of 8 bytes each thread keeps in flight per register batch, and
+ * grid_ctas (0 = one CTA per SM) for the plain launches.  Results do not
+ * depend on either (exact integer combination); only speed does.  Used by
+ * the autotuner.  INVALID_ARG for other values.
+ */
+sk_status_t sk_plan_set_tiles(sk_plan_t plan, int32_t rows_per_batch,
+                              int32_t grid_ctas);
+sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows_per_batch,
+                              int32_t *grid_ctas);
+
+/*
+ * Raw statistics of n_frames frames at d_in (device, 16-byte aligned,
+ * n_frames*M*N bytes).  Per frame f and input i (Eq. 1 / Eq. singlesums):
+ *   S1[f][i] = sum_t |x|^2, S2[f][i] = sum_t |x|^4        (int32, exact)
+ * per frame (Eqs. discreteMean, normedSum2, final; SK~ = Avg(SK^_i)):
+ *   Q[f]   = sum_{i: S1_i > 0} rint(2^32 * fp32(M S2_i - S1_i^2) / fp32(S1_i^2))
+ *            (M S2_i - S1_i^2 formed exactly in int64; one fp32 divide)
+ *   neff[f]= #{i : S1_i > 0}
+ *   sk[f]  = fp32(Q) * 2^-32 * fp32((M+1)/((M-1) neff))   (NaN if neff = 0)
+ * Every output pointer may be NULL (not written); S1 and S2 go together and
+ * must be 16-byte aligned.  Device pointers only.
+ * Errors: INVALID_ARG (null plan or d_in, misaligned pointer, n_frames < 0),
+ * CUDA (launch failure).
+ */
+sk_status_t sk_compute(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
+                       int32_t *d_s1, int32_t *d_s2, int64_t *d_q,
+                       float *d_sk, int32_t *d_neff, sk_cuda_stream_t stream);
+
+/*
+ * Fused compute + threshold: mask[f] = 1 when Q lies above T_hi[neff] or
+ * below T_lo[neff] (SK~ strictly outside the centre +- a*sigma interval,
+ * Sec. 3.2) or neff = 0.  d_sk may be NULL.  Same rules as sk_compute.
+ */
+sk_status_t sk_flag(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
+                    float *d_sk, uint8_t *d_mask, sk_cuda_stream_t stream);
+
+/*
+ * sk_flag on HOST buffers: h_in (n_frames*M*N bytes), h_sk (may be NULL) and
+ * h_mask are host memory (page-locked for full copy speed).  The plan
+ * stages chunks through device buffers it owns, overlapping the host-to-
+ * device copy of one chunk with the kernel on the previous one.  Returns
+ * after the results are in h_sk/h_mask (synchronous).  Calls on one plan
+ * are serialised.
+ */
+sk_status_t sk_flag_host(sk_plan_t plan, const uint8_t *h_in, int64_t n_frames,
+                         float *h_sk, uint8_t *h_mask, sk_cuda_stream_t stream);
+
+/* ------------------------------------------------------ batched launch */
+
+typedef struct {
+    sk_plan_t plan;      /* its N, M and thresholds                     */
+    const uint8_t *d_in; /* n_frames frames, 16-byte aligned            */
+    int64_t n_frames;
+    float *d_sk;         /* may be NULL                                 */
+    uint8_t *d_mask;     /* may be NULL (not both)                      */
+} sk_batch_item_t;
+
+/*
+ * One persistent launch over many (N, M) items (frequencies of different
+ * array sizes and integration lengths).  Builds a static schedule that
+ * gives every CTA an equal share of bytes and captures the launch in a CUDA
+ * graph on first run.  Items (buffers, plans) must stay valid until
+ * destroy.
+ */
+sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_items,
+                            int device, sk_batch_t *out);
+sk_status_t sk_batch_run(sk_batch_t batch, sk_cuda_stream_t stream);
+sk_status_t sk_batch_destroy(sk_batch_t batch);
+
+/* ------------------------------------------------------------ serving */
+
+/*
+ * A continuous-batching server on one device.  Streams (one array of N
+ * inputs each, different N allowed) submit frames as they arrive; a worker
+ * thread launches, whenever frames are ready, one batched kernel over every
+ * ready frame (at most one per stream, in arrival order) while earlier
+ * launches are still on the GPU.  Device memory for a stream (its frame ring
+ * and its per-input power state) is admitted against hbm_budget_bytes.
+ */
+sk_status_t sk_server_create(int device, size_t hbm_budget_bytes,
+                             sk_server_t *out);
+sk_status_t sk_server_destroy(sk_server_t server);
+/* BUSY if the ring and state would exceed the remaining budget. */
+sk_status_t sk_stream_open(sk_server_t server, const sk_params_t *params,
+                           int32_t ring_frames, sk_stream_id *out);
+/*
+ * Queue one frame (M*N bytes of host memory, copied before return) with its
+ * index in the stream.  BUSY if the stream's ring is full.  *ticket
+ * identifies the result.
+ */
+sk_status_t sk_stream_submit(sk_server_t server, sk_stream_id stream,
+                             const uint8_t *frame, int64_t frame_index,
+                             sk_ticket_t *ticket);
+/*
+ * Wait up to timeout_us (< 0: no limit) for a ticket; fills *sk and *mask
+ * (either may be NULL) and releases the ticket.  TIMEOUT if not done in
+ * time, INVALID_ARG for an unknown or already collected ticket.
+ */
+sk_status_t sk_ticket_wait(sk_server_t server, sk_ticket_t ticket,
+                           int64_t timeout_us, float *sk, uint8_t *mask);
+/* Block until every submitted frame of the stream has its result. */
+sk_status_t sk_stream_drain(sk_server_t server, sk_stream_id stream,
+                            int64_t timeout_us);
+/*
+ * Checkpoint of a stream's running state: an initialised flag followed by
+ * the per-input power P_i (uint32); *len is in/out (bytes).  Set restores
+ * it; both need the stream drained.
+ */
+sk_status_t sk_stream_get_state(sk_server_t server, sk_stream_id stream,
+                                void *buf, size_t *len);
+sk_status_t sk_stream_set_state(sk_server_t server, sk_stream_id stream,
+                                const void *buf, size_t len);
+sk_status_t sk_stream_close(sk_server_t server, sk_stream_id stream);
+
+typedef struct {
+    int64_t frames_done;
+    int64_t frames_flagged;
+    int64_t launches;
+    int64_t rejected;       /* BUSY answers to submit and open           */
+    double latency_p50_us;  /* submit -> result host-visible              */
+    double latency_p99_us;
+    size_t hbm_in_use;
+} sk_server_stats_t;
+sk_status_t sk_server_stats(sk_server_t server, sk_server_stats_t *out);
+
+/* --------------------------------------------------------------- misc */
+
+/*
+ * Mean offset delta of SK~ from 1 for 4+4-bit data whose components had rms
+ * sigma before rounding and clipping to [-7, 7] (App. B), from the level
+ * probabilities of the quantised Gaussian: delta = m4/(2 m2^2) - 3/2.
+ */
+sk_status_t sk_digitisation_offset(double sigma, double *delta);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *sk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SK_H */

@@ -1,0 +1,558 @@
+// Plans, the plain launches (sk_compute, sk_flag, sk_flag_host) and the
+// host-side tables: integer thresholds on Q (Sec. 3.2), the fp32 scale of
+// Eq. final and the App. B digitisation offset.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "sk_common.h"
+
+namespace sk {
+
+static thread_local std::string g_err;
+
+sk_status_t set_error(sk_status_t s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+sk_status_t cuda_error(cudaError_t e, const char *what)
+{
+    return set_error(SK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int sm_count(int device)
+{
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <int R, bool S>
+__global__ void __launch_bounds__(kThreads, 1)
+    sk_fused_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
+                    const int32_t *__restrict__ cta_chunks, Item single)
+{
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ TeamSmem ts;
+    const uint32_t lb = build_table(dyn_smem);
+    int parity = 0;
+    if (items == nullptr) {
+        const int64_t F = single.n_frames;
+        const int64_t G = gridDim.x;
+        const int64_t fb = F * (int64_t)blockIdx.x / G;
+        const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
+        if (single.fast)
+            run_fast<R, S>(single, fb, fe, lb, ts, parity);
+        else
+            run_general<S>(single, fb, fe, lb, ts, parity);
+        return;
+    }
+    const int32_t c0 = cta_chunks[blockIdx.x], c1 = cta_chunks[blockIdx.x + 1];
+    for (int32_t c = c0; c < c1; ++c) {
+        const Chunk ch = chunks[c];
+        const Item it = items[ch.item];
+        __syncthreads();
+        if (it.fast)
+            run_fast<R, S>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+        else
+            run_general<S>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+    }
+}
+
+using KernelFn = void (*)(const Item *, const Chunk *, const int32_t *, Item);
+
+static KernelFn pick_kernel(int rows, bool served)
+{
+    if (served)
+        return rows == 8 ? sk_fused_kernel<8, true> : sk_fused_kernel<16, true>;
+    return rows == 8 ? sk_fused_kernel<8, false> : sk_fused_kernel<16, false>;
+}
+
+sk_status_t ensure_kernel_attrs(int device)
+{
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> g(mu);
+    for (int d : done)
+        if (d == device)
+            return SK_OK;
+    KernelFn fns[4] = {sk_fused_kernel<8, false>, sk_fused_kernel<16, false>,
+                       sk_fused_kernel<8, true>, sk_fused_kernel<16, true>};
+    for (KernelFn f : fns) {
+        cudaError_t e = cudaFuncSetAttribute((const void *)f,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kDynSmem);
+        if (e != cudaSuccess)
+            return cuda_error(e, "cudaFuncSetAttribute");
+    }
+    done.push_back(device);
+    return SK_OK;
+}
+
+sk_status_t launch_single(const Item &it, int rows, bool served, int device, cudaStream_t st,
+                          int grid_cap)
+{
+    if (it.n_frames == 0)
+        return SK_OK;
+    sk_status_t s = ensure_kernel_attrs(device);
+    if (s != SK_OK)
+        return s;
+    const int64_t T = kThreads >> it.team_log2;
+    int64_t need = (it.n_frames + T - 1) / T;
+    int64_t g = sm_count(device);
+    if (grid_cap > 0)
+        g = grid_cap;
+    if (need < g)
+        g = need;
+    if (g < 1)
+        g = 1;
+    KernelFn fn = pick_kernel(rows, served);
+    fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, it);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_error(e, "sk kernel launch");
+    return SK_OK;
+}
+
+sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
+                            const int32_t *d_cta_chunks, int grid, int rows, bool served,
+                            int device, cudaStream_t st)
+{
+    if (grid <= 0)
+        return SK_OK;
+    sk_status_t s = ensure_kernel_attrs(device);
+    if (s != SK_OK)
+        return s;
+    Item dummy;
+    memset(&dummy, 0, sizeof dummy);
+    KernelFn fn = pick_kernel(rows, served);
+    fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_error(e, "sk batched kernel launch");
+    return SK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// App. B digitisation model (host).  A component v = clip(round(sigma g), -7, 7):
+// P(v = k) from normal tail probabilities; m2 = E v^2, m4 = E v^4;
+// delta = m4 / (2 m2^2) - 3/2 (offset of SK~ from 1 for large M).
+// ---------------------------------------------------------------------------
+
+static void quantised_moments(double sigma, double *m2, double *m4)
+{
+    const int L = 7;
+    const double s2 = sigma * std::sqrt(2.0);
+    double a2 = 0.0, a4 = 0.0;
+    for (int k = 1; k <= L; ++k) {
+        // Pr(sigma g > k - 1/2) - Pr(sigma g > k + 1/2); the top level takes the tail
+        double upper_in = 0.5 * std::erfc((k - 0.5) / s2);
+        double upper_out = (k == L) ? 0.0 : 0.5 * std::erfc((k + 0.5) / s2);
+        double pk = upper_in - upper_out;
+        double k2 = (double)k * (double)k;
+        a2 += 2.0 * pk * k2;  // levels +k and -k
+        a4 += 2.0 * pk * k2 * k2;
+    }
+    *m2 = a2;
+    *m4 = a4;
+}
+
+double digitisation_delta(double sigma)
+{
+    double m2, m4;
+    quantised_moments(sigma, &m2, &m4);
+    return m4 / (2.0 * m2 * m2) - 1.5;
+}
+
+double sigma_of_power(double mu)
+{
+    double a = std::log(1e-3), b = std::log(1e3);
+    for (int i = 0; i < 200; ++i) {
+        double c = 0.5 * (a + b);
+        double m2, m4;
+        quantised_moments(std::exp(c), &m2, &m4);
+        if (2.0 * m2 < mu)
+            a = c;
+        else
+            b = c;
+    }
+    return std::exp(0.5 * (a + b));
+}
+
+void build_offset_table(int32_t M, int64_t *e)
+{
+    for (int b = 0; b < kOffsetBuckets; ++b) {
+        double mu = ((double)b + 0.5) * 128.0 / (double)kOffsetBuckets;
+        double d = digitisation_delta(sigma_of_power(mu));
+        double x = d * 4294967296.0 * (double)(M - 1) / (double)(M + 1);
+        e[b] = (int64_t)std::llrint(x);
+    }
+}
+
+static int ceil_log2(int64_t v)
+{
+    int l = 0;
+    while ((int64_t(1) << l) < v)
+        ++l;
+    return l;
+}
+
+// Autotune cache: lines "N M layout rows grid" (grid 0 = one CTA per SM).
+static bool cached_tiles(int32_t N, int32_t M, int32_t layout, int *rows, int *grid)
+{
+    const char *path = getenv("SK_AUTOTUNE_CACHE");
+    if (!path || !*path)
+        return false;
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return false;
+    int n, m, l, r, g;
+    bool found = false;
+    char line[256];
+    while (fgets(line, sizeof line, f)) {
+        if (sscanf(line, "%d %d %d %d %d", &n, &m, &l, &r, &g) == 5 && n == N && m == M &&
+            l == layout && (r == 8 || r == 16) && g >= 0) {
+            *rows = r;
+            *grid = g;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+}  // namespace sk
+
+using namespace sk;
+
+sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
+{
+    Item it;
+    memset(&it, 0, sizeof it);
+    it.in = in;
+    it.n_frames = n_frames;
+    it.M = p.n_time;
+    it.N = p.n_inputs;
+    it.layout = p.layout;
+    it.team_log2 = team_log2;
+    it.t_lo = d_t_lo;
+    it.t_hi = d_t_hi;
+    it.c_tab = d_c;
+    it.e_tab = d_e;
+    it.fast = fast ? 1 : 0;
+    return it;
+}
+
+extern "C" const char *sk_last_error(void) { return sk::g_err.c_str(); }
+
+extern "C" sk_status_t sk_digitisation_offset(double sigma, double *delta)
+{
+    if (!delta || !(sigma > 0.0) || !std::isfinite(sigma))
+        return set_error(SK_ERR_INVALID_ARG, "sk_digitisation_offset: sigma must be > 0");
+    *delta = digitisation_delta(sigma);
+    return SK_OK;
+}
+
+static void free_plan_device(sk_plan_s *pl)
+{
+    cudaFree(pl->d_t_lo);
+    cudaFree(pl->d_t_hi);
+    cudaFree(pl->d_c);
+    cudaFree(pl->d_e);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(pl->d_stage[b]);
+        cudaFree(pl->d_sk_stage[b]);
+        cudaFree(pl->d_mask_stage[b]);
+        if (pl->ev_copied[b])
+            cudaEventDestroy(pl->ev_copied[b]);
+        if (pl->ev_used[b])
+            cudaEventDestroy(pl->ev_used[b]);
+    }
+    if (pl->s_copy)
+        cudaStreamDestroy(pl->s_copy);
+}
+
+extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_plan_t *out)
+{
+    if (!out)
+        return set_error(SK_ERR_INVALID_ARG, "sk_plan_create: out is NULL");
+    *out = nullptr;
+    if (!params)
+        return set_error(SK_ERR_INVALID_ARG, "sk_plan_create: params is NULL");
+    const sk_params_t &p = *params;
+    if (p.n_inputs < 1 || p.n_inputs > SK_MAX_INPUTS)
+        return set_error(SK_ERR_INVALID_ARG, "n_inputs %d outside 1..%d", p.n_inputs,
+                         SK_MAX_INPUTS);
+    if (p.n_time < 2 || p.n_time > SK_MAX_TIME)
+        return set_error(SK_ERR_INVALID_ARG, "n_time %d outside 2..%d", p.n_time, SK_MAX_TIME);
+    if (p.layout != SK_LAYOUT_TIME_MAJOR && p.layout != SK_LAYOUT_INPUT_MAJOR)
+        return set_error(SK_ERR_INVALID_ARG, "layout %d unknown", p.layout);
+    if (!(p.n_sigma >= 0.0) || !std::isfinite(p.n_sigma) || !std::isfinite(p.mean_offset))
+        return set_error(SK_ERR_INVALID_ARG, "n_sigma must be finite and >= 0, mean_offset finite");
+    if (p.flags & ~SK_RUNNING_OFFSET)
+        return set_error(SK_ERR_INVALID_ARG, "unknown flags 0x%x", p.flags);
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess)
+        return cuda_error(ce, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev)
+        return set_error(SK_ERR_INVALID_ARG, "device %d not present", device);
+
+    sk_plan_s *pl = new (std::nothrow) sk_plan_s();
+    if (!pl)
+        return set_error(SK_ERR_OOM, "host allocation");
+    pl->p = p;
+    pl->p.offset_table = nullptr;
+    pl->device = device;
+    const int32_t N = p.n_inputs, M = p.n_time;
+    pl->team_log2 = ceil_log2((N + kVec - 1) / kVec);
+    pl->fast = (p.layout == SK_LAYOUT_TIME_MAJOR) && (N % kVec == 0) && (M % kFlushRows == 0);
+    pl->rows = 16;
+    pl->grid_ctas = 0;
+    cached_tiles(N, M, p.layout, &pl->rows, &pl->grid_ctas);
+
+    // thresholds on Q, one pair per N_eff (Sec. 3.2); order of operations fixed
+    pl->t_lo.assign(N + 1, 0);
+    pl->t_hi.assign(N + 1, 0);
+    pl->c_tab.assign(N + 1, 0.0f);
+    const double centre = 1.0 + p.mean_offset;
+    const double a = p.n_sigma;
+    for (int32_t ne = 1; ne <= N; ++ne) {
+        const double s = 2.0 / std::sqrt((double)((int64_t)M * ne));
+        const double x_hi = (centre + a * s) * (double)(M - 1) * (double)ne * 4294967296.0 /
+                            (double)(M + 1);
+        const double x_lo = (centre - a * s) * (double)(M - 1) * (double)ne * 4294967296.0 /
+                            (double)(M + 1);
+        pl->t_hi[ne] = (int64_t)std::floor(x_hi);
+        pl->t_lo[ne] = (int64_t)std::ceil(x_lo);
+        pl->c_tab[ne] = (float)((double)(M + 1) / ((double)(M - 1) * (double)ne));
+    }
+    pl->etab.assign(kOffsetBuckets, 0);
+    if (p.flags & SK_RUNNING_OFFSET) {
+        if (p.offset_table)
+            memcpy(pl->etab.data(), p.offset_table, sizeof(int64_t) * kOffsetBuckets);
+        else
+            build_offset_table(M, pl->etab.data());
+    }
+
+    sk_status_t st = SK_OK;
+    {
+        DeviceGuard dg(device);
+        size_t tb = sizeof(int64_t) * (N + 1);
+        if (cudaMalloc(&pl->d_t_lo, tb) != cudaSuccess ||
+            cudaMalloc(&pl->d_t_hi, tb) != cudaSuccess ||
+            cudaMalloc(&pl->d_c, sizeof(float) * (N + 1)) != cudaSuccess ||
+            cudaMalloc(&pl->d_e, sizeof(int64_t) * kOffsetBuckets) != cudaSuccess) {
+            st = set_error(SK_ERR_OOM, "device allocation of plan tables");
+        } else if (cudaMemcpy(pl->d_t_lo, pl->t_lo.data(), tb, cudaMemcpyHostToDevice) !=
+                       cudaSuccess ||
+                   cudaMemcpy(pl->d_t_hi, pl->t_hi.data(), tb, cudaMemcpyHostToDevice) !=
+                       cudaSuccess ||
+                   cudaMemcpy(pl->d_c, pl->c_tab.data(), sizeof(float) * (N + 1),
+                              cudaMemcpyHostToDevice) != cudaSuccess ||
+                   cudaMemcpy(pl->d_e, pl->etab.data(), sizeof(int64_t) * kOffsetBuckets,
+                              cudaMemcpyHostToDevice) != cudaSuccess) {
+            st = set_error(SK_ERR_CUDA, "copy of plan tables");
+        } else {
+            st = ensure_kernel_attrs(device);
+        }
+        if (st != SK_OK)
+            free_plan_device(pl);
+    }
+    if (st != SK_OK) {
+        delete pl;
+        return st;
+    }
+    *out = pl;
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_plan_destroy(sk_plan_t plan)
+{
+    if (!plan)
+        return SK_OK;
+    {
+        DeviceGuard dg(plan->device);
+        free_plan_device(plan);
+    }
+    delete plan;
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_plan_thresholds(sk_plan_t plan, int64_t *t_lo, int64_t *t_hi)
+{
+    if (!plan || !t_lo || !t_hi)
+        return set_error(SK_ERR_INVALID_ARG, "sk_plan_thresholds: null argument");
+    memcpy(t_lo, plan->t_lo.data(), sizeof(int64_t) * plan->t_lo.size());
+    memcpy(t_hi, plan->t_hi.data(), sizeof(int64_t) * plan->t_hi.size());
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_plan_offset_table(sk_plan_t plan, int64_t *e)
+{
+    if (!plan || !e)
+        return set_error(SK_ERR_INVALID_ARG, "sk_plan_offset_table: null argument");
+    memcpy(e, plan->etab.data(), sizeof(int64_t) * plan->etab.size());
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_plan_set_tiles(sk_plan_t plan, int32_t rows, int32_t grid_ctas)
+{
+    if (!plan)
+        return set_error(SK_ERR_INVALID_ARG, "sk_plan_set_tiles: plan is NULL");
+    if ((rows != 8 && rows != 16) || grid_ctas < 0 || grid_ctas > 65535)
+        return set_error(SK_ERR_INVALID_ARG, "sk_plan_set_tiles: rows 8 or 16, grid >= 0");
+    plan->rows = rows;
+    plan->grid_ctas = grid_ctas;
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows, int32_t *grid_ctas)
+{
+    if (!plan || !rows || !grid_ctas)
+        return set_error(SK_ERR_INVALID_ARG, "sk_plan_get_tiles: null argument");
+    *rows = plan->rows;
+    *grid_ctas = plan->grid_ctas;
+    return SK_OK;
+}
+
+static sk_status_t check_call(sk_plan_t plan, const void *d_in, int64_t n_frames,
+                              const char *who)
+{
+    if (!plan)
+        return set_error(SK_ERR_INVALID_ARG, "%s: plan is NULL", who);
+    if (n_frames < 0)
+        return set_error(SK_ERR_INVALID_ARG, "%s: n_frames < 0", who);
+    if (n_frames > 0 && !d_in)
+        return set_error(SK_ERR_INVALID_ARG, "%s: input is NULL", who);
+    if (((uintptr_t)d_in & 15u) != 0)
+        return set_error(SK_ERR_INVALID_ARG, "%s: input not 16-byte aligned", who);
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_compute(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
+                                  int32_t *d_s1, int32_t *d_s2, int64_t *d_q, float *d_sk,
+                                  int32_t *d_neff, sk_cuda_stream_t stream)
+{
+    sk_status_t s = check_call(plan, d_in, n_frames, "sk_compute");
+    if (s != SK_OK)
+        return s;
+    if ((d_s1 == nullptr) != (d_s2 == nullptr))
+        return set_error(SK_ERR_INVALID_ARG, "sk_compute: give both S1 and S2 or neither");
+    if (((uintptr_t)d_s1 & 15u) || ((uintptr_t)d_s2 & 15u))
+        return set_error(SK_ERR_INVALID_ARG, "sk_compute: S1/S2 not 16-byte aligned");
+    Item it = plan->item(d_in, n_frames);
+    it.s1 = d_s1;
+    it.s2 = d_s2;
+    it.q = d_q;
+    it.sk = d_sk;
+    it.neff = d_neff;
+    DeviceGuard dg(plan->device);
+    return launch_single(it, plan->rows, false, plan->device, (cudaStream_t)stream,
+                         plan->grid_ctas);
+}
+
+extern "C" sk_status_t sk_flag(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
+                               float *d_sk, uint8_t *d_mask, sk_cuda_stream_t stream)
+{
+    sk_status_t s = check_call(plan, d_in, n_frames, "sk_flag");
+    if (s != SK_OK)
+        return s;
+    if (!d_mask && n_frames > 0)
+        return set_error(SK_ERR_INVALID_ARG, "sk_flag: mask is NULL");
+    Item it = plan->item(d_in, n_frames);
+    it.sk = d_sk;
+    it.mask = d_mask;
+    DeviceGuard dg(plan->device);
+    return launch_single(it, plan->rows, false, plan->device, (cudaStream_t)stream,
+                         plan->grid_ctas);
+}
+
+// Host-buffer path: chunks of stage_frames frames alternate between two device
+// staging buffers.  Chunk c's upload (plan's copy stream) overlaps chunk c-1's
+// kernel (caller's stream); an event per buffer keeps an upload from
+// overwriting a buffer whose kernel and download have not finished.
+static sk_status_t ensure_staging(sk_plan_s *pl)
+{
+    if (pl->stage_frames > 0)
+        return SK_OK;
+    const int64_t fb = (int64_t)pl->p.n_time * pl->p.n_inputs;
+    int64_t frames = ((int64_t)64 << 20) / fb;
+    if (frames < 1)
+        frames = 1;
+    for (int b = 0; b < 2; ++b) {
+        if (cudaMalloc(&pl->d_stage[b], (size_t)(frames * fb)) != cudaSuccess ||
+            cudaMalloc(&pl->d_sk_stage[b], sizeof(float) * frames) != cudaSuccess ||
+            cudaMalloc(&pl->d_mask_stage[b], (size_t)frames) != cudaSuccess)
+            return set_error(SK_ERR_OOM, "staging buffers");
+        if (cudaEventCreateWithFlags(&pl->ev_copied[b], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pl->ev_used[b], cudaEventDisableTiming) != cudaSuccess)
+            return set_error(SK_ERR_CUDA, "staging events");
+    }
+    if (cudaStreamCreateWithFlags(&pl->s_copy, cudaStreamNonBlocking) != cudaSuccess)
+        return set_error(SK_ERR_CUDA, "staging stream");
+    pl->stage_frames = frames;
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_flag_host(sk_plan_t plan, const uint8_t *h_in, int64_t n_frames,
+                                    float *h_sk, uint8_t *h_mask, sk_cuda_stream_t stream)
+{
+    if (!plan)
+        return set_error(SK_ERR_INVALID_ARG, "sk_flag_host: plan is NULL");
+    if (n_frames < 0 || (n_frames > 0 && (!h_in || !h_mask)))
+        return set_error(SK_ERR_INVALID_ARG, "sk_flag_host: bad arguments");
+    if (n_frames == 0)
+        return SK_OK;
+    std::lock_guard<std::mutex> g(plan->host_mu);
+    DeviceGuard dg(plan->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    sk_status_t s = ensure_staging(plan);
+    const int64_t fb = (int64_t)plan->p.n_time * plan->p.n_inputs;
+    for (int64_t f0 = 0, c = 0; s == SK_OK && f0 < n_frames; f0 += plan->stage_frames, ++c) {
+        const int b = (int)(c & 1);
+        const int64_t nf = std::min(plan->stage_frames, n_frames - f0);
+        cudaError_t e = cudaStreamWaitEvent(plan->s_copy, plan->ev_used[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(plan->d_stage[b], h_in + f0 * fb, (size_t)(nf * fb),
+                                cudaMemcpyHostToDevice, plan->s_copy);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(plan->ev_copied[b], plan->s_copy);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(st, plan->ev_copied[b], 0);
+        if (e != cudaSuccess) {
+            s = cuda_error(e, "sk_flag_host upload");
+            break;
+        }
+        Item it = plan->item(plan->d_stage[b], nf);
+        it.sk = h_sk ? plan->d_sk_stage[b] : nullptr;
+        it.mask = plan->d_mask_stage[b];
+        s = launch_single(it, plan->rows, false, plan->device, st, plan->grid_ctas);
+        if (s != SK_OK)
+            break;
+        e = cudaMemcpyAsync(h_mask + f0, plan->d_mask_stage[b], (size_t)nf,
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && h_sk)
+            e = cudaMemcpyAsync(h_sk + f0, plan->d_sk_stage[b], sizeof(float) * nf,
+                                cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(plan->ev_used[b], st);
+        if (e != cudaSuccess)
+            s = cuda_error(e, "sk_flag_host download");
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (s == SK_OK && e != cudaSuccess)
+        s = cuda_error(e, "sk_flag_host synchronize");
+    return s;
+}

@@ -1,0 +1,205 @@
+// Batched persistent launch: one grid of one CTA per SM walks a static,
+// byte-balanced schedule of (item, frame range) chunks that mixes items of
+// different N and M (frequencies of a 2048-input array next to a 256-input
+// one, integration lengths 128..1024).  The launch is captured once into a
+// CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "sk_common.h"
+
+struct sk_batch_s {
+    int device = 0;
+    int rows = 16;
+    int grid = 0;
+    std::vector<sk::Item> items;
+    std::vector<sk::Chunk> chunks;
+    std::vector<int32_t> cta;
+    sk::Item *d_items = nullptr;
+    sk::Chunk *d_chunks = nullptr;
+    int32_t *d_cta = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace sk {
+
+// Static schedule.  An item with team size t has T = kThreads / t teams per
+// CTA, so its frames go in rounds of T (one frame per team).  Rounds are laid
+// end to end and cut into `grid` pieces of equal bytes: a round with c bytes
+// before it and b bytes of its own goes to CTA floor((c + b/2) / (total/grid)).
+// Consecutive rounds of one item on one CTA merge into one chunk.
+void build_schedule(const std::vector<Item> &items, int grid, std::vector<Chunk> &chunks,
+                    std::vector<int32_t> &cta)
+{
+    double total = 0.0;
+    for (const Item &it : items)
+        total += (double)it.n_frames * it.M * it.N;
+    chunks.clear();
+    cta.assign(grid + 1, 0);
+    if (total <= 0.0 || grid <= 0)
+        return;
+    const double target = total / grid;
+    std::vector<std::vector<Chunk>> per(grid);
+    double cum = 0.0;
+    for (int32_t k = 0; k < (int32_t)items.size(); ++k) {
+        const Item &it = items[k];
+        const int64_t T = kThreads >> it.team_log2;
+        const double fbytes = (double)it.M * it.N;
+        for (int64_t f0 = 0; f0 < it.n_frames; f0 += T) {
+            const int64_t f1 = std::min(f0 + T, it.n_frames);
+            const double b = fbytes * (double)(f1 - f0);
+            int c = (int)((cum + 0.5 * b) / target);
+            c = std::max(0, std::min(grid - 1, c));
+            cum += b;
+            std::vector<Chunk> &v = per[c];
+            if (!v.empty() && v.back().item == k && v.back().f_end == f0) {
+                v.back().f_end = f1;
+            } else {
+                Chunk ch;
+                ch.item = k;
+                ch.pad = 0;
+                ch.f_begin = f0;
+                ch.f_end = f1;
+                v.push_back(ch);
+            }
+        }
+    }
+    for (int c = 0; c < grid; ++c) {
+        cta[c] = (int32_t)chunks.size();
+        chunks.insert(chunks.end(), per[c].begin(), per[c].end());
+    }
+    cta[grid] = (int32_t)chunks.size();
+}
+
+}  // namespace sk
+
+using namespace sk;
+
+static void free_batch(sk_batch_s *b)
+{
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    if (b->graph)
+        cudaGraphDestroy(b->graph);
+    cudaFree(b->d_items);
+    cudaFree(b->d_chunks);
+    cudaFree(b->d_cta);
+}
+
+extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_items,
+                                       int device, sk_batch_t *out)
+{
+    if (!out)
+        return set_error(SK_ERR_INVALID_ARG, "sk_batch_create: out is NULL");
+    *out = nullptr;
+    if (!items || n_items <= 0)
+        return set_error(SK_ERR_INVALID_ARG, "sk_batch_create: no items");
+    sk_batch_s *b = new (std::nothrow) sk_batch_s();
+    if (!b)
+        return set_error(SK_ERR_OOM, "host allocation");
+    b->device = device;
+    int rows = 0;
+    for (int32_t k = 0; k < n_items; ++k) {
+        const sk_batch_item_t &bi = items[k];
+        if (!bi.plan || bi.n_frames < 0 || (bi.n_frames > 0 && !bi.d_in) ||
+            ((uintptr_t)bi.d_in & 15u) || (bi.n_frames > 0 && !bi.d_mask && !bi.d_sk)) {
+            delete b;
+            return set_error(SK_ERR_INVALID_ARG, "sk_batch_create: bad item %d", k);
+        }
+        if (bi.plan->device != device) {
+            delete b;
+            return set_error(SK_ERR_INVALID_ARG, "sk_batch_create: item %d on another device",
+                             k);
+        }
+        Item it = bi.plan->item(bi.d_in, bi.n_frames);
+        it.sk = bi.d_sk;
+        it.mask = bi.d_mask;
+        b->items.push_back(it);
+        rows = std::max(rows, bi.plan->rows);
+    }
+    b->rows = rows == 8 ? 8 : 16;
+    b->grid = sm_count(device);
+    build_schedule(b->items, b->grid, b->chunks, b->cta);
+    sk_status_t s = SK_OK;
+    {
+        DeviceGuard dg(device);
+        size_t ni = sizeof(Item) * b->items.size();
+        size_t nc = sizeof(Chunk) * std::max<size_t>(1, b->chunks.size());
+        size_t nt = sizeof(int32_t) * b->cta.size();
+        if (cudaMalloc(&b->d_items, ni) != cudaSuccess ||
+            cudaMalloc(&b->d_chunks, nc) != cudaSuccess ||
+            cudaMalloc(&b->d_cta, nt) != cudaSuccess) {
+            s = set_error(SK_ERR_OOM, "batch schedule");
+        } else if (cudaMemcpy(b->d_items, b->items.data(), ni, cudaMemcpyHostToDevice) !=
+                       cudaSuccess ||
+                   (!b->chunks.empty() &&
+                    cudaMemcpy(b->d_chunks, b->chunks.data(), sizeof(Chunk) * b->chunks.size(),
+                               cudaMemcpyHostToDevice) != cudaSuccess) ||
+                   cudaMemcpy(b->d_cta, b->cta.data(), nt, cudaMemcpyHostToDevice) !=
+                       cudaSuccess) {
+            s = set_error(SK_ERR_CUDA, "batch schedule upload");
+        } else {
+            s = ensure_kernel_attrs(device);
+        }
+        if (s != SK_OK)
+            free_batch(b);
+    }
+    if (s != SK_OK) {
+        delete b;
+        return s;
+    }
+    *out = b;
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_batch_run(sk_batch_t b, sk_cuda_stream_t stream)
+{
+    if (!b)
+        return set_error(SK_ERR_INVALID_ARG, "sk_batch_run: batch is NULL");
+    DeviceGuard dg(b->device);
+    sk_status_t s = SK_OK;
+    if (!b->exec) {
+        cudaStream_t cs;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess)
+            return cuda_error(e, "sk_batch_run capture stream");
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            s = launch_schedule(b->d_items, b->d_chunks, b->d_cta, b->grid, b->rows, false,
+                                b->device, cs);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+            if (s == SK_OK && e2 == cudaSuccess) {
+                b->graph = g;
+                e = cudaGraphInstantiate(&b->exec, g, 0);
+            } else {
+                if (g)
+                    cudaGraphDestroy(g);
+                e = e2;
+            }
+        }
+        cudaStreamDestroy(cs);
+        if (s == SK_OK && e != cudaSuccess)
+            s = cuda_error(e, "sk_batch_run graph capture");
+    }
+    if (s == SK_OK) {
+        cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+        if (e != cudaSuccess)
+            s = cuda_error(e, "cudaGraphLaunch");
+    }
+    return s;
+}
+
+extern "C" sk_status_t sk_batch_destroy(sk_batch_t b)
+{
+    if (!b)
+        return SK_OK;
+    {
+        DeviceGuard dg(b->device);
+        free_batch(b);
+    }
+    delete b;
+    return SK_OK;
+}

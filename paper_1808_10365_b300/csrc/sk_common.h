@@ -1,0 +1,76 @@
+// Host-side shared declarations of the library (plan object, error helpers,
+// launch helpers).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/sk.h"
+#include "sk_device.cuh"
+
+namespace sk {
+
+sk_status_t set_error(sk_status_t s, const char *fmt, ...);
+sk_status_t cuda_error(cudaError_t e, const char *what);
+
+// Kernel launch over one item with a contiguous frame range per CTA, or over
+// a prebuilt chunk schedule (items/chunks/cta_chunks on the device).
+sk_status_t launch_single(const Item &it, int rows, bool served, int device, cudaStream_t st,
+                          int grid_cap = 0);
+sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
+                            const int32_t *d_cta_chunks, int grid, int rows, bool served,
+                            int device, cudaStream_t st);
+sk_status_t ensure_kernel_attrs(int device);
+int sm_count(int device);
+
+// Static byte-balanced schedule of items over `grid` CTAs.
+void build_schedule(const std::vector<Item> &items, int grid, std::vector<Chunk> &chunks,
+                    std::vector<int32_t> &cta);
+
+// App. B digitisation model, host double precision.
+double digitisation_delta(double sigma);
+double sigma_of_power(double mu);
+void build_offset_table(int32_t M, int64_t *e);
+
+// Scoped switch of the current device.
+struct DeviceGuard {
+    int prev = 0;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev)
+            cudaSetDevice(dev);
+    }
+    ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
+}  // namespace sk
+
+struct sk_plan_s {
+    sk_params_t p;
+    int device = 0;
+    int team_log2 = 0;
+    bool fast = false;
+    int rows = 16;      // register batch rows of the fast path
+    int grid_ctas = 0;  // 0: one CTA per SM
+    std::vector<int64_t> t_lo, t_hi, etab;
+    std::vector<float> c_tab;
+    int64_t *d_t_lo = nullptr, *d_t_hi = nullptr, *d_e = nullptr;
+    float *d_c = nullptr;
+    // staging for sk_flag_host
+    std::mutex host_mu;
+    uint8_t *d_stage[2] = {nullptr, nullptr};
+    float *d_sk_stage[2] = {nullptr, nullptr};
+    uint8_t *d_mask_stage[2] = {nullptr, nullptr};
+    int64_t stage_frames = 0;
+    cudaStream_t s_copy = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_used[2] = {nullptr, nullptr};
+
+    sk::Item item(const uint8_t *in, int64_t n_frames) const;
+};

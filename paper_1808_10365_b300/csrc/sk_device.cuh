@@ -1,0 +1,428 @@
+// Device code of the fused spectral-kurtosis kernel (sm_103a).
+//
+// One pass over the packed bytes computes, per frame of M samples x N inputs:
+//   a1 unpack    re = (b >> 4) - 8, im = (b & 15) - 8     (4+4-bit offset binary)
+//   a2 power     p = re^2 + im^2                          (Sec. 2.2.3 table)
+//   a3 sums      S1_i = sum p, S2_i = sum p^2  exact int32 (Eq. 1, Eq. singlesums)
+//   a4 normalise r_i = (M S2_i - S1_i^2) / S1_i^2, numerator and denominator exact
+//                in int64, one fp32 divide                  (Eqs. discreteMean, normedSum2)
+//   a5 combine   Q = sum_i rint(2^32 r_i) (int64, order independent), N_eff
+//   a6 SK~       (M+1)/((M-1) N_eff) * Q 2^-32 in fp32     (Eq. final: SK~ = Avg(SK^_i))
+//   a7 flag      Q outside [T_lo, T_hi][N_eff]             (Sec. 3.2, App. B offset)
+//   a8 served    per-input power state shifts the thresholds by its digitisation offset
+//
+// Sample path.  a1-a3 cost one byte of HBM per sample, so they must run in about
+// three instructions per byte to keep up with HBM.  Each sample is:
+//   PRMT  builds a shared-memory address from the byte itself:
+//         [lane*4 | byte << 8 | table base]  (table base 64 KiB aligned),
+//   LDS   reads the packed value p^2 | p << 19 from a 256-entry table replicated
+//         once per lane (entry b of lane L sits in bank L: conflict free),
+//   IADD  accumulates it.
+// Sixteen samples fit the packed 32-bit accumulator (16 p^2 <= 2^18 < 2^19,
+// 16 p <= 2^11), after which it is split into the exact S1 and S2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sk {
+
+constexpr int kThreads = 512;               // one CTA per SM
+constexpr int kVec = 8;                     // inputs per thread: one 8-byte load per row
+constexpr int kFlushRows = 16;              // rows per packed accumulator
+constexpr int kLutRow = 256;                // bytes per table entry (32 lanes x 4 B used)
+constexpr int kLutBytes = 256 * kLutRow;    // 64 KiB
+constexpr int kDynSmem = 2 * kLutBytes;     // room to put the table on a 64 KiB boundary
+constexpr int kSlots = kThreads / 32;       // partial-sum slots per parity
+constexpr int kPackShift = 19;
+constexpr uint32_t kPackMask = (1u << kPackShift) - 1u;
+constexpr int kOffsetBuckets = 4096;
+constexpr int kStateShift = 6;
+
+// Output and table pointers of one work item: frames of one (N, M).
+struct Item {
+    const uint8_t *in;       // [n_frames][M][N] time-major or [n_frames][N][M]
+    int64_t n_frames;
+    int32_t M, N;
+    int32_t layout;          // 0 time-major, 1 input-major
+    int32_t team_log2;       // threads per frame = 1 << team_log2
+    float *sk;
+    uint8_t *mask;
+    int64_t *q;
+    int32_t *neff;
+    int32_t *s1;
+    int32_t *s2;
+    const int64_t *t_lo;     // [N+1]
+    const int64_t *t_hi;     // [N+1]
+    const float *c_tab;      // [N+1]: fp32((M+1)/((M-1) n))
+    uint32_t *state;         // served: per-input power P_i [N], or null
+    const int64_t *e_tab;    // served: offset per power bucket [kOffsetBuckets]
+    int32_t state_init;      // served: 1 on the stream's first frame
+    int32_t fast;            // 1: 8-byte vector path applies
+};
+
+// A contiguous range of frames of one item, processed by one CTA.
+struct Chunk {
+    int32_t item;
+    int32_t pad;
+    int64_t f_begin;
+    int64_t f_end;
+};
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel)
+{
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
+{
+    uint32_t v;
+    asm("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ldg_stream(const uint8_t *p)
+{
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v2.u32 {%0, %1}, [%2];"
+        : "=r"(v.x), "=r"(v.y)
+        : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Packed table value for byte b: p^2 in bits 0..18, p in bits 19..31.
+__device__ __forceinline__ uint32_t packed_power(uint32_t b)
+{
+    int32_t re = (int32_t)(b >> 4) - 8;
+    int32_t im = (int32_t)(b & 15u) - 8;
+    uint32_t p = (uint32_t)(re * re + im * im);
+    return (p << kPackShift) | (p * p);
+}
+
+// Fill the lane-replicated table; returns this thread's lane base address.
+__device__ __forceinline__ uint32_t build_table(uint8_t *dyn_smem)
+{
+    uint32_t raw = (uint32_t)__cvta_generic_to_shared(dyn_smem);
+    uint32_t base = (raw + 0xFFFFu) & ~0xFFFFu;
+    for (int idx = threadIdx.x; idx < 256 * 32; idx += blockDim.x) {
+        uint32_t b = (uint32_t)idx >> 5, lane = (uint32_t)idx & 31u;
+        uint32_t addr = base + b * kLutRow + lane * 4u;
+        asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(packed_power(b)) : "memory");
+    }
+    __syncthreads();
+    // The lane base goes through a volatile shared load issued after the
+    // barrier, so no table read that depends on it can move above the barrier.
+    uint32_t probe;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(probe) : "r"(base) : "memory");
+    uint32_t lane = threadIdx.x & 31u;
+    return (base + (probe & 0u)) | (lane << 2);
+}
+
+// Accumulate one row (8 inputs, bytes in w) into the packed accumulators.
+// PRMT selector 0x76k4: byte0 = lane*4, byte1 = byte k of the data word,
+// bytes 2-3 = table base.
+__device__ __forceinline__ void accum_row(uint2 w, uint32_t lb, uint32_t (&acc)[kVec])
+{
+    acc[0] += lds_u32(prmt(w.x, lb, 0x7604u));
+    acc[1] += lds_u32(prmt(w.x, lb, 0x7614u));
+    acc[2] += lds_u32(prmt(w.x, lb, 0x7624u));
+    acc[3] += lds_u32(prmt(w.x, lb, 0x7634u));
+    acc[4] += lds_u32(prmt(w.y, lb, 0x7604u));
+    acc[5] += lds_u32(prmt(w.y, lb, 0x7614u));
+    acc[6] += lds_u32(prmt(w.y, lb, 0x7624u));
+    acc[7] += lds_u32(prmt(w.y, lb, 0x7634u));
+}
+
+__device__ __forceinline__ void flush(uint32_t (&acc)[kVec], int32_t (&s1)[kVec],
+                                      int32_t (&s2)[kVec])
+{
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+        s1[k] += (int32_t)(acc[k] >> kPackShift);
+        s2[k] += (int32_t)(acc[k] & kPackMask);
+        acc[k] = 0u;
+    }
+}
+
+// r_i scaled to 2^32 fixed point: D_i = M S2_i - S1_i^2 and S1_i^2 exact in
+// int64, converted with round-to-nearest, one IEEE fp32 division, exact
+// scaling by 2^32, round-to-nearest-even to int64.
+__device__ __forceinline__ void input_term(int32_t s1, int32_t s2, int32_t M, int64_t &q,
+                                           int32_t &cnt)
+{
+    if (s1 > 0) {
+        int64_t den = (int64_t)s1 * (int64_t)s1;
+        int64_t d = (int64_t)M * (int64_t)s2 - den;
+        float r = __fdiv_rn(__ll2float_rn(d), __ll2float_rn(den));
+        q += __float2ll_rn(__fmul_rn(r, 4294967296.0f));
+        cnt += 1;
+    }
+}
+
+struct TeamSmem {
+    long long q[2][kSlots];
+    long long e[2][kSlots];
+    int cnt[2][kSlots];
+};
+
+// Sum (q, cnt, e) over the team's threads; every thread of the team gets the
+// totals.  Teams of up to 32 threads stay inside a warp; larger teams go
+// through double-buffered shared slots and one named barrier per frame.
+__device__ __forceinline__ void team_sum(int64_t &q, int32_t &cnt, int64_t &e, int team_log2,
+                                        int team_idx, int parity, TeamSmem &ts, bool with_e)
+{
+    const int team = 1 << team_log2;
+    const int w = team < 32 ? team : 32;
+    for (int o = w >> 1; o > 0; o >>= 1) {
+        q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+        cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+        if (with_e)
+            e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+    }
+    if (team > 32) {
+        const int nw = team >> 5;
+        const int slot0 = team_idx * nw;
+        const int wit = (threadIdx.x >> 5) - slot0;
+        if ((threadIdx.x & 31) == 0) {
+            ts.q[parity][slot0 + wit] = q;
+            ts.cnt[parity][slot0 + wit] = cnt;
+            if (with_e)
+                ts.e[parity][slot0 + wit] = e;
+        }
+        named_sync(1 + team_idx, team);
+        q = 0;
+        cnt = 0;
+        e = 0;
+        for (int j = 0; j < nw; ++j) {
+            q += ts.q[parity][slot0 + j];
+            cnt += ts.cnt[parity][slot0 + j];
+            if (with_e)
+                e += ts.e[parity][slot0 + j];
+        }
+    }
+}
+
+__device__ __forceinline__ int64_t bucket_of(uint32_t P, int32_t M)
+{
+    uint64_t b = ((uint64_t)P * (uint64_t)kOffsetBuckets) /
+                 ((uint64_t)(1u << kStateShift) * (uint64_t)M * 128ull);
+    return b < (uint64_t)(kOffsetBuckets - 1) ? (int64_t)b : (int64_t)(kOffsetBuckets - 1);
+}
+
+// Per-frame epilogue: terms, team sum, outputs (leader), served state.
+template <bool SERVED>
+__device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bool fvalid,
+                                               int col0, int lit, int team_idx, int parity,
+                                               int32_t (&s1)[kVec], int32_t (&s2)[kVec],
+                                               TeamSmem &ts)
+{
+    const bool mine = fvalid && col0 < it.N;
+    const bool stateful = SERVED && it.state != nullptr;
+    int64_t q = 0, e = 0;
+    int32_t cnt = 0;
+    uint32_t P[kVec];
+    if (mine) {
+#pragma unroll
+        for (int k = 0; k < kVec; ++k)
+            if (col0 + k < it.N)
+                input_term(s1[k], s2[k], it.M, q, cnt);
+        if (it.s1) {
+            int32_t *o1 = it.s1 + frame * it.N + col0;
+            int32_t *o2 = it.s2 + frame * it.N + col0;
+#pragma unroll
+            for (int k = 0; k < kVec; ++k)
+                if (col0 + k < it.N) {
+                    o1[k] = s1[k];
+                    o2[k] = s2[k];
+                }
+        }
+        if (stateful) {
+#pragma unroll
+            for (int k = 0; k < kVec; ++k) {
+                P[k] = 0;
+                if (col0 + k < it.N) {
+                    uint32_t pk = it.state_init ? ((uint32_t)s1[k] << kStateShift)
+                                                : it.state[col0 + k];
+                    P[k] = pk;
+                    if (s1[k] > 0)
+                        e += it.e_tab[bucket_of(pk, it.M)];
+                }
+            }
+        }
+    }
+    team_sum(q, cnt, e, it.team_log2, team_idx, parity, ts, SERVED);
+    uint8_t m = 1;
+    if (cnt > 0) {
+        int64_t lo = it.t_lo[cnt] + (stateful ? e : 0);
+        int64_t hi = it.t_hi[cnt] + (stateful ? e : 0);
+        m = (q > hi || q < lo) ? 1 : 0;
+    }
+    if (fvalid && lit == 0) {
+        if (it.sk) {
+            float skv = __int_as_float(0x7FC00000);
+            if (cnt > 0)
+                skv = __fmul_rn(__fmul_rn(__ll2float_rn(q), 0x1p-32f), it.c_tab[cnt]);
+            it.sk[frame] = skv;
+        }
+        if (it.mask)
+            it.mask[frame] = m;
+        if (it.q)
+            it.q[frame] = q;
+        if (it.neff)
+            it.neff[frame] = cnt;
+    }
+    if (stateful && mine) {
+#pragma unroll
+        for (int k = 0; k < kVec; ++k) {
+            if (col0 + k < it.N) {
+                uint32_t pk = P[k];
+                if (!m)
+                    pk = pk - (pk >> kStateShift) + (uint32_t)s1[k];
+                if (!m || it.state_init)
+                    it.state[col0 + k] = pk;
+            }
+        }
+    }
+}
+
+// Fast path: time-major, N % 8 == 0, M % 16 == 0, 8-byte aligned rows.  Rows
+// stream through two register batches of R rows; the first batch of the
+// team's next frame is in flight while the current frame's epilogue runs.
+template <int R, bool SERVED>
+__device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_t f_end,
+                                         uint32_t lb, TeamSmem &ts, int &parity)
+{
+    static_assert(R == 8 || R == 16, "rows per batch");
+    const int team_log2 = it.team_log2;
+    const int T = kThreads >> team_log2;
+    const int team_idx = threadIdx.x >> team_log2;
+    const int lit = threadIdx.x & ((1 << team_log2) - 1);
+    const int col0 = lit * kVec;
+    const bool col_ok = col0 < it.N;
+    const int64_t N = it.N;
+    const int64_t fbytes = (int64_t)it.M * N;
+    const int nb = it.M / R;
+    const int64_t kmax = (f_end - f_begin + T - 1) / T;
+    const uint2 idle = make_uint2(0x88888888u, 0x88888888u);
+
+    uint2 A[R], B[R];
+    int64_t frame = f_begin + team_idx;
+    bool ok = col_ok && frame < f_end;
+    const uint8_t *fp = it.in + frame * fbytes + col0;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        A[r] = ok ? ldg_stream(fp + r * N) : idle;
+
+    for (int64_t k = 0; k < kmax; ++k) {
+        const bool fvalid = frame < f_end;
+        const int64_t nframe = frame + T;
+        const bool nok = col_ok && nframe < f_end;
+        const uint8_t *nfp = it.in + nframe * fbytes + col0;
+        uint32_t acc[kVec];
+        int32_t s1[kVec], s2[kVec];
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            acc[j] = 0u;
+            s1[j] = 0;
+            s2[j] = 0;
+        }
+        for (int jb = 0; jb < nb; jb += 2) {
+            const uint8_t *pb = fp + (int64_t)(jb + 1) * R * N;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                B[r] = ok ? ldg_stream(pb + r * N) : idle;
+            if (ok) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    accum_row(A[r], lb, acc);
+                if (R == 16)
+                    flush(acc, s1, s2);
+            }
+            if (jb + 2 < nb) {
+                const uint8_t *pa = fp + (int64_t)(jb + 2) * R * N;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    A[r] = ok ? ldg_stream(pa + r * N) : idle;
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    A[r] = nok ? ldg_stream(nfp + r * N) : idle;
+            }
+            if (ok) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    accum_row(B[r], lb, acc);
+                flush(acc, s1, s2);
+            }
+        }
+        frame_epilogue<SERVED>(it, frame, fvalid, col0, lit, team_idx, parity, s1, s2, ts);
+        parity ^= 1;
+        frame = nframe;
+        fp = nfp;
+        ok = nok;
+    }
+}
+
+// General path: any N (<= 4096), any M >= 2, either layout.  Byte loads with
+// bounds checks; the same table, terms and epilogue.  Serves the sizes the
+// fast path does not take; it is not tuned.
+template <bool SERVED>
+__device__ __forceinline__ void run_general(const Item &it, int64_t f_begin, int64_t f_end,
+                                            uint32_t lb, TeamSmem &ts, int &parity)
+{
+    const int team_log2 = it.team_log2;
+    const int T = kThreads >> team_log2;
+    const int team_idx = threadIdx.x >> team_log2;
+    const int lit = threadIdx.x & ((1 << team_log2) - 1);
+    const int col0 = lit * kVec;
+    const int64_t N = it.N;
+    const int M = it.M;
+    const int64_t fbytes = (int64_t)M * N;
+    const int64_t kmax = (f_end - f_begin + T - 1) / T;
+    int64_t frame = f_begin + team_idx;
+    for (int64_t k = 0; k < kmax; ++k) {
+        const bool fvalid = frame < f_end;
+        uint32_t acc[kVec];
+        int32_t s1[kVec], s2[kVec];
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            acc[j] = 0u;
+            s1[j] = 0;
+            s2[j] = 0;
+        }
+        if (fvalid && col0 < N) {
+            const uint8_t *fb = it.in + frame * fbytes;
+            for (int t = 0; t < M; ++t) {
+                uint32_t w0 = 0x88888888u, w1 = 0x88888888u;
+#pragma unroll
+                for (int j = 0; j < kVec; ++j) {
+                    const int64_t c = col0 + j;
+                    if (c < N) {
+                        uint32_t b = it.layout == 0 ? fb[(int64_t)t * N + c] : fb[c * M + t];
+                        const uint32_t sh = 8u * (uint32_t)(j & 3);
+                        if (j < 4)
+                            w0 = (w0 & ~(0xFFu << sh)) | (b << sh);
+                        else
+                            w1 = (w1 & ~(0xFFu << sh)) | (b << sh);
+                    }
+                }
+                accum_row(make_uint2(w0, w1), lb, acc);
+                if ((t & (kFlushRows - 1)) == kFlushRows - 1)
+                    flush(acc, s1, s2);
+            }
+            flush(acc, s1, s2);
+        }
+        frame_epilogue<SERVED>(it, frame, fvalid, col0, lit, team_idx, parity, s1, s2, ts);
+        parity ^= 1;
+        frame += T;
+    }
+}
+
+}  // namespace sk
