@@ -1,0 +1,374 @@
+"""Benchmark of the spectral-kurtosis flagging path on B300.
+
+Workload (N=1 line): the full-array plain case -- 4 frequencies x N=2048
+inputs x M=256 samples x 1525 frames (3.2 GB of 4+4-bit samples, synthetic,
+seeded, generated on the device).  One step = one sk_flag call over all 6100
+frames (unpack, S1/S2, normalisation, SK~, threshold, mask).  Inputs are 25x
+the L2 size, so no flush is needed between steps.
+
+metric: Gsamples/s (1 sample = 1 byte); value = whole-job throughput with
+inputs resident in HBM; e2e = the same call on host (pinned) buffers with the
+host-to-device upload and the mask/SK download inside the timed region.
+
+Under torchrun each rank runs its own 4 frequencies (weak scaling, no
+collective in the data path); the timed region is bracketed by barriers and
+the max over ranks is taken.
+
+--impl reference times the oracle (plain C/numpy CPU code, test
+infrastructure) on a bounded sample of the same workload on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SK flagging throughput (Gsamples/s, 1 byte/sample)"
+UNIT = "Gsamples/s"
+N_IN, M_T, N_FREQ, N_FRAMES = 2048, 256, 4, 1525
+WORKLOAD = "full_array_plain: 4 freq x N=2048 x M=256 x 1525 frames, 4+4-bit, 3 sigma"
+KERNEL_SOURCES = ["paper_1808_10365_b300/csrc/sk_device.cuh",
+                  "paper_1808_10365_b300/csrc/sk_api.cu"]
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sk_fused_kernel_full_array.json")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6400.0, "fallback"
+
+
+def profiled_traffic(algorithmic_bytes_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel."""
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            d = json.load(f)
+    except Exception:  # noqa: BLE001
+        return None
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    per_unit = d["dram_bytes_per_launch"] / d["algorithmic_bytes_per_launch"]
+    return per_unit * algorithmic_bytes_per_launch
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:  # noqa: BLE001
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def physical_index(i: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if i < len(ids) and ids[i].isdigit():
+            return int(ids[i])
+    return i
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def workload_datasets(rank: int):
+    import synth
+
+    # each rank owns its own frequencies (weak scaling): distinct seeds per rank
+    return synth.full_array_config(n_freq=N_FREQ, n_frames=N_FRAMES, N=N_IN, M=M_T,
+                                   cfg=1 + 1000 * rank)
+
+
+def static_offset(datasets) -> float:
+    import paper_1808_10365_b300 as sk
+
+    sig = np.concatenate([d.sigma for d in datasets])
+    return float(np.mean([sk.sk_digitisation_offset(s) for s in sig]))
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The oracle as it stands on a bounded sample: 1 frequency x 256 frames of the workload."""
+    import oracle
+    import synth
+
+    ds = synth.full_array_config(n_freq=1, n_frames=N_FRAMES, N=N_IN, M=M_T)[0]
+    nf = 256
+    x = ds.generate_cpu(0, nf)
+    delta = float(np.mean(oracle.digitisation.delta_of_sigma(ds.sigma)))
+    oracle.flag(x[:8], M_T, N_IN, 3.0, delta)  # load the library, first touch
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.flag(x, M_T, N_IN, 3.0, delta)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    samples = reps * nf * M_T * N_IN
+    return {"value": samples / el / 1e9, "unit": UNIT, "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"{nf} frames of 1 frequency (N=2048, M=256; {nf * M_T * N_IN / 1e6:.0f} MB) "
+                      f"x {reps} repetitions, {el:.1f} s, full oracle path (sums, fp32 and fp64 "
+                      f"SK, thresholds, mask)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+
+    ds = synth.full_array_config(n_freq=1, n_frames=N_FRAMES, N=N_IN, M=M_T)[0]
+    nf = 64
+    x = ds.generate_cpu(0, nf)
+    delta = float(np.mean(oracle.digitisation.delta_of_sigma(ds.sigma)))
+    for _ in range(args.warmup):
+        oracle.flag(x, M_T, N_IN, 3.0, delta)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.flag(x, M_T, N_IN, 3.0, delta)
+    el = time.perf_counter() - t0
+    v = args.steps * nf * M_T * N_IN / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_frames_per_step": nf},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"each step: {nf} frames of 1 frequency of the workload "
+                                       f"({nf * M_T * N_IN / 1e6:.0f} MB)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1808_10365_b300 as sk
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    datasets = workload_datasets(rank)
+    F = sum(d.n_frames for d in datasets)
+    fb = M_T * N_IN
+    d_in = torch.empty(F * fb, dtype=torch.uint8, device=dev)
+    off = 0
+    for d in datasets:
+        d.generate_gpu(d_in[off:off + d.nbytes])
+        off += d.nbytes
+    delta = static_offset(datasets)
+    d_sk = torch.empty(F, dtype=torch.float32, device=dev)
+    d_mask = torch.empty(F, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N_IN, M_T, 3.0, delta, device=dev.index)
+    stream = torch.cuda.Stream(dev)
+    bytes_per_step = F * fb
+    alg_bytes = bytes_per_step + F * (4 + 1)
+
+    # ---- device-resident timing ----
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            sk.sk_flag(plan, d_in, F, d_sk, d_mask, stream)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(physical_index(dev.index)) as clk:
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            sk.sk_flag(plan, d_in, F, d_sk, d_mask, stream)
+            ev[k][1].record(stream)
+        t_all1.record(stream)
+        stream.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    clocks = clk.summary()
+    total_ms = t_all0.elapsed_time(t_all1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(total_ms, ws)
+    ms_step = total_ms / args.steps
+    value = ws * bytes_per_step * args.steps / (total_ms * 1e-3) / 1e9
+    mean_launch_s = statistics.mean(launch_ms) * 1e-3
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / mean_launch_s / 1e9
+    traffic = profiled_traffic(alg_bytes)
+
+    # ---- end to end through the host-buffer entry point ----
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    h_in = torch.empty(F * fb, dtype=torch.uint8).pin_memory()
+    h_in.copy_(d_in)
+    h_sk = torch.empty(F, dtype=torch.float32).pin_memory()
+    h_mask = torch.empty(F, dtype=torch.uint8).pin_memory()
+    sk.sk_flag_host(plan, h_in, F, h_sk, h_mask, stream)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sk.sk_flag_host(plan, h_in, F, h_sk, h_mask, stream)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e_value = ws * bytes_per_step * e2e_steps / e2e_s / 1e9
+    ok_e2e = bool((h_mask.numpy() == d_mask.cpu().numpy()).all())
+    sk.sk_plan_destroy(plan)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": F, "bytes_per_step": bytes_per_step,
+                   "l2": "inputs 3.2 GB per rank, 25x L2: no flush needed",
+                   "parallelism": f"frequency sharding x{ws}, no collective",
+                   "mean_offset": delta},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "kernel": "sk_fused_kernel<16,false>",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "mean_launch_ms": mean_launch_s * 1e3},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_per_step,
+                "d2h_bytes_per_step": F * 5, "steps": e2e_steps, "mask_matches_device": ok_e2e},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

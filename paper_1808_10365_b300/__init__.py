@@ -1,0 +1,314 @@
+"""B300 spectral-kurtosis RFI detector (Taylor et al., arXiv:1808.10365).
+
+Python binding of the C ABI in ``include/sk.h``.  Every function here has the
+name of the C entry point it calls and does argument marshalling only; all
+arithmetic runs in ``libsk.so`` (hand-written sm_103a CUDA).  Device buffers
+and streams come from PyTorch (tensors' ``data_ptr()``, ``torch.cuda.Stream``),
+or are given as raw integers.  There is no CPU fallback: if the library is
+missing, importing the binding's functions raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsk.so")
+
+SK_OK = 0
+SK_ERR_INVALID_ARG = 1
+SK_ERR_UNSUPPORTED = 2
+SK_ERR_OOM = 3
+SK_ERR_CUDA = 4
+SK_ERR_BUSY = 5
+SK_ERR_TIMEOUT = 6
+SK_ERR_NOT_READY = 7
+SK_ERR_CLOSED = 8
+SK_LAYOUT_TIME_MAJOR = 0
+SK_LAYOUT_INPUT_MAJOR = 1
+SK_RUNNING_OFFSET = 0x1
+SK_OFFSET_BUCKETS = 4096
+SK_MAX_INPUTS = 4096
+SK_MAX_TIME = 4096
+
+EXPORTED = [
+    "sk_plan_create", "sk_plan_destroy", "sk_plan_thresholds", "sk_plan_offset_table",
+    "sk_plan_set_tiles", "sk_plan_get_tiles", "sk_compute", "sk_flag", "sk_flag_host",
+    "sk_batch_create", "sk_batch_run", "sk_batch_destroy", "sk_server_create",
+    "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_ticket_wait",
+    "sk_stream_drain", "sk_stream_get_state", "sk_stream_set_state", "sk_stream_close",
+    "sk_server_stats", "sk_digitisation_offset", "sk_last_error",
+]
+
+
+class SkError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"sk status {status}: {message}")
+        self.status = status
+        self.message = message
+
+
+class sk_params_t(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int32), ("n_time", ctypes.c_int32),
+                ("layout", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("n_sigma", ctypes.c_double), ("mean_offset", ctypes.c_double),
+                ("offset_table", ctypes.c_void_p)]
+
+
+class sk_batch_item_t(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("d_in", ctypes.c_void_p),
+                ("n_frames", ctypes.c_int64), ("d_sk", ctypes.c_void_p),
+                ("d_mask", ctypes.c_void_p)]
+
+
+class sk_server_stats_t(ctypes.Structure):
+    _fields_ = [("frames_done", ctypes.c_int64), ("frames_flagged", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("latency_p50_us", ctypes.c_double), ("latency_p99_us", ctypes.c_double),
+                ("hbm_in_use", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def library():
+    """The loaded libsk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libsk.so not built ({LIB_PATH}); run paper_1808_10365_b300/build.py")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U8 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint8
+    st = ctypes.c_int
+    sig = {
+        "sk_plan_create": [ctypes.POINTER(sk_params_t), ctypes.c_int, ctypes.POINTER(P)],
+        "sk_plan_destroy": [P],
+        "sk_plan_thresholds": [P, P, P],
+        "sk_plan_offset_table": [P, P],
+        "sk_plan_set_tiles": [P, I32, I32],
+        "sk_plan_get_tiles": [P, ctypes.POINTER(I32), ctypes.POINTER(I32)],
+        "sk_compute": [P, P, I64, P, P, P, P, P, P],
+        "sk_flag": [P, P, I64, P, P, P],
+        "sk_flag_host": [P, P, I64, P, P, P],
+        "sk_batch_create": [ctypes.POINTER(sk_batch_item_t), I32, ctypes.c_int, ctypes.POINTER(P)],
+        "sk_batch_run": [P, P],
+        "sk_batch_destroy": [P],
+        "sk_server_create": [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(P)],
+        "sk_server_destroy": [P],
+        "sk_stream_open": [P, ctypes.POINTER(sk_params_t), I32, ctypes.POINTER(I32)],
+        "sk_stream_submit": [P, I32, P, I64, ctypes.POINTER(I64)],
+        "sk_ticket_wait": [P, I64, I64, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(U8)],
+        "sk_stream_drain": [P, I32, I64],
+        "sk_stream_get_state": [P, I32, P, ctypes.POINTER(ctypes.c_size_t)],
+        "sk_stream_set_state": [P, I32, P, ctypes.c_size_t],
+        "sk_stream_close": [P, I32],
+        "sk_server_stats": [P, ctypes.POINTER(sk_server_stats_t)],
+        "sk_digitisation_offset": [ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = st
+    L.sk_last_error.argtypes = []
+    L.sk_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != SK_OK:
+        raise SkError(status, library().sk_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array, int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _params(n_inputs, n_time, n_sigma, mean_offset, layout, flags, offset_table):
+    p = sk_params_t()
+    p.n_inputs = int(n_inputs)
+    p.n_time = int(n_time)
+    p.layout = int(layout)
+    p.flags = int(flags)
+    p.n_sigma = float(n_sigma)
+    p.mean_offset = float(mean_offset)
+    keep = None
+    if offset_table is not None:
+        keep = np.ascontiguousarray(offset_table, dtype=np.int64)
+        if keep.size != SK_OFFSET_BUCKETS:
+            raise ValueError("offset_table needs SK_OFFSET_BUCKETS entries")
+        p.offset_table = keep.ctypes.data
+    return p, keep
+
+
+# ------------------------------------------------------------------ plans
+
+def sk_plan_create(n_inputs, n_time, n_sigma=3.0, mean_offset=0.0, layout=0, flags=0,
+                   offset_table=None, device=0) -> int:
+    p, keep = _params(n_inputs, n_time, n_sigma, mean_offset, layout, flags, offset_table)
+    h = ctypes.c_void_p()
+    _check(library().sk_plan_create(ctypes.byref(p), int(device), ctypes.byref(h)))
+    return h.value
+
+
+def sk_plan_destroy(plan):
+    _check(library().sk_plan_destroy(plan))
+
+
+def sk_plan_thresholds(plan, n_inputs):
+    lo = np.zeros(n_inputs + 1, dtype=np.int64)
+    hi = np.zeros(n_inputs + 1, dtype=np.int64)
+    _check(library().sk_plan_thresholds(plan, lo.ctypes.data, hi.ctypes.data))
+    return lo, hi
+
+
+def sk_plan_offset_table(plan):
+    e = np.zeros(SK_OFFSET_BUCKETS, dtype=np.int64)
+    _check(library().sk_plan_offset_table(plan, e.ctypes.data))
+    return e
+
+
+def sk_plan_set_tiles(plan, rows_per_batch, grid_ctas=0):
+    _check(library().sk_plan_set_tiles(plan, int(rows_per_batch), int(grid_ctas)))
+
+
+def sk_plan_get_tiles(plan):
+    r = ctypes.c_int32()
+    g = ctypes.c_int32()
+    _check(library().sk_plan_get_tiles(plan, ctypes.byref(r), ctypes.byref(g)))
+    return r.value, g.value
+
+
+def sk_compute(plan, d_in, n_frames, s1=None, s2=None, q=None, sk=None, neff=None, stream=None):
+    _check(library().sk_compute(plan, _ptr(d_in), int(n_frames), _ptr(s1), _ptr(s2), _ptr(q),
+                                _ptr(sk), _ptr(neff), _stream(stream)))
+
+
+def sk_flag(plan, d_in, n_frames, sk, mask, stream=None):
+    _check(library().sk_flag(plan, _ptr(d_in), int(n_frames), _ptr(sk), _ptr(mask),
+                             _stream(stream)))
+
+
+def sk_flag_host(plan, h_in, n_frames, h_sk, h_mask, stream=None):
+    _check(library().sk_flag_host(plan, _ptr(h_in), int(n_frames), _ptr(h_sk), _ptr(h_mask),
+                                  _stream(stream)))
+
+
+# ---------------------------------------------------------------- batched
+
+def sk_batch_create(items, device=0) -> int:
+    """items: sequence of (plan, d_in, n_frames, d_sk, d_mask)."""
+    arr = (sk_batch_item_t * len(items))()
+    for k, (plan, d_in, n, sk, mask) in enumerate(items):
+        arr[k].plan = plan
+        arr[k].d_in = _ptr(d_in)
+        arr[k].n_frames = int(n)
+        arr[k].d_sk = _ptr(sk)
+        arr[k].d_mask = _ptr(mask)
+    h = ctypes.c_void_p()
+    _check(library().sk_batch_create(arr, len(items), int(device), ctypes.byref(h)))
+    return h.value
+
+
+def sk_batch_run(batch, stream=None):
+    _check(library().sk_batch_run(batch, _stream(stream)))
+
+
+def sk_batch_destroy(batch):
+    _check(library().sk_batch_destroy(batch))
+
+
+# ---------------------------------------------------------------- serving
+
+def sk_server_create(device=0, hbm_budget_bytes=1 << 34) -> int:
+    h = ctypes.c_void_p()
+    _check(library().sk_server_create(int(device), int(hbm_budget_bytes), ctypes.byref(h)))
+    return h.value
+
+
+def sk_server_destroy(server):
+    _check(library().sk_server_destroy(server))
+
+
+def sk_stream_open(server, n_inputs, n_time, ring_frames=16, n_sigma=3.0, mean_offset=0.0,
+                   flags=0, offset_table=None) -> int:
+    p, keep = _params(n_inputs, n_time, n_sigma, mean_offset, 0, flags, offset_table)
+    sid = ctypes.c_int32()
+    _check(library().sk_stream_open(server, ctypes.byref(p), int(ring_frames), ctypes.byref(sid)))
+    return sid.value
+
+
+def sk_stream_submit(server, stream_id, frame, frame_index=0) -> int:
+    """frame: host bytes (numpy uint8 or CPU tensor) of one frame; returns the ticket."""
+    t = ctypes.c_int64()
+    _check(library().sk_stream_submit(server, int(stream_id), _ptr(frame), int(frame_index),
+                                      ctypes.byref(t)))
+    return t.value
+
+
+def sk_ticket_wait(server, ticket, timeout_us=-1):
+    sk = ctypes.c_float()
+    m = ctypes.c_uint8()
+    _check(library().sk_ticket_wait(server, int(ticket), int(timeout_us), ctypes.byref(sk),
+                                    ctypes.byref(m)))
+    return sk.value, m.value
+
+
+def sk_stream_drain(server, stream_id, timeout_us=-1):
+    _check(library().sk_stream_drain(server, int(stream_id), int(timeout_us)))
+
+
+def sk_stream_get_state(server, stream_id) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(library().sk_stream_get_state(server, int(stream_id), None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(library().sk_stream_get_state(server, int(stream_id), buf, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def sk_stream_set_state(server, stream_id, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(library().sk_stream_set_state(server, int(stream_id), buf, len(state)))
+
+
+def sk_stream_close(server, stream_id):
+    _check(library().sk_stream_close(server, int(stream_id)))
+
+
+def sk_server_stats(server) -> dict:
+    s = sk_server_stats_t()
+    _check(library().sk_server_stats(server, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in sk_server_stats_t._fields_}
+
+
+# ------------------------------------------------------------------- misc
+
+def sk_digitisation_offset(sigma) -> float:
+    d = ctypes.c_double()
+    _check(library().sk_digitisation_offset(float(sigma), ctypes.byref(d)))
+    return d.value
+
+
+def sk_last_error() -> str:
+    return library().sk_last_error().decode(errors="replace")

@@ -83,10 +83,12 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
     return v;
 }
 
+// volatile: the load must never be hoisted or speculated past the bounds test
+// that guards it (callers only issue it for rows inside the frame).
 __device__ __forceinline__ uint2 ldg_stream(const uint8_t *p)
 {
     uint2 v;
-    asm("ld.global.nc.L1::no_allocate.L2::256B.v2.u32 {%0, %1}, [%2];"
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v2.u32 {%0, %1}, [%2];"
         : "=r"(v.x), "=r"(v.y)
         : "l"(p));
     return v;

@@ -1,0 +1,68 @@
+"""The C ABI without a GPU: the library loads, exports every symbol that
+include/sk.h declares, and its host-only pieces behave."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1808_10365_b300 as sk
+from oracle import digitisation as dg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sk_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = sk.library()
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(sk.EXPORTED) == names
+
+
+def test_digitisation_offset_matches_oracle_model():
+    for s in (0.7, 1.0, 1.52, 2.0, 2.5, 3.0, 3.5, 10.0):
+        assert abs(sk.sk_digitisation_offset(s) - float(dg.delta_of_sigma(s))) < 1e-12
+    with pytest.raises(sk.SkError) as e:
+        sk.sk_digitisation_offset(-1.0)
+    assert e.value.status == sk.SK_ERR_INVALID_ARG
+
+
+def test_argument_errors_are_status_codes():
+    lib = sk.library()
+    out = ctypes.c_void_p(123)
+    assert lib.sk_plan_create(None, 0, ctypes.byref(out)) == sk.SK_ERR_INVALID_ARG
+    assert out.value is None
+    assert "NULL" in sk.sk_last_error()
+    p, _ = sk._params(0, 256, 3.0, 0.0, 0, 0, None)
+    assert lib.sk_plan_create(ctypes.byref(p), 0, ctypes.byref(out)) == sk.SK_ERR_INVALID_ARG
+    p, _ = sk._params(256, 1, 3.0, 0.0, 0, 0, None)
+    assert lib.sk_plan_create(ctypes.byref(p), 0, ctypes.byref(out)) == sk.SK_ERR_INVALID_ARG
+    p, _ = sk._params(256, 256, -1.0, 0.0, 0, 0, None)
+    assert lib.sk_plan_create(ctypes.byref(p), 0, ctypes.byref(out)) == sk.SK_ERR_INVALID_ARG
+    assert lib.sk_compute(None, None, 1, None, None, None, None, None, None) == \
+        sk.SK_ERR_INVALID_ARG
+    assert lib.sk_flag(None, None, 0, None, None, None) == sk.SK_ERR_INVALID_ARG
+    assert lib.sk_batch_create(None, 0, 0, ctypes.byref(out)) == sk.SK_ERR_INVALID_ARG
+    assert lib.sk_ticket_wait(None, 1, 0, None, None) == sk.SK_ERR_INVALID_ARG
+    assert lib.sk_plan_destroy(None) == sk.SK_OK
+    assert lib.sk_server_destroy(None) == sk.SK_OK
+
+
+def test_no_device_is_an_error_not_a_crash():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(sk.SkError) as e:
+        sk.sk_plan_create(256, 256)
+    assert e.value.status in (sk.SK_ERR_CUDA, sk.SK_ERR_INVALID_ARG)

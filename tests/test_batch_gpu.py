@@ -1,0 +1,76 @@
+"""Batched persistent launch (many frequencies of different N and M in one
+graph-captured launch) against the oracle and the plain launch."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1808_10365_b300 as sk  # noqa: E402
+import synth  # noqa: E402
+from oracle import digitisation as dg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch.device("cuda:0")
+
+
+def test_mixed_batch_matches_oracle_and_replays():
+    dev = _dev()
+    shapes = [(2048, 256, 23), (256, 128, 70), (2048, 1024, 5), (256, 1024, 31),
+              (100, 48, 9), (512, 256, 1), (2048, 128, 0), (256, 256, 64)]
+    items, plans, bufs, wants = [], [], [], []
+    for k, (N, M, F) in enumerate(shapes):
+        ds = synth.Dataset(n_frames=max(F, 1), M=M, N=N, seed=synth.sub_seed(2, k),
+                           rfi=synth.rfi_plan(synth.sub_seed(2, k), max(F, 1), 0.2, 0.1))
+        x = ds.generate_cpu()[:F]
+        delta = float(np.mean(dg.delta_of_sigma(ds.sigma)))
+        wants.append(oracle.flag(x, M, N, 3.0, delta) if F else None)
+        plan = sk.sk_plan_create(N, M, 3.0, delta)
+        d_in = torch.from_numpy(x.reshape(-1)).to(dev) if F else torch.empty(16, dtype=torch.uint8,
+                                                                             device=dev)
+        skv = torch.full((max(F, 1),), -1.0, dtype=torch.float32, device=dev)
+        mask = torch.full((max(F, 1),), 9, dtype=torch.uint8, device=dev)
+        plans.append(plan)
+        bufs.append((d_in, skv, mask))
+        items.append((plan, d_in, F, skv, mask))
+    batch = sk.sk_batch_create(items)
+    try:
+        for rep in range(2):
+            for _, skv, mask in bufs:
+                skv.fill_(-1.0)
+                mask.fill_(9)
+            sk.sk_batch_run(batch)
+            torch.cuda.synchronize()
+            for (N, M, F), w, (_, skv, mask) in zip(shapes, wants, bufs):
+                if F == 0:
+                    assert mask[0].item() == 9
+                    continue
+                assert np.array_equal(mask.cpu().numpy()[:F], w["mask"])
+                assert np.array_equal(skv.cpu().numpy()[:F].view(np.uint32),
+                                      w["sk"].view(np.uint32))
+    finally:
+        sk.sk_batch_destroy(batch)
+        for p in plans:
+            sk.sk_plan_destroy(p)
+
+
+def test_batch_rejects_bad_items():
+    dev = _dev()
+    plan = sk.sk_plan_create(256, 256)
+    buf = torch.zeros(256 * 256 + 16, dtype=torch.uint8, device=dev)
+    mask = torch.zeros(1, dtype=torch.uint8, device=dev)
+    try:
+        with pytest.raises(sk.SkError):
+            sk.sk_batch_create([(plan, buf.data_ptr() + 8, 1, None, mask)])
+        with pytest.raises(sk.SkError):
+            sk.sk_batch_create([(plan, buf, 1, None, None)])
+        with pytest.raises(sk.SkError):
+            sk.sk_batch_create([])
+    finally:
+        sk.sk_plan_destroy(plan)

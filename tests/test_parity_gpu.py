@@ -1,0 +1,258 @@
+"""Parity of the CUDA path with the oracle, through the C ABI.
+
+Bar: S1, S2, Q, N_eff and masks bit-exact; SK fp32 bit-identical to the
+oracle's kernel-precision statement and within 1e-6 relative of the fp64
+oracle (Eq. final).  Inputs are seeded and synthetic (the `synth` generator,
+or uniform random bytes that include nibble 0 = -8).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1808_10365_b300 as sk  # noqa: E402
+import synth  # noqa: E402
+from oracle import digitisation as dg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+SK_REL = 1e-6
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch.device("cuda:0")
+
+
+def run_compute(x, M, N, n_sigma=3.0, delta=0.0, layout=0, rows=None, grid=0):
+    """sk_compute + sk_flag on bytes x [F, M*N]; numpy outputs."""
+    dev = _dev()
+    x = np.ascontiguousarray(x, dtype=np.uint8).reshape(-1, M * N)
+    F = x.shape[0]
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev) if F else torch.empty(16, dtype=torch.uint8,
+                                                                          device=dev)
+    s1 = torch.full((max(F, 1), N), -1, dtype=torch.int32, device=dev)
+    s2 = torch.full_like(s1, -1)
+    q = torch.full((max(F, 1),), -1, dtype=torch.int64, device=dev)
+    skv = torch.full((max(F, 1),), -1.0, dtype=torch.float32, device=dev)
+    ne = torch.full((max(F, 1),), -1, dtype=torch.int32, device=dev)
+    mask = torch.full((max(F, 1),), 7, dtype=torch.uint8, device=dev)
+    sk2 = torch.full_like(skv, -1.0)
+    plan = sk.sk_plan_create(N, M, n_sigma, delta, layout=layout)
+    try:
+        if rows is not None:
+            sk.sk_plan_set_tiles(plan, rows, grid)
+        sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
+        sk.sk_flag(plan, d_in, F, sk2, mask)
+        torch.cuda.synchronize()
+        t_lo, t_hi = sk.sk_plan_thresholds(plan, N)
+    finally:
+        sk.sk_plan_destroy(plan)
+    return dict(S1=s1.cpu().numpy()[:F], S2=s2.cpu().numpy()[:F], Q=q.cpu().numpy()[:F],
+                neff=ne.cpu().numpy()[:F], sk=skv.cpu().numpy()[:F], sk_flag=sk2.cpu().numpy()[:F],
+                mask=mask.cpu().numpy()[:F], t_lo=t_lo, t_hi=t_hi)
+
+
+def assert_parity(got, want, check_sums=True):
+    if check_sums:
+        assert np.array_equal(got["S1"], want["S1"])
+        assert np.array_equal(got["S2"], want["S2"])
+    assert np.array_equal(got["Q"], want["Q"])
+    assert np.array_equal(got["neff"], want["neff"])
+    assert np.array_equal(got["sk"].view(np.uint32), want["sk"].view(np.uint32))
+    assert np.array_equal(got["sk_flag"].view(np.uint32), want["sk"].view(np.uint32))
+    assert np.array_equal(got["mask"], want["mask"])
+    ok = np.isfinite(want["sk64"])
+    rel = np.abs(got["sk"][ok] - want["sk64"][ok]) / np.maximum(np.abs(want["sk64"][ok]), 1e-30)
+    near0 = np.abs(want["sk64"][ok]) < 1e-6
+    assert np.all((rel <= SK_REL) | near0)
+    assert np.all(np.isnan(got["sk"][~ok]))
+
+
+def test_pathfinder_workload_bit_exact():
+    """N=256, M=256, 64 frames, CW frames 10-19, 50 % pulse frames 40-44, 3 sigma."""
+    ds = synth.pathfinder_config()
+    x = ds.generate_cpu()
+    delta = float(np.mean(dg.delta_of_sigma(ds.sigma)))
+    want = oracle.flag(x, 256, 256, 3.0, delta)
+    got = run_compute(x, 256, 256, 3.0, delta)
+    assert np.array_equal(got["t_lo"][1:], want["t_lo"][1:])
+    assert np.array_equal(got["t_hi"][1:], want["t_hi"][1:])
+    assert_parity(got, want)
+    assert got["mask"][10:20].all()
+
+
+def test_pathfinder_25pct_pulse_flags_high():
+    ds = synth.pathfinder_config(duty=0.25)
+    x = ds.generate_cpu()
+    delta = float(np.mean(dg.delta_of_sigma(ds.sigma)))
+    want = oracle.flag(x, 256, 256, 3.0, delta)
+    got = run_compute(x, 256, 256, 3.0, delta)
+    assert_parity(got, want)
+    assert got["mask"][40:45].all() and (got["sk"][40:45] > 1.0).all()
+
+
+@pytest.mark.parametrize("N,M,F", [
+    (8, 16, 5), (16, 32, 33), (24, 48, 17), (256, 128, 40), (1000, 64, 9),
+    (2048, 256, 7), (4096, 32, 5), (2048, 1024, 3), (512, 4096, 2), (64, 16, 70)])
+def test_fast_path_shapes_random_bytes(N, M, F):
+    rng = np.random.default_rng(N * 7 + M + F)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    want = oracle.flag(x, M, N, 2.5, 0.0)
+    for rows in (8, 16):
+        got = run_compute(x, M, N, 2.5, 0.0, rows=rows)
+        assert_parity(got, want)
+
+
+@pytest.mark.parametrize("N,M,F,layout", [
+    (1, 2, 3, 0), (3, 17, 4, 0), (100, 100, 6, 0), (257, 33, 5, 0), (4095, 16, 2, 0),
+    (7, 64, 9, 0), (1, 2, 3, 1), (100, 100, 6, 1), (256, 256, 4, 1), (37, 5, 11, 1)])
+def test_general_path_ragged_shapes(N, M, F, layout):
+    rng = np.random.default_rng(N * 13 + M * 3 + F + layout)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    want = oracle.flag(x, M, N, 3.0, 0.1, layout=layout)
+    got = run_compute(x, M, N, 3.0, 0.1, layout=layout)
+    assert_parity(got, want)
+
+
+def test_empty_single_and_dead_frames():
+    M, N = 64, 128
+    rng = np.random.default_rng(3)
+    x = rng.integers(0, 256, size=(5, M, N), dtype=np.uint8)
+    x[1, :, 7] = 0x88        # one dead input
+    x[2] = 0x88              # no input has power
+    x[3, :, :] = 0x00        # every sample (-8, -8): constant modulus, SK = 0
+    x = x.reshape(5, -1)
+    want = oracle.flag(x, M, N)
+    got = run_compute(x, M, N)
+    assert_parity(got, want)
+    assert got["neff"][2] == 0 and got["mask"][2] == 1 and np.isnan(got["sk"][2])
+    assert got["neff"][1] == N - 1 and got["Q"][3] == 0
+    got1 = run_compute(x[:1], M, N)
+    assert np.array_equal(got1["Q"], want["Q"][:1])
+    got0 = run_compute(x[:0], M, N)
+    assert got0["Q"].size == 0
+
+
+def test_tiles_and_grid_do_not_change_results():
+    rng = np.random.default_rng(17)
+    M, N, F = 256, 2048, 37
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    ref = run_compute(x, M, N)
+    for rows, grid in ((8, 0), (16, 1), (8, 5), (16, 300)):
+        got = run_compute(x, M, N, rows=rows, grid=grid)
+        for k in ("S1", "S2", "Q", "neff", "mask"):
+            assert np.array_equal(got[k], ref[k])
+
+
+def test_misaligned_and_bad_arguments_rejected():
+    dev = _dev()
+    buf = torch.zeros(4096 + 16, dtype=torch.uint8, device=dev)
+    mask = torch.zeros(4, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(16, 16)
+    try:
+        with pytest.raises(sk.SkError) as e:
+            sk.sk_flag(plan, buf.data_ptr() + 1, 1, None, mask)
+        assert e.value.status == sk.SK_ERR_INVALID_ARG
+        with pytest.raises(sk.SkError):
+            sk.sk_flag(plan, buf, -1, None, mask)
+        with pytest.raises(sk.SkError):
+            sk.sk_flag(plan, buf, 1, None, None)
+        with pytest.raises(sk.SkError):
+            sk.sk_plan_set_tiles(plan, 12, 0)
+    finally:
+        sk.sk_plan_destroy(plan)
+
+
+def test_gpu_generator_matches_cpu_generator():
+    dev = _dev()
+    ds = synth.full_array_config(n_freq=1, n_frames=40, N=512, M=128)[0]
+    cpu = ds.generate_cpu()
+    d = torch.empty(ds.nbytes, dtype=torch.uint8, device=dev)
+    ds.generate_gpu(d)
+    assert np.array_equal(d.cpu().numpy().reshape(cpu.shape), cpu)
+    part = torch.empty(5 * ds.frame_bytes, dtype=torch.uint8, device=dev)
+    ds.generate_gpu(part, frame0=11, n=5)
+    assert np.array_equal(part.cpu().numpy().reshape(5, -1), cpu[11:16])
+
+
+def test_flag_host_matches_device_path():
+    dev = _dev()
+    ds = synth.full_array_config(n_freq=1, n_frames=300, N=512, M=256)[0]
+    x = ds.generate_cpu()
+    delta = float(np.mean(dg.delta_of_sigma(ds.sigma)))
+    want = oracle.flag(x, 256, 512, 3.0, delta)
+    h_in = torch.from_numpy(x.reshape(-1)).pin_memory()
+    h_sk = torch.zeros(300, dtype=torch.float32).pin_memory()
+    h_mask = torch.zeros(300, dtype=torch.uint8).pin_memory()
+    plan = sk.sk_plan_create(512, 256, 3.0, delta)
+    try:
+        sk.sk_flag_host(plan, h_in, 300, h_sk, h_mask)
+    finally:
+        sk.sk_plan_destroy(plan)
+    assert np.array_equal(h_mask.numpy(), want["mask"])
+    assert np.array_equal(h_sk.numpy().view(np.uint32), want["sk"].view(np.uint32))
+
+
+def _sampled_full_size(datasets, sample_frames, n_sigma=3.0):
+    """Run sk_compute on a full multi-frequency workload generated on the GPU (the
+    launch shape the benchmark times) and compare sampled frames with the oracle."""
+    dev = _dev()
+    ds0 = datasets[0]
+    M, N = ds0.M, ds0.N
+    F = sum(d.n_frames for d in datasets)
+    d_in = torch.empty(F * M * N, dtype=torch.uint8, device=dev)
+    off = 0
+    for d in datasets:
+        d.generate_gpu(d_in[off:off + d.nbytes])
+        off += d.nbytes
+    sigma = np.concatenate([d.sigma for d in datasets])
+    delta = float(np.mean(dg.delta_of_sigma(sigma)))
+    q = torch.empty(F, dtype=torch.int64, device=dev)
+    skv = torch.empty(F, dtype=torch.float32, device=dev)
+    ne = torch.empty(F, dtype=torch.int32, device=dev)
+    mask = torch.empty(F, dtype=torch.uint8, device=dev)
+    sk2 = torch.empty(F, dtype=torch.float32, device=dev)
+    plan = sk.sk_plan_create(N, M, n_sigma, delta)
+    try:
+        sk.sk_compute(plan, d_in, F, None, None, q, skv, ne)
+        sk.sk_flag(plan, d_in, F, sk2, mask)
+        torch.cuda.synchronize()
+    finally:
+        sk.sk_plan_destroy(plan)
+    q, skv, ne, mask = (t.cpu().numpy() for t in (q, skv, ne, mask))
+    starts = np.cumsum([0] + [d.n_frames for d in datasets])
+    checked = 0
+    for g in sample_frames:
+        k = int(np.searchsorted(starts, g, side="right") - 1)
+        f = int(g - starts[k])
+        x = datasets[k].generate_cpu(frame0=f, n=1)
+        dev_bytes = d_in[g * M * N:(g + 1) * M * N].cpu().numpy()
+        assert np.array_equal(dev_bytes, x[0])
+        w = oracle.flag(x, M, N, n_sigma, delta)
+        assert q[g] == w["Q"][0] and ne[g] == w["neff"][0] and mask[g] == w["mask"][0]
+        assert skv[g].view(np.uint32) == w["sk"][0].view(np.uint32)
+        assert abs(skv[g] - w["sk64"][0]) <= SK_REL * abs(w["sk64"][0])
+        checked += 1
+    return dict(q=q, sk=skv, sk_flag=sk2.cpu().numpy(), mask=mask, F=F, checked=checked)
+
+
+def test_full_array_workload_sampled():
+    """4 frequencies x N=2048, M=256, 1525 frames (3.2 GB), sampled frames vs the oracle."""
+    datasets = synth.full_array_config()
+    rng = np.random.default_rng(5)
+    F = 4 * 1525
+    # frames with RFI, frequency and CTA-range boundaries, and random ones
+    rfi = [1525 * k + r.frame for k, d in enumerate(datasets) for r in d.rfi[:4]]
+    sample = sorted(set([0, 1, 1524, 1525, 3049, 3050, F - 1] + rfi +
+                        list(rng.integers(0, F, size=24))))
+    r = _sampled_full_size(datasets, sample)
+    assert np.array_equal(r["sk"].view(np.uint32), r["sk_flag"].view(np.uint32))
+    # the CW frames the sample contains are flagged; clean frames mostly are not
+    cw = [1525 * k + x.frame for k, d in enumerate(datasets) for x in d.rfi if x.kind == "cw"
+          and x.amp > 2.5]
+    assert r["mask"][cw].all()
+    assert r["mask"].mean() < 0.06

@@ -1,0 +1,241 @@
+"""The continuous-batching server: results equal the oracle alone and in the
+mix, the running per-input power state follows the oracle's served path,
+checkpoint/resume continues identically, admission refuses what does not fit,
+and a full ring answers BUSY.  Failures are made on the host."""
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1808_10365_b300 as sk  # noqa: E402
+import synth  # noqa: E402
+from oracle import digitisation as dg  # noqa: E402
+from oracle import served  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _stream_data(k, N, M, T):
+    s = synth.sub_seed(3, k)
+    ds = synth.Dataset(n_frames=T, M=M, N=N, seed=s, rfi=synth.rfi_plan(s, T, 0.1, 0.05))
+    return ds, ds.generate_cpu()
+
+
+def _run_streams(server, specs, datas, interleave=True, ring=8, stateful=True, tables=None):
+    """Submit every stream's frames (interleaved across streams, or one stream
+    after another) and collect (sk, mask) per stream in frame order."""
+    ids = []
+    for (N, M), (ds, x), e in zip(specs, datas, tables):
+        ids.append(sk.sk_stream_open(server, N, M, ring_frames=ring, n_sigma=3.0,
+                                     flags=sk.SK_RUNNING_OFFSET if stateful else 0,
+                                     offset_table=e))
+    out = [([], []) for _ in specs]
+    order = []
+    T = max(x.shape[0] for _, x in datas)
+    if interleave:
+        for f in range(T):
+            for j, (_, x) in enumerate(datas):
+                if f < x.shape[0]:
+                    order.append((j, f))
+    else:
+        for j, (_, x) in enumerate(datas):
+            order += [(j, f) for f in range(x.shape[0])]
+    pending = [[] for _ in specs]
+    for j, f in order:
+        x = datas[j][1]
+        while True:
+            try:
+                t = sk.sk_stream_submit(server, ids[j], x[f], f)
+                break
+            except sk.SkError as e:
+                assert e.status == sk.SK_ERR_BUSY
+                skv, m = sk.sk_ticket_wait(server, pending[j].pop(0))
+                out[j][0].append(skv)
+                out[j][1].append(m)
+        pending[j].append(t)
+    for j in range(len(specs)):
+        for t in pending[j]:
+            skv, m = sk.sk_ticket_wait(server, t)
+            out[j][0].append(skv)
+            out[j][1].append(m)
+    for i in ids:
+        sk.sk_stream_close(server, i)
+    return [(np.array(a, dtype=np.float32), np.array(b, dtype=np.uint8)) for a, b in out]
+
+
+def test_served_results_match_oracle_alone_and_in_mix():
+    _need_gpu()
+    specs = [(2048, 256), (256, 256), (256, 256), (2048, 256), (512, 128)]
+    T = 30
+    datas = [_stream_data(k, N, M, T) for k, (N, M) in enumerate(specs)]
+    tables = [dg.offset_table(M) for (_, M) in specs]
+    wants = [served.served_flags(x, M, N, e) for (N, M), (_, x), e in zip(specs, datas, tables)]
+    server = sk.sk_server_create(0, 8 << 30)
+    try:
+        mix = _run_streams(server, specs, datas, True, tables=tables)
+        alone = [_run_streams(server, [s], [d], False, tables=[e])[0]
+                 for s, d, e in zip(specs, datas, tables)]
+        st = sk.sk_server_stats(server)
+    finally:
+        sk.sk_server_destroy(server)
+    for w, m, a in zip(wants, mix, alone):
+        assert np.array_equal(m[1], w["mask"])
+        assert np.array_equal(m[0].view(np.uint32), w["sk"].view(np.uint32))
+        assert np.array_equal(a[0].view(np.uint32), m[0].view(np.uint32))
+        assert np.array_equal(a[1], m[1])
+    assert st["frames_done"] == 2 * len(specs) * T
+    assert st["latency_p99_us"] >= st["latency_p50_us"] > 0
+
+
+def test_stateless_stream_matches_plain_flag():
+    _need_gpu()
+    N, M, T = 256, 256, 20
+    ds, x = _stream_data(9, N, M, T)
+    delta = float(np.mean(dg.delta_of_sigma(ds.sigma)))
+    want = oracle.flag(x, M, N, 3.0, delta)
+    server = sk.sk_server_create(0, 1 << 30)
+    try:
+        sid = sk.sk_stream_open(server, N, M, ring_frames=4, n_sigma=3.0, mean_offset=delta)
+        tickets = []
+        got = []
+        for f in range(T):
+            while True:
+                try:
+                    tickets.append(sk.sk_stream_submit(server, sid, x[f], f))
+                    break
+                except sk.SkError as e:
+                    assert e.status == sk.SK_ERR_BUSY
+                    got.append(sk.sk_ticket_wait(server, tickets.pop(0)))
+        got += [sk.sk_ticket_wait(server, t) for t in tickets]
+        sk.sk_stream_close(server, sid)
+    finally:
+        sk.sk_server_destroy(server)
+    assert np.array_equal(np.array([m for _, m in got], dtype=np.uint8), want["mask"])
+    assert np.array_equal(np.array([s for s, _ in got], dtype=np.float32).view(np.uint32),
+                          want["sk"].view(np.uint32))
+
+
+def test_checkpoint_resume_continues_identically():
+    _need_gpu()
+    N, M, T = 512, 256, 24
+    ds, x = _stream_data(11, N, M, T)
+    e = dg.offset_table(M)
+    want = served.served_flags(x, M, N, e)
+    server = sk.sk_server_create(0, 1 << 30)
+    try:
+        a = sk.sk_stream_open(server, N, M, ring_frames=4, flags=sk.SK_RUNNING_OFFSET,
+                              offset_table=e)
+        first = []
+        for f in range(10):
+            t = sk.sk_stream_submit(server, a, x[f], f)
+            first.append(sk.sk_ticket_wait(server, t))
+        sk.sk_stream_drain(server, a)
+        state = sk.sk_stream_get_state(server, a)
+        sk.sk_stream_close(server, a)
+        b = sk.sk_stream_open(server, N, M, ring_frames=4, flags=sk.SK_RUNNING_OFFSET,
+                              offset_table=e)
+        sk.sk_stream_set_state(server, b, state)
+        second = []
+        for f in range(10, T):
+            t = sk.sk_stream_submit(server, b, x[f], f)
+            second.append(sk.sk_ticket_wait(server, t))
+        sk.sk_stream_drain(server, b)
+        final = sk.sk_stream_get_state(server, b)
+        sk.sk_stream_close(server, b)
+    finally:
+        sk.sk_server_destroy(server)
+    got = np.array([m for _, m in first + second], dtype=np.uint8)
+    assert np.array_equal(got, want["mask"])
+    P = np.frombuffer(final, dtype=np.uint32)[2:]
+    assert np.array_equal(P.astype(np.int64), want["P"])
+
+
+def test_admission_budget_and_ring_full():
+    _need_gpu()
+    N, M = 2048, 256
+    fb = N * M
+    server = sk.sk_server_create(0, 10 * fb)
+    try:
+        a = sk.sk_stream_open(server, N, M, ring_frames=4)
+        with pytest.raises(sk.SkError) as e:
+            sk.sk_stream_open(server, N, M, ring_frames=8)
+        assert e.value.status == sk.SK_ERR_BUSY
+        frame = np.full(fb, 0x99, dtype=np.uint8)
+        # fill the ring faster than it drains, host-side: BUSY must come back
+        busy = 0
+        tickets = []
+        for f in range(200):
+            try:
+                tickets.append(sk.sk_stream_submit(server, a, frame, f))
+            except sk.SkError as err:
+                assert err.status == sk.SK_ERR_BUSY
+                busy += 1
+                sk.sk_ticket_wait(server, tickets.pop(0))
+        for t in tickets:
+            sk.sk_ticket_wait(server, t)
+        with pytest.raises(sk.SkError) as e:
+            sk.sk_ticket_wait(server, 10 ** 9, 0)
+        assert e.value.status == sk.SK_ERR_INVALID_ARG
+        sk.sk_stream_close(server, a)
+        # memory is returned: a second stream fits now
+        b = sk.sk_stream_open(server, N, M, ring_frames=8)
+        sk.sk_stream_close(server, b)
+        st = sk.sk_server_stats(server)
+        assert st["rejected"] >= 1 + busy
+    finally:
+        sk.sk_server_destroy(server)
+
+
+def test_ticket_timeout_and_concurrent_submitters():
+    _need_gpu()
+    N, M, T = 256, 256, 40
+    server = sk.sk_server_create(0, 1 << 30)
+    errors = []
+    try:
+        datas = [_stream_data(20 + k, N, M, T) for k in range(4)]
+        wants = [oracle.flag(x, M, N, 3.0, 0.0)["mask"] for _, x in datas]
+        results = [None] * 4
+
+        def worker(k):
+            try:
+                sid = sk.sk_stream_open(server, N, M, ring_frames=6)
+                out = []
+                for f in range(T):
+                    t = sk.sk_stream_submit(server, sid, datas[k][1][f], f)
+                    out.append(sk.sk_ticket_wait(server, t, 10_000_000)[1])
+                sk.sk_stream_close(server, sid)
+                results[k] = np.array(out, dtype=np.uint8)
+            except Exception as ex:  # noqa: BLE001
+                errors.append(ex)
+
+        th = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join(120)
+        assert not errors, errors
+        for r, w in zip(results, wants):
+            assert np.array_equal(r, w)
+        # a wait with a zero limit on a ticket whose frame cannot have run yet times out
+        sid = sk.sk_stream_open(server, N, M, ring_frames=2)
+        t0 = time.time()
+        t = sk.sk_stream_submit(server, sid, datas[0][1][0], 0)
+        try:
+            sk.sk_ticket_wait(server, t, 0)
+        except sk.SkError as e:
+            assert e.status == sk.SK_ERR_TIMEOUT
+        sk.sk_ticket_wait(server, t, 10_000_000)
+        assert time.time() - t0 < 30
+        sk.sk_stream_close(server, sid)
+    finally:
+        sk.sk_server_destroy(server)
