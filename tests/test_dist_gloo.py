@@ -1,0 +1,56 @@
+"""Multi-rank host logic of bench.py on CPU (gloo, world size 2): barrier,
+max-over-ranks timing, and per-rank frequency sharding (independent seeds, no
+data-path collective)."""
+
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        w, r, loc = bench.dist_setup()
+        bench.barrier(w)
+        m = bench.max_over_ranks(1.0 + 2.0 * r, w)
+        ds = bench.workload_datasets(r)
+        seeds = [d.seed for d in ds]
+        x = ds[0].generate_cpu(0, 1)
+        q.put((r, w, m, seeds, int(x.sum())))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_time_max_and_disjoint_shards():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=240) for _ in procs]
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    out.sort()
+    assert [o[1] for o in out] == [2, 2]
+    assert out[0][2] == out[1][2] == 3.0           # max over ranks of 1 and 3
+    assert set(out[0][3]).isdisjoint(out[1][3])    # each rank its own frequencies
+    assert out[0][4] != out[1][4]
