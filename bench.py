@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "SK flagging throughput (Gsamples/s, 1 byte/sample)"
 UNIT = "Gsamples/s"
 N_IN, M_T, N_FREQ, N_FRAMES = 2048, 256, 4, 1525
-WORKLOAD = "full_array_plain: 4 freq x N=2048 x M=256 x 1525 frames, 4+4-bit, 3 sigma"
+WORKLOAD = "full_array_plain: {f} freq x N=2048 x M=256 x 1525 frames, 4+4-bit, 3 sigma"
 KERNEL_SOURCES = ["paper_1808_10365_b300/csrc/sk_device.cuh",
                   "paper_1808_10365_b300/csrc/sk_api.cu"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sk_fused_kernel_full_array.json")
@@ -176,11 +176,11 @@ def barrier(ws: int):
         dist.barrier()
 
 
-def workload_datasets(rank: int):
+def workload_datasets(rank: int, n_freq: int = N_FREQ):
     import synth
 
     # each rank owns its own frequencies (weak scaling): distinct seeds per rank
-    return synth.full_array_config(n_freq=N_FREQ, n_frames=N_FRAMES, N=N_IN, M=M_T,
+    return synth.full_array_config(n_freq=n_freq, n_frames=N_FRAMES, N=N_IN, M=M_T,
                                    cfg=1 + 1000 * rank)
 
 
@@ -239,13 +239,33 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_frames_per_step": nf},
+            "config": {"workload": WORKLOAD.format(f=N_FREQ), "sample_frames_per_step": nf},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                              "sample": f"each step: {nf} frames of 1 frequency of the workload "
                                        f"({nf * M_T * N_IN / 1e6:.0f} MB)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_e2e(sk, plan, d_in, d_mask, F, fb, bytes_per_step, e2e_steps, stream, ws):
+    """Same metric through sk_flag_host: pinned host input, upload and download timed."""
+    import torch
+
+    h_in = torch.empty(F * fb, dtype=torch.uint8).pin_memory()
+    h_in.copy_(d_in)
+    h_sk = torch.empty(F, dtype=torch.float32).pin_memory()
+    h_mask = torch.empty(F, dtype=torch.uint8).pin_memory()
+    sk.sk_flag_host(plan, h_in, F, h_sk, h_mask, stream)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sk.sk_flag_host(plan, h_in, F, h_sk, h_mask, stream)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    ok = bool((h_mask.numpy() == d_mask.cpu().numpy()).all())
+    return {"value": ws * bytes_per_step * e2e_steps / e2e_s / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": F * 5,
+            "steps": e2e_steps, "mask_matches_device": ok}
 
 
 def run_gpu(args):
@@ -261,7 +281,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
-    datasets = workload_datasets(rank)
+    datasets = workload_datasets(rank, args.freqs)
     F = sum(d.n_frames for d in datasets)
     fb = M_T * N_IN
     d_in = torch.empty(F * fb, dtype=torch.uint8, device=dev)
@@ -273,6 +293,7 @@ def run_gpu(args):
     d_sk = torch.empty(F, dtype=torch.float32, device=dev)
     d_mask = torch.empty(F, dtype=torch.uint8, device=dev)
     plan = sk.sk_plan_create(N_IN, M_T, 3.0, delta, device=dev.index)
+    rows, _ = sk.sk_plan_get_tiles(plan)
     stream = torch.cuda.Stream(dev)
     bytes_per_step = F * fb
     alg_bytes = bytes_per_step + F * (4 + 1)
@@ -310,37 +331,28 @@ def run_gpu(args):
     traffic = profiled_traffic(alg_bytes)
 
     # ---- end to end through the host-buffer entry point ----
-    e2e_steps = max(1, min(args.e2e_steps, args.steps))
-    h_in = torch.empty(F * fb, dtype=torch.uint8).pin_memory()
-    h_in.copy_(d_in)
-    h_sk = torch.empty(F, dtype=torch.float32).pin_memory()
-    h_mask = torch.empty(F, dtype=torch.uint8).pin_memory()
-    sk.sk_flag_host(plan, h_in, F, h_sk, h_mask, stream)
-    barrier(ws)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        sk.sk_flag_host(plan, h_in, F, h_sk, h_mask, stream)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
-    e2e_value = ws * bytes_per_step * e2e_steps / e2e_s / 1e9
-    ok_e2e = bool((h_mask.numpy() == d_mask.cpu().numpy()).all())
+    e2e = None
+    e2e_steps = min(args.e2e_steps, args.steps)
+    if e2e_steps > 0:
+        e2e = run_e2e(sk, plan, d_in, d_mask, F, fb, bytes_per_step, e2e_steps, stream, ws)
     sk.sk_plan_destroy(plan)
-
+    line_tail = dict(e2e=e2e)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames_per_step": F, "bytes_per_step": bytes_per_step,
-                   "l2": "inputs 3.2 GB per rank, 25x L2: no flush needed",
+        "config": {"workload": WORKLOAD.format(f=args.freqs), "frames_per_step": F,
+                   "bytes_per_step": bytes_per_step,
+                   "l2": f"inputs {bytes_per_step / 1e9:.1f} GB per rank, > L2 (126 MB): no flush",
                    "parallelism": f"frequency sharding x{ws}, no collective",
                    "mean_offset": delta},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": "sk_fused_kernel<16,false>",
+                     "kernel": f"sk_fused_kernel<{rows},false>",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": mean_launch_s * 1e3},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_per_step,
-                "d2h_bytes_per_step": F * 5, "steps": e2e_steps, "mask_matches_device": ok_e2e},
+        "e2e": line_tail["e2e"],
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
@@ -362,6 +374,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--freqs", type=int, default=N_FREQ, help="frequencies per rank")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

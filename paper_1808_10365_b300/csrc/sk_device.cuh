@@ -294,7 +294,8 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
     }
 }
 
-// Fast path: time-major, N % 8 == 0, M % 16 == 0, 8-byte aligned rows.  Rows
+// Fast path: time-major, N % 8 == 0, M % 16 == 0, 8-byte aligned rows.  Every
+// load stays inside rows 0..M-1 of a frame below f_end.  Rows
 // stream through two register batches of R rows; the first batch of the
 // team's next frame is in flight while the current frame's epilogue runs.
 template <int R, bool SERVED>
@@ -336,10 +337,15 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
             s2[j] = 0;
         }
         for (int jb = 0; jb < nb; jb += 2) {
+            // nb is odd only for R = 16 and M an odd multiple of 16: the last
+            // pair then has no second batch
+            const bool has_b = jb + 1 < nb;
             const uint8_t *pb = fp + (int64_t)(jb + 1) * R * N;
+            if (has_b) {
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                B[r] = ok ? ldg_stream(pb + r * N) : idle;
+                for (int r = 0; r < R; ++r)
+                    B[r] = ok ? ldg_stream(pb + r * N) : idle;
+            }
             if (ok) {
 #pragma unroll
                 for (int r = 0; r < R; ++r)
@@ -357,7 +363,7 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
                 for (int r = 0; r < R; ++r)
                     A[r] = nok ? ldg_stream(nfp + r * N) : idle;
             }
-            if (ok) {
+            if (ok && has_b) {
 #pragma unroll
                 for (int r = 0; r < R; ++r)
                     accum_row(B[r], lb, acc);

@@ -222,8 +222,8 @@ def pathfinder_config(seed: Optional[int] = None, duty: float = 0.5, N: int = 25
         seed = sub_seed(0, 0)
     period = 32
     on = int(round(duty * period))
-    rfi = [RFI(f, "cw", 3.0) for f in range(10, 20)]
-    rfi += [RFI(f, "pulse", 4.0, period, on) for f in range(40, 45)]
+    rfi = [RFI(f, "cw", 3.0) for f in range(10, 20) if f < n_frames]
+    rfi += [RFI(f, "pulse", 4.0, period, on) for f in range(40, 45) if f < n_frames]
     return Dataset(n_frames=n_frames, M=M, N=N, seed=seed, rfi=rfi)
 
 

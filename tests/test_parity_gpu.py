@@ -92,7 +92,8 @@ def test_pathfinder_25pct_pulse_flags_high():
     want = oracle.flag(x, 256, 256, 3.0, delta)
     got = run_compute(x, 256, 256, 3.0, delta)
     assert_parity(got, want)
-    assert got["mask"][40:45].all() and (got["sk"][40:45] > 1.0).all()
+    # above the digitisation-shifted centre 1 + delta (App. B), not necessarily above 1
+    assert got["mask"][40:45].all() and (got["sk"][40:45] > 1.0 + delta).all()
 
 
 @pytest.mark.parametrize("N,M,F", [

@@ -231,10 +231,10 @@ def test_ticket_timeout_and_concurrent_submitters():
         t0 = time.time()
         t = sk.sk_stream_submit(server, sid, datas[0][1][0], 0)
         try:
-            sk.sk_ticket_wait(server, t, 0)
+            sk.sk_ticket_wait(server, t, 0)          # done already, or times out
         except sk.SkError as e:
             assert e.status == sk.SK_ERR_TIMEOUT
-        sk.sk_ticket_wait(server, t, 10_000_000)
+            sk.sk_ticket_wait(server, t, 10_000_000)  # a timed-out ticket stays valid
         assert time.time() - t0 < 30
         sk.sk_stream_close(server, sid)
     finally:
