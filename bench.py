@@ -248,6 +248,167 @@ def run_reference(args):
     return 0
 
 
+def batched_bench(reps: int = 10, dev_index: int = 0):
+    """Mixed workload: 64 frequencies of N=2048 and 64 of N=256, M in {128, 256, 1024}
+    per frequency from the seed, 500 frames each.  One graph-captured persistent launch
+    (sk_batch_run) against one sk_flag launch per frequency, same buffers."""
+    import torch
+
+    import paper_1808_10365_b300 as sk
+    import synth
+
+    dev = torch.device("cuda", dev_index)
+    datasets = synth.mixed_config()
+    total = sum(d.nbytes for d in datasets)
+    buf = torch.empty(total + 16 * len(datasets), dtype=torch.uint8, device=dev)
+    items, plans, views = [], [], []
+    off = 0
+    for d in datasets:
+        off = (off + 15) // 16 * 16
+        v = buf[off:off + d.nbytes]
+        d.generate_gpu(v)
+        off += d.nbytes
+        delta = float(np.mean([sk.sk_digitisation_offset(x) for x in d.sigma]))
+        plan = sk.sk_plan_create(d.N, d.M, 3.0, delta, device=dev_index)
+        skv = torch.empty(d.n_frames, dtype=torch.float32, device=dev)
+        mask = torch.empty(d.n_frames, dtype=torch.uint8, device=dev)
+        plans.append(plan)
+        views.append((v, skv, mask))
+        items.append((plan, v, d.n_frames, skv, mask))
+    batch = sk.sk_batch_create(items, dev_index)
+    st = torch.cuda.Stream(dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        st.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_batch = timed(lambda: sk.sk_batch_run(batch, st))
+    mask_b = [m.clone() for _, _, m in views]
+
+    def plain():
+        for (plan, v, n, skv, mask) in items:
+            sk.sk_flag(plan, v, n, skv, mask, st)
+
+    ms_plain = timed(plain)
+    same = all(bool(torch.equal(a, m)) for a, (_, _, m) in zip(mask_b, views))
+    sk.sk_batch_destroy(batch)
+    for p in plans:
+        sk.sk_plan_destroy(p)
+    del buf
+    torch.cuda.empty_cache()
+    ms_list = sorted({d.M for d in datasets})
+    return {"workload": "64 freq x N=2048 + 64 freq x N=256, M per freq from {128,256,1024}, "
+                        "500 frames each, graph-captured persistent launch",
+            "bytes": total, "M_values": ms_list,
+            "value": total / (ms_batch * 1e-3) / 1e9, "unit": UNIT, "ms": ms_batch,
+            "plain_value": total / (ms_plain * 1e-3) / 1e9, "plain_ms": ms_plain,
+            "plain_launches": len(items), "speedup_vs_plain": ms_plain / ms_batch,
+            "masks_identical": same}
+
+
+def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
+                 pool: int = 32, submitters: int = 8):
+    """32 streams (24 x N=2048, 8 x N=256), M=256 frames arriving every 0.65536 ms per
+    stream with exponential jitter (mean T/4), for `seconds` of simulated time, through
+    the continuous-batching server with the running power state.  Frames cycle through
+    a pool of pre-generated frames per stream.  Latency = submit -> result host-visible.
+    The plain reference is one sk_flag_host call per frame, one at a time."""
+    import threading
+
+    import torch
+
+    import paper_1808_10365_b300 as sk
+    import synth
+
+    specs = [2048] * 24 + [256] * 8
+    M = 256
+    T = M * 2.56e-6
+    frames = []
+    for k, N in enumerate(specs):
+        s = synth.sub_seed(4, k)
+        ds = synth.Dataset(n_frames=pool, M=M, N=N, seed=s, rfi=synth.rfi_plan(s, pool))
+        frames.append(ds.generate_cpu())
+    n_per = int(seconds / T)
+    server = sk.sk_server_create(dev_index, 64 << 30)
+    sids = [sk.sk_stream_open(server, N, M, ring_frames=32, flags=sk.SK_RUNNING_OFFSET)
+            for N in specs]
+    rng = np.random.default_rng(1234)
+    jitter = rng.exponential(T / 4, size=(len(specs), n_per))
+    errors = []
+
+    def submitter(idx):
+        mine = list(range(idx, len(specs), submitters))
+        sched = sorted((k * T + jitter[j, k], j, k) for j in mine for k in range(n_per))
+        pending = {j: [] for j in mine}
+        t0 = time.perf_counter()
+        try:
+            for due, j, k in sched:
+                if paced:
+                    while time.perf_counter() - t0 < due:
+                        time.sleep(0)
+                while True:
+                    try:
+                        pending[j].append(sk.sk_stream_submit(server, sids[j],
+                                                              frames[j][k % pool], k))
+                        break
+                    except sk.SkError as e:
+                        if e.status != sk.SK_ERR_BUSY:
+                            raise
+                        sk.sk_ticket_wait(server, pending[j].pop(0))
+                if len(pending[j]) > 16:
+                    sk.sk_ticket_wait(server, pending[j].pop(0))
+            for j in mine:
+                for t in pending[j]:
+                    sk.sk_ticket_wait(server, t)
+        except Exception as ex:  # noqa: BLE001
+            errors.append(repr(ex))
+
+    th = [threading.Thread(target=submitter, args=(i,)) for i in range(submitters)]
+    w0 = time.perf_counter()
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    wall = time.perf_counter() - w0
+    st = sk.sk_server_stats(server)
+    for sid in sids:
+        sk.sk_stream_close(server, sid)
+    sk.sk_server_destroy(server)
+    total = sum(N * M for N in specs) * n_per
+    out = {"streams": "24 x N=2048 + 8 x N=256, M=256, running power state",
+           "paced": paced, "simulated_s": seconds, "frames": st["frames_done"],
+           "wall_s": wall, "value": total / wall / 1e9, "unit": UNIT,
+           "latency_p50_us": st["latency_p50_us"], "latency_p99_us": st["latency_p99_us"],
+           "launches": st["launches"], "frames_per_launch": st["frames_done"] / max(1, st["launches"]),
+           "errors": errors[:3]}
+    if paced:
+        # plain per-frame path on the same frames: one synchronous sk_flag_host per frame
+        lat = []
+        plans = {N: sk.sk_plan_create(N, M, 3.0, 0.0, device=dev_index) for N in set(specs)}
+        hm = torch.zeros(1, dtype=torch.uint8).pin_memory()
+        hs = torch.zeros(1, dtype=torch.float32).pin_memory()
+        pinned = [torch.from_numpy(f[0]).pin_memory() for f in frames]
+        for r in range(400):
+            j = r % len(specs)
+            t1 = time.perf_counter()
+            sk.sk_flag_host(plans[specs[j]], pinned[j], 1, hs, hm)
+            lat.append((time.perf_counter() - t1) * 1e6)
+        for p in plans.values():
+            sk.sk_plan_destroy(p)
+        lat = np.sort(np.array(lat[20:]))
+        out["plain_latency_p50_us"] = float(lat[len(lat) // 2])
+        out["plain_latency_p99_us"] = float(lat[int(0.99 * (len(lat) - 1))])
+    return out
+
+
 def run_e2e(sk, plan, d_in, d_mask, F, fb, bytes_per_step, e2e_steps, stream, ws):
     """Same metric through sk_flag_host: pinned host input, upload and download timed."""
     import torch
@@ -356,6 +517,12 @@ def run_gpu(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if ws == 1 and not args.no_extras:
+        del d_in
+        torch.cuda.empty_cache()
+        line["batched"] = batched_bench(dev_index=dev.index)
+        line["served"] = served_bench(args.served_seconds, True, dev.index)
+        line["served_replay"] = served_bench(min(args.served_seconds, 1.0), False, dev.index)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -377,6 +544,9 @@ def main(argv=None):
     ap.add_argument("--freqs", type=int, default=N_FREQ, help="frequencies per rank")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and served measurements")
+    ap.add_argument("--served-seconds", type=float, default=2.0)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
