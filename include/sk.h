@@ -151,6 +151,28 @@ sk_status_t sk_flag(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
 sk_status_t sk_flag_host(sk_plan_t plan, const uint8_t *h_in, int64_t n_frames,
                          float *h_sk, uint8_t *h_mask, sk_cuda_stream_t stream);
 
+/*
+ * sk_flag_host without any device allocation (the paper has no counterpart;
+ * this is an interface for callers that cannot allocate).  Some callers must
+ * not call cudaMalloc after start-up: their device memory belongs to another
+ * allocator, or an allocation could stall a real-time loop.  This call stages
+ * the bytes through a fixed array built into the library instead of the
+ * buffers sk_flag_host allocates, so it allocates nothing (the plan itself is
+ * made beforehand with sk_plan_create).  One call takes at most
+ * SK_NOALLOC_MAX_BYTES input bytes (n_frames*M*N) and SK_NOALLOC_MAX_FRAMES
+ * frames; larger requests get INVALID_ARG and must be split.  Every device
+ * that loads the library keeps the array (about 16.3 MiB) until the process
+ * exits.  The first call on a device looks up the array's device address;
+ * make it before any stream capture.  Calls on one device share the array:
+ * this process serialises them and each returns after its results are in
+ * h_sk/h_mask, but other work that overlaps a call on the GPU would race.
+ */
+#define SK_NOALLOC_MAX_BYTES (16 * 1024 * 1024)
+#define SK_NOALLOC_MAX_FRAMES 65536
+sk_status_t sk_flag_host_noalloc(sk_plan_t plan, const uint8_t *h_in,
+                                 int64_t n_frames, float *h_sk, uint8_t *h_mask,
+                                 sk_cuda_stream_t stream);
+
 /* ------------------------------------------------------ batched launch */
 
 typedef struct {

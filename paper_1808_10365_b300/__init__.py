@@ -33,10 +33,13 @@ SK_RUNNING_OFFSET = 0x1
 SK_OFFSET_BUCKETS = 4096
 SK_MAX_INPUTS = 4096
 SK_MAX_TIME = 4096
+SK_NOALLOC_MAX_BYTES = 16 * 1024 * 1024
+SK_NOALLOC_MAX_FRAMES = 65536
 
 EXPORTED = [
     "sk_plan_create", "sk_plan_destroy", "sk_plan_thresholds", "sk_plan_offset_table",
     "sk_plan_set_tiles", "sk_plan_get_tiles", "sk_compute", "sk_flag", "sk_flag_host",
+    "sk_flag_host_noalloc",
     "sk_batch_create", "sk_batch_run", "sk_batch_destroy", "sk_server_create",
     "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_ticket_wait",
     "sk_stream_drain", "sk_stream_get_state", "sk_stream_set_state", "sk_stream_close",
@@ -94,6 +97,7 @@ def library():
         "sk_compute": [P, P, I64, P, P, P, P, P, P],
         "sk_flag": [P, P, I64, P, P, P],
         "sk_flag_host": [P, P, I64, P, P, P],
+        "sk_flag_host_noalloc": [P, P, I64, P, P, P],
         "sk_batch_create": [ctypes.POINTER(sk_batch_item_t), I32, ctypes.c_int, ctypes.POINTER(P)],
         "sk_batch_run": [P, P],
         "sk_batch_destroy": [P],
@@ -213,6 +217,14 @@ def sk_flag(plan, d_in, n_frames, sk, mask, stream=None):
 def sk_flag_host(plan, h_in, n_frames, h_sk, h_mask, stream=None):
     _check(library().sk_flag_host(plan, _ptr(h_in), int(n_frames), _ptr(h_sk), _ptr(h_mask),
                                   _stream(stream)))
+
+
+def sk_flag_host_noalloc(plan, h_in, n_frames, h_sk, h_mask, stream=None):
+    """sk_flag_host for callers that cannot allocate device memory: stages through a
+    fixed array inside the library (at most SK_NOALLOC_MAX_BYTES input bytes and
+    SK_NOALLOC_MAX_FRAMES frames per call)."""
+    _check(library().sk_flag_host_noalloc(plan, _ptr(h_in), int(n_frames), _ptr(h_sk),
+                                          _ptr(h_mask), _stream(stream)))
 
 
 # ---------------------------------------------------------------- batched
