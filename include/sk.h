@@ -141,6 +141,22 @@ sk_status_t sk_flag(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
                     float *d_sk, uint8_t *d_mask, sk_cuda_stream_t stream);
 
 /*
+ * Per-input (independent) estimates, the "Independent SK^ Estimates" variant
+ * of Sec. 2.2.3: for every frame f and input i,
+ *   sk_in[f][i]   = fp32(r_i) * fp32((M+1)/(M-1)) = SK^_i of Eq. originalSK,
+ *                   NaN when S1_i = 0;
+ *   mask_in[f][i] = 1 when rint(2^32 r_i) lies outside [T_lo[1], T_hi[1]]
+ *                   (the one-input interval centre +- a*2/sqrt(M)) or S1_i = 0.
+ * The average of SK^_i over inputs is SK~ (Eq. final).  d_sk_in is
+ * [n_frames][N] float (required), d_mask_in [n_frames][N] uint8 (may be NULL);
+ * d_sk and d_mask per frame as in sk_flag (may be NULL).
+ */
+sk_status_t sk_compute_inputs(sk_plan_t plan, const uint8_t *d_in,
+                              int64_t n_frames, float *d_sk_in,
+                              uint8_t *d_mask_in, float *d_sk, uint8_t *d_mask,
+                              sk_cuda_stream_t stream);
+
+/*
  * sk_flag on HOST buffers: h_in (n_frames*M*N bytes), h_sk (may be NULL) and
  * h_mask are host memory (page-locked for full copy speed).  The plan
  * stages chunks through device buffers it owns, overlapping the host-to-

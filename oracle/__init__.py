@@ -66,6 +66,7 @@ def _load():
         lib.oracle_sk_f64.argtypes = [P, P, i64, i32, i32, P, P, P]
         lib.oracle_sk_spec.argtypes = [P, P, i64, i32, i32, P, P, P]
         lib.oracle_sk_single_f64.argtypes = [P, P, i64, i32, P]
+        lib.oracle_terms_spec.argtypes = [P, P, i64, i32, P, P, P]
         lib.oracle_max_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -120,6 +121,28 @@ def sk_single_f64(S1: np.ndarray, S2: np.ndarray, M: int) -> np.ndarray:
     out = np.zeros(S1.shape, dtype=np.float64)
     _load().oracle_sk_single_f64(_p(S1), _p(S2), S1.size, M, _p(out))
     return out
+
+
+def terms_spec(S1: np.ndarray, S2: np.ndarray, M: int):
+    """Per-input (q_i, SK^_i fp32, valid) in the kernel precision (Eq. originalSK)."""
+    S1 = np.ascontiguousarray(S1, dtype=np.int64)
+    S2 = np.ascontiguousarray(S2, dtype=np.int64)
+    q = np.zeros(S1.shape, dtype=np.int64)
+    sk1 = np.zeros(S1.shape, dtype=np.float32)
+    valid = np.zeros(S1.shape, dtype=np.uint8)
+    _load().oracle_terms_spec(_p(S1), _p(S2), S1.size, M, _p(q), _p(sk1), _p(valid))
+    return q, sk1, valid
+
+
+def flag_inputs(x: np.ndarray, M: int, N: int, n_sigma: float = 3.0, mean_offset: float = 0.0,
+                layout: int = 0):
+    """Independent single-receiver estimates and flags (Sec. 2.2.3, Eq. originalSK):
+    each input tested alone against the one-input interval (N_eff = 1 thresholds)."""
+    S1, S2 = power_sums(x, M, N, layout)
+    q, sk1, valid = terms_spec(S1, S2, M)
+    t_lo, t_hi = thresholds(M, 1, n_sigma, mean_offset)
+    m = ((q > t_hi[1]) | (q < t_lo[1]) | (valid == 0)).astype(np.uint8)
+    return dict(sk_in=sk1, mask_in=m, sk_in64=sk_single_f64(S1, S2, M), valid=valid)
 
 
 def sk_from_complex(x: np.ndarray) -> np.ndarray:

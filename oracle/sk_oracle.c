@@ -131,6 +131,32 @@ void oracle_sk_spec(const int64_t *S1, const int64_t *S2, int64_t n_frames,
     }
 }
 
+/*
+ * Per-input terms in the kernel precision: q[j] = rint(2^32 r_j) with r_j as
+ * in oracle_sk_spec, and sk1[j] = fp32(r_j) * fp32((n+1)/(n-1)), the single-
+ * receiver SK^_j of Eq. originalSK; valid[j] = 0 (q = 0, sk1 = NaN) when
+ * S1_j = 0.
+ */
+void oracle_terms_spec(const int64_t *S1, const int64_t *S2, int64_t count, int32_t M,
+                       int64_t *q, float *sk1, uint8_t *valid)
+{
+    const float c1 = (float)((double)(M + 1) / ((double)(M - 1) * 1.0));
+    for (int64_t j = 0; j < count; ++j) {
+        int64_t s1 = S1[j];
+        if (s1 <= 0) {
+            q[j] = 0;
+            sk1[j] = NAN;
+            valid[j] = 0;
+            continue;
+        }
+        int64_t d = (int64_t)M * S2[j] - s1 * s1;
+        float r = (float)d / (float)(s1 * s1);
+        q[j] = (int64_t)llrintf(r * 4294967296.0f);
+        sk1[j] = r * c1;
+        valid[j] = 1;
+    }
+}
+
 /* Per-input single-receiver SK^_i (Eq. originalSK) in fp64; NaN if S1_i = 0. */
 void oracle_sk_single_f64(const int64_t *S1, const int64_t *S2, int64_t count,
                           int32_t M, double *out)

@@ -39,7 +39,7 @@ SK_NOALLOC_MAX_FRAMES = 65536
 EXPORTED = [
     "sk_plan_create", "sk_plan_destroy", "sk_plan_thresholds", "sk_plan_offset_table",
     "sk_plan_set_tiles", "sk_plan_get_tiles", "sk_compute", "sk_flag", "sk_flag_host",
-    "sk_flag_host_noalloc",
+    "sk_flag_host_noalloc", "sk_compute_inputs",
     "sk_batch_create", "sk_batch_run", "sk_batch_destroy", "sk_server_create",
     "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_ticket_wait",
     "sk_stream_drain", "sk_stream_get_state", "sk_stream_set_state", "sk_stream_close",
@@ -98,6 +98,7 @@ def library():
         "sk_flag": [P, P, I64, P, P, P],
         "sk_flag_host": [P, P, I64, P, P, P],
         "sk_flag_host_noalloc": [P, P, I64, P, P, P],
+        "sk_compute_inputs": [P, P, I64, P, P, P, P, P],
         "sk_batch_create": [ctypes.POINTER(sk_batch_item_t), I32, ctypes.c_int, ctypes.POINTER(P)],
         "sk_batch_run": [P, P],
         "sk_batch_destroy": [P],
@@ -207,6 +208,12 @@ def sk_plan_get_tiles(plan):
 def sk_compute(plan, d_in, n_frames, s1=None, s2=None, q=None, sk=None, neff=None, stream=None):
     _check(library().sk_compute(plan, _ptr(d_in), int(n_frames), _ptr(s1), _ptr(s2), _ptr(q),
                                 _ptr(sk), _ptr(neff), _stream(stream)))
+
+
+def sk_compute_inputs(plan, d_in, n_frames, sk_in, mask_in=None, sk=None, mask=None,
+                      stream=None):
+    _check(library().sk_compute_inputs(plan, _ptr(d_in), int(n_frames), _ptr(sk_in),
+                                       _ptr(mask_in), _ptr(sk), _ptr(mask), _stream(stream)))
 
 
 def sk_flag(plan, d_in, n_frames, sk, mask, stream=None):

@@ -76,7 +76,7 @@ def main(argv=None):
     for s in a.shapes:
         N, M = (int(v) for v in s.split(":"))
         e = tune(N, M)
-        print(f"N={N} M={M}: rows={e['rows']} grid={e['grid']} {e['gbs']:.0f} GB/s")
+        print(f"N={N} M={M}: rows={e['rows']} grid={e['grid']} {e['gbs']:.0f} GB/s", e["all"])
         entries.append(e)
     write_cache(a.out, entries)
 

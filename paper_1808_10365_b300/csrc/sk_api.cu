@@ -38,7 +38,9 @@ int sm_count(int device)
     return n;
 }
 
-template <int R, bool S>
+// Register pipelines of the fast path: (rows per batch, batches in the ring).
+// Tile 0: 16 x 2, tile 1: 8 x 4 (both need M % 32 == 0), tile 2: 8 x 2 (M % 16).
+template <int R, int S, bool SRV>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_fused_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
                     const int32_t *__restrict__ cta_chunks, Item single)
@@ -52,10 +54,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t G = gridDim.x;
         const int64_t fb = F * (int64_t)blockIdx.x / G;
         const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
-        if (single.fast)
-            run_fast<R, S>(single, fb, fe, lb, ts, parity);
+        if (single.fast && single.M % (R * S) == 0)
+            run_fast<R, S, SRV>(single, fb, fe, lb, ts, parity);
         else
-            run_general<S>(single, fb, fe, lb, ts, parity);
+            run_general<SRV>(single, fb, fe, lb, ts, parity);
         return;
     }
     const int32_t c0 = cta_chunks[blockIdx.x], c1 = cta_chunks[blockIdx.x + 1];
@@ -63,20 +65,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         const Chunk ch = chunks[c];
         const Item it = items[ch.item];
         __syncthreads();
-        if (it.fast)
-            run_fast<R, S>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+        if (it.fast && it.M % (R * S) == 0)
+            run_fast<R, S, SRV>(it, ch.f_begin, ch.f_end, lb, ts, parity);
         else
-            run_general<S>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+            run_general<SRV>(it, ch.f_begin, ch.f_end, lb, ts, parity);
     }
 }
 
 using KernelFn = void (*)(const Item *, const Chunk *, const int32_t *, Item);
 
-static KernelFn pick_kernel(int rows, bool served)
+static KernelFn kernel_of(int tile, bool served)
 {
-    if (served)
-        return rows == 8 ? sk_fused_kernel<8, true> : sk_fused_kernel<16, true>;
-    return rows == 8 ? sk_fused_kernel<8, false> : sk_fused_kernel<16, false>;
+    static const KernelFn tab[2][3] = {
+        {sk_fused_kernel<16, 2, false>, sk_fused_kernel<8, 4, false>, sk_fused_kernel<8, 2, false>},
+        {sk_fused_kernel<16, 2, true>, sk_fused_kernel<8, 4, true>, sk_fused_kernel<8, 2, true>}};
+    return tab[served ? 1 : 0][tile];
+}
+
+// Tile for a requested rows-per-batch and the Ms the launch will see.
+int pick_tile(int rows, bool all_m32)
+{
+    if (!all_m32)
+        return 2;
+    return rows == 8 ? 1 : 0;
+}
+
+static KernelFn pick_kernel(int rows, bool served, int M)
+{
+    return kernel_of(pick_tile(rows, M % 32 == 0), served);
 }
 
 sk_status_t ensure_kernel_attrs(int device)
@@ -87,9 +103,8 @@ sk_status_t ensure_kernel_attrs(int device)
     for (int d : done)
         if (d == device)
             return SK_OK;
-    KernelFn fns[4] = {sk_fused_kernel<8, false>, sk_fused_kernel<16, false>,
-                       sk_fused_kernel<8, true>, sk_fused_kernel<16, true>};
-    for (KernelFn f : fns) {
+    for (int k = 0; k < 6; ++k) {
+        KernelFn f = kernel_of(k % 3, k >= 3);
         cudaError_t e = cudaFuncSetAttribute((const void *)f,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kDynSmem);
@@ -117,7 +132,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         g = need;
     if (g < 1)
         g = 1;
-    KernelFn fn = pick_kernel(rows, served);
+    KernelFn fn = pick_kernel(rows, served, it.M);
     fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, it);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -126,7 +141,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
 }
 
 sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
-                            const int32_t *d_cta_chunks, int grid, int rows, bool served,
+                            const int32_t *d_cta_chunks, int grid, int tile, bool served,
                             int device, cudaStream_t st)
 {
     if (grid <= 0)
@@ -136,7 +151,7 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
         return s;
     Item dummy;
     memset(&dummy, 0, sizeof dummy);
-    KernelFn fn = pick_kernel(rows, served);
+    KernelFn fn = kernel_of(tile, served);
     fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -472,6 +487,25 @@ extern "C" sk_status_t sk_flag(sk_plan_t plan, const uint8_t *d_in, int64_t n_fr
     if (!d_mask && n_frames > 0)
         return set_error(SK_ERR_INVALID_ARG, "sk_flag: mask is NULL");
     Item it = plan->item(d_in, n_frames);
+    it.sk = d_sk;
+    it.mask = d_mask;
+    DeviceGuard dg(plan->device);
+    return launch_single(it, plan->rows, false, plan->device, (cudaStream_t)stream,
+                         plan->grid_ctas);
+}
+
+extern "C" sk_status_t sk_compute_inputs(sk_plan_t plan, const uint8_t *d_in,
+                                         int64_t n_frames, float *d_sk_in, uint8_t *d_mask_in,
+                                         float *d_sk, uint8_t *d_mask, sk_cuda_stream_t stream)
+{
+    sk_status_t s = check_call(plan, d_in, n_frames, "sk_compute_inputs");
+    if (s != SK_OK)
+        return s;
+    if (!d_sk_in && n_frames > 0)
+        return set_error(SK_ERR_INVALID_ARG, "sk_compute_inputs: sk_in is NULL");
+    Item it = plan->item(d_in, n_frames);
+    it.sk_in = d_sk_in;
+    it.mask_in = d_mask_in;
     it.sk = d_sk;
     it.mask = d_mask;
     DeviceGuard dg(plan->device);

@@ -11,7 +11,7 @@
 
 struct sk_batch_s {
     int device = 0;
-    int rows = 16;
+    int tile = 0;  // kernel tile (see launch_schedule)
     int grid = 0;
     std::vector<sk::Item> items;
     std::vector<sk::Chunk> chunks;
@@ -101,6 +101,7 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
         return set_error(SK_ERR_OOM, "host allocation");
     b->device = device;
     int rows = 0;
+    bool all_m32 = true;
     for (int32_t k = 0; k < n_items; ++k) {
         const sk_batch_item_t &bi = items[k];
         if (!bi.plan || bi.n_frames < 0 || (bi.n_frames > 0 && !bi.d_in) ||
@@ -118,8 +119,9 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
         it.mask = bi.d_mask;
         b->items.push_back(it);
         rows = std::max(rows, bi.plan->rows);
+        all_m32 = all_m32 && (bi.plan->p.n_time % 32 == 0);
     }
-    b->rows = rows == 8 ? 8 : 16;
+    b->tile = pick_tile(rows == 8 ? 8 : 16, all_m32);
     b->grid = sm_count(device);
     build_schedule(b->items, b->grid, b->chunks, b->cta);
     sk_status_t s = SK_OK;
@@ -167,7 +169,7 @@ extern "C" sk_status_t sk_batch_run(sk_batch_t b, sk_cuda_stream_t stream)
             return cuda_error(e, "sk_batch_run capture stream");
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            s = launch_schedule(b->d_items, b->d_chunks, b->d_cta, b->grid, b->rows, false,
+            s = launch_schedule(b->d_items, b->d_chunks, b->d_cta, b->grid, b->tile, false,
                                 b->device, cs);
             cudaGraph_t g = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(cs, &g);

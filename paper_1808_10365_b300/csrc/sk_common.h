@@ -22,9 +22,11 @@ sk_status_t cuda_error(cudaError_t e, const char *what);
 // a prebuilt chunk schedule (items/chunks/cta_chunks on the device).
 sk_status_t launch_single(const Item &it, int rows, bool served, int device, cudaStream_t st,
                           int grid_cap = 0);
+// tile: 0 = 16 rows x 2 batches, 1 = 8 x 4 (M % 32 == 0 for both), 2 = 8 x 2
 sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
-                            const int32_t *d_cta_chunks, int grid, int rows, bool served,
+                            const int32_t *d_cta_chunks, int grid, int tile, bool served,
                             int device, cudaStream_t st);
+int pick_tile(int rows, bool all_m32);
 sk_status_t ensure_kernel_attrs(int device);
 int sm_count(int device);
 

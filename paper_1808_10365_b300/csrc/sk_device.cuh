@@ -59,6 +59,8 @@ struct Item {
     const int64_t *e_tab;    // served: offset per power bucket [kOffsetBuckets]
     int32_t state_init;      // served: 1 on the stream's first frame
     int32_t fast;            // 1: 8-byte vector path applies
+    float *sk_in;            // per-input SK^_i [n_frames][N] (Eq. originalSK), or null
+    uint8_t *mask_in;        // per-input flag at the N_eff = 1 thresholds, or null
 };
 
 // A contiguous range of frames of one item, processed by one CTA.
@@ -155,17 +157,18 @@ __device__ __forceinline__ void flush(uint32_t (&acc)[kVec], int32_t (&s1)[kVec]
 
 // r_i scaled to 2^32 fixed point: D_i = M S2_i - S1_i^2 and S1_i^2 exact in
 // int64, converted with round-to-nearest, one IEEE fp32 division, exact
-// scaling by 2^32, round-to-nearest-even to int64.
-__device__ __forceinline__ void input_term(int32_t s1, int32_t s2, int32_t M, int64_t &q,
-                                           int32_t &cnt)
+// scaling by 2^32, round-to-nearest-even to int64.  Returns false (and leaves
+// r, qi alone) for an input without power.
+__device__ __forceinline__ bool input_term(int32_t s1, int32_t s2, int32_t M, float &r,
+                                           int64_t &qi)
 {
-    if (s1 > 0) {
-        int64_t den = (int64_t)s1 * (int64_t)s1;
-        int64_t d = (int64_t)M * (int64_t)s2 - den;
-        float r = __fdiv_rn(__ll2float_rn(d), __ll2float_rn(den));
-        q += __float2ll_rn(__fmul_rn(r, 4294967296.0f));
-        cnt += 1;
-    }
+    if (s1 <= 0)
+        return false;
+    int64_t den = (int64_t)s1 * (int64_t)s1;
+    int64_t d = (int64_t)M * (int64_t)s2 - den;
+    r = __fdiv_rn(__ll2float_rn(d), __ll2float_rn(den));
+    qi = __float2ll_rn(__fmul_rn(r, 4294967296.0f));
+    return true;
 }
 
 struct TeamSmem {
@@ -232,9 +235,26 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
     uint32_t P[kVec];
     if (mine) {
 #pragma unroll
-        for (int k = 0; k < kVec; ++k)
-            if (col0 + k < it.N)
-                input_term(s1[k], s2[k], it.M, q, cnt);
+        for (int k = 0; k < kVec; ++k) {
+            if (col0 + k < it.N) {
+                float r = 0.0f;
+                int64_t qi = 0;
+                const bool has = input_term(s1[k], s2[k], it.M, r, qi);
+                if (has) {
+                    q += qi;
+                    cnt += 1;
+                }
+                if (it.sk_in) {
+                    // single-receiver estimate SK^_i = (M+1)/(M-1) r_i and its own
+                    // flag against the one-input thresholds (Sec. 2.2.3, independent
+                    // estimates)
+                    const int64_t o = frame * it.N + col0 + k;
+                    it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
+                    if (it.mask_in)
+                        it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+                }
+            }
+        }
         if (it.s1) {
             int32_t *o1 = it.s1 + frame * it.N + col0;
             int32_t *o2 = it.s2 + frame * it.N + col0;
@@ -294,15 +314,19 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
     }
 }
 
-// Fast path: time-major, N % 8 == 0, M % 16 == 0, 8-byte aligned rows.  Every
-// load stays inside rows 0..M-1 of a frame below f_end.  Rows
-// stream through two register batches of R rows; the first batch of the
-// team's next frame is in flight while the current frame's epilogue runs.
-template <int R, bool SERVED>
+// Fast path: time-major, N % 8 == 0, M % (R*S) == 0, 8-byte aligned rows.
+// Every load stays inside rows 0..M-1 of a frame below f_end.  Rows stream
+// through a ring of S register batches of R rows: batch g is loaded right after
+// batch g-S has been consumed, so each load has S-1 batches of work to hide
+// behind, and the first S batches of the team's next frame are in flight while
+// the current frame's epilogue runs.  A thread whose frame or columns are out of
+// range issues no loads and skips the accumulation.
+template <int R, int S, bool SERVED>
 __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_t f_end,
                                          uint32_t lb, TeamSmem &ts, int &parity)
 {
     static_assert(R == 8 || R == 16, "rows per batch");
+    static_assert((R * S) % kFlushRows == 0, "flush cadence");
     const int team_log2 = it.team_log2;
     const int T = kThreads >> team_log2;
     const int team_idx = threadIdx.x >> team_log2;
@@ -313,15 +337,18 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
     const int64_t fbytes = (int64_t)it.M * N;
     const int nb = it.M / R;
     const int64_t kmax = (f_end - f_begin + T - 1) / T;
-    const uint2 idle = make_uint2(0x88888888u, 0x88888888u);
 
-    uint2 A[R], B[R];
+    uint2 buf[S][R];
     int64_t frame = f_begin + team_idx;
     bool ok = col_ok && frame < f_end;
     const uint8_t *fp = it.in + frame * fbytes + col0;
+    if (ok) {
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-        A[r] = ok ? ldg_stream(fp + r * N) : idle;
+        for (int j = 0; j < S; ++j)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                buf[j][r] = ldg_stream(fp + (int64_t)(j * R + r) * N);
+    }
 
     for (int64_t k = 0; k < kmax; ++k) {
         const bool fvalid = frame < f_end;
@@ -336,38 +363,24 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
             s1[j] = 0;
             s2[j] = 0;
         }
-        for (int jb = 0; jb < nb; jb += 2) {
-            // nb is odd only for R = 16 and M an odd multiple of 16: the last
-            // pair then has no second batch
-            const bool has_b = jb + 1 < nb;
-            const uint8_t *pb = fp + (int64_t)(jb + 1) * R * N;
-            if (has_b) {
+        for (int jb = 0; jb < nb; jb += S) {
+            const bool same_frame = jb + S < nb;
+            const uint8_t *pn = same_frame ? fp + (int64_t)(jb + S) * R * N : nfp;
+            const bool lok = same_frame ? ok : nok;
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    B[r] = ok ? ldg_stream(pb + r * N) : idle;
-            }
-            if (ok) {
+            for (int j = 0; j < S; ++j) {
+                if (ok) {
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    accum_row(A[r], lb, acc);
-                if (R == 16)
-                    flush(acc, s1, s2);
-            }
-            if (jb + 2 < nb) {
-                const uint8_t *pa = fp + (int64_t)(jb + 2) * R * N;
+                    for (int r = 0; r < R; ++r)
+                        accum_row(buf[j][r], lb, acc);
+                    if (((j + 1) * R) % kFlushRows == 0)
+                        flush(acc, s1, s2);
+                }
+                if (lok) {
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    A[r] = ok ? ldg_stream(pa + r * N) : idle;
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    A[r] = nok ? ldg_stream(nfp + r * N) : idle;
-            }
-            if (ok && has_b) {
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    accum_row(B[r], lb, acc);
-                flush(acc, s1, s2);
+                    for (int r = 0; r < R; ++r)
+                        buf[j][r] = ldg_stream(pn + (int64_t)(j * R + r) * N);
+                }
             }
         }
         frame_epilogue<SERVED>(it, frame, fvalid, col0, lit, team_idx, parity, s1, s2, ts);

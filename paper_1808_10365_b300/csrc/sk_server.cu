@@ -70,6 +70,7 @@ struct TicketRec {
 struct LaunchSlot {
     bool busy = false;
     int n = 0;
+    int tile = 0;
     std::vector<sk_ticket_t> tickets;
     std::vector<sk_stream_id> streams;
     // pinned host mirrors and device copies of the work list and results
@@ -168,6 +169,10 @@ static bool launch_batch(sk_server_s *s, int slot_idx)
     s->rr = (s->rr + 1) % ns;
     if (items.empty())
         return false;
+    bool all_m32 = true;
+    for (const Item &it : items)
+        all_m32 = all_m32 && (it.M % 32 == 0);
+    L.tile = pick_tile(16, all_m32);
     // schedule over at most one CTA per frame-round, at most one per SM
     int rounds = 0;
     for (const Item &it : items)
@@ -202,7 +207,7 @@ static bool launch_batch(sk_server_s *s, int slot_idx)
                             cudaMemcpyHostToDevice, s->s_compute);
     sk_status_t st = SK_OK;
     if (e == cudaSuccess)
-        st = launch_schedule(L.d_items, L.d_chunks, L.d_cta, grid, 16, true, s->device,
+        st = launch_schedule(L.d_items, L.d_chunks, L.d_cta, grid, L.tile, true, s->device,
                              s->s_compute);
     if (e == cudaSuccess && st == SK_OK)
         e = cudaMemcpyAsync(L.h_sk, L.d_sk, sizeof(float) * items.size(), cudaMemcpyDeviceToHost,

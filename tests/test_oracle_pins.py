@@ -312,3 +312,31 @@ def test_false_alarm_rate_at_three_sigma():
         n_flag += int(((sk > 1 + half) | (sk < 1 - half)).sum())
         T += 1000
     assert 0.0008 < n_flag / T < 0.0065
+
+
+def test_independent_estimates_against_exact_rationals():
+    """Per-input SK^_i (Eq. originalSK) and its one-input flag (Sec. 2.2.3 independent
+    estimates); their average is SK~ (Eq. final, third line)."""
+    rng = np.random.default_rng(44)
+    M, N = 16, 6
+    x = _random_bytes(rng, 12, M, N)
+    x[3, :N] = 0x88   # make a few inputs dead in frame 3 (t = 0 row only: still powered)
+    r = oracle.flag_inputs(x, M, N, n_sigma=1.0, mean_offset=0.2)
+    full = oracle.flag(x, M, N)
+    for f in range(12):
+        bs1, bs2 = brute.sums(list(x[f]), M, N)
+        vals = []
+        for i in range(N):
+            if bs1[i] == 0:
+                assert r["valid"][f, i] == 0 and np.isnan(r["sk_in"][f, i])
+                assert r["mask_in"][f, i] == 1
+                continue
+            e = brute.sk_single(bs1[i], bs2[i], M)
+            vals.append(e)
+            assert abs(float(r["sk_in"][f, i]) - float(e)) <= 1e-6 * abs(float(e)) + 1e-9
+            want = brute.outside(e, M, 1, 1.0, 0.2)
+            edge = min(abs(float(e) - 1.2 - 2 / math.sqrt(M)), abs(float(e) - 1.2 + 2 / math.sqrt(M)))
+            assert r["mask_in"][f, i] == want or edge < 1e-5
+        if vals:
+            avg = sum(vals, Fraction(0)) / len(vals)
+            assert abs(float(avg) - full["sk64"][f]) <= 1e-12 * max(1, abs(float(avg)))

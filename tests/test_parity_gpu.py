@@ -257,3 +257,32 @@ def test_full_array_workload_sampled():
           and x.amp > 2.5]
     assert r["mask"][cw].all()
     assert r["mask"].mean() < 0.06
+
+
+@pytest.mark.parametrize("N,M,F", [(256, 256, 40), (2048, 128, 6), (100, 64, 9)])
+def test_independent_estimates_bit_exact(N, M, F):
+    """sk_compute_inputs: per-input SK^_i and one-input flags against the oracle."""
+    dev = _dev()
+    rng = np.random.default_rng(N + M + F)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    x[1, ::N] = 0x88
+    want = oracle.flag_inputs(x, M, N, 3.0, 0.05)
+    whole = oracle.flag(x, M, N, 3.0, 0.05)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    sk_in = torch.empty((F, N), dtype=torch.float32, device=dev)
+    m_in = torch.empty((F, N), dtype=torch.uint8, device=dev)
+    skv = torch.empty(F, dtype=torch.float32, device=dev)
+    mask = torch.empty(F, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.05)
+    try:
+        sk.sk_compute_inputs(plan, d_in, F, sk_in, m_in, skv, mask)
+        torch.cuda.synchronize()
+    finally:
+        sk.sk_plan_destroy(plan)
+    got = sk_in.cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), want["sk_in"].view(np.uint32))
+    assert np.array_equal(m_in.cpu().numpy(), want["mask_in"])
+    assert np.array_equal(mask.cpu().numpy(), whole["mask"])
+    ok = want["valid"] == 1
+    rel = np.abs(got[ok] - want["sk_in64"][ok]) / np.maximum(np.abs(want["sk_in64"][ok]), 1e-6)
+    assert rel.max() <= SK_REL
