@@ -315,14 +315,13 @@ def batched_bench(reps: int = 10, dev_index: int = 0):
 
 
 def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
-                 pool: int = 32, submitters: int = 8):
+                 pool: int = 32, threads: int = 8):
     """32 streams (24 x N=2048, 8 x N=256), M=256 frames arriving every 0.65536 ms per
     stream with exponential jitter (mean T/4), for `seconds` of simulated time, through
-    the continuous-batching server with the running power state.  Frames cycle through
-    a pool of pre-generated frames per stream.  Latency = submit -> result host-visible.
-    The plain reference is one sk_flag_host call per frame, one at a time."""
-    import threading
-
+    the continuous-batching server with the running power state, driven by the
+    library's load generator (sk_server_replay).  Frames cycle through a pool of
+    pre-generated frames per stream.  Latency = submit -> result host-visible.
+    The plain reference is one synchronous sk_flag_host call per frame."""
     import torch
 
     import paper_1808_10365_b300 as sk
@@ -331,81 +330,46 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
     specs = [2048] * 24 + [256] * 8
     M = 256
     T = M * 2.56e-6
-    frames = []
+    pools = []
     for k, N in enumerate(specs):
         s = synth.sub_seed(4, k)
         ds = synth.Dataset(n_frames=pool, M=M, N=N, seed=s, rfi=synth.rfi_plan(s, pool))
-        frames.append(ds.generate_cpu())
+        pools.append(ds.generate_cpu())
     n_per = int(seconds / T)
-    server = sk.sk_server_create(dev_index, 64 << 30)
+    server = sk.sk_server_create(dev_index, 8 << 30)
     sids = [sk.sk_stream_open(server, N, M, ring_frames=32, flags=sk.SK_RUNNING_OFFSET)
             for N in specs]
-    rng = np.random.default_rng(1234)
-    jitter = rng.exponential(T / 4, size=(len(specs), n_per))
-    errors = []
-
-    def submitter(idx):
-        mine = list(range(idx, len(specs), submitters))
-        sched = sorted((k * T + jitter[j, k], j, k) for j in mine for k in range(n_per))
-        pending = {j: [] for j in mine}
-        t0 = time.perf_counter()
-        try:
-            for due, j, k in sched:
-                if paced:
-                    while time.perf_counter() - t0 < due:
-                        time.sleep(0)
-                while True:
-                    try:
-                        pending[j].append(sk.sk_stream_submit(server, sids[j],
-                                                              frames[j][k % pool], k))
-                        break
-                    except sk.SkError as e:
-                        if e.status != sk.SK_ERR_BUSY:
-                            raise
-                        sk.sk_ticket_wait(server, pending[j].pop(0))
-                if len(pending[j]) > 16:
-                    sk.sk_ticket_wait(server, pending[j].pop(0))
-            for j in mine:
-                for t in pending[j]:
-                    sk.sk_ticket_wait(server, t)
-        except Exception as ex:  # noqa: BLE001
-            errors.append(repr(ex))
-
-    th = [threading.Thread(target=submitter, args=(i,)) for i in range(submitters)]
-    w0 = time.perf_counter()
-    for t in th:
-        t.start()
-    for t in th:
-        t.join()
-    wall = time.perf_counter() - w0
-    st = sk.sk_server_stats(server)
+    r = sk.sk_server_replay(server, sids, pools, n_per, T, T / 4, paced=paced, threads=threads)
     for sid in sids:
         sk.sk_stream_close(server, sid)
     sk.sk_server_destroy(server)
-    total = sum(N * M for N in specs) * n_per
     out = {"streams": "24 x N=2048 + 8 x N=256, M=256, running power state",
-           "paced": paced, "simulated_s": seconds, "frames": st["frames_done"],
-           "wall_s": wall, "value": total / wall / 1e9, "unit": UNIT,
-           "latency_p50_us": st["latency_p50_us"], "latency_p99_us": st["latency_p99_us"],
-           "launches": st["launches"], "frames_per_launch": st["frames_done"] / max(1, st["launches"]),
-           "errors": errors[:3]}
+           "paced": paced, "simulated_s": seconds, "frames": r["frames"], "wall_s": r["wall_s"],
+           "value": r["bytes"] / r["wall_s"] / 1e9, "unit": UNIT,
+           "realtime_input_gbs": sum(specs) * M / T / 1e9,
+           "latency_p50_us": r["latency_p50_us"], "latency_p99_us": r["latency_p99_us"],
+           "launches": r["launches"], "frames_per_launch": r["frames"] / max(1, r["launches"]),
+           "submit_p50_us": r["submit_p50_us"], "busy_retries": r["busy_retries"],
+           "driver": f"sk_server_replay, {threads} submitter threads"}
     if paced:
-        # plain per-frame path on the same frames: one synchronous sk_flag_host per frame
+        # plain path on the same frames: one synchronous sk_flag_host per frame
         lat = []
         plans = {N: sk.sk_plan_create(N, M, 3.0, 0.0, device=dev_index) for N in set(specs)}
         hm = torch.zeros(1, dtype=torch.uint8).pin_memory()
         hs = torch.zeros(1, dtype=torch.float32).pin_memory()
-        pinned = [torch.from_numpy(f[0]).pin_memory() for f in frames]
-        for r in range(400):
-            j = r % len(specs)
+        pinned = [torch.from_numpy(p[0]).pin_memory() for p in pools]
+        for i in range(640):
+            j = i % len(specs)
             t1 = time.perf_counter()
             sk.sk_flag_host(plans[specs[j]], pinned[j], 1, hs, hm)
             lat.append((time.perf_counter() - t1) * 1e6)
         for p in plans.values():
             sk.sk_plan_destroy(p)
-        lat = np.sort(np.array(lat[20:]))
+        lat = np.sort(np.array(lat[32:]))
         out["plain_latency_p50_us"] = float(lat[len(lat) // 2])
         out["plain_latency_p99_us"] = float(lat[int(0.99 * (len(lat) - 1))])
+        out["plain_max_frames_per_s"] = float(1e6 / lat.mean())
+        out["realtime_frames_per_s"] = len(specs) / T
     return out
 
 
@@ -510,7 +474,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": f"sk_fused_kernel<{rows},false>",
+                     "kernel": f"sk_fused_kernel<{rows},2,false,2048>",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": mean_launch_s * 1e3},
         "e2e": line_tail["e2e"],

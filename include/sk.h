@@ -267,6 +267,43 @@ typedef struct {
 } sk_server_stats_t;
 sk_status_t sk_server_stats(sk_server_t server, sk_server_stats_t *out);
 
+/*
+ * Load generator for a server (measurement, not part of the method): replays
+ * pools of frames into open streams from `threads` submitter threads.  Stream
+ * j submits frames_per_stream frames, frame k due at k*cadence_s plus an
+ * exponential jitter of mean jitter_mean_s (seeded), or as fast as admission
+ * allows when paced = 0; frame k is pool entry k % pool_frames[j] of
+ * frames[j] (host memory, pool_frames[j] * M * N bytes).  A BUSY answer makes
+ * the submitter wait for its stream's oldest result and retry.  Latencies are
+ * the server's submit-to-result times over this replay only.
+ */
+typedef struct {
+    int32_t n_streams;
+    int32_t threads;
+    const sk_stream_id *streams;
+    const uint8_t *const *frames;
+    const int32_t *pool_frames;
+    int64_t frames_per_stream;
+    double cadence_s;
+    double jitter_mean_s;
+    int32_t paced;
+    int32_t pad;
+    uint64_t seed;
+} sk_replay_t;
+typedef struct {
+    double wall_s;
+    int64_t frames;
+    int64_t launches;
+    int64_t busy_retries;
+    double bytes;
+    double latency_p50_us;
+    double latency_p99_us;
+    double submit_p50_us;
+    double submit_p99_us;
+} sk_replay_result_t;
+sk_status_t sk_server_replay(sk_server_t server, const sk_replay_t *replay,
+                             sk_replay_result_t *out);
+
 /* --------------------------------------------------------------- misc */
 
 /*

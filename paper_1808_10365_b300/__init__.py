@@ -43,7 +43,7 @@ EXPORTED = [
     "sk_batch_create", "sk_batch_run", "sk_batch_destroy", "sk_server_create",
     "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_ticket_wait",
     "sk_stream_drain", "sk_stream_get_state", "sk_stream_set_state", "sk_stream_close",
-    "sk_server_stats", "sk_digitisation_offset", "sk_last_error",
+    "sk_server_stats", "sk_server_replay", "sk_digitisation_offset", "sk_last_error",
 ]
 
 
@@ -65,6 +65,22 @@ class sk_batch_item_t(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("d_in", ctypes.c_void_p),
                 ("n_frames", ctypes.c_int64), ("d_sk", ctypes.c_void_p),
                 ("d_mask", ctypes.c_void_p)]
+
+
+class sk_replay_t(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("streams", ctypes.c_void_p), ("frames", ctypes.c_void_p),
+                ("pool_frames", ctypes.c_void_p), ("frames_per_stream", ctypes.c_int64),
+                ("cadence_s", ctypes.c_double), ("jitter_mean_s", ctypes.c_double),
+                ("paced", ctypes.c_int32), ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class sk_replay_result_t(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("frames", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("busy_retries", ctypes.c_int64),
+                ("bytes", ctypes.c_double), ("latency_p50_us", ctypes.c_double),
+                ("latency_p99_us", ctypes.c_double), ("submit_p50_us", ctypes.c_double),
+                ("submit_p99_us", ctypes.c_double)]
 
 
 class sk_server_stats_t(ctypes.Structure):
@@ -112,6 +128,7 @@ def library():
         "sk_stream_set_state": [P, I32, P, ctypes.c_size_t],
         "sk_stream_close": [P, I32],
         "sk_server_stats": [P, ctypes.POINTER(sk_server_stats_t)],
+        "sk_server_replay": [P, ctypes.POINTER(sk_replay_t), ctypes.POINTER(sk_replay_result_t)],
         "sk_digitisation_offset": [ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
@@ -319,6 +336,23 @@ def sk_server_stats(server) -> dict:
     s = sk_server_stats_t()
     _check(library().sk_server_stats(server, ctypes.byref(s)))
     return {k: getattr(s, k) for k, _ in sk_server_stats_t._fields_}
+
+
+def sk_server_replay(server, stream_ids, pools, frames_per_stream, cadence_s, jitter_mean_s,
+                     paced=True, threads=8, seed=1):
+    """Replay frame pools (one uint8 numpy array [pool, M*N] per stream) into open streams."""
+    n = len(stream_ids)
+    pools = [np.ascontiguousarray(p, dtype=np.uint8) for p in pools]
+    ids = (ctypes.c_int32 * n)(*stream_ids)
+    ptrs = (ctypes.c_void_p * n)(*[p.ctypes.data for p in pools])
+    npool = (ctypes.c_int32 * n)(*[p.shape[0] for p in pools])
+    r = sk_replay_t(n, int(threads), ctypes.cast(ids, ctypes.c_void_p).value,
+                    ctypes.cast(ptrs, ctypes.c_void_p).value,
+                    ctypes.cast(npool, ctypes.c_void_p).value, int(frames_per_stream),
+                    float(cadence_s), float(jitter_mean_s), 1 if paced else 0, 0, int(seed))
+    out = sk_replay_result_t()
+    _check(library().sk_server_replay(server, ctypes.byref(r), ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in sk_replay_result_t._fields_}
 
 
 # ------------------------------------------------------------------- misc

@@ -39,8 +39,11 @@ int sm_count(int device)
 }
 
 // Register pipelines of the fast path: (rows per batch, batches in the ring).
-// Tile 0: 16 x 2, tile 1: 8 x 4 (both need M % 32 == 0), tile 2: 8 x 2 (M % 16).
-template <int R, int S, bool SRV>
+// Tile 0: 16 x 2 (needs M % 32 == 0), tile 1: 8 x 2 (M % 16 == 0).  NC fixes
+// the row stride N at compile time (0: read it from the item); a kernel is only
+// launched with NC > 0 for items of that N, and any other item takes the
+// general path.
+template <int R, int S, bool SRV, int NC>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_fused_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
                     const int32_t *__restrict__ cta_chunks, Item single)
@@ -54,8 +57,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t G = gridDim.x;
         const int64_t fb = F * (int64_t)blockIdx.x / G;
         const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
-        if (single.fast && single.M % (R * S) == 0)
-            run_fast<R, S, SRV>(single, fb, fe, lb, ts, parity);
+        if (single.fast && single.M % (R * S) == 0 && (NC == 0 || single.N == NC))
+            run_fast<R, S, SRV, NC>(single, fb, fe, lb, ts, parity);
         else
             run_general<SRV>(single, fb, fe, lb, ts, parity);
         return;
@@ -63,36 +66,65 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int32_t c0 = cta_chunks[blockIdx.x], c1 = cta_chunks[blockIdx.x + 1];
     for (int32_t c = c0; c < c1; ++c) {
         const Chunk ch = chunks[c];
-        const Item it = items[ch.item];
         __syncthreads();
-        if (it.fast && it.M % (R * S) == 0)
-            run_fast<R, S, SRV>(it, ch.f_begin, ch.f_end, lb, ts, parity);
-        else
-            run_general<SRV>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+        if (ch.kind == 0) {
+            const Item it = items[ch.item];
+            if (it.fast && it.M % (R * S) == 0 && (NC == 0 || it.N == NC))
+                run_fast<R, S, SRV, NC>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+            else
+                run_general<SRV>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+            continue;
+        }
+        // one frame per item, teams on different items; every item of the chunk
+        // has the same shape, so all teams take the same path the same number
+        // of times
+        const Item it0 = items[ch.f_begin];
+        const int tl = it0.team_log2;
+        const int64_t T = kThreads >> tl;
+        const int64_t team_idx = threadIdx.x >> tl;
+        const bool fast = it0.fast && it0.M % (R * S) == 0 && (NC == 0 || it0.N == NC);
+        for (int64_t base = ch.f_begin; base < ch.f_end; base += T) {
+            const int64_t idx = base + team_idx;
+            const bool v = idx < ch.f_end;
+            const Item it = items[v ? idx : ch.f_begin];
+            if (fast)
+                run_fast<R, S, SRV, NC>(it, 0, v ? 1 : 0, lb, ts, parity, true);
+            else
+                run_general<SRV>(it, 0, v ? 1 : 0, lb, ts, parity, true);
+        }
     }
 }
 
 using KernelFn = void (*)(const Item *, const Chunk *, const int32_t *, Item);
 
-static KernelFn kernel_of(int tile, bool served)
+// [tile][nc index: 0 -> runtime N, 1 -> 256, 2 -> 2048]; served kernels use runtime N
+static const KernelFn kPlain[2][3] = {
+    {sk_fused_kernel<16, 2, false, 0>, sk_fused_kernel<16, 2, false, 256>,
+     sk_fused_kernel<16, 2, false, 2048>},
+    {sk_fused_kernel<8, 2, false, 0>, sk_fused_kernel<8, 2, false, 256>,
+     sk_fused_kernel<8, 2, false, 2048>}};
+static const KernelFn kServed[2] = {sk_fused_kernel<16, 2, true, 0>,
+                                    sk_fused_kernel<8, 2, true, 0>};
+
+static KernelFn kernel_of(int tile, bool served, int N)
 {
-    static const KernelFn tab[2][3] = {
-        {sk_fused_kernel<16, 2, false>, sk_fused_kernel<8, 4, false>, sk_fused_kernel<8, 2, false>},
-        {sk_fused_kernel<16, 2, true>, sk_fused_kernel<8, 4, true>, sk_fused_kernel<8, 2, true>}};
-    return tab[served ? 1 : 0][tile];
+    if (served)
+        return kServed[tile];
+    const int nci = N == 256 ? 1 : (N == 2048 ? 2 : 0);
+    return kPlain[tile][nci];
 }
 
-// Tile for a requested rows-per-batch and the Ms the launch will see.
+// Tile for a requested rows-per-batch and whether every M is a multiple of 32.
 int pick_tile(int rows, bool all_m32)
 {
-    if (!all_m32)
-        return 2;
-    return rows == 8 ? 1 : 0;
+    if (!all_m32 || rows == 8)
+        return 1;
+    return 0;
 }
 
-static KernelFn pick_kernel(int rows, bool served, int M)
+static KernelFn pick_kernel(int rows, bool served, int M, int N)
 {
-    return kernel_of(pick_tile(rows, M % 32 == 0), served);
+    return kernel_of(pick_tile(rows, M % 32 == 0), served, N);
 }
 
 sk_status_t ensure_kernel_attrs(int device)
@@ -103,8 +135,13 @@ sk_status_t ensure_kernel_attrs(int device)
     for (int d : done)
         if (d == device)
             return SK_OK;
-    for (int k = 0; k < 6; ++k) {
-        KernelFn f = kernel_of(k % 3, k >= 3);
+    std::vector<KernelFn> fns;
+    for (int t = 0; t < 2; ++t) {
+        fns.push_back(kServed[t]);
+        for (int j = 0; j < 3; ++j)
+            fns.push_back(kPlain[t][j]);
+    }
+    for (KernelFn f : fns) {
         cudaError_t e = cudaFuncSetAttribute((const void *)f,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kDynSmem);
@@ -132,7 +169,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         g = need;
     if (g < 1)
         g = 1;
-    KernelFn fn = pick_kernel(rows, served, it.M);
+    KernelFn fn = pick_kernel(rows, served, it.M, it.N);
     fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, it);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -151,7 +188,7 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
         return s;
     Item dummy;
     memset(&dummy, 0, sizeof dummy);
-    KernelFn fn = kernel_of(tile, served);
+    KernelFn fn = kernel_of(tile, served, 0);
     fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

@@ -59,7 +59,7 @@ void build_schedule(const std::vector<Item> &items, int grid, std::vector<Chunk>
             } else {
                 Chunk ch;
                 ch.item = k;
-                ch.pad = 0;
+                ch.kind = 0;
                 ch.f_begin = f0;
                 ch.f_end = f1;
                 v.push_back(ch);
@@ -71,6 +71,57 @@ void build_schedule(const std::vector<Item> &items, int grid, std::vector<Chunk>
         chunks.insert(chunks.end(), per[c].begin(), per[c].end());
     }
     cta[grid] = (int32_t)chunks.size();
+}
+
+// Schedule for items of one frame each (a served batch): items of one shape
+// (team size, N, M, layout) are grouped, up to T per chunk so that every team
+// of a CTA takes one; chunks go round-robin to at most `grid_max` CTAs.  The
+// items are reordered in place (their outputs are addressed through their own
+// pointers, so order does not matter); perm[k] = original index of item k.
+int build_item_schedule(std::vector<Item> &items, int grid_max, std::vector<Chunk> &chunks,
+                        std::vector<int32_t> &cta, std::vector<int32_t> &perm)
+{
+    const int n = (int)items.size();
+    perm.resize(n);
+    for (int k = 0; k < n; ++k)
+        perm[k] = k;
+    auto key = [&](int k) {
+        const Item &it = items[k];
+        return std::make_tuple(it.team_log2, it.N, it.M, it.layout);
+    };
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return key(a) < key(b); });
+    std::vector<Item> sorted(n);
+    for (int k = 0; k < n; ++k)
+        sorted[k] = items[perm[k]];
+    items.swap(sorted);
+    std::vector<Chunk> all;
+    for (int k = 0; k < n;) {
+        const int64_t T = kThreads >> items[k].team_log2;
+        int e = k + 1;
+        while (e < n && e - k < T && items[e].team_log2 == items[k].team_log2 &&
+               items[e].N == items[k].N && items[e].M == items[k].M &&
+               items[e].layout == items[k].layout)
+            ++e;
+        Chunk ch;
+        ch.item = k;
+        ch.kind = 1;
+        ch.f_begin = k;
+        ch.f_end = e;
+        all.push_back(ch);
+        k = e;
+    }
+    const int grid = std::max(1, std::min(grid_max, (int)all.size()));
+    std::vector<std::vector<Chunk>> per(grid);
+    for (size_t c = 0; c < all.size(); ++c)
+        per[c % grid].push_back(all[c]);
+    chunks.clear();
+    cta.assign(grid + 1, 0);
+    for (int c = 0; c < grid; ++c) {
+        cta[c] = (int32_t)chunks.size();
+        chunks.insert(chunks.end(), per[c].begin(), per[c].end());
+    }
+    cta[grid] = (int32_t)chunks.size();
+    return grid;
 }
 
 }  // namespace sk

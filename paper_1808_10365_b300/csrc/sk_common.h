@@ -22,7 +22,7 @@ sk_status_t cuda_error(cudaError_t e, const char *what);
 // a prebuilt chunk schedule (items/chunks/cta_chunks on the device).
 sk_status_t launch_single(const Item &it, int rows, bool served, int device, cudaStream_t st,
                           int grid_cap = 0);
-// tile: 0 = 16 rows x 2 batches, 1 = 8 x 4 (M % 32 == 0 for both), 2 = 8 x 2
+// tile: 0 = 16 rows x 2 batches (M % 32 == 0), 1 = 8 x 2 (M % 16 == 0)
 sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
                             const int32_t *d_cta_chunks, int grid, int tile, bool served,
                             int device, cudaStream_t st);
@@ -33,6 +33,10 @@ int sm_count(int device);
 // Static byte-balanced schedule of items over `grid` CTAs.
 void build_schedule(const std::vector<Item> &items, int grid, std::vector<Chunk> &chunks,
                     std::vector<int32_t> &cta);
+
+// Schedule for a batch of one-frame items; reorders items, returns the grid.
+int build_item_schedule(std::vector<Item> &items, int grid_max, std::vector<Chunk> &chunks,
+                        std::vector<int32_t> &cta, std::vector<int32_t> &perm);
 
 // App. B digitisation model, host double precision.
 double digitisation_delta(double sigma);

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace sk {
 
 constexpr int kThreads = 512;               // one CTA per SM
@@ -63,10 +65,12 @@ struct Item {
     uint8_t *mask_in;        // per-input flag at the N_eff = 1 thresholds, or null
 };
 
-// A contiguous range of frames of one item, processed by one CTA.
+// Work of one CTA.  kind 0: frames [f_begin, f_end) of item `item`, the CTA's
+// teams striding through them.  kind 1: items [f_begin, f_end), one frame each
+// and all of one shape (N, M, layout), each team taking its own items.
 struct Chunk {
     int32_t item;
-    int32_t pad;
+    int32_t kind;
     int64_t f_begin;
     int64_t f_end;
 };
@@ -94,6 +98,32 @@ __device__ __forceinline__ uint2 ldg_stream(const uint8_t *p)
         : "=r"(v.x), "=r"(v.y)
         : "l"(p));
     return v;
+}
+
+// Same load at base + OFF with OFF a compile-time immediate of the instruction.
+template <int OFF>
+__device__ __forceinline__ uint2 ldg_stream_at(const uint8_t *base)
+{
+    uint2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v2.u32 {%0, %1}, [%2+%3];"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(base), "n"(OFF));
+    return v;
+}
+
+// Rows 0..R-1 of a batch whose row stride NC is known at compile time.
+template <int NC, int... Rs>
+__device__ __forceinline__ void load_rows_imm(uint2 *b, const uint8_t *base,
+                                              std::integer_sequence<int, Rs...>)
+{
+    ((b[Rs] = ldg_stream_at<Rs * NC>(base)), ...);
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of
+// 16); a hint only, results never depend on it.
+__device__ __forceinline__ void prefetch_l2(const uint8_t *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void named_sync(int id, int nthreads)
@@ -142,6 +172,19 @@ __device__ __forceinline__ void accum_row(uint2 w, uint32_t lb, uint32_t (&acc)[
     acc[5] += lds_u32(prmt(w.y, lb, 0x7614u));
     acc[6] += lds_u32(prmt(w.y, lb, 0x7624u));
     acc[7] += lds_u32(prmt(w.y, lb, 0x7634u));
+}
+
+// Two rows at once: both table values of an input go into one three-input add.
+__device__ __forceinline__ void accum_pair(uint2 w0, uint2 w1, uint32_t lb, uint32_t (&acc)[kVec])
+{
+    acc[0] += lds_u32(prmt(w0.x, lb, 0x7604u)) + lds_u32(prmt(w1.x, lb, 0x7604u));
+    acc[1] += lds_u32(prmt(w0.x, lb, 0x7614u)) + lds_u32(prmt(w1.x, lb, 0x7614u));
+    acc[2] += lds_u32(prmt(w0.x, lb, 0x7624u)) + lds_u32(prmt(w1.x, lb, 0x7624u));
+    acc[3] += lds_u32(prmt(w0.x, lb, 0x7634u)) + lds_u32(prmt(w1.x, lb, 0x7634u));
+    acc[4] += lds_u32(prmt(w0.y, lb, 0x7604u)) + lds_u32(prmt(w1.y, lb, 0x7604u));
+    acc[5] += lds_u32(prmt(w0.y, lb, 0x7614u)) + lds_u32(prmt(w1.y, lb, 0x7614u));
+    acc[6] += lds_u32(prmt(w0.y, lb, 0x7624u)) + lds_u32(prmt(w1.y, lb, 0x7624u));
+    acc[7] += lds_u32(prmt(w0.y, lb, 0x7634u)) + lds_u32(prmt(w1.y, lb, 0x7634u));
 }
 
 __device__ __forceinline__ void flush(uint32_t (&acc)[kVec], int32_t (&s1)[kVec],
@@ -321,9 +364,15 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
 // behind, and the first S batches of the team's next frame are in flight while
 // the current frame's epilogue runs.  A thread whose frame or columns are out of
 // range issues no loads and skips the accumulation.
-template <int R, int S, bool SERVED>
+// NC > 0 fixes the row stride N at compile time (row offsets become load
+// immediates); NC = 0 reads it from the item.
+// one = true: the team takes frame f_begin alone (f_end is f_begin + 1, or
+// f_begin when it has nothing to do) -- teams of a CTA then work on different
+// items; otherwise the CTA's teams stride through [f_begin, f_end).
+template <int R, int S, bool SERVED, int NC, bool PF = true, int PD = 1>
 __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_t f_end,
-                                         uint32_t lb, TeamSmem &ts, int &parity)
+                                         uint32_t lb, TeamSmem &ts, int &parity,
+                                         bool one = false)
 {
     static_assert(R == 8 || R == 16, "rows per batch");
     static_assert((R * S) % kFlushRows == 0, "flush cadence");
@@ -333,26 +382,33 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
     const int lit = threadIdx.x & ((1 << team_log2) - 1);
     const int col0 = lit * kVec;
     const bool col_ok = col0 < it.N;
-    const int64_t N = it.N;
+    const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
     const int64_t fbytes = (int64_t)it.M * N;
     const int nb = it.M / R;
-    const int64_t kmax = (f_end - f_begin + T - 1) / T;
+    const int64_t fstride = one ? 1 : T;
+    const int64_t kmax = one ? 1 : (f_end - f_begin + T - 1) / T;
 
     uint2 buf[S][R];
-    int64_t frame = f_begin + team_idx;
+    int64_t frame = one ? f_begin : f_begin + team_idx;
     bool ok = col_ok && frame < f_end;
     const uint8_t *fp = it.in + frame * fbytes + col0;
     if (ok) {
 #pragma unroll
-        for (int j = 0; j < S; ++j)
+        for (int j = 0; j < S; ++j) {
+            if constexpr (NC > 0) {
+                load_rows_imm<NC>(buf[j], fp + (int64_t)j * R * NC,
+                                  std::make_integer_sequence<int, R>{});
+            } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                buf[j][r] = ldg_stream(fp + (int64_t)(j * R + r) * N);
+                for (int r = 0; r < R; ++r)
+                    buf[j][r] = ldg_stream(fp + (int64_t)(j * R + r) * N);
+            }
+        }
     }
 
     for (int64_t k = 0; k < kmax; ++k) {
         const bool fvalid = frame < f_end;
-        const int64_t nframe = frame + T;
+        const int64_t nframe = frame + fstride;
         const bool nok = col_ok && nframe < f_end;
         const uint8_t *nfp = it.in + nframe * fbytes + col0;
         uint32_t acc[kVec];
@@ -364,6 +420,26 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
             s2[j] = 0;
         }
         for (int jb = 0; jb < nb; jb += S) {
+            if (PF && lit == 0) {
+                // the S batches a later iteration will load, in this frame or,
+                // past its end, in the team's next frame
+                // PD iterations ahead: batches jb+(PD+1)S .. jb+(PD+2)S-1
+                const uint8_t *pp = nullptr;
+                const int ba = jb + (PD + 1) * S;
+                if (ba < nb) {
+                    if (ok)
+                        pp = fp + (int64_t)ba * R * N;
+                } else {
+                    const int b0 = ba - nb;
+                    if (nok && b0 + S <= nb)
+                        pp = nfp + (int64_t)b0 * R * N - col0;
+                }
+                if (pp) {
+                    const uint32_t total = (uint32_t)(S * R) * (uint32_t)N;
+                    for (uint32_t o = 0; o < total; o += 32768u)
+                        prefetch_l2(pp + o, total - o < 32768u ? total - o : 32768u);
+                }
+            }
             const bool same_frame = jb + S < nb;
             const uint8_t *pn = same_frame ? fp + (int64_t)(jb + S) * R * N : nfp;
             const bool lok = same_frame ? ok : nok;
@@ -371,15 +447,20 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
             for (int j = 0; j < S; ++j) {
                 if (ok) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        accum_row(buf[j][r], lb, acc);
+                    for (int r = 0; r < R; r += 2)
+                        accum_pair(buf[j][r], buf[j][r + 1], lb, acc);
                     if (((j + 1) * R) % kFlushRows == 0)
                         flush(acc, s1, s2);
                 }
                 if (lok) {
+                    if constexpr (NC > 0) {
+                        load_rows_imm<NC>(buf[j], pn + (int64_t)j * R * NC,
+                                          std::make_integer_sequence<int, R>{});
+                    } else {
 #pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        buf[j][r] = ldg_stream(pn + (int64_t)(j * R + r) * N);
+                        for (int r = 0; r < R; ++r)
+                            buf[j][r] = ldg_stream(pn + (int64_t)(j * R + r) * N);
+                    }
                 }
             }
         }
@@ -396,7 +477,8 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
 // fast path does not take; it is not tuned.
 template <bool SERVED>
 __device__ __forceinline__ void run_general(const Item &it, int64_t f_begin, int64_t f_end,
-                                            uint32_t lb, TeamSmem &ts, int &parity)
+                                            uint32_t lb, TeamSmem &ts, int &parity,
+                                            bool one = false)
 {
     const int team_log2 = it.team_log2;
     const int T = kThreads >> team_log2;
@@ -406,8 +488,9 @@ __device__ __forceinline__ void run_general(const Item &it, int64_t f_begin, int
     const int64_t N = it.N;
     const int M = it.M;
     const int64_t fbytes = (int64_t)M * N;
-    const int64_t kmax = (f_end - f_begin + T - 1) / T;
-    int64_t frame = f_begin + team_idx;
+    const int64_t fstride = one ? 1 : T;
+    const int64_t kmax = one ? 1 : (f_end - f_begin + T - 1) / T;
+    int64_t frame = one ? f_begin : f_begin + team_idx;
     for (int64_t k = 0; k < kmax; ++k) {
         const bool fvalid = frame < f_end;
         uint32_t acc[kVec];
@@ -442,7 +525,7 @@ __device__ __forceinline__ void run_general(const Item &it, int64_t f_begin, int
         }
         frame_epilogue<SERVED>(it, frame, fvalid, col0, lit, team_idx, parity, s1, s2, ts);
         parity ^= 1;
-        frame += T;
+        frame += fstride;
     }
 }
 

@@ -1,21 +1,26 @@
 // Continuous-batching serving loop.
 //
-// Streams are arrays (N inputs, M samples per frame) that submit frames as they
-// arrive.  sk_stream_submit copies the frame into the stream's page-locked
-// staging ring and queues it.  A launcher thread forms a batch from whatever is
-// queued -- the oldest frame of every stream that has one -- uploads those
-// frames into the streams' device rings (copy stream), and launches the fused
-// kernel over the batch (compute stream), without waiting for earlier batches:
-// up to kLaunchSlots batches are in flight, so frames that arrive while a batch
-// runs are admitted and launched behind it.  A completion thread waits for each
-// batch in launch order, hands sk and mask to the tickets and frees the ring
-// slots.  One frame per stream per batch plus in-order launches on one compute
-// stream keep each stream's running power state (SK_RUNNING_OFFSET) updated in
-// frame order.  Device memory per stream is admitted against the server's HBM
-// budget.
+// All streams share one arrival-ordered frame ring: page-locked host memory
+// mirrored by a device ring of the same size.  sk_stream_submit reserves the
+// next bytes of the ring, copies the frame there and marks it ready.  A
+// launcher thread takes the ready prefix of the ring -- stopping before a
+// second frame of a stream with running state, so each stream's state is
+// updated in frame order -- and launches it as one batch: one contiguous
+// host-to-device copy of the prefix (two when it wraps), one copy of the work
+// list, one kernel over every frame in it, one copy of the results back.  With
+// two launches in flight, the upload of the next batch overlaps the kernel of
+// the current one, and frames that arrive meanwhile join the batch after it.
+// A completion thread retires launches in order: it hands sk and mask to the
+// tickets, frees the ring bytes and records submit-to-result latency.
+//
+// Device memory: the ring takes half of the server's HBM budget (at most
+// 4 GiB); streams are admitted while their ring share (ring_frames frames) fits
+// the ring and their state and tables fit the other half.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -31,35 +36,36 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
-constexpr int kLaunchSlots = 4;
-constexpr int kMaxBatch = 1024;  // frames per launch
-
-struct Pending {
-    int32_t slot;
-    sk_ticket_t ticket;
-};
+constexpr int kLaunchSlots = 8;  // at most this many launches in flight
+constexpr int kMaxBatch = 1024;        // frames per launch
+constexpr uint64_t kAlign = 256;       // ring placement granularity
+constexpr size_t kMaxRing = (size_t)4 << 30;
 
 struct StreamRec {
     sk_stream_id id = -1;
     sk_plan_t plan = nullptr;
     int32_t N = 0, M = 0;
     int64_t fbytes = 0;
-    int32_t ring = 0;
-    uint8_t *h_stage = nullptr;  // pinned [ring][fbytes]
-    uint8_t *d_ring = nullptr;   // [ring][fbytes]
-    uint32_t *d_state = nullptr; // [N] when SK_RUNNING_OFFSET
+    int32_t ring_frames = 0;     // frames it may have outstanding
+    uint32_t *d_state = nullptr; // [N]
     bool stateful = false;
-    bool initialised = false;    // state holds a stream history
-    size_t hbm = 0;
-    int32_t next_slot = 0;
-    int32_t used = 0;            // queued + in flight
-    int64_t in_flight = 0;
-    std::deque<Pending> queue;
+    bool initialised = false;
+    size_t share = 0;            // ring bytes reserved
+    size_t small = 0;            // state + tables bytes
+    int32_t outstanding = 0;     // submitted, not yet retired
     bool closing = false;
 };
 
+struct Frame {
+    StreamRec *stream;
+    uint64_t off;   // monotonic ring offset
+    uint64_t size;  // bytes reserved (aligned)
+    sk_ticket_t ticket;
+    bool ready;
+    bool first;     // the stream's first frame with running state (set at launch)
+};
+
 struct TicketRec {
-    sk_stream_id stream;
     bool done = false;
     sk_status_t status = SK_OK;
     float sk = 0.0f;
@@ -67,27 +73,30 @@ struct TicketRec {
     Clock::time_point t_submit;
 };
 
-struct LaunchSlot {
+struct Launch {
     bool busy = false;
     int n = 0;
-    int tile = 0;
+    uint64_t end = 0;  // ring offset after its last frame
     std::vector<sk_ticket_t> tickets;
-    std::vector<sk_stream_id> streams;
-    // pinned host mirrors and device copies of the work list and results
-    Item *h_items = nullptr;
-    Chunk *h_chunks = nullptr;
-    int32_t *h_cta = nullptr;
-    float *h_sk = nullptr;
-    uint8_t *h_mask = nullptr;
-    Item *d_items = nullptr;
-    Chunk *d_chunks = nullptr;
-    int32_t *d_cta = nullptr;
-    float *d_sk = nullptr;
-    uint8_t *d_mask = nullptr;
-    int max_chunks = 0;
-    cudaEvent_t uploaded = nullptr;
-    cudaEvent_t done = nullptr;
+    std::vector<StreamRec *> streams;
+    // work block: items | chunks | cta (one copy); result block: sk | mask
+    uint8_t *h_work = nullptr, *d_work = nullptr;
+    uint8_t *h_res = nullptr, *d_res = nullptr;
+    cudaEvent_t uploaded = nullptr, done = nullptr;
+    // tracing (SK_SERVER_TRACE=1): timing events and host times of one launch
+    cudaEvent_t t_copy0 = nullptr, t_copy1 = nullptr, t_k0 = nullptr, t_k1 = nullptr;
+    Clock::time_point t_issue, t_issued;
+    uint64_t bytes = 0;
 };
+
+size_t round16(size_t v) { return (v + 15) / 16 * 16; }
+
+// Work block of one launch, packed: cta offsets | chunks | items.
+size_t work_bytes(int sms)
+{
+    return round16(sizeof(int32_t) * (sms + 1)) + round16(sizeof(Chunk) * (kMaxBatch + sms + 1)) +
+           sizeof(Item) * kMaxBatch;
+}
 
 }  // namespace
 
@@ -95,27 +104,32 @@ struct sk_server_s {
     int device = 0;
     int sms = 0;
     size_t budget = 0;
-    size_t in_use = 0;
+    size_t ring_cap = 0;
+    size_t ring_reserved = 0;  // sum of stream shares
+    size_t small_in_use = 0;   // sum of stream state + tables
+    uint8_t *h_ring = nullptr, *d_ring = nullptr;
+    uint64_t head = 0, tail = 0;  // monotonic byte offsets
     std::mutex mu;
-    std::condition_variable cv_work;   // launcher: queued frames or a free slot
-    std::condition_variable cv_flight; // completion thread: a launch in flight
-    std::condition_variable cv_done;   // waiters: a ticket finished
+    std::condition_variable cv_work, cv_flight, cv_done;
     bool stop = false;
     std::map<sk_stream_id, std::unique_ptr<StreamRec>> streams;
+    std::deque<Frame> fifo;  // submitted, not launched
     std::unordered_map<sk_ticket_t, TicketRec> tickets;
     sk_stream_id next_stream = 1;
     sk_ticket_t next_ticket = 1;
-    size_t rr = 0;  // round-robin start among streams
-    LaunchSlot slots[kLaunchSlots];
-    std::deque<int> flight;  // launch slots in launch order
+    Launch slots[kLaunchSlots];
+    int nslots = 2;  // launches allowed in flight (SK_SERVER_INFLIGHT, 1..8)
+    std::deque<int> flight;
     cudaStream_t s_copy = nullptr, s_compute = nullptr;
     std::thread launcher, completer;
-    // statistics
     int64_t frames_done = 0, frames_flagged = 0, launches = 0, rejected = 0;
     std::vector<double> lat_us;
     size_t lat_next = 0;
     sk_status_t fault = SK_OK;
     std::string fault_msg;
+    bool trace = false;
+    double tr_n = 0, tr_frames = 0, tr_bytes = 0, tr_host_issue = 0, tr_host_total = 0,
+           tr_copy = 0, tr_kernel = 0, tr_copy_to_kernel_end = 0;
 };
 
 static constexpr size_t kLatKeep = 1 << 20;
@@ -128,128 +142,156 @@ static void record_latency(sk_server_s *s, double us)
         s->lat_us[s->lat_next++ % kLatKeep] = us;
 }
 
-// Build and launch one batch from the queues (called with the lock held; the
-// CUDA calls are asynchronous).  Returns false when nothing was launched.
-static bool launch_batch(sk_server_s *s, int slot_idx)
+static void set_fault(sk_server_s *s, sk_status_t st, const char *msg)
 {
-    LaunchSlot &L = s->slots[slot_idx];
-    L.tickets.clear();
-    L.streams.clear();
-    std::vector<Item> items;
-    std::vector<StreamRec *> recs;
-    std::vector<int32_t> ring_slots;
-    const size_t ns = s->streams.size();
-    if (ns == 0)
-        return false;
-    std::vector<StreamRec *> order;
-    for (auto &kv : s->streams)
-        order.push_back(kv.second.get());
-    for (size_t j = 0; j < ns && (int)items.size() < kMaxBatch; ++j) {
-        StreamRec *r = order[(s->rr + j) % ns];
-        if (r->queue.empty())
-            continue;
-        Pending pd = r->queue.front();
-        r->queue.pop_front();
-        Item it = r->plan->item(r->d_ring + (int64_t)pd.slot * r->fbytes, 1);
-        const int k = (int)items.size();
-        it.sk = L.d_sk + k;
-        it.mask = L.d_mask + k;
+    if (s->fault == SK_OK) {
+        s->fault = st;
+        s->fault_msg = msg;
+    }
+}
+
+// Issue one batch (the lock is NOT held; `frames` were taken off the fifo).
+static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &frames)
+{
+    const int n = (int)frames.size();
+    std::vector<Item> items(n);
+    float *d_sk = (float *)L.d_res;
+    uint8_t *d_mask = L.d_res + sizeof(float) * n;
+    bool all_m32 = true;
+    for (int k = 0; k < n; ++k) {
+        const Frame &f = frames[k];
+        StreamRec *r = f.stream;
+        Item it = r->plan->item(s->d_ring + (f.off % s->ring_cap), 1);
+        it.sk = d_sk + k;
+        it.mask = d_mask + k;
         if (r->stateful) {
             it.state = r->d_state;
-            it.state_init = r->initialised ? 0 : 1;
-            r->initialised = true;
+            it.state_init = f.first ? 1 : 0;
         }
-        items.push_back(it);
-        recs.push_back(r);
-        ring_slots.push_back(pd.slot);
-        L.tickets.push_back(pd.ticket);
-        L.streams.push_back(r->id);
-        r->in_flight += 1;
-    }
-    s->rr = (s->rr + 1) % ns;
-    if (items.empty())
-        return false;
-    bool all_m32 = true;
-    for (const Item &it : items)
         all_m32 = all_m32 && (it.M % 32 == 0);
-    L.tile = pick_tile(16, all_m32);
-    // schedule over at most one CTA per frame-round, at most one per SM
-    int rounds = 0;
-    for (const Item &it : items)
-        rounds += 1;
-    const int grid = std::min(s->sms, rounds);
+        items[k] = it;
+    }
     std::vector<Chunk> chunks;
     std::vector<int32_t> cta;
-    build_schedule(items, grid, chunks, cta);
-    L.n = (int)items.size();
-    memcpy(L.h_items, items.data(), sizeof(Item) * items.size());
-    memcpy(L.h_chunks, chunks.data(), sizeof(Chunk) * chunks.size());
-    memcpy(L.h_cta, cta.data(), sizeof(int32_t) * cta.size());
+    std::vector<int32_t> perm;
+    const int grid = build_item_schedule(items, s->sms, chunks, cta, perm);
+    // result slot k now belongs to the frame items[k] came from
+    {
+        std::vector<sk_ticket_t> tk(n);
+        std::vector<StreamRec *> sr(n);
+        for (int k = 0; k < n; ++k) {
+            tk[k] = L.tickets[perm[k]];
+            sr[k] = L.streams[perm[k]];
+            items[k].sk = d_sk + k;
+            items[k].mask = d_mask + k;
+        }
+        L.tickets.swap(tk);
+        L.streams.swap(sr);
+    }
+    const size_t o_chunks = round16(sizeof(int32_t) * cta.size());
+    const size_t o_items = o_chunks + round16(sizeof(Chunk) * chunks.size());
+    const size_t used = o_items + sizeof(Item) * n;
+    memcpy(L.h_work, cta.data(), sizeof(int32_t) * cta.size());
+    memcpy(L.h_work + o_chunks, chunks.data(), sizeof(Chunk) * chunks.size());
+    memcpy(L.h_work + o_items, items.data(), sizeof(Item) * n);
+    // frames: one contiguous range of the ring, split at the wrap point
+    const uint64_t a = frames.front().off;
+    const uint64_t b = frames.back().off + frames.back().size;
     cudaError_t e = cudaSuccess;
-    for (size_t k = 0; k < items.size() && e == cudaSuccess; ++k) {
-        StreamRec *r = recs[k];
-        e = cudaMemcpyAsync(r->d_ring + (int64_t)ring_slots[k] * r->fbytes,
-                            r->h_stage + (int64_t)ring_slots[k] * r->fbytes, (size_t)r->fbytes,
-                            cudaMemcpyHostToDevice, s->s_copy);
+    if (s->trace)
+        e = cudaEventRecord(L.t_copy0, s->s_copy);
+    L.bytes = b - a;
+    uint64_t pos = a;
+    while (pos < b && e == cudaSuccess) {
+        const uint64_t ra = pos % s->ring_cap;
+        const uint64_t len = std::min<uint64_t>(b - pos, s->ring_cap - ra);
+        e = cudaMemcpyAsync(s->d_ring + ra, s->h_ring + ra, len, cudaMemcpyHostToDevice,
+                            s->s_copy);
+        pos += len;
     }
     if (e == cudaSuccess)
         e = cudaEventRecord(L.uploaded, s->s_copy);
+    if (e == cudaSuccess && s->trace)
+        e = cudaEventRecord(L.t_copy1, s->s_copy);
     if (e == cudaSuccess)
         e = cudaStreamWaitEvent(s->s_compute, L.uploaded, 0);
+    if (e == cudaSuccess && s->trace)
+        e = cudaEventRecord(L.t_k0, s->s_compute);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(L.d_items, L.h_items, sizeof(Item) * items.size(),
-                            cudaMemcpyHostToDevice, s->s_compute);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(L.d_chunks, L.h_chunks, sizeof(Chunk) * chunks.size(),
-                            cudaMemcpyHostToDevice, s->s_compute);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(L.d_cta, L.h_cta, sizeof(int32_t) * cta.size(),
-                            cudaMemcpyHostToDevice, s->s_compute);
+        e = cudaMemcpyAsync(L.d_work, L.h_work, used, cudaMemcpyHostToDevice, s->s_compute);
     sk_status_t st = SK_OK;
     if (e == cudaSuccess)
-        st = launch_schedule(L.d_items, L.d_chunks, L.d_cta, grid, L.tile, true, s->device,
-                             s->s_compute);
+        st = launch_schedule((const Item *)(L.d_work + o_items),
+                             (const Chunk *)(L.d_work + o_chunks), (const int32_t *)L.d_work,
+                             grid, pick_tile(16, all_m32), true, s->device, s->s_compute);
+    if (e == cudaSuccess && st == SK_OK && s->trace)
+        e = cudaEventRecord(L.t_k1, s->s_compute);
     if (e == cudaSuccess && st == SK_OK)
-        e = cudaMemcpyAsync(L.h_sk, L.d_sk, sizeof(float) * items.size(), cudaMemcpyDeviceToHost,
-                            s->s_compute);
-    if (e == cudaSuccess && st == SK_OK)
-        e = cudaMemcpyAsync(L.h_mask, L.d_mask, items.size(), cudaMemcpyDeviceToHost,
-                            s->s_compute);
+        e = cudaMemcpyAsync(L.h_res, L.d_res, (sizeof(float) + 1) * (size_t)n,
+                            cudaMemcpyDeviceToHost, s->s_compute);
     if (e == cudaSuccess && st == SK_OK)
         e = cudaEventRecord(L.done, s->s_compute);
     if (e != cudaSuccess || st != SK_OK) {
-        s->fault = e != cudaSuccess ? SK_ERR_CUDA : st;
-        s->fault_msg = e != cudaSuccess ? cudaGetErrorString(e) : "launch failed";
+        std::lock_guard<std::mutex> g(s->mu);
+        set_fault(s, e != cudaSuccess ? SK_ERR_CUDA : st,
+                  e != cudaSuccess ? cudaGetErrorString(e) : "batch launch failed");
     }
-    L.busy = true;
-    s->launches += 1;
-    s->flight.push_back(slot_idx);
-    return true;
 }
 
 static void launcher_main(sk_server_s *s)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
-    while (!s->stop) {
-        int free_slot = -1;
-        for (int i = 0; i < kLaunchSlots; ++i)
+    for (;;) {
+        int slot = -1;
+        for (int i = 0; i < s->nslots; ++i)
             if (!s->slots[i].busy) {
-                free_slot = i;
+                slot = i;
                 break;
             }
-        bool any = false;
-        for (auto &kv : s->streams)
-            if (!kv.second->queue.empty()) {
-                any = true;
-                break;
-            }
-        if (free_slot < 0 || !any || s->fault != SK_OK) {
+        const bool ready = !s->fifo.empty() && s->fifo.front().ready;
+        if (s->stop)
+            return;
+        if (slot < 0 || !ready || s->fault != SK_OK) {
             s->cv_work.wait(lk);
             continue;
         }
-        if (launch_batch(s, free_slot))
-            s->cv_flight.notify_one();
+        // ready prefix, at most one frame per stream with running state
+        std::vector<Frame> batch;
+        std::vector<StreamRec *> seen;
+        while (!s->fifo.empty() && (int)batch.size() < kMaxBatch) {
+            const Frame &f = s->fifo.front();
+            if (!f.ready)
+                break;
+            if (f.stream->stateful &&
+                std::find(seen.begin(), seen.end(), f.stream) != seen.end())
+                break;
+            batch.push_back(f);
+            if (f.stream->stateful) {
+                seen.push_back(f.stream);
+                batch.back().first = !f.stream->initialised;
+                f.stream->initialised = true;
+            }
+            s->fifo.pop_front();
+        }
+        Launch &L = s->slots[slot];
+        L.busy = true;
+        L.n = (int)batch.size();
+        L.end = batch.back().off + batch.back().size;
+        L.tickets.clear();
+        L.streams.clear();
+        for (const Frame &f : batch) {
+            L.tickets.push_back(f.ticket);
+            L.streams.push_back(f.stream);
+        }
+        s->launches += 1;
+        lk.unlock();
+        L.t_issue = Clock::now();
+        issue_batch(s, L, batch);
+        L.t_issued = Clock::now();
+        lk.lock();
+        s->flight.push_back(slot);
+        s->cv_flight.notify_one();
     }
 }
 
@@ -260,36 +302,47 @@ static void completer_main(sk_server_s *s)
     for (;;) {
         while (s->flight.empty() && !s->stop)
             s->cv_flight.wait(lk);
-        if (s->flight.empty() && s->stop)
+        if (s->flight.empty())
             return;
         const int idx = s->flight.front();
-        LaunchSlot &L = s->slots[idx];
+        Launch &L = s->slots[idx];
         lk.unlock();
         cudaError_t e = cudaEventSynchronize(L.done);
         const Clock::time_point now = Clock::now();
         lk.lock();
         s->flight.pop_front();
-        if (e != cudaSuccess && s->fault == SK_OK) {
-            s->fault = SK_ERR_CUDA;
-            s->fault_msg = cudaGetErrorString(e);
-        }
+        if (e != cudaSuccess)
+            set_fault(s, SK_ERR_CUDA, cudaGetErrorString(e));
+        const float *h_sk = (const float *)L.h_res;
+        const uint8_t *h_mask = L.h_res + sizeof(float) * L.n;
         for (int k = 0; k < L.n; ++k) {
             auto t = s->tickets.find(L.tickets[k]);
             if (t != s->tickets.end()) {
                 t->second.done = true;
                 t->second.status = s->fault;
-                t->second.sk = L.h_sk[k];
-                t->second.mask = L.h_mask[k];
+                t->second.sk = h_sk[k];
+                t->second.mask = h_mask[k];
                 record_latency(s, std::chrono::duration<double, std::micro>(
                                       now - t->second.t_submit).count());
             }
             s->frames_done += 1;
-            s->frames_flagged += L.h_mask[k] ? 1 : 0;
-            auto r = s->streams.find(L.streams[k]);
-            if (r != s->streams.end()) {
-                r->second->in_flight -= 1;
-                r->second->used -= 1;
-            }
+            s->frames_flagged += h_mask[k] ? 1 : 0;
+            L.streams[k]->outstanding -= 1;
+        }
+        s->tail = std::max(s->tail, L.end);
+        if (s->trace && e == cudaSuccess) {
+            float c = 0, k = 0, ck = 0;
+            cudaEventElapsedTime(&c, L.t_copy0, L.t_copy1);
+            cudaEventElapsedTime(&k, L.t_k0, L.t_k1);
+            cudaEventElapsedTime(&ck, L.t_copy0, L.t_k1);
+            s->tr_n += 1;
+            s->tr_frames += L.n;
+            s->tr_bytes += (double)L.bytes;
+            s->tr_copy += c * 1e3;
+            s->tr_kernel += k * 1e3;
+            s->tr_copy_to_kernel_end += ck * 1e3;
+            s->tr_host_issue += std::chrono::duration<double, std::micro>(L.t_issued - L.t_issue).count();
+            s->tr_host_total += std::chrono::duration<double, std::micro>(now - L.t_issue).count();
         }
         L.busy = false;
         L.n = 0;
@@ -298,28 +351,23 @@ static void completer_main(sk_server_s *s)
     }
 }
 
-static void free_slot_buffers(LaunchSlot &L)
+static void free_launch(Launch &L)
 {
-    cudaFreeHost(L.h_items);
-    cudaFreeHost(L.h_chunks);
-    cudaFreeHost(L.h_cta);
-    cudaFreeHost(L.h_sk);
-    cudaFreeHost(L.h_mask);
-    cudaFree(L.d_items);
-    cudaFree(L.d_chunks);
-    cudaFree(L.d_cta);
-    cudaFree(L.d_sk);
-    cudaFree(L.d_mask);
+    cudaFreeHost(L.h_work);
+    cudaFreeHost(L.h_res);
+    cudaFree(L.d_work);
+    cudaFree(L.d_res);
     if (L.uploaded)
         cudaEventDestroy(L.uploaded);
     if (L.done)
         cudaEventDestroy(L.done);
+    for (cudaEvent_t ev : {L.t_copy0, L.t_copy1, L.t_k0, L.t_k1})
+        if (ev)
+            cudaEventDestroy(ev);
 }
 
 static void free_stream(StreamRec *r)
 {
-    cudaFreeHost(r->h_stage);
-    cudaFree(r->d_ring);
     cudaFree(r->d_state);
     sk_plan_destroy(r->plan);
 }
@@ -332,33 +380,43 @@ extern "C" sk_status_t sk_server_create(int device, size_t hbm_budget_bytes, sk_
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return set_error(SK_ERR_INVALID_ARG, "sk_server_create: device %d not present", device);
+    if (hbm_budget_bytes < ((size_t)2 << 20))
+        return set_error(SK_ERR_INVALID_ARG, "sk_server_create: budget below 2 MiB");
     sk_server_s *s = new (std::nothrow) sk_server_s();
     if (!s)
         return set_error(SK_ERR_OOM, "host allocation");
     s->device = device;
     s->budget = hbm_budget_bytes;
+    s->ring_cap = std::min(kMaxRing, hbm_budget_bytes / 2) / kAlign * kAlign;
     s->sms = sm_count(device);
+    if (const char *v = getenv("SK_SERVER_TRACE"))
+        s->trace = atoi(v) != 0;
+    if (const char *v = getenv("SK_SERVER_INFLIGHT")) {
+        const int k = atoi(v);
+        if (k >= 1 && k <= kLaunchSlots)
+            s->nslots = k;
+    }
     sk_status_t st = SK_OK;
     {
         DeviceGuard dg(device);
-        const int max_chunks = kMaxBatch + s->sms + 1;
-        for (int i = 0; i < kLaunchSlots && st == SK_OK; ++i) {
-            LaunchSlot &L = s->slots[i];
-            L.max_chunks = max_chunks;
-            if (cudaHostAlloc(&L.h_items, sizeof(Item) * kMaxBatch, 0) != cudaSuccess ||
-                cudaHostAlloc(&L.h_chunks, sizeof(Chunk) * max_chunks, 0) != cudaSuccess ||
-                cudaHostAlloc(&L.h_cta, sizeof(int32_t) * (s->sms + 1), 0) != cudaSuccess ||
-                cudaHostAlloc(&L.h_sk, sizeof(float) * kMaxBatch, 0) != cudaSuccess ||
-                cudaHostAlloc(&L.h_mask, kMaxBatch, 0) != cudaSuccess ||
-                cudaMalloc(&L.d_items, sizeof(Item) * kMaxBatch) != cudaSuccess ||
-                cudaMalloc(&L.d_chunks, sizeof(Chunk) * max_chunks) != cudaSuccess ||
-                cudaMalloc(&L.d_cta, sizeof(int32_t) * (s->sms + 1)) != cudaSuccess ||
-                cudaMalloc(&L.d_sk, sizeof(float) * kMaxBatch) != cudaSuccess ||
-                cudaMalloc(&L.d_mask, kMaxBatch) != cudaSuccess)
+        if (cudaHostAlloc(&s->h_ring, s->ring_cap, 0) != cudaSuccess ||
+            cudaMalloc(&s->d_ring, s->ring_cap) != cudaSuccess)
+            st = set_error(SK_ERR_OOM, "server frame ring (%zu bytes)", s->ring_cap);
+        const size_t wb = work_bytes(s->sms), rb = sizeof(float) * kMaxBatch + kMaxBatch;
+        for (int i = 0; i < s->nslots && st == SK_OK; ++i) {
+            Launch &L = s->slots[i];
+            if (cudaHostAlloc(&L.h_work, wb, 0) != cudaSuccess ||
+                cudaHostAlloc(&L.h_res, rb, 0) != cudaSuccess ||
+                cudaMalloc(&L.d_work, wb) != cudaSuccess || cudaMalloc(&L.d_res, rb) != cudaSuccess)
                 st = set_error(SK_ERR_OOM, "server launch buffers");
             else if (cudaEventCreateWithFlags(&L.uploaded, cudaEventDisableTiming) != cudaSuccess ||
                      cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess)
                 st = set_error(SK_ERR_CUDA, "server events");
+            else if (s->trace && (cudaEventCreate(&L.t_copy0) != cudaSuccess ||
+                                  cudaEventCreate(&L.t_copy1) != cudaSuccess ||
+                                  cudaEventCreate(&L.t_k0) != cudaSuccess ||
+                                  cudaEventCreate(&L.t_k1) != cudaSuccess))
+                st = set_error(SK_ERR_CUDA, "server trace events");
         }
         if (st == SK_OK &&
             (cudaStreamCreateWithFlags(&s->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
@@ -368,7 +426,9 @@ extern "C" sk_status_t sk_server_create(int device, size_t hbm_budget_bytes, sk_
             st = ensure_kernel_attrs(device);
         if (st != SK_OK) {
             for (auto &L : s->slots)
-                free_slot_buffers(L);
+                free_launch(L);
+            cudaFreeHost(s->h_ring);
+            cudaFree(s->d_ring);
             if (s->s_copy)
                 cudaStreamDestroy(s->s_copy);
             if (s->s_compute)
@@ -397,6 +457,15 @@ extern "C" sk_status_t sk_server_destroy(sk_server_t s)
     s->cv_flight.notify_all();
     s->launcher.join();
     s->completer.join();
+    if (s->trace && s->tr_n > 0)
+        fprintf(stderr,
+                "sk_server trace: %.0f launches, %.2f frames and %.0f KB each; host issue %.1f us, "
+                "issue->retire %.1f us, upload %.1f us (%.1f GB/s), kernel %.1f us, "
+                "upload start->kernel end %.1f us\n",
+                s->tr_n, s->tr_frames / s->tr_n, s->tr_bytes / s->tr_n / 1024.0,
+                s->tr_host_issue / s->tr_n, s->tr_host_total / s->tr_n, s->tr_copy / s->tr_n,
+                s->tr_bytes / (s->tr_copy * 1e3 + 1e-9), s->tr_kernel / s->tr_n,
+                s->tr_copy_to_kernel_end / s->tr_n);
     {
         DeviceGuard dg(s->device);
         cudaStreamSynchronize(s->s_compute);
@@ -404,13 +473,17 @@ extern "C" sk_status_t sk_server_destroy(sk_server_t s)
         for (auto &kv : s->streams)
             free_stream(kv.second.get());
         for (auto &L : s->slots)
-            free_slot_buffers(L);
+            free_launch(L);
+        cudaFreeHost(s->h_ring);
+        cudaFree(s->d_ring);
         cudaStreamDestroy(s->s_copy);
         cudaStreamDestroy(s->s_compute);
     }
     delete s;
     return SK_OK;
 }
+
+static uint64_t frame_span(int64_t fbytes) { return ((uint64_t)fbytes + kAlign - 1) / kAlign * kAlign; }
 
 extern "C" sk_status_t sk_stream_open(sk_server_t s, const sk_params_t *params,
                                       int32_t ring_frames, sk_stream_id *out)
@@ -422,18 +495,24 @@ extern "C" sk_status_t sk_stream_open(sk_server_t s, const sk_params_t *params,
         return set_error(SK_ERR_INVALID_ARG, "sk_stream_open: ring_frames outside 1..65536");
     if (params->layout != SK_LAYOUT_TIME_MAJOR)
         return set_error(SK_ERR_UNSUPPORTED, "sk_stream_open: served streams are time-major");
+    if (params->n_inputs < 1 || params->n_inputs > SK_MAX_INPUTS || params->n_time < 2 ||
+        params->n_time > SK_MAX_TIME)
+        return set_error(SK_ERR_INVALID_ARG, "sk_stream_open: N or M out of range");
     const int64_t fbytes = (int64_t)params->n_time * params->n_inputs;
-    const size_t need = (size_t)fbytes * ring_frames + sizeof(uint32_t) * params->n_inputs +
-                        sizeof(int64_t) * (2 * (params->n_inputs + 1) + SK_OFFSET_BUCKETS) +
-                        sizeof(float) * (params->n_inputs + 1);
+    const size_t share = (size_t)frame_span(fbytes) * ring_frames;
+    const size_t small = sizeof(uint32_t) * params->n_inputs +
+                         sizeof(int64_t) * (2 * (params->n_inputs + 1) + SK_OFFSET_BUCKETS) +
+                         sizeof(float) * (params->n_inputs + 1);
     {
         std::lock_guard<std::mutex> g(s->mu);
-        if (s->in_use + need > s->budget) {
+        if (s->ring_reserved + share > s->ring_cap ||
+            s->small_in_use + small > s->budget - s->ring_cap) {
             s->rejected += 1;
-            return set_error(SK_ERR_BUSY, "sk_stream_open: %zu bytes over the HBM budget",
-                             s->in_use + need - s->budget);
+            return set_error(SK_ERR_BUSY, "sk_stream_open: no room (ring share %zu of %zu free)",
+                             share, s->ring_cap - s->ring_reserved);
         }
-        s->in_use += need;  // reserve
+        s->ring_reserved += share;
+        s->small_in_use += small;
     }
     auto r = std::make_unique<StreamRec>();
     sk_status_t st = sk_plan_create(params, s->device, &r->plan);
@@ -442,17 +521,17 @@ extern "C" sk_status_t sk_stream_open(sk_server_t s, const sk_params_t *params,
         r->N = params->n_inputs;
         r->M = params->n_time;
         r->fbytes = fbytes;
-        r->ring = ring_frames;
+        r->ring_frames = ring_frames;
         r->stateful = (params->flags & SK_RUNNING_OFFSET) != 0;
-        r->hbm = need;
-        if (cudaHostAlloc(&r->h_stage, (size_t)fbytes * ring_frames, 0) != cudaSuccess ||
-            cudaMalloc(&r->d_ring, (size_t)fbytes * ring_frames) != cudaSuccess ||
-            cudaMalloc(&r->d_state, sizeof(uint32_t) * r->N) != cudaSuccess)
-            st = set_error(SK_ERR_OOM, "sk_stream_open: ring or state allocation");
+        r->share = share;
+        r->small = small;
+        if (cudaMalloc(&r->d_state, sizeof(uint32_t) * r->N) != cudaSuccess)
+            st = set_error(SK_ERR_OOM, "sk_stream_open: state allocation");
     }
     std::lock_guard<std::mutex> g(s->mu);
     if (st != SK_OK) {
-        s->in_use -= need;
+        s->ring_reserved -= share;
+        s->small_in_use -= small;
         if (r->plan)
             free_stream(r.get());
         return st;
@@ -469,6 +548,7 @@ extern "C" sk_status_t sk_stream_submit(sk_server_t s, sk_stream_id id, const ui
     if (!s || !frame || !ticket)
         return set_error(SK_ERR_INVALID_ARG, "sk_stream_submit: null argument");
     (void)frame_index;
+    const Clock::time_point t0 = Clock::now();
     std::unique_lock<std::mutex> lk(s->mu);
     if (s->fault != SK_OK)
         return set_error(s->fault, "server fault: %s", s->fault_msg.c_str());
@@ -478,28 +558,36 @@ extern "C" sk_status_t sk_stream_submit(sk_server_t s, sk_stream_id id, const ui
     StreamRec *r = it->second.get();
     if (r->closing)
         return set_error(SK_ERR_CLOSED, "sk_stream_submit: stream %d closing", id);
-    if (r->used >= r->ring) {
+    if (r->outstanding >= r->ring_frames) {
         s->rejected += 1;
-        return set_error(SK_ERR_BUSY, "sk_stream_submit: ring of stream %d full", id);
+        return set_error(SK_ERR_BUSY, "sk_stream_submit: stream %d has %d frames outstanding",
+                         id, r->outstanding);
     }
-    const int32_t slot = r->next_slot;
-    r->next_slot = (r->next_slot + 1) % r->ring;
-    r->used += 1;
+    const uint64_t size = frame_span(r->fbytes);
+    uint64_t off = s->head;
+    if (off % s->ring_cap + size > s->ring_cap)  // do not straddle the wrap point
+        off = (off / s->ring_cap + 1) * s->ring_cap;
+    if (off + size - s->tail > s->ring_cap) {
+        s->rejected += 1;
+        return set_error(SK_ERR_BUSY, "sk_stream_submit: frame ring full");
+    }
+    s->head = off + size;
+    r->outstanding += 1;
     const sk_ticket_t t = s->next_ticket++;
     TicketRec tr;
-    tr.stream = id;
-    tr.t_submit = Clock::now();
+    tr.t_submit = t0;
     s->tickets.emplace(t, tr);
-    // the slot is ours until its launch completes: copy outside the lock
-    uint8_t *dst = r->h_stage + (int64_t)slot * r->fbytes;
+    s->fifo.push_back(Frame{r, off, size, t, false, false});
+    uint8_t *dst = s->h_ring + off % s->ring_cap;
     const int64_t fb = r->fbytes;
     lk.unlock();
-    memcpy(dst, frame, (size_t)fb);
+    memcpy(dst, frame, (size_t)fb);  // the reserved bytes are ours until retired
     lk.lock();
-    auto it2 = s->streams.find(id);
-    if (it2 == s->streams.end())
-        return set_error(SK_ERR_CLOSED, "sk_stream_submit: stream %d closed", id);
-    it2->second->queue.push_back(Pending{slot, t});
+    for (auto f = s->fifo.rbegin(); f != s->fifo.rend(); ++f)
+        if (f->ticket == t) {
+            f->ready = true;
+            break;
+        }
     *ticket = t;
     lk.unlock();
     s->cv_work.notify_one();
@@ -512,8 +600,7 @@ extern "C" sk_status_t sk_ticket_wait(sk_server_t s, sk_ticket_t ticket, int64_t
     if (!s)
         return set_error(SK_ERR_INVALID_ARG, "sk_ticket_wait: server is NULL");
     std::unique_lock<std::mutex> lk(s->mu);
-    auto it = s->tickets.find(ticket);
-    if (it == s->tickets.end())
+    if (s->tickets.find(ticket) == s->tickets.end())
         return set_error(SK_ERR_INVALID_ARG, "sk_ticket_wait: unknown ticket %lld",
                          (long long)ticket);
     auto ready = [&] {
@@ -525,7 +612,7 @@ extern "C" sk_status_t sk_ticket_wait(sk_server_t s, sk_ticket_t ticket, int64_t
     else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready))
         return set_error(SK_ERR_TIMEOUT, "sk_ticket_wait: ticket %lld not done",
                          (long long)ticket);
-    it = s->tickets.find(ticket);
+    auto it = s->tickets.find(ticket);
     if (it == s->tickets.end())
         return set_error(SK_ERR_INVALID_ARG, "sk_ticket_wait: ticket gone");
     const TicketRec tr = it->second;
@@ -542,7 +629,7 @@ extern "C" sk_status_t sk_ticket_wait(sk_server_t s, sk_ticket_t ticket, int64_t
 static bool stream_idle(sk_server_s *s, sk_stream_id id)
 {
     auto it = s->streams.find(id);
-    return it == s->streams.end() || it->second->used == 0;
+    return it == s->streams.end() || it->second->outstanding == 0;
 }
 
 extern "C" sk_status_t sk_stream_drain(sk_server_t s, sk_stream_id id, int64_t timeout_us)
@@ -579,7 +666,7 @@ extern "C" sk_status_t sk_stream_get_state(sk_server_t s, sk_stream_id id, void 
     }
     if (*len < need)
         return set_error(SK_ERR_INVALID_ARG, "sk_stream_get_state: need %zu bytes", need);
-    if (r->used != 0)
+    if (r->outstanding != 0)
         return set_error(SK_ERR_BUSY, "sk_stream_get_state: stream %d not drained", id);
     uint32_t *u = (uint32_t *)buf;
     u[0] = r->initialised ? 1u : 0u;
@@ -605,7 +692,7 @@ extern "C" sk_status_t sk_stream_set_state(sk_server_t s, sk_stream_id id, const
     const uint32_t *u = (const uint32_t *)buf;
     if (len != sizeof(uint32_t) * (2 + (size_t)r->N) || u[1] != (uint32_t)r->N || u[0] > 1)
         return set_error(SK_ERR_INVALID_ARG, "sk_stream_set_state: state of another shape");
-    if (r->used != 0)
+    if (r->outstanding != 0)
         return set_error(SK_ERR_BUSY, "sk_stream_set_state: stream %d not drained", id);
     DeviceGuard dg(s->device);
     cudaError_t e = cudaMemcpy(r->d_state, u + 2, sizeof(uint32_t) * r->N, cudaMemcpyHostToDevice);
@@ -624,17 +711,15 @@ extern "C" sk_status_t sk_stream_close(sk_server_t s, sk_stream_id id)
     if (it == s->streams.end())
         return set_error(SK_ERR_CLOSED, "sk_stream_close: unknown or closed stream %d", id);
     it->second->closing = true;
-    // in-flight launches reference the ring and state: wait for them (bounded)
+    // launches in flight reference its state: wait for them (bounded)
     bool idle = s->cv_done.wait_for(lk, std::chrono::seconds(30),
                                     [&] { return stream_idle(s, id) || s->fault != SK_OK; });
     if (!idle)
         return set_error(SK_ERR_TIMEOUT, "sk_stream_close: stream %d still busy", id);
     std::unique_ptr<StreamRec> r = std::move(s->streams[id]);
     s->streams.erase(id);
-    s->in_use -= r->hbm;
-    // drop its uncollected tickets of frames never launched
-    for (const Pending &p : r->queue)
-        s->tickets.erase(p.ticket);
+    s->ring_reserved -= r->share;
+    s->small_in_use -= r->small;
     lk.unlock();
     DeviceGuard dg(s->device);
     cudaStreamSynchronize(s->s_compute);
@@ -653,7 +738,7 @@ extern "C" sk_status_t sk_server_stats(sk_server_t s, sk_server_stats_t *out)
         out->frames_flagged = s->frames_flagged;
         out->launches = s->launches;
         out->rejected = s->rejected;
-        out->hbm_in_use = s->in_use;
+        out->hbm_in_use = s->ring_cap + s->small_in_use;
         lat = s->lat_us;
     }
     out->latency_p50_us = 0.0;
@@ -662,6 +747,120 @@ extern "C" sk_status_t sk_server_stats(sk_server_t s, sk_server_stats_t *out)
         std::sort(lat.begin(), lat.end());
         out->latency_p50_us = lat[(size_t)(0.50 * (lat.size() - 1))];
         out->latency_p99_us = lat[(size_t)(0.99 * (lat.size() - 1))];
+    }
+    return SK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Load generator: replays frames into open streams from several submitter
+// threads, paced at a cadence with exponential jitter or flat out.
+// ---------------------------------------------------------------------------
+#include <random>
+
+extern "C" sk_status_t sk_server_replay(sk_server_t s, const sk_replay_t *rp,
+                                        sk_replay_result_t *out)
+{
+    if (!s || !rp || !out || rp->n_streams <= 0 || !rp->streams || !rp->frames ||
+        !rp->pool_frames || rp->frames_per_stream < 0 || rp->threads <= 0 ||
+        rp->threads > 256 || !(rp->cadence_s >= 0.0))
+        return set_error(SK_ERR_INVALID_ARG, "sk_server_replay: bad arguments");
+    std::vector<int64_t> fbytes(rp->n_streams);
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        for (int j = 0; j < rp->n_streams; ++j) {
+            auto it = s->streams.find(rp->streams[j]);
+            if (it == s->streams.end() || rp->pool_frames[j] <= 0 || !rp->frames[j])
+                return set_error(SK_ERR_INVALID_ARG, "sk_server_replay: stream %d", j);
+            fbytes[j] = it->second->fbytes;
+        }
+        s->lat_us.clear();
+        s->lat_next = 0;
+    }
+    sk_server_stats_t before;
+    sk_server_stats(s, &before);
+    const int nt = rp->threads;
+    std::vector<std::vector<double>> sub_us(nt);
+    std::vector<int64_t> retries(nt, 0);
+    std::vector<sk_status_t> status(nt, SK_OK);
+    const Clock::time_point t0 = Clock::now();
+    auto worker = [&](int w) {
+        std::mt19937_64 rng(rp->seed * 1000003ull + (uint64_t)w);
+        std::exponential_distribution<double> jit(rp->jitter_mean_s > 0 ? 1.0 / rp->jitter_mean_s
+                                                                         : 1.0);
+        struct Ev {
+            double t;
+            int j;
+            int64_t k;
+        };
+        std::vector<Ev> sched;
+        for (int j = w; j < rp->n_streams; j += nt)
+            for (int64_t k = 0; k < rp->frames_per_stream; ++k)
+                sched.push_back(Ev{k * rp->cadence_s + (rp->jitter_mean_s > 0 ? jit(rng) : 0.0),
+                                   j, k});
+        std::sort(sched.begin(), sched.end(), [](const Ev &a, const Ev &b) { return a.t < b.t; });
+        std::vector<std::deque<sk_ticket_t>> pend(rp->n_streams);
+        for (const Ev &e : sched) {
+            if (rp->paced)
+                while (std::chrono::duration<double>(Clock::now() - t0).count() < e.t) {
+                }
+            const uint8_t *fr = rp->frames[e.j] + (e.k % rp->pool_frames[e.j]) * fbytes[e.j];
+            for (;;) {
+                sk_ticket_t t;
+                const Clock::time_point a = Clock::now();
+                sk_status_t st = sk_stream_submit(s, rp->streams[e.j], fr, e.k, &t);
+                sub_us[w].push_back(std::chrono::duration<double, std::micro>(Clock::now() - a).count());
+                if (st == SK_OK) {
+                    pend[e.j].push_back(t);
+                    break;
+                }
+                if (st != SK_ERR_BUSY || pend[e.j].empty()) {
+                    status[w] = st;
+                    return;
+                }
+                retries[w] += 1;
+                sk_ticket_wait(s, pend[e.j].front(), -1, nullptr, nullptr);
+                pend[e.j].pop_front();
+            }
+            // collect results lazily, keeping at most half of a small window open
+            while (pend[e.j].size() > 8) {
+                sk_ticket_wait(s, pend[e.j].front(), -1, nullptr, nullptr);
+                pend[e.j].pop_front();
+            }
+        }
+        for (auto &q : pend)
+            for (sk_ticket_t t : q)
+                sk_ticket_wait(s, t, -1, nullptr, nullptr);
+    };
+    std::vector<std::thread> th;
+    for (int w = 0; w < nt; ++w)
+        th.emplace_back(worker, w);
+    for (auto &t : th)
+        t.join();
+    const double wall = std::chrono::duration<double>(Clock::now() - t0).count();
+    for (int w = 0; w < nt; ++w)
+        if (status[w] != SK_OK)
+            return set_error(status[w], "sk_server_replay: submit failed: %s", sk_last_error());
+    sk_server_stats_t after;
+    sk_server_stats(s, &after);
+    std::vector<double> all;
+    for (auto &v : sub_us)
+        all.insert(all.end(), v.begin(), v.end());
+    std::sort(all.begin(), all.end());
+    memset(out, 0, sizeof *out);
+    out->wall_s = wall;
+    out->frames = after.frames_done - before.frames_done;
+    out->launches = after.launches - before.launches;
+    for (int64_t r : retries)
+        out->busy_retries += r;
+    double bytes = 0.0;
+    for (int j = 0; j < rp->n_streams; ++j)
+        bytes += (double)fbytes[j] * (double)rp->frames_per_stream;
+    out->bytes = bytes;
+    out->latency_p50_us = after.latency_p50_us;
+    out->latency_p99_us = after.latency_p99_us;
+    if (!all.empty()) {
+        out->submit_p50_us = all[all.size() / 2];
+        out->submit_p99_us = all[(size_t)(0.99 * (all.size() - 1))];
     }
     return SK_OK;
 }

@@ -1,0 +1,77 @@
+"""Precision and scale: 1024 frequencies x N=2048 x M=256 x 40 frames (21.5 GB of
+input resident on the device), one sk_compute launch.  SK~ in fp32 (from the
+exact int64 M*S2 - S1^2 and one fp32 divide) against the fp64 oracle (Eq. final)
+on frames sampled across the whole band; Q, N_eff and masks bit-exact against the
+oracle's kernel-precision statement.  The error statistics are printed."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1808_10365_b300 as sk  # noqa: E402
+import synth  # noqa: E402
+from oracle import digitisation as dg  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+N_FREQ, N, M, T = 1024, 2048, 256, 40
+
+
+def test_full_band_precision_and_masks():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    dev = torch.device("cuda:0")
+    free, _ = torch.cuda.mem_get_info(dev)
+    F = N_FREQ * T
+    nbytes = F * M * N
+    if free < nbytes + (4 << 30):
+        pytest.skip("not enough device memory for the 21.5 GB workload")
+    # each frequency its own seed and RFI; built lazily to keep host memory small
+    datasets = synth.full_array_config(n_freq=N_FREQ, n_frames=T, N=N, M=M, cfg=4)
+    d_in = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    for k, d in enumerate(datasets):
+        d.generate_gpu(d_in[k * d.nbytes:(k + 1) * d.nbytes])
+    sigma = np.concatenate([d.sigma for d in datasets[:64]])
+    delta = float(np.mean(dg.delta_of_sigma(sigma)))
+    q = torch.empty(F, dtype=torch.int64, device=dev)
+    skv = torch.empty(F, dtype=torch.float32, device=dev)
+    ne = torch.empty(F, dtype=torch.int32, device=dev)
+    mask = torch.empty(F, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, 3.0, delta)
+    try:
+        sk.sk_compute(plan, d_in, F, None, None, q, skv, ne)
+        sk.sk_flag(plan, d_in, F, None, mask)
+        torch.cuda.synchronize()
+    finally:
+        sk.sk_plan_destroy(plan)
+    q, skv, ne, mask = (t.cpu().numpy() for t in (q, skv, ne, mask))
+    del d_in
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(2024)
+    sample = np.unique(np.concatenate([rng.integers(0, F, 640), [0, F - 1, T - 1, T, F // 2]]))
+    rel = []
+    flips = 0
+    for g in sample:
+        k, f = divmod(int(g), T)
+        x = datasets[k].generate_cpu(frame0=f, n=1)
+        w = oracle.flag(x, M, N, 3.0, delta)
+        assert q[g] == w["Q"][0] and ne[g] == w["neff"][0]
+        assert skv[g].view(np.uint32) == w["sk"][0].view(np.uint32)
+        flips += int(mask[g] != w["mask"][0])
+        rel.append(abs(float(skv[g]) - w["sk64"][0]) / abs(w["sk64"][0]))
+    rel = np.array(rel)
+    stats = {"frames": int(F), "bytes": int(nbytes), "sampled": int(len(sample)),
+             "max_rel_err_fp32_vs_fp64": float(rel.max()), "mean_rel_err": float(rel.mean()),
+             "mask_mismatches": flips, "flag_rate": float(mask.mean())}
+    print("precision-scale", json.dumps(stats))
+    out = os.environ.get("SK_PRECISION_JSON")
+    if out:
+        with open(out, "w") as fh:
+            json.dump(stats, fh)
+    assert flips == 0
+    assert rel.max() <= 1e-6

@@ -187,8 +187,8 @@ def test_admission_budget_and_ring_full():
             sk.sk_ticket_wait(server, 10 ** 9, 0)
         assert e.value.status == sk.SK_ERR_INVALID_ARG
         sk.sk_stream_close(server, a)
-        # memory is returned: a second stream fits now
-        b = sk.sk_stream_open(server, N, M, ring_frames=8)
+        # its ring share is returned: a second stream of the same share fits now
+        b = sk.sk_stream_open(server, N, M, ring_frames=4)
         sk.sk_stream_close(server, b)
         st = sk.sk_server_stats(server)
         assert st["rejected"] >= 1 + busy
