@@ -215,11 +215,18 @@ sk_status_t sk_batch_destroy(sk_batch_t batch);
 
 /*
  * A continuous-batching server on one device.  Streams (one array of N
- * inputs each, different N allowed) submit frames as they arrive; a worker
- * thread launches, whenever frames are ready, one batched kernel over every
- * ready frame (at most one per stream, in arrival order) while earlier
- * launches are still on the GPU.  Device memory for a stream (its frame ring
- * and its per-input power state) is admitted against hbm_budget_bytes.
+ * inputs each, different N allowed) submit frames as they arrive into one
+ * shared, arrival-ordered ring of page-locked host memory; a launcher thread
+ * takes the ready frames (at most one per stream with running state, so its
+ * state advances in frame order) and launches one batched kernel over them
+ * while the previous launch is still on the GPU.  The kernel reads the frames
+ * from the host ring directly (zero copy); SK_SERVER_ZEROCOPY=0 selects a
+ * device mirror of the ring with one upload per batch instead.  The ring is
+ * half of hbm_budget_bytes (at most 4 GiB); a stream is admitted while its
+ * ring share (ring_frames frames) fits the ring and its device state and
+ * tables fit the rest of the budget.  SK_SERVER_INFLIGHT (1..8, default 2)
+ * sets how many launches may be in flight; SK_SERVER_TRACE=1 prints per-launch
+ * timing averages when the server is destroyed.
  */
 sk_status_t sk_server_create(int device, size_t hbm_budget_bytes,
                              sk_server_t *out);

@@ -303,6 +303,7 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.c_tab = d_c;
     it.e_tab = d_e;
     it.fast = fast ? 1 : 0;
+    it.prefetch = 1;
     return it;
 }
 

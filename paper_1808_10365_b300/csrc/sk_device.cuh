@@ -63,6 +63,8 @@ struct Item {
     int32_t fast;            // 1: 8-byte vector path applies
     float *sk_in;            // per-input SK^_i [n_frames][N] (Eq. originalSK), or null
     uint8_t *mask_in;        // per-input flag at the N_eff = 1 thresholds, or null
+    int32_t prefetch;        // 1: input in device memory, L2 bulk prefetch allowed
+    int32_t pad2;
 };
 
 // Work of one CTA.  kind 0: frames [f_begin, f_end) of item `item`, the CTA's
@@ -420,7 +422,7 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
             s2[j] = 0;
         }
         for (int jb = 0; jb < nb; jb += S) {
-            if (PF && lit == 0) {
+            if (PF && it.prefetch && lit == 0) {
                 // the S batches a later iteration will load, in this frame or,
                 // past its end, in the team's next frame
                 // PD iterations ahead: batches jb+(PD+1)S .. jb+(PD+2)S-1

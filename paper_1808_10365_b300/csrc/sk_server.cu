@@ -1,21 +1,25 @@
 // Continuous-batching serving loop.
 //
-// All streams share one arrival-ordered frame ring: page-locked host memory
-// mirrored by a device ring of the same size.  sk_stream_submit reserves the
+// All streams share one arrival-ordered frame ring of page-locked host memory.
+// sk_stream_submit reserves the
 // next bytes of the ring, copies the frame there and marks it ready.  A
 // launcher thread takes the ready prefix of the ring -- stopping before a
 // second frame of a stream with running state, so each stream's state is
-// updated in frame order -- and launches it as one batch: one contiguous
-// host-to-device copy of the prefix (two when it wraps), one copy of the work
+// updated in frame order -- and launches it as one batch: one copy of the work
 // list, one kernel over every frame in it, one copy of the results back.  With
-// two launches in flight, the upload of the next batch overlaps the kernel of
-// the current one, and frames that arrive meanwhile join the batch after it.
+// two launches in flight, the next batch is prepared while the current one
+// runs, and frames that arrive meanwhile join the batch after it.
 // A completion thread retires launches in order: it hands sk and mask to the
 // tickets, frees the ring bytes and records submit-to-result latency.
 //
-// Device memory: the ring takes half of the server's HBM budget (at most
-// 4 GiB); streams are admitted while their ring share (ring_frames frames) fits
-// the ring and their state and tables fit the other half.
+// Frames reach the GPU in one of two ways.  By default (zero copy) the ring is
+// page-locked host memory mapped into the device address space and the kernel
+// reads each frame straight from it, so the PCIe transfer overlaps the
+// reduction instead of preceding it.  With SK_SERVER_ZEROCOPY=0 the ring has a
+// device mirror and each batch is one contiguous host-to-device copy before its
+// kernel.  The ring is sized to half of the server's budget (at most 4 GiB);
+// streams are admitted while their ring share (ring_frames frames) fits the
+// ring and their device state and tables fit the other half of the budget.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -108,6 +112,8 @@ struct sk_server_s {
     size_t ring_reserved = 0;  // sum of stream shares
     size_t small_in_use = 0;   // sum of stream state + tables
     uint8_t *h_ring = nullptr, *d_ring = nullptr;
+    uint8_t *h_ring_dev = nullptr;  // device address of h_ring (zero-copy mode)
+    bool zero_copy = true;          // kernel reads frames from the host ring directly
     uint64_t head = 0, tail = 0;  // monotonic byte offsets
     std::mutex mu;
     std::condition_variable cv_work, cv_flight, cv_done;
@@ -161,7 +167,10 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
     for (int k = 0; k < n; ++k) {
         const Frame &f = frames[k];
         StreamRec *r = f.stream;
-        Item it = r->plan->item(s->d_ring + (f.off % s->ring_cap), 1);
+        Item it = r->plan->item(
+            (s->zero_copy ? s->h_ring_dev : s->d_ring) + (f.off % s->ring_cap), 1);
+        if (s->zero_copy)
+            it.prefetch = 0;
         it.sk = d_sk + k;
         it.mask = d_mask + k;
         if (r->stateful) {
@@ -201,7 +210,11 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
     if (s->trace)
         e = cudaEventRecord(L.t_copy0, s->s_copy);
     L.bytes = b - a;
-    uint64_t pos = a;
+    // the work list goes first on the copy stream: a copy queued on the compute
+    // stream would wait on the copy engine behind the next batch's frames
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(L.d_work, L.h_work, used, cudaMemcpyHostToDevice, s->s_copy);
+    uint64_t pos = s->zero_copy ? b : a;
     while (pos < b && e == cudaSuccess) {
         const uint64_t ra = pos % s->ring_cap;
         const uint64_t len = std::min<uint64_t>(b - pos, s->ring_cap - ra);
@@ -217,8 +230,6 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
         e = cudaStreamWaitEvent(s->s_compute, L.uploaded, 0);
     if (e == cudaSuccess && s->trace)
         e = cudaEventRecord(L.t_k0, s->s_compute);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(L.d_work, L.h_work, used, cudaMemcpyHostToDevice, s->s_compute);
     sk_status_t st = SK_OK;
     if (e == cudaSuccess)
         st = launch_schedule((const Item *)(L.d_work + o_items),
@@ -389,6 +400,8 @@ extern "C" sk_status_t sk_server_create(int device, size_t hbm_budget_bytes, sk_
     s->budget = hbm_budget_bytes;
     s->ring_cap = std::min(kMaxRing, hbm_budget_bytes / 2) / kAlign * kAlign;
     s->sms = sm_count(device);
+    if (const char *v = getenv("SK_SERVER_ZEROCOPY"))
+        s->zero_copy = atoi(v) != 0;
     if (const char *v = getenv("SK_SERVER_TRACE"))
         s->trace = atoi(v) != 0;
     if (const char *v = getenv("SK_SERVER_INFLIGHT")) {
@@ -399,9 +412,13 @@ extern "C" sk_status_t sk_server_create(int device, size_t hbm_budget_bytes, sk_
     sk_status_t st = SK_OK;
     {
         DeviceGuard dg(device);
-        if (cudaHostAlloc(&s->h_ring, s->ring_cap, 0) != cudaSuccess ||
-            cudaMalloc(&s->d_ring, s->ring_cap) != cudaSuccess)
+        if (cudaHostAlloc(&s->h_ring, s->ring_cap, cudaHostAllocMapped | cudaHostAllocPortable) !=
+                cudaSuccess ||
+            (!s->zero_copy && cudaMalloc(&s->d_ring, s->ring_cap) != cudaSuccess))
             st = set_error(SK_ERR_OOM, "server frame ring (%zu bytes)", s->ring_cap);
+        else if (s->zero_copy &&
+                 cudaHostGetDevicePointer((void **)&s->h_ring_dev, s->h_ring, 0) != cudaSuccess)
+            st = set_error(SK_ERR_CUDA, "server frame ring mapping");
         const size_t wb = work_bytes(s->sms), rb = sizeof(float) * kMaxBatch + kMaxBatch;
         for (int i = 0; i < s->nslots && st == SK_OK; ++i) {
             Launch &L = s->slots[i];

@@ -239,3 +239,38 @@ def test_ticket_timeout_and_concurrent_submitters():
         sk.sk_stream_close(server, sid)
     finally:
         sk.sk_server_destroy(server)
+
+
+def test_ring_wraps_many_times_with_changing_data():
+    """A small ring reused many times over: every result must belong to the frame
+    just submitted (no stale bytes from an earlier pass over the ring)."""
+    _need_gpu()
+    N, M, T = 2048, 256, 48
+    ds, x = _stream_data(31, N, M, T)
+    e = dg.offset_table(M)
+    want = served.served_flags(x, M, N, e)
+    server = sk.sk_server_create(0, 8 * N * M)   # ring = 4 frames
+    try:
+        sid = sk.sk_stream_open(server, N, M, ring_frames=3, flags=sk.SK_RUNNING_OFFSET,
+                                offset_table=e)
+        got_sk, got_m, pend = [], [], []
+        for f in range(T):
+            while True:
+                try:
+                    pend.append(sk.sk_stream_submit(server, sid, x[f], f))
+                    break
+                except sk.SkError as err:
+                    assert err.status == sk.SK_ERR_BUSY
+                    a, b = sk.sk_ticket_wait(server, pend.pop(0))
+                    got_sk.append(a)
+                    got_m.append(b)
+        for t in pend:
+            a, b = sk.sk_ticket_wait(server, t)
+            got_sk.append(a)
+            got_m.append(b)
+        sk.sk_stream_close(server, sid)
+    finally:
+        sk.sk_server_destroy(server)
+    assert np.array_equal(np.array(got_m, dtype=np.uint8), want["mask"])
+    assert np.array_equal(np.array(got_sk, dtype=np.float32).view(np.uint32),
+                          want["sk"].view(np.uint32))
