@@ -54,6 +54,12 @@ typedef enum {
 /* sk_params_t.flags */
 #define SK_RUNNING_OFFSET 0x1u /* served streams: per-input power state sets the
                                   digitisation offset of the threshold centre */
+#define SK_THRESH_PEARSON3 0x2u /* false-alarm thresholds for small M*N_eff (Sec.
+                                  3.2): SK~ modelled as a Pearson type III with
+                                  mean 1+delta, variance 4/m, skewness 10/sqrt(m),
+                                  m = M*N_eff; each tail at probability Phi(-a)
+                                  (Wilson-Hilferty gamma quantile).  Tends to
+                                  the symmetric interval as m grows. */
 
 #define SK_MAX_INPUTS 4096
 #define SK_MAX_TIME 4096
@@ -64,7 +70,7 @@ typedef struct {
     int32_t n_inputs;   /* N, 1..SK_MAX_INPUTS                              */
     int32_t n_time;     /* M (the paper's n), 2..SK_MAX_TIME                */
     int32_t layout;     /* sk_layout_t                                      */
-    uint32_t flags;     /* SK_RUNNING_OFFSET                                */
+    uint32_t flags;     /* SK_RUNNING_OFFSET | SK_THRESH_PEARSON3           */
     double n_sigma;     /* a: flag outside centre +- a*sqrt(4/(M N_eff))    */
     double mean_offset; /* static delta added to the centre 1 (App. B)     */
     /* optional host table [SK_OFFSET_BUCKETS] of per-input offsets in Q

@@ -164,7 +164,8 @@ def sk_from_complex(x: np.ndarray) -> np.ndarray:
 # thresholds and mask (Sec. 3.2, Eq. final moments, App. B)
 # ----------------------------------------------------------------------------
 
-def thresholds(M: int, N: int, n_sigma: float, mean_offset: float = 0.0):
+def thresholds(M: int, N: int, n_sigma: float, mean_offset: float = 0.0,
+               pearson3: bool = False):
     """Integer thresholds on Q for N_eff = 0..N (entry 0 unused).
 
     The centre is mean(SK~) = 1 (Eq. final moments) plus the digitisation offset
@@ -174,15 +175,32 @@ def thresholds(M: int, N: int, n_sigma: float, mean_offset: float = 0.0):
       X_hi = ((1+delta) + a*s) * (n-1) * N_eff * 2^32 / (n+1),  T_hi = floor(X_hi)
       X_lo = ((1+delta) - a*s) * (n-1) * N_eff * 2^32 / (n+1),  T_lo = ceil(X_lo)
     with s = 2 / sqrt(n * N_eff).
+
+    pearson3: false-alarm thresholds for small m = n N_eff (Sec. 3.2).  SK~ is
+    taken as a Pearson type III (shifted gamma) with mean 1+delta, variance 4/m
+    and skewness 10/sqrt(m) (Sec. 2.1 moments averaged over N_eff inputs), i.e.
+    shape k = m/25, scale 10/m, location (1+delta) - 0.4; each threshold is its
+    gamma quantile at normal deviate +-a by Wilson-Hilferty,
+    k (1 - 1/(9k) + z/(3 sqrt(k)))^3.
     """
     t_lo = np.zeros(N + 1, dtype=np.int64)
     t_hi = np.zeros(N + 1, dtype=np.int64)
     centre = 1.0 + float(mean_offset)
     a = float(n_sigma)
     for ne in range(1, N + 1):
-        s = 2.0 / math.sqrt(float(M * ne))
-        x_hi = (centre + a * s) * float(M - 1) * float(ne) * TWO32 / float(M + 1)
-        x_lo = (centre - a * s) * float(M - 1) * float(ne) * TWO32 / float(M + 1)
+        m = float(M * ne)
+        if pearson3:
+            k = m / 25.0
+            b_hi = 1.0 - 1.0 / (9.0 * k) + a / (3.0 * math.sqrt(k))
+            b_lo = 1.0 - 1.0 / (9.0 * k) - a / (3.0 * math.sqrt(k))
+            v_hi = (centre - 0.4) + 0.4 * (b_hi * b_hi * b_hi)
+            v_lo = (centre - 0.4) + 0.4 * (b_lo * b_lo * b_lo)
+        else:
+            s = 2.0 / math.sqrt(m)
+            v_hi = centre + a * s
+            v_lo = centre - a * s
+        x_hi = v_hi * float(M - 1) * float(ne) * TWO32 / float(M + 1)
+        x_lo = v_lo * float(M - 1) * float(ne) * TWO32 / float(M + 1)
         t_hi[ne] = math.floor(x_hi)
         t_lo[ne] = math.ceil(x_lo)
     return t_lo, t_hi
@@ -202,12 +220,12 @@ def mask(Q: np.ndarray, neff: np.ndarray, t_lo: np.ndarray, t_hi: np.ndarray,
 
 
 def flag(x: np.ndarray, M: int, N: int, n_sigma: float = 3.0, mean_offset: float = 0.0,
-         layout: int = 0):
+         layout: int = 0, pearson3: bool = False):
     """Whole plain path on bytes x: dict with S1, S2, Q, neff, sk (fp32), mask, sk64."""
     S1, S2 = power_sums(x, M, N, layout)
     Q, ne, sk = sk_spec(S1, S2, M)
     sk64, _, _ = sk_f64(S1, S2, M)
-    t_lo, t_hi = thresholds(M, N, n_sigma, mean_offset)
+    t_lo, t_hi = thresholds(M, N, n_sigma, mean_offset, pearson3)
     return dict(S1=S1, S2=S2, Q=Q, neff=ne, sk=sk, sk64=sk64,
                 mask=mask(Q, ne, t_lo, t_hi), t_lo=t_lo, t_hi=t_hi)
 

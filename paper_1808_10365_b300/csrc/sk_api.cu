@@ -42,8 +42,12 @@ int sm_count(int device)
 // Tile 0: 16 x 2 (needs M % 32 == 0), tile 1: 8 x 2 (M % 16 == 0).  NC fixes
 // the row stride N at compile time (0: read it from the item); a kernel is only
 // launched with NC > 0 for items of that N, and any other item takes the
-// general path.
-template <int R, int S, bool SRV, int NC>
+// general path.  MODE selects the one work layout a kernel handles, so that
+// each instantiation holds a single copy of the pipeline:
+//   0  one item, a contiguous frame range per CTA (sk_compute, sk_flag)
+//   1  chunk list of frame ranges (batched launch)
+//   2  chunk list of one-frame items, teams on different items (served batch)
+template <int R, int S, bool SRV, int NC, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_fused_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
                     const int32_t *__restrict__ cta_chunks, Item single)
@@ -52,7 +56,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ TeamSmem ts;
     const uint32_t lb = build_table(dyn_smem);
     int parity = 0;
-    if (items == nullptr) {
+    if (MODE == 0) {
         const int64_t F = single.n_frames;
         const int64_t G = gridDim.x;
         const int64_t fb = F * (int64_t)blockIdx.x / G;
@@ -67,52 +71,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int32_t c = c0; c < c1; ++c) {
         const Chunk ch = chunks[c];
         __syncthreads();
-        if (ch.kind == 0) {
+        if (MODE == 1) {
             const Item it = items[ch.item];
             if (it.fast && it.M % (R * S) == 0 && (NC == 0 || it.N == NC))
                 run_fast<R, S, SRV, NC>(it, ch.f_begin, ch.f_end, lb, ts, parity);
             else
                 run_general<SRV>(it, ch.f_begin, ch.f_end, lb, ts, parity);
-            continue;
-        }
-        // one frame per item, teams on different items; every item of the chunk
-        // has the same shape, so all teams take the same path the same number
-        // of times
-        const Item it0 = items[ch.f_begin];
-        const int tl = it0.team_log2;
-        const int64_t T = kThreads >> tl;
-        const int64_t team_idx = threadIdx.x >> tl;
-        const bool fast = it0.fast && it0.M % (R * S) == 0 && (NC == 0 || it0.N == NC);
-        for (int64_t base = ch.f_begin; base < ch.f_end; base += T) {
-            const int64_t idx = base + team_idx;
-            const bool v = idx < ch.f_end;
-            const Item it = items[v ? idx : ch.f_begin];
-            if (fast)
-                run_fast<R, S, SRV, NC>(it, 0, v ? 1 : 0, lb, ts, parity, true);
-            else
-                run_general<SRV>(it, 0, v ? 1 : 0, lb, ts, parity, true);
+        } else {
+            // one frame per item, teams on different items; every item of the
+            // chunk has the same shape, so all teams take the same path the same
+            // number of times
+            const Item it0 = items[ch.f_begin];
+            const int tl = it0.team_log2;
+            const int64_t T = kThreads >> tl;
+            const int64_t team_idx = threadIdx.x >> tl;
+            const bool fast = it0.fast && it0.M % (R * S) == 0 && (NC == 0 || it0.N == NC);
+            for (int64_t base = ch.f_begin; base < ch.f_end; base += T) {
+                const int64_t idx = base + team_idx;
+                const bool v = idx < ch.f_end;
+                const Item it = items[v ? idx : ch.f_begin];
+                if (fast)
+                    run_fast<R, S, SRV, NC>(it, 0, v ? 1 : 0, lb, ts, parity, true);
+                else
+                    run_general<SRV>(it, 0, v ? 1 : 0, lb, ts, parity, true);
+            }
         }
     }
 }
 
 using KernelFn = void (*)(const Item *, const Chunk *, const int32_t *, Item);
 
-// [tile][nc index: 0 -> runtime N, 1 -> 256, 2 -> 2048]; served kernels use runtime N
-static const KernelFn kPlain[2][3] = {
-    {sk_fused_kernel<16, 2, false, 0>, sk_fused_kernel<16, 2, false, 256>,
-     sk_fused_kernel<16, 2, false, 2048>},
-    {sk_fused_kernel<8, 2, false, 0>, sk_fused_kernel<8, 2, false, 256>,
-     sk_fused_kernel<8, 2, false, 2048>}};
-static const KernelFn kServed[2] = {sk_fused_kernel<16, 2, true, 0>,
-                                    sk_fused_kernel<8, 2, true, 0>};
-
-static KernelFn kernel_of(int tile, bool served, int N)
-{
-    if (served)
-        return kServed[tile];
-    const int nci = N == 256 ? 1 : (N == 2048 ? 2 : 0);
-    return kPlain[tile][nci];
-}
+// one-item launches: [tile][0 -> runtime N, 1 -> N = 256, 2 -> N = 2048]
+static const KernelFn kSingle[2][3] = {
+    {sk_fused_kernel<16, 2, false, 0, 0>, sk_fused_kernel<16, 2, false, 256, 0>,
+     sk_fused_kernel<16, 2, false, 2048, 0>},
+    {sk_fused_kernel<8, 2, false, 0, 0>, sk_fused_kernel<8, 2, false, 256, 0>,
+     sk_fused_kernel<8, 2, false, 2048, 0>}};
+static const KernelFn kBatched[2] = {sk_fused_kernel<16, 2, false, 0, 1>,
+                                     sk_fused_kernel<8, 2, false, 0, 1>};
+static const KernelFn kServed[2] = {sk_fused_kernel<16, 2, true, 0, 2>,
+                                    sk_fused_kernel<8, 2, true, 0, 2>};
 
 // Tile for a requested rows-per-batch and whether every M is a multiple of 32.
 int pick_tile(int rows, bool all_m32)
@@ -120,11 +118,6 @@ int pick_tile(int rows, bool all_m32)
     if (!all_m32 || rows == 8)
         return 1;
     return 0;
-}
-
-static KernelFn pick_kernel(int rows, bool served, int M, int N)
-{
-    return kernel_of(pick_tile(rows, M % 32 == 0), served, N);
 }
 
 sk_status_t ensure_kernel_attrs(int device)
@@ -138,8 +131,9 @@ sk_status_t ensure_kernel_attrs(int device)
     std::vector<KernelFn> fns;
     for (int t = 0; t < 2; ++t) {
         fns.push_back(kServed[t]);
+        fns.push_back(kBatched[t]);
         for (int j = 0; j < 3; ++j)
-            fns.push_back(kPlain[t][j]);
+            fns.push_back(kSingle[t][j]);
     }
     for (KernelFn f : fns) {
         cudaError_t e = cudaFuncSetAttribute((const void *)f,
@@ -169,7 +163,10 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         g = need;
     if (g < 1)
         g = 1;
-    KernelFn fn = pick_kernel(rows, served, it.M, it.N);
+    if (served)
+        return set_error(SK_ERR_UNSUPPORTED, "served items go through launch_schedule");
+    const int nci = it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
+    KernelFn fn = kSingle[pick_tile(rows, it.M % 32 == 0)][nci];
     fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, it);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -188,7 +185,7 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
         return s;
     Item dummy;
     memset(&dummy, 0, sizeof dummy);
-    KernelFn fn = kernel_of(tile, served, 0);
+    KernelFn fn = served ? kServed[tile] : kBatched[tile];
     fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -353,7 +350,7 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
         return set_error(SK_ERR_INVALID_ARG, "layout %d unknown", p.layout);
     if (!(p.n_sigma >= 0.0) || !std::isfinite(p.n_sigma) || !std::isfinite(p.mean_offset))
         return set_error(SK_ERR_INVALID_ARG, "n_sigma must be finite and >= 0, mean_offset finite");
-    if (p.flags & ~SK_RUNNING_OFFSET)
+    if (p.flags & ~(SK_RUNNING_OFFSET | SK_THRESH_PEARSON3))
         return set_error(SK_ERR_INVALID_ARG, "unknown flags 0x%x", p.flags);
     int ndev = 0;
     cudaError_t ce = cudaGetDeviceCount(&ndev);
@@ -381,12 +378,25 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
     pl->c_tab.assign(N + 1, 0.0f);
     const double centre = 1.0 + p.mean_offset;
     const double a = p.n_sigma;
+    const bool pearson = (p.flags & SK_THRESH_PEARSON3) != 0;
     for (int32_t ne = 1; ne <= N; ++ne) {
-        const double s = 2.0 / std::sqrt((double)((int64_t)M * ne));
-        const double x_hi = (centre + a * s) * (double)(M - 1) * (double)ne * 4294967296.0 /
-                            (double)(M + 1);
-        const double x_lo = (centre - a * s) * (double)(M - 1) * (double)ne * 4294967296.0 /
-                            (double)(M + 1);
+        const double m = (double)((int64_t)M * ne);
+        double v_hi, v_lo;
+        if (pearson) {
+            // shifted gamma: shape k = 4/skew^2 = m/25, scale 10/m, location
+            // centre - 0.4; quantile k (1 - 1/(9k) + z/(3 sqrt k))^3, z = +-a
+            const double k = m / 25.0;
+            const double b_hi = 1.0 - 1.0 / (9.0 * k) + a / (3.0 * std::sqrt(k));
+            const double b_lo = 1.0 - 1.0 / (9.0 * k) - a / (3.0 * std::sqrt(k));
+            v_hi = (centre - 0.4) + 0.4 * (b_hi * b_hi * b_hi);
+            v_lo = (centre - 0.4) + 0.4 * (b_lo * b_lo * b_lo);
+        } else {
+            const double s = 2.0 / std::sqrt(m);
+            v_hi = centre + a * s;
+            v_lo = centre - a * s;
+        }
+        const double x_hi = v_hi * (double)(M - 1) * (double)ne * 4294967296.0 / (double)(M + 1);
+        const double x_lo = v_lo * (double)(M - 1) * (double)ne * 4294967296.0 / (double)(M + 1);
         pl->t_hi[ne] = (int64_t)std::floor(x_hi);
         pl->t_lo[ne] = (int64_t)std::ceil(x_lo);
         pl->c_tab[ne] = (float)((double)(M + 1) / ((double)(M - 1) * (double)ne));

@@ -340,3 +340,47 @@ def test_independent_estimates_against_exact_rationals():
         if vals:
             avg = sum(vals, Fraction(0)) / len(vals)
             assert abs(float(avg) - full["sk64"][f]) <= 1e-12 * max(1, abs(float(avg)))
+
+
+def test_pearson3_thresholds_limits():
+    """Large m: the Pearson III edges tend to the symmetric +-a sigma interval, their
+    offset shrinking like the skewness, 1/sqrt(m)."""
+    M, N = 256, 4096
+    slo, shi = oracle.thresholds(M, N, 3.0, 0.01)
+    plo, phi = oracle.thresholds(M, N, 3.0, 0.01, pearson3=True)
+
+    def rel(ne):
+        half = (shi[ne] - slo[ne]) / 2
+        return (phi[ne] - shi[ne]) / half, (plo[ne] - slo[ne]) / half
+
+    hi_n, lo_n = rel(N)
+    hi_q, lo_q = rel(N // 4)
+    assert 0 < hi_n < 0.01 and 0 < lo_n < 0.01
+    assert abs(hi_q / hi_n - 2.0) < 0.05 and abs(lo_q / lo_n - 2.0) < 0.05
+    # skewed to the right at small m: both edges above the symmetric ones
+    assert phi[1] > shi[1] and plo[1] > slo[1]
+
+
+@pytest.mark.slow
+def test_pearson3_false_alarm_balance():
+    """Small nN (Sec. 3.2): the skewed thresholds balance the two tails, which the
+    symmetric interval does not.  Complex Gaussian input, a = 2 (p = 2.28 % per tail)."""
+    from scipy.stats import norm
+
+    rng = np.random.default_rng(2018)
+    M, N, a = 128, 2, 2.0
+    p = norm.sf(a)
+    sk = np.concatenate([oracle.sk_from_complex(_cgauss(rng, (20000, M, N))) for _ in range(8)])
+    m = M * N
+    slo, shi = 1 - a * 2 / math.sqrt(m), 1 + a * 2 / math.sqrt(m)
+    k = m / 25.0
+    phi = 0.6 + 0.4 * (1 - 1 / (9 * k) + a / (3 * math.sqrt(k))) ** 3
+    plo = 0.6 + 0.4 * (1 - 1 / (9 * k) - a / (3 * math.sqrt(k))) ** 3
+    # the oracle's integer thresholds encode these edges
+    tlo, thi = oracle.thresholds(M, 1, a, 0.0, pearson3=True)
+    scale = (M - 1) * 2 ** 32 / (M + 1)
+    assert abs(thi[1] / scale - (0.6 + 0.4 * (1 - 1 / (9 * M / 25) + a / (3 * math.sqrt(M / 25))) ** 3)) < 1e-9
+    up_s, lo_s = (sk > shi).mean(), (sk < slo).mean()
+    up_p, lo_p = (sk > phi).mean(), (sk < plo).mean()
+    assert up_s > 1.3 * p and lo_s < 0.5 * p                 # symmetric: unbalanced
+    assert 0.7 * p < up_p < 1.4 * p and 0.7 * p < lo_p < 1.4 * p

@@ -286,3 +286,25 @@ def test_independent_estimates_bit_exact(N, M, F):
     ok = want["valid"] == 1
     rel = np.abs(got[ok] - want["sk_in64"][ok]) / np.maximum(np.abs(want["sk_in64"][ok]), 1e-6)
     assert rel.max() <= SK_REL
+
+
+@pytest.mark.parametrize("N,M", [(256, 64), (16, 32), (2048, 256)])
+def test_pearson3_thresholds_and_masks_bit_exact(N, M):
+    """SK_THRESH_PEARSON3: plan thresholds and masks equal the oracle's."""
+    dev = _dev()
+    ds = synth.Dataset(n_frames=80, M=M, N=N, seed=synth.sub_seed(7, N + M),
+                       rfi=synth.rfi_plan(synth.sub_seed(7, N + M), 80, 0.1, 0.05))
+    x = ds.generate_cpu()
+    delta = float(np.mean(dg.delta_of_sigma(ds.sigma)))
+    want = oracle.flag(x, M, N, 2.0, delta, pearson3=True)
+    plan = sk.sk_plan_create(N, M, 2.0, delta, flags=sk.SK_THRESH_PEARSON3)
+    try:
+        t_lo, t_hi = sk.sk_plan_thresholds(plan, N)
+        d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+        mask = torch.empty(80, dtype=torch.uint8, device=dev)
+        sk.sk_flag(plan, d_in, 80, None, mask)
+        torch.cuda.synchronize()
+    finally:
+        sk.sk_plan_destroy(plan)
+    assert np.array_equal(t_lo[1:], want["t_lo"][1:]) and np.array_equal(t_hi[1:], want["t_hi"][1:])
+    assert np.array_equal(mask.cpu().numpy(), want["mask"])
