@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t G = gridDim.x;
         const int64_t fb = F * (int64_t)blockIdx.x / G;
         const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
-        if (single.fast && single.M % (R * S) == 0 && (NC == 0 || single.N == NC))
+        if (single.fast == 1 && single.M % (R * S) == 0 && (NC == 0 || single.N == NC))
             run_fast<R, S, SRV, NC>(single, fb, fe, lb, ts, parity);
         else
             run_general<SRV>(single, fb, fe, lb, ts, parity);
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         if (MODE == 1) {
             const Item it = items[ch.item];
-            if (it.fast && it.M % (R * S) == 0 && (NC == 0 || it.N == NC))
+            if (it.fast == 1 && it.M % (R * S) == 0 && (NC == 0 || it.N == NC))
                 run_fast<R, S, SRV, NC>(it, ch.f_begin, ch.f_end, lb, ts, parity);
             else
                 run_general<SRV>(it, ch.f_begin, ch.f_end, lb, ts, parity);
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int tl = it0.team_log2;
             const int64_t T = kThreads >> tl;
             const int64_t team_idx = threadIdx.x >> tl;
-            const bool fast = it0.fast && it0.M % (R * S) == 0 && (NC == 0 || it0.N == NC);
+            const bool fast = it0.fast == 1 && it0.M % (R * S) == 0 && (NC == 0 || it0.N == NC);
             for (int64_t base = ch.f_begin; base < ch.f_end; base += T) {
                 const int64_t idx = base + team_idx;
                 const bool v = idx < ch.f_end;
@@ -97,6 +97,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     }
+}
+
+// Input-major fast path, one-item launches only (batched and served launches
+// take input-major items through the general path).  G lanes per input.
+template <int G>
+__global__ void __launch_bounds__(kThreads, 1)
+    sk_imajor_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
+                     const int32_t *__restrict__ cta_chunks, Item single)
+{
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ TeamSmem ts;
+    const uint32_t lb = build_table(dyn_smem);
+    int parity = 0;
+    const int64_t F = single.n_frames;
+    const int64_t Gd = gridDim.x;
+    const int64_t fb = F * (int64_t)blockIdx.x / Gd;
+    const int64_t fe = F * ((int64_t)blockIdx.x + 1) / Gd;
+    if (single.fast == 2 && single.M % (16 * G) == 0 && single.team_log2 >= 5)
+        run_imajor<G, 8>(single, fb, fe, lb, ts, parity);
+    else
+        run_general<false>(single, fb, fe, lb, ts, parity);
 }
 
 using KernelFn = void (*)(const Item *, const Chunk *, const int32_t *, Item);
@@ -111,6 +132,22 @@ static const KernelFn kBatched[2] = {sk_fused_kernel<16, 2, false, 0, 1>,
                                      sk_fused_kernel<8, 2, false, 0, 1>};
 static const KernelFn kServed[2] = {sk_fused_kernel<16, 2, true, 0, 2>,
                                     sk_fused_kernel<8, 2, true, 0, 2>};
+
+// Lanes per input on the input-major path: 4 up to M = 512, 8 above (measured
+// best on B300), or SK_IMAJOR_LANES (2, 4 or 8); reduced while 16 G does not
+// divide M.
+int imajor_lanes(int M)
+{
+    static const int forced = [] {
+        const char *v = getenv("SK_IMAJOR_LANES");
+        const int x = v ? atoi(v) : 0;
+        return (x == 2 || x == 4 || x == 8) ? x : 0;
+    }();
+    int g = forced ? forced : (M <= 512 ? 4 : 8);
+    while (g > 2 && M % (16 * g) != 0)
+        g /= 2;
+    return g;
+}
 
 // Tile for a requested rows-per-batch and whether every M is a multiple of 32.
 int pick_tile(int rows, bool all_m32)
@@ -129,6 +166,9 @@ sk_status_t ensure_kernel_attrs(int device)
         if (d == device)
             return SK_OK;
     std::vector<KernelFn> fns;
+    fns.push_back(sk_imajor_kernel<2>);
+    fns.push_back(sk_imajor_kernel<4>);
+    fns.push_back(sk_imajor_kernel<8>);
     for (int t = 0; t < 2; ++t) {
         fns.push_back(kServed[t]);
         fns.push_back(kBatched[t]);
@@ -167,6 +207,10 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         return set_error(SK_ERR_UNSUPPORTED, "served items go through launch_schedule");
     const int nci = it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
     KernelFn fn = kSingle[pick_tile(rows, it.M % 32 == 0)][nci];
+    if (it.fast == 2) {
+        const int gsel = imajor_lanes(it.M);
+        fn = gsel == 2 ? sk_imajor_kernel<2> : (gsel == 4 ? sk_imajor_kernel<4> : sk_imajor_kernel<8>);
+    }
     fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, it);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -299,7 +343,7 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.t_hi = d_t_hi;
     it.c_tab = d_c;
     it.e_tab = d_e;
-    it.fast = fast ? 1 : 0;
+    it.fast = fast ? 1 : (imajor ? 2 : 0);
     it.prefetch = 1;
     return it;
 }
@@ -368,6 +412,13 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
     const int32_t N = p.n_inputs, M = p.n_time;
     pl->team_log2 = ceil_log2((N + kVec - 1) / kVec);
     pl->fast = (p.layout == SK_LAYOUT_TIME_MAJOR) && (N % kVec == 0) && (M % kFlushRows == 0);
+    const int gl = imajor_lanes(M);
+    pl->imajor = (p.layout == SK_LAYOUT_INPUT_MAJOR) && (M % (16 * gl) == 0);
+    if (pl->imajor) {
+        // segments of gl lanes, about 8 inputs per segment, 32..512 threads
+        int tl = ceil_log2(((int64_t)N * gl + 7) / 8);
+        pl->team_log2 = tl < 5 ? 5 : (tl > 9 ? 9 : tl);
+    }
     pl->rows = 16;
     pl->grid_ctas = 0;
     cached_tiles(N, M, p.layout, &pl->rows, &pl->grid_ctas);

@@ -27,6 +27,7 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
                             const int32_t *d_cta_chunks, int grid, int tile, bool served,
                             int device, cudaStream_t st);
 int pick_tile(int rows, bool all_m32);
+int imajor_lanes(int M);
 sk_status_t ensure_kernel_attrs(int device);
 int sm_count(int device);
 
@@ -62,6 +63,7 @@ struct sk_plan_s {
     int device = 0;
     int team_log2 = 0;
     bool fast = false;
+    bool imajor = false;  // input-major fast path applies
     int rows = 16;      // register batch rows of the fast path
     int grid_ctas = 0;  // 0: one CTA per SM
     std::vector<int64_t> t_lo, t_hi, etab;

@@ -40,6 +40,7 @@ constexpr int kPackShift = 19;
 constexpr uint32_t kPackMask = (1u << kPackShift) - 1u;
 constexpr int kOffsetBuckets = 4096;
 constexpr int kStateShift = 6;
+constexpr int kImajorG = 8;                 // lanes per input on the input-major path
 
 // Output and table pointers of one work item: frames of one (N, M).
 struct Item {
@@ -60,7 +61,7 @@ struct Item {
     uint32_t *state;         // served: per-input power P_i [N], or null
     const int64_t *e_tab;    // served: offset per power bucket [kOffsetBuckets]
     int32_t state_init;      // served: 1 on the stream's first frame
-    int32_t fast;            // 1: 8-byte vector path applies
+    int32_t fast;            // 1: time-major vector path, 2: input-major path, 0: general
     float *sk_in;            // per-input SK^_i [n_frames][N] (Eq. originalSK), or null
     uint8_t *mask_in;        // per-input flag at the N_eff = 1 thresholds, or null
     int32_t prefetch;        // 1: input in device memory, L2 bulk prefetch allowed
@@ -471,6 +472,189 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
         frame = nframe;
         fp = nfp;
         ok = nok;
+    }
+}
+
+__device__ __forceinline__ uint4 ldg_stream16(const uint8_t *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// 16 samples of one input (one 16-byte chunk) into one packed accumulator.
+__device__ __forceinline__ uint32_t accum16(uint4 w, uint32_t lb)
+{
+    uint32_t a = 0u;
+    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        a += lds_u32(prmt(ww[h], lb, 0x7604u)) + lds_u32(prmt(ww[h], lb, 0x7614u));
+        a += lds_u32(prmt(ww[h], lb, 0x7624u)) + lds_u32(prmt(ww[h], lb, 0x7634u));
+    }
+    return a;
+}
+
+// Input-major fast path: layout [frame][input][t], M % (16 G) == 0, team of at
+// least 32 threads.  A segment of G lanes owns one input at a time: lane j reads
+// the 16-byte chunks j, j+G, j+2G, ... of that input's M bytes, so one warp
+// instruction reads 32/G runs of 16 G contiguous bytes.  Each chunk (16 samples)
+// fills one packed accumulator, which is split into exact S1, S2 at once.  After
+// an input's last chunk the segment adds S1 and S2 over its G lanes with
+// log2(G) shuffles and its lane 0 forms the input's term.  The lane's chunks of
+// successive inputs, and of the team's next frame, form one flat sequence that
+// streams through two register batches of KB chunks; a frame's sequence is padded
+// to a multiple of KB so that frame ends fall on batch boundaries.
+template <int G, int KB>
+__device__ __forceinline__ void run_imajor(const Item &it, int64_t f_begin, int64_t f_end,
+                                           uint32_t lb, TeamSmem &ts, int &parity)
+{
+    const int team_log2 = it.team_log2;
+    const int T = kThreads >> team_log2;
+    const int team_idx = threadIdx.x >> team_log2;
+    const int lit = threadIdx.x & ((1 << team_log2) - 1);
+    const int nseg = (1 << team_log2) / G;
+    const int seg = lit / G, j = lit % G;
+    const int N = it.N, M = it.M;
+    const int C = M / (16 * G);                 // chunks per lane per input
+    const int K = (N + nseg - 1) / nseg;        // inputs per segment
+    const int per = ((K * C + KB - 1) / KB) * KB;  // padded flat chunks per frame
+    const int nbat = per / KB;
+    const int64_t fbytes = (int64_t)M * N;
+    const int64_t kmax = (f_end - f_begin + T - 1) / T;
+
+    // load cursor: frame, input slot k, chunk c, flat position g
+    int64_t lf = f_begin + team_idx;
+    int lk = 0, lc = 0, lg = 0;
+    auto load_batch = [&](uint4 (&buf)[KB]) {
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int i = seg + lk * nseg;
+            if (lf < f_end && lk < K && i < N)
+                buf[u] = ldg_stream16(it.in + lf * fbytes + (int64_t)i * M +
+                                      (int64_t)(j + lc * G) * 16);
+            if (++lc == C) {
+                lc = 0;
+                ++lk;
+            }
+        }
+        // frame ends fall on batch boundaries (per is a multiple of KB)
+        lg += KB;
+        if (lg >= per) {
+            lg = 0;
+            lk = 0;
+            lc = 0;
+            lf += T;
+        }
+        // one thread of the team brings the block of inputs one step beyond the
+        // next batch into L2: the team reads inputs in contiguous blocks of nseg
+        if (lit == 0 && lc == 0) {
+            const int step = C >= KB ? 1 : KB / C;
+            int i0 = (lk + step) * nseg;
+            int64_t pf_frame = lf;
+            if (i0 >= N) {
+                i0 -= ((N + nseg - 1) / nseg) * nseg;  // into the next frame
+                pf_frame += T;
+            }
+            if (i0 >= 0 && i0 < N && pf_frame < f_end) {
+                const int i1 = min(N, i0 + step * nseg);
+                const uint32_t total = (uint32_t)(i1 - i0) * (uint32_t)M;
+                const uint8_t *pp = it.in + pf_frame * fbytes + (int64_t)i0 * M;
+                for (uint32_t o = 0; o < total; o += 32768u)
+                    prefetch_l2(pp + o, total - o < 32768u ? total - o : 32768u);
+            }
+        }
+    };
+
+    uint4 A[KB], B[KB];
+    load_batch(A);
+    int64_t frame = f_begin + team_idx;
+    for (int64_t kk = 0; kk < kmax; ++kk) {
+        const bool fvalid = frame < f_end;
+        int64_t q = 0, e = 0;
+        int32_t cnt = 0;
+        int32_t s1 = 0, s2 = 0;
+        int pk = 0, pc = 0;  // process cursor inside the frame
+        for (int b = 0; b < nbat; b += 2) {
+            const bool has_b = b + 1 < nbat;
+            if (has_b)
+                load_batch(B);
+            // process A then B; the same code for both buffers
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1 && !has_b)
+                    break;
+                uint4 (&buf)[KB] = half == 0 ? A : B;
+#pragma unroll
+                for (int u = 0; u < KB; ++u) {
+                    const int i = seg + pk * nseg;
+                    const bool live = fvalid && pk < K && i < N;
+                    if (live) {
+                        const uint32_t a = accum16(buf[u], lb);
+                        s1 += (int32_t)(a >> kPackShift);
+                        s2 += (int32_t)(a & kPackMask);
+                    }
+                    if (++pc == C) {
+                        // input done: combine the segment's lanes (all lanes of a
+                        // warp reach this point together)
+                        pc = 0;
+#pragma unroll
+                        for (int o = 1; o < G; o <<= 1) {
+                            s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+                            s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+                        }
+                        if (live && j == 0) {
+                            float r = 0.0f;
+                            int64_t qi = 0;
+                            const bool has = input_term(s1, s2, M, r, qi);
+                            if (has) {
+                                q += qi;
+                                cnt += 1;
+                            }
+                            const int64_t o = frame * N + i;
+                            if (it.s1) {
+                                it.s1[o] = s1;
+                                it.s2[o] = s2;
+                            }
+                            if (it.sk_in) {
+                                it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1])
+                                                  : __int_as_float(0x7FC00000);
+                                if (it.mask_in)
+                                    it.mask_in[o] =
+                                        has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+                            }
+                        }
+                        s1 = 0;
+                        s2 = 0;
+                        ++pk;
+                    }
+                }
+                if (half == 0)
+                    load_batch(A);
+            }
+        }
+        team_sum(q, cnt, e, team_log2, team_idx, parity, ts, false);
+        if (fvalid && lit == 0) {
+            uint8_t m = 1;
+            if (cnt > 0)
+                m = (q > it.t_hi[cnt] || q < it.t_lo[cnt]) ? 1 : 0;
+            if (it.sk) {
+                float skv = __int_as_float(0x7FC00000);
+                if (cnt > 0)
+                    skv = __fmul_rn(__fmul_rn(__ll2float_rn(q), 0x1p-32f), it.c_tab[cnt]);
+                it.sk[frame] = skv;
+            }
+            if (it.mask)
+                it.mask[frame] = m;
+            if (it.q)
+                it.q[frame] = q;
+            if (it.neff)
+                it.neff[frame] = cnt;
+        }
+        parity ^= 1;
+        frame += T;
     }
 }
 

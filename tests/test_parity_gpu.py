@@ -308,3 +308,29 @@ def test_pearson3_thresholds_and_masks_bit_exact(N, M):
         sk.sk_plan_destroy(plan)
     assert np.array_equal(t_lo[1:], want["t_lo"][1:]) and np.array_equal(t_hi[1:], want["t_hi"][1:])
     assert np.array_equal(mask.cpu().numpy(), want["mask"])
+
+
+@pytest.mark.parametrize("N,M,F", [(2048, 256, 9), (256, 256, 37), (100, 128, 11), (7, 1024, 5),
+                                   (1, 128, 3), (512, 2048, 3), (4096, 128, 2), (33, 384, 6)])
+def test_input_major_fast_path_bit_exact(N, M, F):
+    """Layout [frame][input][t] through the input-major path (M % 128 == 0)."""
+    rng = np.random.default_rng(N * 3 + M * 5 + F)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    x[0, : M] = 0x88                       # input 0 of frame 0 has no power
+    want = oracle.flag(x, M, N, 3.0, 0.05, layout=1)
+    got = run_compute(x, M, N, 3.0, 0.05, layout=1)
+    assert_parity(got, want)
+    # independent estimates through the same path
+    dev = _dev()
+    wi = oracle.flag_inputs(x, M, N, 3.0, 0.05, layout=1)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    sk_in = torch.empty((F, N), dtype=torch.float32, device=dev)
+    m_in = torch.empty((F, N), dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.05, layout=1)
+    try:
+        sk.sk_compute_inputs(plan, d_in, F, sk_in, m_in)
+        torch.cuda.synchronize()
+    finally:
+        sk.sk_plan_destroy(plan)
+    assert np.array_equal(sk_in.cpu().numpy().view(np.uint32), wi["sk_in"].view(np.uint32))
+    assert np.array_equal(m_in.cpu().numpy(), wi["mask_in"])

@@ -104,3 +104,56 @@ def test_served_offset_tracks_per_input_sigma():
     want = float(np.sum(dg.delta_of_sigma(ds.sigma))) * 2 ** 32 * (M - 1) / (M + 1)
     got = float(full["E"][-1])
     assert abs(got - want) < 0.05 * abs(want) + 0.002 * 2 ** 32 * N
+
+
+def test_f32_of_int_rounds_once():
+    from oracle.served import f32_of_int
+
+    for v in [0, 1, 2 ** 24 - 1, 2 ** 24 + 1, 2 ** 24 + 3, 2 ** 53 + 2 ** 29 + 1, 3 * 2 ** 60 + 12345,
+              2 ** 62 - 1]:
+        want = np.float32(np.longdouble(v)) if v < 2 ** 64 else None
+        # exact reference: the closer of the two neighbouring fp32 values, ties to even
+        got = f32_of_int(v)
+        lo = np.nextafter(got, np.float32(0))
+        hi = np.nextafter(got, np.float32(np.inf))
+        from fractions import Fraction
+        d = abs(Fraction(int(got)) - v) if got == int(got) else None
+        assert d is not None
+        assert d <= abs(Fraction(int(lo)) - v) and d <= abs(Fraction(int(hi)) - v)
+        del want
+
+
+def test_running_mu_first_frame_equals_frame_normalisation():
+    """With the state initialised from the frame (mu_i = S1_i/n), Eq. avgSK's general form
+    rescaled by Eq. final equals the per-frame estimator."""
+    ds = synth.Dataset(n_frames=3, M=256, N=64, seed=3)
+    x = ds.generate_cpu()
+    e = dg.offset_table(256)
+    a = served.served_flags(x[:1], 256, 64, e)
+    b = served.served_flags(x[:1], 256, 64, e, running_mu=True)
+    assert abs(float(a["sk"][0]) - float(b["sk"][0])) <= 1e-6 * abs(float(a["sk"][0]))
+
+
+def test_running_mu_sees_a_power_step():
+    """Half the inputs jump in power against their running state: the running-mu
+    estimator moves by about 2 N sum(l^2)/(sum l)^2 - 1 (l the power ratios), the
+    per-frame normalisation does not."""
+    M, N, T = 256, 128, 30
+    sig = np.full(N, 1.6)
+    ds1 = synth.Dataset(n_frames=T, M=M, N=N, seed=41, sigma=sig)
+    sig2 = sig.copy()
+    sig2[: N // 2] *= np.sqrt(2.0)          # power x2 on half of the inputs
+    ds2 = synth.Dataset(n_frames=T, M=M, N=N, seed=42, sigma=sig2)
+    x = np.concatenate([ds1.generate_cpu(), ds2.generate_cpu()[:1]])
+    e = dg.offset_table(M)
+    rm = served.served_flags(x, M, N, e, running_mu=True)
+    pf = served.served_flags(x, M, N, e)
+    lam = np.where(np.arange(N) < N // 2, 2.0, 1.0)
+    want = 2 * N * (lam ** 2).sum() / lam.sum() ** 2 - 1      # 1 + 1/9 for this split
+    step_rm = float(rm["sk"][-1]) - float(np.mean(rm["sk"][T - 10:T]))
+    step_pf = float(pf["sk"][-1]) - float(np.mean(pf["sk"][T - 10:T]))
+    # quantisation makes the power ratio and the kurtosis of the stepped inputs differ a
+    # little from the continuous-Gaussian closed form: a coarse band around it
+    assert 0.6 * (want - 1.0) < step_rm < 1.2 * (want - 1.0)
+    assert abs(step_pf) < 0.04
+    assert rm["mask"][-1] == 1 and pf["mask"][-1] == 0
