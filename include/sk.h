@@ -60,6 +60,16 @@ typedef enum {
                                   m = M*N_eff; each tail at probability Phi(-a)
                                   (Wilson-Hilferty gamma quantile).  Tends to
                                   the symmetric interval as m grows. */
+#define SK_RUNNING_MU 0x4u      /* served streams: normalise each input by its
+                                  running power mu_i = P_i / (2^6 M) from the
+                                  state instead of the frame's S1_i / M, and use
+                                  Eq. avgSK (first line) with n' = M N_eff and
+                                  S1bar = sum S1_i/mu_i, S2bar = sum S2_i/mu_i^2,
+                                  rescaled by Eq. final (first line); flagged
+                                  in double against the symmetric interval.
+                                  Unlike the per-frame normalisation it also
+                                  reacts to power steps.  Keeps the state like
+                                  SK_RUNNING_OFFSET. */
 
 #define SK_MAX_INPUTS 4096
 #define SK_MAX_TIME 4096
@@ -70,7 +80,7 @@ typedef struct {
     int32_t n_inputs;   /* N, 1..SK_MAX_INPUTS                              */
     int32_t n_time;     /* M (the paper's n), 2..SK_MAX_TIME                */
     int32_t layout;     /* sk_layout_t                                      */
-    uint32_t flags;     /* SK_RUNNING_OFFSET | SK_THRESH_PEARSON3           */
+    uint32_t flags;     /* SK_RUNNING_OFFSET | SK_THRESH_PEARSON3 | SK_RUNNING_MU */
     double n_sigma;     /* a: flag outside centre +- a*sqrt(4/(M N_eff))    */
     double mean_offset; /* static delta added to the centre 1 (App. B)     */
     /* optional host table [SK_OFFSET_BUCKETS] of per-input offsets in Q

@@ -31,6 +31,7 @@ SK_LAYOUT_TIME_MAJOR = 0
 SK_LAYOUT_INPUT_MAJOR = 1
 SK_RUNNING_OFFSET = 0x1
 SK_THRESH_PEARSON3 = 0x2
+SK_RUNNING_MU = 0x4
 SK_OFFSET_BUCKETS = 4096
 SK_MAX_INPUTS = 4096
 SK_MAX_TIME = 4096

@@ -345,6 +345,9 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.e_tab = d_e;
     it.fast = fast ? 1 : (imajor ? 2 : 0);
     it.prefetch = 1;
+    it.running_mu = (p.flags & SK_RUNNING_MU) ? 1 : 0;
+    it.n_sigma = p.n_sigma;
+    it.mean_offset = p.mean_offset;
     return it;
 }
 
@@ -394,7 +397,7 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
         return set_error(SK_ERR_INVALID_ARG, "layout %d unknown", p.layout);
     if (!(p.n_sigma >= 0.0) || !std::isfinite(p.n_sigma) || !std::isfinite(p.mean_offset))
         return set_error(SK_ERR_INVALID_ARG, "n_sigma must be finite and >= 0, mean_offset finite");
-    if (p.flags & ~(SK_RUNNING_OFFSET | SK_THRESH_PEARSON3))
+    if (p.flags & ~(SK_RUNNING_OFFSET | SK_THRESH_PEARSON3 | SK_RUNNING_MU))
         return set_error(SK_ERR_INVALID_ARG, "unknown flags 0x%x", p.flags);
     int ndev = 0;
     cudaError_t ce = cudaGetDeviceCount(&ndev);
@@ -453,7 +456,7 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
         pl->c_tab[ne] = (float)((double)(M + 1) / ((double)(M - 1) * (double)ne));
     }
     pl->etab.assign(kOffsetBuckets, 0);
-    if (p.flags & SK_RUNNING_OFFSET) {
+    if (p.flags & (SK_RUNNING_OFFSET | SK_RUNNING_MU)) {
         if (p.offset_table)
             memcpy(pl->etab.data(), p.offset_table, sizeof(int64_t) * kOffsetBuckets);
         else

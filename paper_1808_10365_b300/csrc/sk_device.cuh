@@ -65,7 +65,9 @@ struct Item {
     float *sk_in;            // per-input SK^_i [n_frames][N] (Eq. originalSK), or null
     uint8_t *mask_in;        // per-input flag at the N_eff = 1 thresholds, or null
     int32_t prefetch;        // 1: input in device memory, L2 bulk prefetch allowed
-    int32_t pad2;
+    int32_t running_mu;      // served: normalise by the running power in the state
+    double n_sigma;          // running-mu decision (double domain)
+    double mean_offset;
 };
 
 // Work of one CTA.  kind 0: frames [f_begin, f_end) of item `item`, the CTA's
@@ -220,8 +222,45 @@ __device__ __forceinline__ bool input_term(int32_t s1, int32_t s2, int32_t M, fl
 struct TeamSmem {
     long long q[2][kSlots];
     long long e[2][kSlots];
+    long long ra[2][kSlots];
+    long long rb[2][kSlots];
     int cnt[2][kSlots];
+    int rn[2][kSlots];
 };
+
+// Sum of the running-mu terms (A, B, n) over the team, every thread gets them.
+// Called by every thread of a served kernel whatever its item's flags, so that
+// teams sharing a warp take the same shuffles.
+__device__ __forceinline__ void team_sum_rmu(int64_t &a, int64_t &b, int32_t &n, int team_log2,
+                                            int team_idx, int parity, TeamSmem &ts)
+{
+    const int team = 1 << team_log2;
+    const int w = team < 32 ? team : 32;
+    for (int o = w >> 1; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+        n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
+    }
+    if (team > 32) {
+        const int nw = team >> 5;
+        const int slot0 = team_idx * nw;
+        const int wit = (threadIdx.x >> 5) - slot0;
+        if ((threadIdx.x & 31) == 0) {
+            ts.ra[parity][slot0 + wit] = a;
+            ts.rb[parity][slot0 + wit] = b;
+            ts.rn[parity][slot0 + wit] = n;
+        }
+        named_sync(1 + team_idx, team);
+        a = 0;
+        b = 0;
+        n = 0;
+        for (int j = 0; j < nw; ++j) {
+            a += ts.ra[parity][slot0 + j];
+            b += ts.rb[parity][slot0 + j];
+            n += ts.rn[parity][slot0 + j];
+        }
+    }
+}
 
 // Sum (q, cnt, e) over the team's threads; every thread of the team gets the
 // totals.  Teams of up to 32 threads stay inside a warp; larger teams go
@@ -276,7 +315,8 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
 {
     const bool mine = fvalid && col0 < it.N;
     const bool stateful = SERVED && it.state != nullptr;
-    int64_t q = 0, e = 0;
+    int64_t q = 0, e = 0, ra = 0, rb = 0;
+    int32_t rn = 0;
     int32_t cnt = 0;
     uint32_t P[kVec];
     if (mine) {
@@ -312,6 +352,7 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
                 }
         }
         if (stateful) {
+            const int64_t sc = (int64_t)(1 << kStateShift) * it.M;
 #pragma unroll
             for (int k = 0; k < kVec; ++k) {
                 P[k] = 0;
@@ -321,13 +362,49 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
                     P[k] = pk;
                     if (s1[k] > 0)
                         e += it.e_tab[bucket_of(pk, it.M)];
+                    if (it.running_mu && s1[k] > 0 && pk > 0) {
+                        // a = S1 / mu, b = S2 / mu^2 with mu = P / (2^k M): exact
+                        // integer numerators and denominators, one fp32 divide each
+                        const float fa = __fdiv_rn(__ll2float_rn((int64_t)s1[k] * sc),
+                                                   __ll2float_rn((int64_t)pk));
+                        const float fb =
+                            __fdiv_rn(__ll2float_rn((int64_t)s2[k] * sc * sc),
+                                      __ll2float_rn((int64_t)pk * (int64_t)pk));
+                        ra += __float2ll_rn(__fmul_rn(fa, 16777216.0f));
+                        rb += __float2ll_rn(__fmul_rn(fb, 16777216.0f));
+                        rn += 1;
+                    }
                 }
             }
         }
     }
     team_sum(q, cnt, e, it.team_log2, team_idx, parity, ts, SERVED);
+    if (SERVED)
+        team_sum_rmu(ra, rb, rn, it.team_log2, team_idx, parity, ts);
     uint8_t m = 1;
-    if (cnt > 0) {
+    float sk_rmu = __int_as_float(0x7FC00000);
+    if (SERVED && it.running_mu && stateful) {
+        // Eq. (avgSK) first line over n' = M N_eff samples, rescaled by Eq. (final)
+        // first line; flagged against the symmetric interval around 1 + delta
+        if (rn > 0 && ra > 0) {
+            const double mp = (double)((int64_t)it.M * rn);
+            const double af = __dmul_rn(__ll2double_rn(ra), 0x1p-24);
+            const double bf = __dmul_rn(__ll2double_rn(rb), 0x1p-24);
+            const double t1 = __ddiv_rn(__dadd_rn(mp, 1.0), __dsub_rn(mp, 1.0));
+            const double t2 = __dsub_rn(__ddiv_rn(__dmul_rn(mp, bf), __dmul_rn(af, af)), 1.0);
+            const double skh = __dmul_rn(t1, t2);
+            const double sc2 = __ddiv_rn(__dmul_rn(__dsub_rn(mp, 1.0), (double)(it.M + 1)),
+                                         __dmul_rn(__dadd_rn(mp, 1.0), (double)(it.M - 1)));
+            const double skd = __dmul_rn(sc2, skh);
+            const double cen = __dadd_rn(
+                __dadd_rn(1.0, it.mean_offset),
+                __ddiv_rn(__dmul_rn(__ll2double_rn(e), (double)(it.M + 1)),
+                          __dmul_rn(__dmul_rn((double)(it.M - 1), (double)rn), 4294967296.0)));
+            const double half = __ddiv_rn(__dmul_rn(it.n_sigma, 2.0), __dsqrt_rn(mp));
+            m = (skd > __dadd_rn(cen, half) || skd < __dsub_rn(cen, half)) ? 1 : 0;
+            sk_rmu = __double2float_rn(skd);
+        }
+    } else if (cnt > 0) {
         int64_t lo = it.t_lo[cnt] + (stateful ? e : 0);
         int64_t hi = it.t_hi[cnt] + (stateful ? e : 0);
         m = (q > hi || q < lo) ? 1 : 0;
@@ -335,7 +412,9 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
     if (fvalid && lit == 0) {
         if (it.sk) {
             float skv = __int_as_float(0x7FC00000);
-            if (cnt > 0)
+            if (SERVED && it.running_mu && stateful)
+                skv = sk_rmu;
+            else if (cnt > 0)
                 skv = __fmul_rn(__fmul_rn(__ll2float_rn(q), 0x1p-32f), it.c_tab[cnt]);
             it.sk[frame] = skv;
         }
@@ -547,24 +626,6 @@ __device__ __forceinline__ void run_imajor(const Item &it, int64_t f_begin, int6
             lk = 0;
             lc = 0;
             lf += T;
-        }
-        // one thread of the team brings the block of inputs one step beyond the
-        // next batch into L2: the team reads inputs in contiguous blocks of nseg
-        if (lit == 0 && lc == 0) {
-            const int step = C >= KB ? 1 : KB / C;
-            int i0 = (lk + step) * nseg;
-            int64_t pf_frame = lf;
-            if (i0 >= N) {
-                i0 -= ((N + nseg - 1) / nseg) * nseg;  // into the next frame
-                pf_frame += T;
-            }
-            if (i0 >= 0 && i0 < N && pf_frame < f_end) {
-                const int i1 = min(N, i0 + step * nseg);
-                const uint32_t total = (uint32_t)(i1 - i0) * (uint32_t)M;
-                const uint8_t *pp = it.in + pf_frame * fbytes + (int64_t)i0 * M;
-                for (uint32_t o = 0; o < total; o += 32768u)
-                    prefetch_l2(pp + o, total - o < 32768u ? total - o : 32768u);
-            }
         }
     };
 

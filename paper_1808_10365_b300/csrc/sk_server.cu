@@ -539,7 +539,7 @@ extern "C" sk_status_t sk_stream_open(sk_server_t s, const sk_params_t *params,
         r->M = params->n_time;
         r->fbytes = fbytes;
         r->ring_frames = ring_frames;
-        r->stateful = (params->flags & SK_RUNNING_OFFSET) != 0;
+        r->stateful = (params->flags & (SK_RUNNING_OFFSET | SK_RUNNING_MU)) != 0;
         r->share = share;
         r->small = small;
         if (cudaMalloc(&r->d_state, sizeof(uint32_t) * r->N) != cudaSuccess)

@@ -274,3 +274,35 @@ def test_ring_wraps_many_times_with_changing_data():
     assert np.array_equal(np.array(got_m, dtype=np.uint8), want["mask"])
     assert np.array_equal(np.array(got_sk, dtype=np.float32).view(np.uint32),
                           want["sk"].view(np.uint32))
+
+
+def test_running_mu_streams_match_oracle():
+    """SK_RUNNING_MU: frames normalised by the running power of each input; SK and
+    masks equal the oracle's running-mu statement, including a power step."""
+    _need_gpu()
+    M, N, T = 256, 128, 24
+    sig = np.full(N, 1.6)
+    ds1 = synth.Dataset(n_frames=T, M=M, N=N, seed=41, sigma=sig,
+                        rfi=[synth.RFI(9, "cw", 3.0)])
+    sig2 = sig.copy()
+    sig2[: N // 2] *= np.sqrt(2.0)
+    ds2 = synth.Dataset(n_frames=4, M=M, N=N, seed=42, sigma=sig2)
+    x = np.concatenate([ds1.generate_cpu(), ds2.generate_cpu()])
+    e = dg.offset_table(M)
+    want = served.served_flags(x, M, N, e, running_mu=True)
+    server = sk.sk_server_create(0, 1 << 30)
+    try:
+        sid = sk.sk_stream_open(server, N, M, ring_frames=4, flags=sk.SK_RUNNING_MU,
+                                offset_table=e)
+        got = [sk.sk_ticket_wait(server, sk.sk_stream_submit(server, sid, x[f], f))
+               for f in range(x.shape[0])]
+        sk.sk_stream_drain(server, sid)
+        P = np.frombuffer(sk.sk_stream_get_state(server, sid), dtype=np.uint32)[2:]
+        sk.sk_stream_close(server, sid)
+    finally:
+        sk.sk_server_destroy(server)
+    assert np.array_equal(np.array([m for _, m in got], dtype=np.uint8), want["mask"])
+    assert np.array_equal(np.array([v for v, _ in got], dtype=np.float32).view(np.uint32),
+                          want["sk"].astype(np.float32).view(np.uint32))
+    assert np.array_equal(P.astype(np.int64), want["P"])
+    assert want["mask"][9] == 1 and want["mask"][T] == 1
