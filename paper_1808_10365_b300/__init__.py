@@ -17,6 +17,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsk.so")
+# tile choices measured on B300 by autotune.py; a caller's SK_AUTOTUNE_CACHE wins
+os.environ.setdefault("SK_AUTOTUNE_CACHE", os.path.join(HERE, "tiles_b300.txt"))
 
 SK_OK = 0
 SK_ERR_INVALID_ARG = 1
