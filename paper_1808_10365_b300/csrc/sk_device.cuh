@@ -219,6 +219,52 @@ __device__ __forceinline__ bool input_term(int32_t s1, int32_t s2, int32_t M, fl
     return true;
 }
 
+// Exact conversions on the ALU and FMA pipes (the int64 <-> fp32 conversion
+// instructions run on the FP64 pipe, which this GPU has little of).
+//
+// fp32 nearest to 0 <= x < 2^43: x = h 2^20 + l with h, l < 2^23 both exact in
+// fp32 (formed by OR-ing them into the mantissa of 2^23 and subtracting 2^23);
+// fmaf forms h 2^20 + l exactly and rounds once, so the result is x rounded to
+// nearest even.
+__device__ __forceinline__ float u43_to_f32_rn(int64_t x)
+{
+    const uint32_t h = (uint32_t)((uint64_t)x >> 20);
+    const uint32_t l = (uint32_t)x & 0xFFFFFu;
+    const float fh = __fsub_rn(__uint_as_float(0x4B000000u | h), 8388608.0f);
+    const float fl = __fsub_rn(__uint_as_float(0x4B000000u | l), 8388608.0f);
+    return __fmaf_rn(fh, 1048576.0f, fl);
+}
+
+// Nearest integer (ties to even) to a non-negative fp32 y < 2^62: below 2^23 by
+// adding and removing 2^23 (the fp32 addition rounds to an integer), above it y
+// already is an integer, its mantissa shifted by its exponent.
+__device__ __forceinline__ int64_t f32_to_i64_rn(float y)
+{
+    const uint32_t bits = __float_as_uint(y);
+    if (y < 8388608.0f)
+        return (int64_t)(__float_as_uint(__fadd_rn(y, 8388608.0f)) - 0x4B000000u);
+    const uint32_t m = (bits & 0x7FFFFFu) | 0x800000u;
+    const int sh = (int)(bits >> 23) - 150;  // exponent - 127 - 23 >= 0
+    return (int64_t)((uint64_t)m << sh);
+}
+
+#ifndef SK_EPILOGUE_ALU
+#define SK_EPILOGUE_ALU 1
+#endif
+
+// input_term with the conversions above (bit-identical results).
+__device__ __forceinline__ bool input_term_alu(int32_t s1, int32_t s2, int32_t M, float &r,
+                                               int64_t &qi)
+{
+    if (s1 <= 0)
+        return false;
+    int64_t den = (int64_t)s1 * (int64_t)s1;
+    int64_t d = (int64_t)M * (int64_t)s2 - den;
+    r = __fdiv_rn(u43_to_f32_rn(d), u43_to_f32_rn(den));
+    qi = f32_to_i64_rn(__fmul_rn(r, 4294967296.0f));
+    return true;
+}
+
 struct TeamSmem {
     long long q[2][kSlots];
     long long e[2][kSlots];
@@ -325,7 +371,8 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
             if (col0 + k < it.N) {
                 float r = 0.0f;
                 int64_t qi = 0;
-                const bool has = input_term(s1[k], s2[k], it.M, r, qi);
+                const bool has = SK_EPILOGUE_ALU ? input_term_alu(s1[k], s2[k], it.M, r, qi)
+                                                 : input_term(s1[k], s2[k], it.M, r, qi);
                 if (has) {
                     q += qi;
                     cnt += 1;
