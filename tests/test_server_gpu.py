@@ -306,3 +306,36 @@ def test_running_mu_streams_match_oracle():
                           want["sk"].astype(np.float32).view(np.uint32))
     assert np.array_equal(P.astype(np.int64), want["P"])
     assert want["mask"][9] == 1 and want["mask"][T] == 1
+
+
+def test_close_and_destroy_with_work_outstanding():
+    """Closing a stream waits for its frames; submits to a closed or unknown stream are
+    refused; a server destroyed with tickets still uncollected shuts down cleanly."""
+    _need_gpu()
+    N, M = 256, 256
+    ds, x = _stream_data(50, N, M, 12)
+    server = sk.sk_server_create(0, 1 << 30)
+    sid = sk.sk_stream_open(server, N, M, ring_frames=8, flags=sk.SK_RUNNING_OFFSET)
+    tickets = [sk.sk_stream_submit(server, sid, x[f], f) for f in range(8)]
+    sk.sk_stream_close(server, sid)                  # waits for the 8 frames
+    for t in tickets:                                # their results are still collectable
+        skv, m = sk.sk_ticket_wait(server, t, 5_000_000)
+        assert m in (0, 1)
+    for bad in (sid, 12345):
+        with pytest.raises(sk.SkError) as e:
+            sk.sk_stream_submit(server, bad, x[0], 0)
+        assert e.value.status == sk.SK_ERR_INVALID_ARG
+    with pytest.raises(sk.SkError) as e:
+        sk.sk_stream_close(server, sid)
+    assert e.value.status == sk.SK_ERR_CLOSED
+    sid2 = sk.sk_stream_open(server, N, M, ring_frames=8)
+    for f in range(6):
+        sk.sk_stream_submit(server, sid2, x[f], f)   # never collected
+    sk.sk_server_destroy(server)
+    # the device is still usable afterwards
+    plan = sk.sk_plan_create(N, M)
+    d = torch.from_numpy(x[:2].reshape(-1)).to("cuda")
+    mask = torch.empty(2, dtype=torch.uint8, device="cuda")
+    sk.sk_flag(plan, d, 2, None, mask)
+    torch.cuda.synchronize()
+    sk.sk_plan_destroy(plan)
