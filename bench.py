@@ -248,6 +248,52 @@ def run_reference(args):
     return 0
 
 
+def input_major_bench(n_freq: int, ref_mask, reps: int = 10, dev_index: int = 0):
+    """The benchmark workload in the input-major layout [frame][input][t] (the same
+    samples, transposed per frame by the generator) through sk_flag; its masks are
+    compared with the time-major run's."""
+    import dataclasses
+
+    import torch
+
+    import paper_1808_10365_b300 as sk
+
+    dev = torch.device("cuda", dev_index)
+    datasets = [dataclasses.replace(d, layout=1) for d in workload_datasets(0, n_freq)]
+    F = sum(d.n_frames for d in datasets)
+    nbytes = F * M_T * N_IN
+    d_in = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    off = 0
+    for d in datasets:
+        d.generate_gpu(d_in[off:off + d.nbytes])
+        off += d.nbytes
+    d_sk = torch.empty(F, dtype=torch.float32, device=dev)
+    d_mask = torch.empty(F, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N_IN, M_T, 3.0, static_offset(datasets), layout=1,
+                             device=dev_index)
+    st = torch.cuda.Stream(dev)
+    for _ in range(3):
+        sk.sk_flag(plan, d_in, F, d_sk, d_mask, st)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    for a, b in ev:
+        a.record(st)
+        sk.sk_flag(plan, d_in, F, d_sk, d_mask, st)
+        b.record(st)
+    st.synchronize()
+    sk.sk_plan_destroy(plan)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    same = bool(torch.equal(d_mask, ref_mask)) if ref_mask is not None else None
+    del d_in
+    torch.cuda.empty_cache()
+    alg = nbytes + F * 5
+    peak, _ = peaks()
+    return {"workload": WORKLOAD.format(f=n_freq) + ", input-major [frame][input][t]",
+            "value": nbytes / (ms * 1e-3) / 1e9, "unit": UNIT, "ms": ms,
+            "roofline_frac": alg / (ms * 1e-3) / 1e9 / peak,
+            "masks_identical_to_time_major": same}
+
+
 def batched_bench(reps: int = 10, dev_index: int = 0):
     """Mixed workload: 64 frequencies of N=2048 and 64 of N=256, M in {128, 256, 1024}
     per frequency from the seed, 500 frames each.  One graph-captured persistent launch
@@ -484,6 +530,7 @@ def run_gpu(args):
     if ws == 1 and not args.no_extras:
         del d_in
         torch.cuda.empty_cache()
+        line["input_major"] = input_major_bench(args.freqs, d_mask, dev_index=dev.index)
         line["batched"] = batched_bench(dev_index=dev.index)
         line["served"] = served_bench(args.served_seconds, True, dev.index)
         line["served_replay"] = served_bench(min(args.served_seconds, 1.0), False, dev.index)

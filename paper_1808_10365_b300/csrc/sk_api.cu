@@ -99,9 +99,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Input-major fast path, one-item launches only (batched and served launches
-// take input-major items through the general path).  G lanes per input.
-template <int G>
+// Input-major fast paths, one-item launches only (batched and served launches
+// take input-major items through the general path).  G lanes per input; CH > 0
+// selects the grouped path for M = 16 G CH (PF: L2 prefetch of the next group),
+// CH = 0 the per-input path for any M that 16 G divides.
+template <int G, int CH, bool PF>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_imajor_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
                      const int32_t *__restrict__ cta_chunks, Item single)
@@ -114,10 +116,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t Gd = gridDim.x;
     const int64_t fb = F * (int64_t)blockIdx.x / Gd;
     const int64_t fe = F * ((int64_t)blockIdx.x + 1) / Gd;
-    if (single.fast == 2 && single.M % (16 * G) == 0 && single.team_log2 >= 5)
-        run_imajor<G, 8>(single, fb, fe, lb, ts, parity);
-    else
-        run_general<false>(single, fb, fe, lb, ts, parity);
+    if constexpr (CH > 0) {
+        if (single.fast == 2 && single.M == 16 * G * CH && single.team_log2 >= 5)
+            run_imajor_grouped<G, CH, PF>(single, fb, fe, lb, ts, parity);
+        else
+            run_general<false>(single, fb, fe, lb, ts, parity);
+    } else {
+        if (single.fast == 2 && single.M % (16 * G) == 0 && single.team_log2 >= 5)
+            run_imajor<G, 8>(single, fb, fe, lb, ts, parity);
+        else
+            run_general<false>(single, fb, fe, lb, ts, parity);
+    }
 }
 
 using KernelFn = void (*)(const Item *, const Chunk *, const int32_t *, Item);
@@ -132,10 +141,19 @@ static const KernelFn kBatched[2] = {sk_fused_kernel<16, 2, false, 0, 1>,
                                      sk_fused_kernel<8, 2, false, 0, 1>};
 static const KernelFn kServed[2] = {sk_fused_kernel<16, 2, true, 0, 2>,
                                     sk_fused_kernel<8, 2, true, 0, 2>};
+// input-major: per-input path G = 2, 4, 8; grouped path G = 8, CH = 1, 2, 4, 8
+// without and with the L2 prefetch
+static const KernelFn kImajor[11] = {
+    sk_imajor_kernel<2, 0, false>,    sk_imajor_kernel<4, 0, false>,
+    sk_imajor_kernel<8, 0, false>,    sk_imajor_kernel<8, 1, false>,
+    sk_imajor_kernel<8, 2, false>,    sk_imajor_kernel<8, 4, false>,
+    sk_imajor_kernel<8, 8, false>,    sk_imajor_kernel<8, 1, true>,
+    sk_imajor_kernel<8, 2, true>,     sk_imajor_kernel<8, 4, true>,
+    sk_imajor_kernel<8, 8, true>};
 
-// Lanes per input on the input-major path: 4 up to M = 512, 8 above (measured
-// best on B300), or SK_IMAJOR_LANES (2, 4 or 8); reduced while 16 G does not
-// divide M.
+// Lanes per input on the per-input input-major path: 4 up to M = 512, 8 above
+// (measured best on B300), or SK_IMAJOR_LANES (2, 4 or 8); reduced while 16 G
+// does not divide M.
 int imajor_lanes(int M)
 {
     static const int forced = [] {
@@ -147,6 +165,40 @@ int imajor_lanes(int M)
     while (g > 2 && M % (16 * g) != 0)
         g /= 2;
     return g;
+}
+
+// Chunks per lane per input on the grouped input-major path (G = 8 lanes): M/128
+// for M in {128, 256, 512, 1024}, else 0 (the per-input path).
+// SK_IMAJOR_GROUPED=0 turns the grouped path off.
+int imajor_chunks(int M)
+{
+    static const bool off = [] {
+        const char *v = getenv("SK_IMAJOR_GROUPED");
+        return v && atoi(v) == 0;
+    }();
+    if (off)
+        return 0;
+    return (M == 128 || M == 256 || M == 512 || M == 1024) ? M / 128 : 0;
+}
+
+static bool imajor_prefetch()
+{
+    static const bool on = [] {
+        const char *v = getenv("SK_IMAJOR_PREFETCH");
+        return !(v && atoi(v) == 0);
+    }();
+    return on;
+}
+
+static KernelFn imajor_kernel(int M)
+{
+    const int ch = imajor_chunks(M);
+    if (ch > 0) {
+        const int c = ch == 1 ? 0 : (ch == 2 ? 1 : (ch == 4 ? 2 : 3));
+        return kImajor[(imajor_prefetch() ? 7 : 3) + c];
+    }
+    const int g = imajor_lanes(M);
+    return kImajor[g == 2 ? 0 : (g == 4 ? 1 : 2)];
 }
 
 // Tile for a requested rows-per-batch and whether every M is a multiple of 32.
@@ -166,9 +218,8 @@ sk_status_t ensure_kernel_attrs(int device)
         if (d == device)
             return SK_OK;
     std::vector<KernelFn> fns;
-    fns.push_back(sk_imajor_kernel<2>);
-    fns.push_back(sk_imajor_kernel<4>);
-    fns.push_back(sk_imajor_kernel<8>);
+    for (KernelFn f : kImajor)
+        fns.push_back(f);
     for (int t = 0; t < 2; ++t) {
         fns.push_back(kServed[t]);
         fns.push_back(kBatched[t]);
@@ -207,10 +258,8 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         return set_error(SK_ERR_UNSUPPORTED, "served items go through launch_schedule");
     const int nci = it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
     KernelFn fn = kSingle[pick_tile(rows, it.M % 32 == 0)][nci];
-    if (it.fast == 2) {
-        const int gsel = imajor_lanes(it.M);
-        fn = gsel == 2 ? sk_imajor_kernel<2> : (gsel == 4 ? sk_imajor_kernel<4> : sk_imajor_kernel<8>);
-    }
+    if (it.fast == 2)
+        fn = imajor_kernel(it.M);
     fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, it);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -416,10 +465,12 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
     pl->team_log2 = ceil_log2((N + kVec - 1) / kVec);
     pl->fast = (p.layout == SK_LAYOUT_TIME_MAJOR) && (N % kVec == 0) && (M % kFlushRows == 0);
     const int gl = imajor_lanes(M);
-    pl->imajor = (p.layout == SK_LAYOUT_INPUT_MAJOR) && (M % (16 * gl) == 0);
+    const bool grouped = imajor_chunks(M) > 0;
+    pl->imajor = (p.layout == SK_LAYOUT_INPUT_MAJOR) && (grouped || M % (16 * gl) == 0);
     if (pl->imajor) {
-        // segments of gl lanes, about 8 inputs per segment, 32..512 threads
-        int tl = ceil_log2(((int64_t)N * gl + 7) / 8);
+        // grouped: one team thread per input of a group row, 32..512 threads;
+        // per-input: segments of gl lanes, about 8 inputs per segment, 32..512
+        int tl = grouped ? ceil_log2(N) : ceil_log2(((int64_t)N * gl + 7) / 8);
         pl->team_log2 = tl < 5 ? 5 : (tl > 9 ? 9 : tl);
     }
     pl->rows = 16;

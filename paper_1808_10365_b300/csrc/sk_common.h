@@ -28,6 +28,7 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
                             int device, cudaStream_t st);
 int pick_tile(int rows, bool all_m32);
 int imajor_lanes(int M);
+int imajor_chunks(int M);
 sk_status_t ensure_kernel_attrs(int device);
 int sm_count(int device);
 

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <utility>
 
 namespace sk {
@@ -742,6 +743,196 @@ __device__ __forceinline__ void run_imajor(const Item &it, int64_t f_begin, int6
                 if (half == 0)
                     load_batch(A);
             }
+        }
+        team_sum(q, cnt, e, team_log2, team_idx, parity, ts, false);
+        if (fvalid && lit == 0) {
+            uint8_t m = 1;
+            if (cnt > 0)
+                m = (q > it.t_hi[cnt] || q < it.t_lo[cnt]) ? 1 : 0;
+            if (it.sk) {
+                float skv = __int_as_float(0x7FC00000);
+                if (cnt > 0)
+                    skv = __fmul_rn(__fmul_rn(__ll2float_rn(q), 0x1p-32f), it.c_tab[cnt]);
+                it.sk[frame] = skv;
+            }
+            if (it.mask)
+                it.mask[frame] = m;
+            if (it.q)
+                it.q[frame] = q;
+            if (it.neff)
+                it.neff[frame] = cnt;
+        }
+        parity ^= 1;
+        frame += T;
+    }
+}
+
+// 16-byte streaming load at base + OFF, OFF an immediate of the instruction.
+template <int OFF>
+__device__ __forceinline__ uint4 ldg_stream16_at(const uint8_t *base)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4+%5];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(base), "n"(OFF));
+    return v;
+}
+
+// Batch nb of a group on the grouped input-major path: chunk t is chunk t % CH of
+// input nb IPB + t / CH; all offsets are load immediates.
+template <int M, int G, int CH, int IPB, int nb, int... Ts>
+__device__ __forceinline__ void load_group_imm(uint4 *buf, const uint8_t *base,
+                                               std::integer_sequence<int, Ts...>)
+{
+    ((buf[Ts] = ldg_stream16_at<(nb * IPB + Ts / CH) * M + (Ts % CH) * G * 16>(base)), ...);
+}
+
+template <int M, int G, int CH, int KB, int nb>
+__device__ __forceinline__ void load_group_batch(uint4 (&buf)[KB], const uint8_t *base, int live)
+{
+    constexpr int IPB = KB / CH;
+    if (live == G) {
+        load_group_imm<M, G, CH, IPB, nb>(buf, base, std::make_integer_sequence<int, KB>{});
+    } else {
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+            const int u = nb * IPB + t / CH;
+            buf[t] = u < live ? ldg_stream16(base + u * M + (t % CH) * G * 16)
+                              : make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+}
+
+// Batches nb .. NB-1 of a group: load the following batch into nxt (the group's
+// next one, or batch 0 of the next group), then add cur into the sums.
+template <int M, int G, int CH, int NB, int KB, int nb>
+__device__ __forceinline__ void group_batches(uint4 (&cur)[KB], uint4 (&nxt)[KB],
+                                              const uint8_t *cur_base, int cur_live,
+                                              const uint8_t *nxt_base, int nxt_live,
+                                              uint32_t lb, int32_t (&s1)[G], int32_t (&s2)[G])
+{
+    if constexpr (nb < NB) {
+        constexpr int IPB = KB / CH;
+        if constexpr (nb + 1 < NB)
+            load_group_batch<M, G, CH, KB, nb + 1>(nxt, cur_base, cur_live);
+        else
+            load_group_batch<M, G, CH, KB, 0>(nxt, nxt_base, nxt_live);
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+            const uint32_t a = accum16(cur[t], lb);
+            s1[nb * IPB + t / CH] += (int32_t)(a >> kPackShift);
+            s2[nb * IPB + t / CH] += (int32_t)(a & kPackMask);
+        }
+        group_batches<M, G, CH, NB, KB, nb + 1>(nxt, cur, cur_base, cur_live, nxt_base, nxt_live,
+                                                lb, s1, s2);
+    }
+}
+
+// Input-major path with grouped inputs: layout [frame][input][t] with
+// M = 16 G CH.  A segment of G lanes owns a group of G consecutive inputs; lane
+// j reads the 16-byte chunks j, j+G, ..., j+(CH-1)G of each of them (one warp
+// instruction reads 32/G whole 128-byte lines when G = 8), every offset inside
+// the group a load immediate.  Each lane keeps S1, S2 for all G inputs of the
+// group; a reduce-scatter over the segment's lanes (G-1 shuffle pairs) leaves
+// input u's totals in lane u, so all lanes form an input term at once.  The
+// segment's groups are (k nseg + seg) G .. + G-1 for k = 0, 1, ...; a frame is
+// NG = ceil(N / team) groups per segment.  The group streams through two
+// register batches of KB chunks (NB batches per group, NB even, so every group
+// starts in batch A); with PF the next group's bytes are requested into L2 while
+// this one is read.
+template <int G, int CH, bool PF>
+__device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_begin,
+                                                   int64_t f_end, uint32_t lb, TeamSmem &ts,
+                                                   int &parity)
+{
+    constexpr int M = 16 * G * CH;
+    constexpr int NB = (G * CH / 8) < 2 ? 2 : G * CH / 8;  // batches per group
+    constexpr int KB = G * CH / NB;                       // chunks per batch
+    static_assert(KB % CH == 0 && NB % 2 == 0, "batch shape");
+    const int team_log2 = it.team_log2;
+    const int team = 1 << team_log2;
+    const int T = kThreads >> team_log2;
+    const int team_idx = threadIdx.x >> team_log2;
+    const int lit = threadIdx.x & (team - 1);
+    const int nseg = team / G;
+    const int seg = lit / G, j = lit % G;
+    const int N = it.N;
+    const int NG = (N + team - 1) / team;
+    const int64_t fbytes = (int64_t)M * N;
+    const int64_t kmax = (f_end - f_begin + T - 1) / T;
+
+    // inputs of group (frame f, k) that this segment may read: 0..G
+    auto live_of = [&](int64_t f, int k) -> int {
+        const int i0 = (k * nseg + seg) * G;
+        const int r = N - i0;
+        return (f < f_end) ? (r < 0 ? 0 : (r > G ? G : r)) : 0;
+    };
+    auto base_of = [&](int64_t f, int k) -> const uint8_t * {
+        return it.in + f * fbytes + (int64_t)((k * nseg + seg) * G) * M + j * 16;
+    };
+    uint4 A[KB], B[KB];
+    int64_t frame = f_begin + team_idx;
+    const uint8_t *cur_base = base_of(frame, 0);
+    int cur_live = live_of(frame, 0);
+    load_group_batch<M, G, CH, KB, 0>(A, cur_base, cur_live);
+    for (int64_t kk = 0; kk < kmax; ++kk) {
+        const bool fvalid = frame < f_end;
+        int64_t q = 0, e = 0;
+        int32_t cnt = 0;
+        for (int k = 0; k < NG; ++k) {
+            // the group after this one: next k, else the team's next frame
+            const int64_t nf = (k + 1 < NG) ? frame : frame + T;
+            const int nk = (k + 1 < NG) ? k + 1 : 0;
+            const uint8_t *nxt_base = base_of(nf, nk);
+            const int nxt_live = live_of(nf, nk);
+            if (PF && nxt_live > 0 && j == 0)
+                prefetch_l2(nxt_base, (uint32_t)(nxt_live * M));
+            int32_t s1[G], s2[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                s1[u] = 0;
+                s2[u] = 0;
+            }
+            group_batches<M, G, CH, NB, KB, 0>(A, B, cur_base, cur_live, nxt_base, nxt_live, lb,
+                                               s1, s2);
+            // reduce-scatter: lane j ends with input j's sums in s1[0], s2[0]
+#pragma unroll
+            for (int o = G / 2; o >= 1; o >>= 1) {
+                const bool up = (j & o) != 0;
+#pragma unroll
+                for (int t = 0; t < o; ++t) {
+                    const int32_t send1 = up ? s1[t] : s1[t + o];
+                    const int32_t send2 = up ? s2[t] : s2[t + o];
+                    const int32_t keep1 = up ? s1[t + o] : s1[t];
+                    const int32_t keep2 = up ? s2[t + o] : s2[t];
+                    s1[t] = keep1 + __shfl_xor_sync(0xFFFFFFFFu, send1, o);
+                    s2[t] = keep2 + __shfl_xor_sync(0xFFFFFFFFu, send2, o);
+                }
+            }
+            if (j < cur_live) {
+                const int i = (k * nseg + seg) * G + j;
+                float r = 0.0f;
+                int64_t qi = 0;
+                const bool has = SK_EPILOGUE_ALU ? input_term_alu(s1[0], s2[0], M, r, qi)
+                                                 : input_term(s1[0], s2[0], M, r, qi);
+                if (has) {
+                    q += qi;
+                    cnt += 1;
+                }
+                const int64_t o = frame * N + i;
+                if (it.s1) {
+                    it.s1[o] = s1[0];
+                    it.s2[o] = s2[0];
+                }
+                if (it.sk_in) {
+                    it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
+                    if (it.mask_in)
+                        it.mask_in[o] =
+                            has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+                }
+            }
+            cur_base = nxt_base;
+            cur_live = nxt_live;
         }
         team_sum(q, cnt, e, team_log2, team_idx, parity, ts, false);
         if (fvalid && lit == 0) {
