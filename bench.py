@@ -41,7 +41,9 @@ N_IN, M_T, N_FREQ, N_FRAMES = 2048, 256, 4, 1525
 WORKLOAD = "full_array_plain: {f} freq x N=2048 x M=256 x 1525 frames, 4+4-bit, 3 sigma"
 KERNEL_SOURCES = ["paper_1808_10365_b300/csrc/sk_device.cuh",
                   "paper_1808_10365_b300/csrc/sk_api.cu"]
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sk_fused_kernel_full_array.json")
+PROFILE_SUMMARY = {0: os.path.join(ROOT, "profiles", "sk_fused_kernel_full_array.json"),
+                   1: os.path.join(ROOT, "profiles", "sk_imajor_kernel_full_array.json")}
+LAYOUT_SUFFIX = {0: "", 1: ", input-major [frame][input][t]"}
 
 
 def kernel_hash() -> str:
@@ -61,10 +63,10 @@ def peaks():
         return 6400.0, "fallback"
 
 
-def profiled_traffic(algorithmic_bytes_per_launch: float):
+def profiled_traffic(algorithmic_bytes_per_launch: float, layout: int = 0):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel."""
     try:
-        with open(PROFILE_SUMMARY) as f:
+        with open(PROFILE_SUMMARY[layout]) as f:
             d = json.load(f)
     except Exception:  # noqa: BLE001
         return None
@@ -176,12 +178,15 @@ def barrier(ws: int):
         dist.barrier()
 
 
-def workload_datasets(rank: int, n_freq: int = N_FREQ):
+def workload_datasets(rank: int, n_freq: int = N_FREQ, layout: int = 0):
+    import dataclasses
+
     import synth
 
     # each rank owns its own frequencies (weak scaling): distinct seeds per rank
-    return synth.full_array_config(n_freq=n_freq, n_frames=N_FRAMES, N=N_IN, M=M_T,
-                                   cfg=1 + 1000 * rank)
+    ds = synth.full_array_config(n_freq=n_freq, n_frames=N_FRAMES, N=N_IN, M=M_T,
+                                 cfg=1 + 1000 * rank)
+    return [dataclasses.replace(d, layout=layout) for d in ds] if layout else ds
 
 
 def static_offset(datasets) -> float:
@@ -222,24 +227,25 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    import synth
 
-    ds = synth.full_array_config(n_freq=1, n_frames=N_FRAMES, N=N_IN, M=M_T)[0]
+    layout = 1 if args.layout == "input" else 0
+    ds = workload_datasets(0, 1, layout)[0]
     nf = 64
     x = ds.generate_cpu(0, nf)
     delta = float(np.mean(oracle.digitisation.delta_of_sigma(ds.sigma)))
     for _ in range(args.warmup):
-        oracle.flag(x, M_T, N_IN, 3.0, delta)
+        oracle.flag(x, M_T, N_IN, 3.0, delta, layout=layout)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.flag(x, M_T, N_IN, 3.0, delta)
+        oracle.flag(x, M_T, N_IN, 3.0, delta, layout=layout)
     el = time.perf_counter() - t0
     v = args.steps * nf * M_T * N_IN / el / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(f=N_FREQ), "sample_frames_per_step": nf},
+            "config": {"workload": WORKLOAD.format(f=args.freqs) + LAYOUT_SUFFIX[layout],
+                       "sample_frames_per_step": nf},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                              "sample": f"each step: {nf} frames of 1 frequency of the workload "
                                        f"({nf * M_T * N_IN / 1e6:.0f} MB)"},
@@ -252,14 +258,12 @@ def input_major_bench(n_freq: int, ref_mask, reps: int = 10, dev_index: int = 0)
     """The benchmark workload in the input-major layout [frame][input][t] (the same
     samples, transposed per frame by the generator) through sk_flag; its masks are
     compared with the time-major run's."""
-    import dataclasses
-
     import torch
 
     import paper_1808_10365_b300 as sk
 
     dev = torch.device("cuda", dev_index)
-    datasets = [dataclasses.replace(d, layout=1) for d in workload_datasets(0, n_freq)]
+    datasets = workload_datasets(0, n_freq, layout=1)
     F = sum(d.n_frames for d in datasets)
     nbytes = F * M_T * N_IN
     d_in = torch.empty(nbytes, dtype=torch.uint8, device=dev)
@@ -288,7 +292,7 @@ def input_major_bench(n_freq: int, ref_mask, reps: int = 10, dev_index: int = 0)
     torch.cuda.empty_cache()
     alg = nbytes + F * 5
     peak, _ = peaks()
-    return {"workload": WORKLOAD.format(f=n_freq) + ", input-major [frame][input][t]",
+    return {"workload": WORKLOAD.format(f=n_freq) + LAYOUT_SUFFIX[1],
             "value": nbytes / (ms * 1e-3) / 1e9, "unit": UNIT, "ms": ms,
             "roofline_frac": alg / (ms * 1e-3) / 1e9 / peak,
             "masks_identical_to_time_major": same}
@@ -452,7 +456,8 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
-    datasets = workload_datasets(rank, args.freqs)
+    layout = 1 if args.layout == "input" else 0
+    datasets = workload_datasets(rank, args.freqs, layout)
     F = sum(d.n_frames for d in datasets)
     fb = M_T * N_IN
     d_in = torch.empty(F * fb, dtype=torch.uint8, device=dev)
@@ -463,7 +468,7 @@ def run_gpu(args):
     delta = static_offset(datasets)
     d_sk = torch.empty(F, dtype=torch.float32, device=dev)
     d_mask = torch.empty(F, dtype=torch.uint8, device=dev)
-    plan = sk.sk_plan_create(N_IN, M_T, 3.0, delta, device=dev.index)
+    plan = sk.sk_plan_create(N_IN, M_T, 3.0, delta, layout=layout, device=dev.index)
     rows, _ = sk.sk_plan_get_tiles(plan)
     stream = torch.cuda.Stream(dev)
     bytes_per_step = F * fb
@@ -499,7 +504,7 @@ def run_gpu(args):
     mean_launch_s = statistics.mean(launch_ms) * 1e-3
     peak, peak_kind = peaks()
     achieved = alg_bytes / mean_launch_s / 1e9
-    traffic = profiled_traffic(alg_bytes)
+    traffic = profiled_traffic(alg_bytes, layout)
 
     # ---- end to end through the host-buffer entry point ----
     e2e = None
@@ -512,7 +517,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD.format(f=args.freqs), "frames_per_step": F,
+        "config": {"workload": WORKLOAD.format(f=args.freqs) + LAYOUT_SUFFIX[layout],
+                   "frames_per_step": F,
                    "bytes_per_step": bytes_per_step,
                    "l2": f"inputs {bytes_per_step / 1e9:.1f} GB per rank, > L2 (126 MB): no flush",
                    "parallelism": f"frequency sharding x{ws}, no collective",
@@ -520,7 +526,8 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": f"sk_fused_kernel<{rows},2,false,2048>",
+                     "kernel": (f"sk_fused_kernel<{rows},2,false,2048>" if layout == 0
+                                else "sk_imajor_kernel<8,2,true>"),
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": mean_launch_s * 1e3},
         "e2e": line_tail["e2e"],
@@ -530,7 +537,8 @@ def run_gpu(args):
     if ws == 1 and not args.no_extras:
         del d_in
         torch.cuda.empty_cache()
-        line["input_major"] = input_major_bench(args.freqs, d_mask, dev_index=dev.index)
+        if layout == 0:
+            line["input_major"] = input_major_bench(args.freqs, d_mask, dev_index=dev.index)
         line["batched"] = batched_bench(dev_index=dev.index)
         line["served"] = served_bench(args.served_seconds, True, dev.index)
         line["served_replay"] = served_bench(min(args.served_seconds, 1.0), False, dev.index)
@@ -553,6 +561,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--freqs", type=int, default=N_FREQ, help="frequencies per rank")
+    ap.add_argument("--layout", default="time", choices=["time", "input"],
+                    help="sample layout of the timed workload: time-major [frame][t][input] "
+                         "or input-major [frame][input][t]")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",

@@ -468,10 +468,15 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
     const bool grouped = imajor_chunks(M) > 0;
     pl->imajor = (p.layout == SK_LAYOUT_INPUT_MAJOR) && (grouped || M % (16 * gl) == 0);
     if (pl->imajor) {
-        // grouped: one team thread per input of a group row, 32..512 threads;
-        // per-input: segments of gl lanes, about 8 inputs per segment, 32..512
-        int tl = grouped ? ceil_log2(N) : ceil_log2(((int64_t)N * gl + 7) / 8);
-        pl->team_log2 = tl < 5 ? 5 : (tl > 9 ? 9 : tl);
+        // grouped: about 2 KB of the frame per team thread, 32..256 threads (a
+        // sweep over N in {256, 1024, 2048}, M in {128, 256, 512} on B300: fewer
+        // team barriers per byte than one thread per input, and two or more
+        // frames in flight per CTA); per-input: segments of gl lanes, about 8
+        // inputs per segment, 32..512 threads
+        const int tl = grouped ? ceil_log2(((int64_t)N * M + 2047) / 2048)
+                               : ceil_log2(((int64_t)N * gl + 7) / 8);
+        const int tmax = grouped ? 8 : 9;
+        pl->team_log2 = tl < 5 ? 5 : (tl > tmax ? tmax : tl);
     }
     pl->rows = 16;
     pl->grid_ctas = 0;

@@ -836,7 +836,8 @@ __device__ __forceinline__ void group_batches(uint4 (&cur)[KB], uint4 (&nxt)[KB]
 // group; a reduce-scatter over the segment's lanes (G-1 shuffle pairs) leaves
 // input u's totals in lane u, so all lanes form an input term at once.  The
 // segment's groups are (k nseg + seg) G .. + G-1 for k = 0, 1, ...; a frame is
-// NG = ceil(N / team) groups per segment.  The group streams through two
+// NG = ceil(N / team) groups per segment (team = threads per frame, which the
+// plan sets to about one per 2 KB of frame).  The group streams through two
 // register batches of KB chunks (NB batches per group, NB even, so every group
 // starts in batch A); with PF the next group's bytes are requested into L2 while
 // this one is read.

@@ -98,7 +98,8 @@ def test_pathfinder_25pct_pulse_flags_high():
 
 @pytest.mark.parametrize("N,M,F", [
     (8, 16, 5), (16, 32, 33), (24, 48, 17), (256, 128, 40), (1000, 64, 9),
-    (2048, 256, 7), (4096, 32, 5), (2048, 1024, 3), (512, 4096, 2), (64, 16, 70)])
+    (2048, 256, 7), (4096, 32, 5), (2048, 1024, 3), (512, 4096, 2), (64, 16, 70),
+    (4096, 4096, 2)])
 def test_fast_path_shapes_random_bytes(N, M, F):
     rng = np.random.default_rng(N * 7 + M + F)
     x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
@@ -203,7 +204,7 @@ def _sampled_full_size(datasets, sample_frames, n_sigma=3.0):
     launch shape the benchmark times) and compare sampled frames with the oracle."""
     dev = _dev()
     ds0 = datasets[0]
-    M, N = ds0.M, ds0.N
+    M, N, layout = ds0.M, ds0.N, ds0.layout
     F = sum(d.n_frames for d in datasets)
     d_in = torch.empty(F * M * N, dtype=torch.uint8, device=dev)
     off = 0
@@ -217,7 +218,7 @@ def _sampled_full_size(datasets, sample_frames, n_sigma=3.0):
     ne = torch.empty(F, dtype=torch.int32, device=dev)
     mask = torch.empty(F, dtype=torch.uint8, device=dev)
     sk2 = torch.empty(F, dtype=torch.float32, device=dev)
-    plan = sk.sk_plan_create(N, M, n_sigma, delta)
+    plan = sk.sk_plan_create(N, M, n_sigma, delta, layout=layout)
     try:
         sk.sk_compute(plan, d_in, F, None, None, q, skv, ne)
         sk.sk_flag(plan, d_in, F, sk2, mask)
@@ -233,7 +234,7 @@ def _sampled_full_size(datasets, sample_frames, n_sigma=3.0):
         x = datasets[k].generate_cpu(frame0=f, n=1)
         dev_bytes = d_in[g * M * N:(g + 1) * M * N].cpu().numpy()
         assert np.array_equal(dev_bytes, x[0])
-        w = oracle.flag(x, M, N, n_sigma, delta)
+        w = oracle.flag(x, M, N, n_sigma, delta, layout=layout)
         assert q[g] == w["Q"][0] and ne[g] == w["neff"][0] and mask[g] == w["mask"][0]
         assert skv[g].view(np.uint32) == w["sk"][0].view(np.uint32)
         assert abs(skv[g] - w["sk64"][0]) <= SK_REL * abs(w["sk64"][0])
@@ -334,3 +335,30 @@ def test_input_major_fast_path_bit_exact(N, M, F):
         sk.sk_plan_destroy(plan)
     assert np.array_equal(sk_in.cpu().numpy().view(np.uint32), wi["sk_in"].view(np.uint32))
     assert np.array_equal(m_in.cpu().numpy(), wi["mask_in"])
+
+
+def test_full_array_input_major_sampled():
+    """The same 3.2 GB workload in the input-major layout [frame][input][t] (the grouped
+    input-major launch the benchmark times), sampled frames vs the oracle."""
+    import dataclasses
+
+    datasets = [dataclasses.replace(d, layout=1) for d in synth.full_array_config()]
+    rng = np.random.default_rng(6)
+    F = 4 * 1525
+    rfi = [1525 * k + r.frame for k, d in enumerate(datasets) for r in d.rfi[:3]]
+    sample = sorted(set([0, 1, 1524, 1525, F - 1] + rfi + list(rng.integers(0, F, size=16))))
+    r = _sampled_full_size(datasets, sample)
+    assert np.array_equal(r["sk"].view(np.uint32), r["sk_flag"].view(np.uint32))
+    assert r["checked"] == len(sample)
+
+
+@pytest.mark.parametrize("N,M,F", [(4096, 1024, 2), (4096, 4096, 1), (9, 512, 4)])
+def test_input_major_maximum_and_ragged_sizes(N, M, F):
+    """Input-major at the largest N (grouped path, M = 1024; per-input path, M = 4096)
+    and a ragged N on the grouped path; worst-case bytes (every sample -8-8j) in one frame."""
+    rng = np.random.default_rng(N + M + F)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    x[F - 1, : M * min(N, 64)] = 0x00
+    want = oracle.flag(x, M, N, 3.0, 0.0, layout=1)
+    got = run_compute(x, M, N, 3.0, 0.0, layout=1)
+    assert_parity(got, want)
