@@ -1,8 +1,9 @@
 """Precision and scale: 1024 frequencies x N=2048 x M=256 x 40 frames (21.5 GB of
-input resident on the device), one sk_compute launch.  SK~ in fp32 (from the
-exact int64 M*S2 - S1^2 and one fp32 divide) against the fp64 oracle (Eq. final)
-on frames sampled across the whole band; Q, N_eff and masks bit-exact against the
-oracle's kernel-precision statement.  The error statistics are printed."""
+input resident on the device), one sk_compute launch, and the same band with 160
+frames (85.9 GB resident).  SK~ in fp32 (from the exact int64 M*S2 - S1^2 and one
+fp32 divide) against the fp64 oracle (Eq. final) on frames sampled across the whole
+band; Q, N_eff and masks bit-exact against the oracle's kernel-precision statement.
+The error statistics and the sk_flag throughput over the resident band are printed."""
 
 import json
 import os
@@ -19,10 +20,11 @@ from oracle import digitisation as dg  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-N_FREQ, N, M, T = 1024, 2048, 256, 40
+N_FREQ, N, M = 1024, 2048, 256
 
 
-def test_full_band_precision_and_masks():
+@pytest.mark.parametrize("T", [40, 160])
+def test_full_band_precision_and_masks(T):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     dev = torch.device("cuda:0")
@@ -30,7 +32,7 @@ def test_full_band_precision_and_masks():
     F = N_FREQ * T
     nbytes = F * M * N
     if free < nbytes + (4 << 30):
-        pytest.skip("not enough device memory for the 21.5 GB workload")
+        pytest.skip(f"not enough device memory for the {nbytes / 1e9:.1f} GB workload")
     # each frequency its own seed and RFI; built lazily to keep host memory small
     datasets = synth.full_array_config(n_freq=N_FREQ, n_frames=T, N=N, M=M, cfg=4)
     d_in = torch.empty(nbytes, dtype=torch.uint8, device=dev)
@@ -47,6 +49,15 @@ def test_full_band_precision_and_masks():
         sk.sk_compute(plan, d_in, F, None, None, q, skv, ne)
         sk.sk_flag(plan, d_in, F, None, mask)
         torch.cuda.synchronize()
+        # throughput over the resident band (inputs far larger than L2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        a.record()
+        for _ in range(reps):
+            sk.sk_flag(plan, d_in, F, None, mask)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
     finally:
         sk.sk_plan_destroy(plan)
     q, skv, ne, mask = (t.cpu().numpy() for t in (q, skv, ne, mask))
@@ -67,11 +78,12 @@ def test_full_band_precision_and_masks():
     rel = np.array(rel)
     stats = {"frames": int(F), "bytes": int(nbytes), "sampled": int(len(sample)),
              "max_rel_err_fp32_vs_fp64": float(rel.max()), "mean_rel_err": float(rel.mean()),
-             "mask_mismatches": flips, "flag_rate": float(mask.mean())}
+             "mask_mismatches": flips, "flag_rate": float(mask.mean()),
+             "sk_flag_ms": ms, "gsamples_per_s": nbytes / (ms * 1e-3) / 1e9}
     print("precision-scale", json.dumps(stats))
     out = os.environ.get("SK_PRECISION_JSON")
     if out:
-        with open(out, "w") as fh:
+        with open(f"{out}.{T}", "w") as fh:
             json.dump(stats, fh)
     assert flips == 0
     assert rel.max() <= 1e-6
