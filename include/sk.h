@@ -247,7 +247,8 @@ sk_status_t sk_batch_destroy(sk_batch_t batch);
 sk_status_t sk_server_create(int device, size_t hbm_budget_bytes,
                              sk_server_t *out);
 sk_status_t sk_server_destroy(sk_server_t server);
-/* BUSY if the ring and state would exceed the remaining budget. */
+/* BUSY if the ring and state would exceed the remaining budget.  Either
+ * layout; input-major frames take the kernel's general (byte-load) path. */
 sk_status_t sk_stream_open(sk_server_t server, const sk_params_t *params,
                            int32_t ring_frames, sk_stream_id *out);
 /*

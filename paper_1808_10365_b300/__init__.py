@@ -292,8 +292,8 @@ def sk_server_destroy(server):
 
 
 def sk_stream_open(server, n_inputs, n_time, ring_frames=16, n_sigma=3.0, mean_offset=0.0,
-                   flags=0, offset_table=None) -> int:
-    p, keep = _params(n_inputs, n_time, n_sigma, mean_offset, 0, flags, offset_table)
+                   flags=0, offset_table=None, layout=0) -> int:
+    p, keep = _params(n_inputs, n_time, n_sigma, mean_offset, layout, flags, offset_table)
     sid = ctypes.c_int32()
     _check(library().sk_stream_open(server, ctypes.byref(p), int(ring_frames), ctypes.byref(sid)))
     return sid.value

@@ -116,14 +116,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t Gd = gridDim.x;
     const int64_t fb = F * (int64_t)blockIdx.x / Gd;
     const int64_t fe = F * ((int64_t)blockIdx.x + 1) / Gd;
+    Item im = single;  // the same item with the input-major team size
+    im.team_log2 = single.imajor_team_log2;
     if constexpr (CH > 0) {
-        if (single.fast == 2 && single.M == 16 * G * CH && single.team_log2 >= 5)
-            run_imajor_grouped<G, CH, PF>(single, fb, fe, lb, ts, parity);
+        if (single.fast == 2 && single.M == 16 * G * CH && im.team_log2 >= 5)
+            run_imajor_grouped<G, CH, PF>(im, fb, fe, lb, ts, parity);
         else
             run_general<false>(single, fb, fe, lb, ts, parity);
     } else {
-        if (single.fast == 2 && single.M % (16 * G) == 0 && single.team_log2 >= 5)
-            run_imajor<G, 8>(single, fb, fe, lb, ts, parity);
+        if (single.fast == 2 && single.M % (16 * G) == 0 && im.team_log2 >= 5)
+            run_imajor<G, 8>(im, fb, fe, lb, ts, parity);
         else
             run_general<false>(single, fb, fe, lb, ts, parity);
     }
@@ -137,8 +139,14 @@ static const KernelFn kSingle[2][3] = {
      sk_fused_kernel<16, 2, false, 2048, 0>},
     {sk_fused_kernel<8, 2, false, 0, 0>, sk_fused_kernel<8, 2, false, 256, 0>,
      sk_fused_kernel<8, 2, false, 2048, 0>}};
-static const KernelFn kBatched[2] = {sk_fused_kernel<16, 2, false, 0, 1>,
-                                     sk_fused_kernel<8, 2, false, 0, 1>};
+// batched launches: [tile][0 -> runtime N, 1 -> N = 256, 2 -> N = 2048] (the row
+// stride as a load immediate is worth 7-12 % here too; one kernel holding the
+// three pipelines spills, so a batch launches once per class)
+static const KernelFn kBatched[2][3] = {
+    {sk_fused_kernel<16, 2, false, 0, 1>, sk_fused_kernel<16, 2, false, 256, 1>,
+     sk_fused_kernel<16, 2, false, 2048, 1>},
+    {sk_fused_kernel<8, 2, false, 0, 1>, sk_fused_kernel<8, 2, false, 256, 1>,
+     sk_fused_kernel<8, 2, false, 2048, 1>}};
 static const KernelFn kServed[2] = {sk_fused_kernel<16, 2, true, 0, 2>,
                                     sk_fused_kernel<8, 2, true, 0, 2>};
 // input-major: per-input path G = 2, 4, 8; grouped path G = 8, CH = 1, 2, 4, 8
@@ -222,9 +230,10 @@ sk_status_t ensure_kernel_attrs(int device)
         fns.push_back(f);
     for (int t = 0; t < 2; ++t) {
         fns.push_back(kServed[t]);
-        fns.push_back(kBatched[t]);
-        for (int j = 0; j < 3; ++j)
+        for (int j = 0; j < 3; ++j) {
             fns.push_back(kSingle[t][j]);
+            fns.push_back(kBatched[t][j]);
+        }
     }
     for (KernelFn f : fns) {
         cudaError_t e = cudaFuncSetAttribute((const void *)f,
@@ -245,7 +254,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     sk_status_t s = ensure_kernel_attrs(device);
     if (s != SK_OK)
         return s;
-    const int64_t T = kThreads >> it.team_log2;
+    const int64_t T = kThreads >> (it.fast == 2 ? it.imajor_team_log2 : it.team_log2);
     int64_t need = (it.n_frames + T - 1) / T;
     int64_t g = sm_count(device);
     if (grid_cap > 0)
@@ -267,9 +276,16 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     return SK_OK;
 }
 
+int batch_class(const Item &it)
+{
+    if (it.fast != 1)
+        return 0;
+    return it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
+}
+
 sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
                             const int32_t *d_cta_chunks, int grid, int tile, bool served,
-                            int device, cudaStream_t st)
+                            int device, cudaStream_t st, int nclass)
 {
     if (grid <= 0)
         return SK_OK;
@@ -278,7 +294,7 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
         return s;
     Item dummy;
     memset(&dummy, 0, sizeof dummy);
-    KernelFn fn = served ? kServed[tile] : kBatched[tile];
+    KernelFn fn = served ? kServed[tile] : kBatched[tile][nclass];
     fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -388,6 +404,7 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.N = p.n_inputs;
     it.layout = p.layout;
     it.team_log2 = team_log2;
+    it.imajor_team_log2 = imajor_team_log2;
     it.t_lo = d_t_lo;
     it.t_hi = d_t_hi;
     it.c_tab = d_c;
@@ -476,7 +493,7 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
         const int tl = grouped ? ceil_log2(((int64_t)N * M + 2047) / 2048)
                                : ceil_log2(((int64_t)N * gl + 7) / 8);
         const int tmax = grouped ? 8 : 9;
-        pl->team_log2 = tl < 5 ? 5 : (tl > tmax ? tmax : tl);
+        pl->imajor_team_log2 = tl < 5 ? 5 : (tl > tmax ? tmax : tl);
     }
     pl->rows = 16;
     pl->grid_ctas = 0;

@@ -1,8 +1,9 @@
 // Batched persistent launch: one grid of one CTA per SM walks a static,
 // byte-balanced schedule of (item, frame range) chunks that mixes items of
-// different N and M (frequencies of a 2048-input array next to a 256-input
-// one, integration lengths 128..1024).  The launch is captured once into a
-// CUDA graph and replayed.
+// different M (integration lengths 128..1024).  Items are split by kernel class
+// (N = 2048, N = 256, any other N or layout: the first two with the row stride
+// compiled in), and each non-empty class is one such launch; the launches are
+// captured once into a CUDA graph and replayed.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -11,11 +12,12 @@
 
 struct sk_batch_s {
     int device = 0;
-    int tile = 0;  // kernel tile (see launch_schedule)
     int grid = 0;
     std::vector<sk::Item> items;
-    std::vector<sk::Chunk> chunks;
-    std::vector<int32_t> cta;
+    std::vector<sk::Chunk> chunks;  // all classes, concatenated
+    std::vector<int32_t> cta;       // per class: grid + 1 offsets into chunks
+    int tile[sk::kBatchClasses] = {0, 0, 0};  // kernel tile (see launch_schedule)
+    bool used[sk::kBatchClasses] = {false, false, false};
     sk::Item *d_items = nullptr;
     sk::Chunk *d_chunks = nullptr;
     int32_t *d_cta = nullptr;
@@ -30,12 +32,12 @@ namespace sk {
 // end to end and cut into `grid` pieces of equal bytes: a round with c bytes
 // before it and b bytes of its own goes to CTA floor((c + b/2) / (total/grid)).
 // Consecutive rounds of one item on one CTA merge into one chunk.
-void build_schedule(const std::vector<Item> &items, int grid, std::vector<Chunk> &chunks,
-                    std::vector<int32_t> &cta)
+void build_schedule(const std::vector<Item> &items, const std::vector<int32_t> &sel, int grid,
+                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta)
 {
     double total = 0.0;
-    for (const Item &it : items)
-        total += (double)it.n_frames * it.M * it.N;
+    for (int32_t k : sel)
+        total += (double)items[k].n_frames * items[k].M * items[k].N;
     chunks.clear();
     cta.assign(grid + 1, 0);
     if (total <= 0.0 || grid <= 0)
@@ -43,7 +45,7 @@ void build_schedule(const std::vector<Item> &items, int grid, std::vector<Chunk>
     const double target = total / grid;
     std::vector<std::vector<Chunk>> per(grid);
     double cum = 0.0;
-    for (int32_t k = 0; k < (int32_t)items.size(); ++k) {
+    for (int32_t k : sel) {
         const Item &it = items[k];
         const int64_t T = kThreads >> it.team_log2;
         const double fbytes = (double)it.M * it.N;
@@ -151,8 +153,9 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
     if (!b)
         return set_error(SK_ERR_OOM, "host allocation");
     b->device = device;
-    int rows = 0;
-    bool all_m32 = true;
+    int rows[kBatchClasses] = {0, 0, 0};
+    bool all_m32[kBatchClasses] = {true, true, true};
+    std::vector<int32_t> sel[kBatchClasses];
     for (int32_t k = 0; k < n_items; ++k) {
         const sk_batch_item_t &bi = items[k];
         if (!bi.plan || bi.n_frames < 0 || (bi.n_frames > 0 && !bi.d_in) ||
@@ -168,13 +171,25 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
         Item it = bi.plan->item(bi.d_in, bi.n_frames);
         it.sk = bi.d_sk;
         it.mask = bi.d_mask;
+        const int c = batch_class(it);
         b->items.push_back(it);
-        rows = std::max(rows, bi.plan->rows);
-        all_m32 = all_m32 && (bi.plan->p.n_time % 32 == 0);
+        sel[c].push_back(k);
+        rows[c] = std::max(rows[c], bi.plan->rows);
+        all_m32[c] = all_m32[c] && (bi.plan->p.n_time % 32 == 0);
     }
-    b->tile = pick_tile(rows == 8 ? 8 : 16, all_m32);
     b->grid = sm_count(device);
-    build_schedule(b->items, b->grid, b->chunks, b->cta);
+    for (int c = 0; c < kBatchClasses; ++c) {
+        b->tile[c] = pick_tile(rows[c] == 8 ? 8 : 16, all_m32[c]);
+        std::vector<Chunk> ch;
+        std::vector<int32_t> cta;
+        build_schedule(b->items, sel[c], b->grid, ch, cta);
+        b->used[c] = !ch.empty();
+        const int32_t base = (int32_t)b->chunks.size();
+        for (int32_t &x : cta)
+            x += base;
+        b->chunks.insert(b->chunks.end(), ch.begin(), ch.end());
+        b->cta.insert(b->cta.end(), cta.begin(), cta.end());
+    }
     sk_status_t s = SK_OK;
     {
         DeviceGuard dg(device);
@@ -213,6 +228,8 @@ extern "C" sk_status_t sk_batch_run(sk_batch_t b, sk_cuda_stream_t stream)
         return set_error(SK_ERR_INVALID_ARG, "sk_batch_run: batch is NULL");
     DeviceGuard dg(b->device);
     sk_status_t s = SK_OK;
+    if (b->chunks.empty())
+        return SK_OK;  // no frames in any item
     if (!b->exec) {
         cudaStream_t cs;
         cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -220,8 +237,10 @@ extern "C" sk_status_t sk_batch_run(sk_batch_t b, sk_cuda_stream_t stream)
             return cuda_error(e, "sk_batch_run capture stream");
         e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            s = launch_schedule(b->d_items, b->d_chunks, b->d_cta, b->grid, b->tile, false,
-                                b->device, cs);
+            for (int c = 0; c < kBatchClasses && s == SK_OK; ++c)
+                if (b->used[c])
+                    s = launch_schedule(b->d_items, b->d_chunks, b->d_cta + c * (b->grid + 1),
+                                        b->grid, b->tile[c], false, b->device, cs, c);
             cudaGraph_t g = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(cs, &g);
             if (s == SK_OK && e2 == cudaSuccess) {

@@ -22,19 +22,25 @@ sk_status_t cuda_error(cudaError_t e, const char *what);
 // a prebuilt chunk schedule (items/chunks/cta_chunks on the device).
 sk_status_t launch_single(const Item &it, int rows, bool served, int device, cudaStream_t st,
                           int grid_cap = 0);
-// tile: 0 = 16 rows x 2 batches (M % 32 == 0), 1 = 8 x 2 (M % 16 == 0)
+// tile: 0 = 16 rows x 2 batches (M % 32 == 0), 1 = 8 x 2 (M % 16 == 0);
+// nclass (batched launches): the kernel for items of batch_class nclass
 sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
                             const int32_t *d_cta_chunks, int grid, int tile, bool served,
-                            int device, cudaStream_t st);
+                            int device, cudaStream_t st, int nclass = 0);
+// Kernel class of a batched item: 2 for time-major fast-path items of N = 2048,
+// 1 for N = 256, 0 for the rest (runtime row stride or the general path).
+int batch_class(const Item &it);
+constexpr int kBatchClasses = 3;
 int pick_tile(int rows, bool all_m32);
 int imajor_lanes(int M);
 int imajor_chunks(int M);
 sk_status_t ensure_kernel_attrs(int device);
 int sm_count(int device);
 
-// Static byte-balanced schedule of items over `grid` CTAs.
-void build_schedule(const std::vector<Item> &items, int grid, std::vector<Chunk> &chunks,
-                    std::vector<int32_t> &cta);
+// Static byte-balanced schedule of the items listed in `sel` over `grid` CTAs;
+// chunk item indices refer to `items`.
+void build_schedule(const std::vector<Item> &items, const std::vector<int32_t> &sel, int grid,
+                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta);
 
 // Schedule for a batch of one-frame items; reorders items, returns the grid.
 int build_item_schedule(std::vector<Item> &items, int grid_max, std::vector<Chunk> &chunks,
@@ -62,7 +68,8 @@ struct DeviceGuard {
 struct sk_plan_s {
     sk_params_t p;
     int device = 0;
-    int team_log2 = 0;
+    int team_log2 = 0;         // vector and general paths (8 inputs per thread)
+    int imajor_team_log2 = 0;  // input-major kernel
     bool fast = false;
     bool imajor = false;  // input-major fast path applies
     int rows = 16;      // register batch rows of the fast path

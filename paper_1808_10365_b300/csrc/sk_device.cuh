@@ -49,7 +49,8 @@ struct Item {
     int64_t n_frames;
     int32_t M, N;
     int32_t layout;          // 0 time-major, 1 input-major
-    int32_t team_log2;       // threads per frame = 1 << team_log2
+    int32_t team_log2;       // threads per frame = 1 << team_log2 (vector and general paths)
+    int32_t imajor_team_log2;  // threads per frame on the input-major kernel
     float *sk;
     uint8_t *mask;
     int64_t *q;

@@ -510,8 +510,8 @@ extern "C" sk_status_t sk_stream_open(sk_server_t s, const sk_params_t *params,
     *out = -1;
     if (ring_frames < 1 || ring_frames > 65536)
         return set_error(SK_ERR_INVALID_ARG, "sk_stream_open: ring_frames outside 1..65536");
-    if (params->layout != SK_LAYOUT_TIME_MAJOR)
-        return set_error(SK_ERR_UNSUPPORTED, "sk_stream_open: served streams are time-major");
+    if (params->layout != SK_LAYOUT_TIME_MAJOR && params->layout != SK_LAYOUT_INPUT_MAJOR)
+        return set_error(SK_ERR_INVALID_ARG, "sk_stream_open: unknown layout %d", params->layout);
     if (params->n_inputs < 1 || params->n_inputs > SK_MAX_INPUTS || params->n_time < 2 ||
         params->n_time > SK_MAX_TIME)
         return set_error(SK_ERR_INVALID_ARG, "sk_stream_open: N or M out of range");

@@ -20,18 +20,27 @@ def _dev():
     return torch.device("cuda:0")
 
 
-def test_mixed_batch_matches_oracle_and_replays():
+@pytest.mark.parametrize("shapes", [
+    # every kernel class: N = 2048 (16- and 8-row tiles), N = 256, other N on the
+    # fast path, the general path, input-major items, empty items
+    [(2048, 256, 23, 0), (256, 128, 70, 0), (2048, 1024, 5, 0), (256, 1024, 31, 0),
+     (100, 48, 9, 0), (512, 256, 1, 0), (2048, 128, 0, 0), (256, 256, 64, 0),
+     (2048, 48, 4, 0), (256, 256, 10, 1), (2048, 128, 3, 1)],
+    # one class only
+    [(256, 256, 40, 0), (256, 128, 17, 0)],
+    [(2048, 256, 7, 0)],
+    # nothing to do
+    [(2048, 256, 0, 0), (256, 128, 0, 0)]])
+def test_mixed_batch_matches_oracle_and_replays(shapes):
     dev = _dev()
-    shapes = [(2048, 256, 23), (256, 128, 70), (2048, 1024, 5), (256, 1024, 31),
-              (100, 48, 9), (512, 256, 1), (2048, 128, 0), (256, 256, 64)]
     items, plans, bufs, wants = [], [], [], []
-    for k, (N, M, F) in enumerate(shapes):
-        ds = synth.Dataset(n_frames=max(F, 1), M=M, N=N, seed=synth.sub_seed(2, k),
+    for k, (N, M, F, layout) in enumerate(shapes):
+        ds = synth.Dataset(n_frames=max(F, 1), M=M, N=N, seed=synth.sub_seed(2, k), layout=layout,
                            rfi=synth.rfi_plan(synth.sub_seed(2, k), max(F, 1), 0.2, 0.1))
         x = ds.generate_cpu()[:F]
         delta = float(np.mean(dg.delta_of_sigma(ds.sigma)))
-        wants.append(oracle.flag(x, M, N, 3.0, delta) if F else None)
-        plan = sk.sk_plan_create(N, M, 3.0, delta)
+        wants.append(oracle.flag(x, M, N, 3.0, delta, layout=layout) if F else None)
+        plan = sk.sk_plan_create(N, M, 3.0, delta, layout=layout)
         d_in = torch.from_numpy(x.reshape(-1)).to(dev) if F else torch.empty(16, dtype=torch.uint8,
                                                                              device=dev)
         skv = torch.full((max(F, 1),), -1.0, dtype=torch.float32, device=dev)
@@ -47,7 +56,7 @@ def test_mixed_batch_matches_oracle_and_replays():
                 mask.fill_(9)
             sk.sk_batch_run(batch)
             torch.cuda.synchronize()
-            for (N, M, F), w, (_, skv, mask) in zip(shapes, wants, bufs):
+            for (N, M, F, _), w, (_, skv, mask) in zip(shapes, wants, bufs):
                 if F == 0:
                     assert mask[0].item() == 9
                     continue

@@ -125,6 +125,35 @@ def test_stateless_stream_matches_plain_flag():
                           want["sk"].view(np.uint32))
 
 
+@pytest.mark.parametrize("N,M", [(2048, 128), (256, 256), (100, 64)])
+def test_input_major_stream_matches_time_major_stream(N, M):
+    """The same frames served as [input][t] and as [t][input] give identical results,
+    and the time-major stream matches the served-state oracle."""
+    _need_gpu()
+    T = 24
+    ds, x = _stream_data(21, N, M, T)
+    xi = np.ascontiguousarray(x.reshape(T, M, N).transpose(0, 2, 1).reshape(T, -1))
+    e = dg.offset_table(M)
+    want = served.served_flags(x, M, N, e)
+    server = sk.sk_server_create(0, 2 << 30)
+    try:
+        ids = [sk.sk_stream_open(server, N, M, ring_frames=T, flags=sk.SK_RUNNING_OFFSET,
+                                 offset_table=e, layout=lay) for lay in (0, 1)]
+        tickets = [[sk.sk_stream_submit(server, i, d[f], f) for f in range(T)]
+                   for i, d in zip(ids, (x, xi))]
+        got = [[sk.sk_ticket_wait(server, t, 10_000_000) for t in ts] for ts in tickets]
+        for i in ids:
+            sk.sk_stream_close(server, i)
+    finally:
+        sk.sk_server_destroy(server)
+    sk_t = np.array([a for a, _ in got[0]], dtype=np.float32)
+    sk_i = np.array([a for a, _ in got[1]], dtype=np.float32)
+    assert np.array_equal(np.array([m for _, m in got[0]], dtype=np.uint8), want["mask"])
+    assert np.array_equal(sk_t.view(np.uint32), want["sk"].view(np.uint32))
+    assert np.array_equal(sk_i.view(np.uint32), sk_t.view(np.uint32))
+    assert [m for _, m in got[1]] == [m for _, m in got[0]]
+
+
 def test_checkpoint_resume_continues_identically():
     _need_gpu()
     N, M, T = 512, 256, 24
