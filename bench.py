@@ -215,11 +215,29 @@ def cpu_baseline(budget_s: float = 12.0):
         if el >= budget_s:
             break
     samples = reps * nf * M_T * N_IN
-    return {"value": samples / el / 1e9, "unit": UNIT, "cores": oracle.threads(),
+    cores = oracle.threads()
+    # the same path on one core, on a 16-frame sample
+    oracle.set_threads(1)
+    try:
+        n1 = 16
+        x1 = x[:n1]
+        reps1 = 0
+        t1 = time.perf_counter()
+        while True:
+            oracle.flag(x1, M_T, N_IN, 3.0, delta)
+            reps1 += 1
+            el1 = time.perf_counter() - t1
+            if el1 >= budget_s / 4:
+                break
+    finally:
+        oracle.set_threads(cores)
+    return {"value": samples / el / 1e9, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"{nf} frames of 1 frequency (N=2048, M=256; {nf * M_T * N_IN / 1e6:.0f} MB) "
                       f"x {reps} repetitions, {el:.1f} s, full oracle path (sums, fp32 and fp64 "
-                      f"SK, thresholds, mask)"}
+                      f"SK, thresholds, mask)",
+            "value_1core": reps1 * n1 * M_T * N_IN / el1 / 1e9,
+            "sample_1core": f"{n1} frames x {reps1} repetitions, {el1:.1f} s, 1 thread"}
 
 
 def run_reference(args):

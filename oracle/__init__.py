@@ -68,6 +68,7 @@ def _load():
         lib.oracle_sk_single_f64.argtypes = [P, P, i64, i32, P]
         lib.oracle_terms_spec.argtypes = [P, P, i64, i32, P, P, P]
         lib.oracle_max_threads.restype = ctypes.c_int
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -78,6 +79,11 @@ def _p(a):
 
 def threads() -> int:
     return int(_load().oracle_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads the oracle's C loops use from now on (timing only)."""
+    _load().oracle_set_threads(int(n))
 
 
 def power_sums(x: np.ndarray, M: int, N: int, layout: int = 0):
