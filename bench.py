@@ -316,17 +316,18 @@ def input_major_bench(n_freq: int, ref_mask, reps: int = 10, dev_index: int = 0)
             "masks_identical_to_time_major": same}
 
 
-def batched_bench(reps: int = 10, dev_index: int = 0):
+def batched_bench(reps: int = 10, dev_index: int = 0, n_frames: int = 500):
     """Mixed workload: 64 frequencies of N=2048 and 64 of N=256, M in {128, 256, 1024}
-    per frequency from the seed, 500 frames each.  One graph-captured persistent launch
-    (sk_batch_run) against one sk_flag launch per frequency, same buffers."""
+    per frequency from the seed, 500 frames each (n_frames: a smaller case for
+    profiling).  One captured graph of persistent launches (sk_batch_run, one launch
+    per N class) against one sk_flag launch per frequency, same buffers."""
     import torch
 
     import paper_1808_10365_b300 as sk
     import synth
 
     dev = torch.device("cuda", dev_index)
-    datasets = synth.mixed_config()
+    datasets = synth.mixed_config(n_frames=n_frames)
     total = sum(d.nbytes for d in datasets)
     buf = torch.empty(total + 16 * len(datasets), dtype=torch.uint8, device=dev)
     items, plans, views = [], [], []
@@ -374,9 +375,12 @@ def batched_bench(reps: int = 10, dev_index: int = 0):
     torch.cuda.empty_cache()
     ms_list = sorted({d.M for d in datasets})
     return {"workload": "64 freq x N=2048 + 64 freq x N=256, M per freq from {128,256,1024}, "
-                        "500 frames each, graph-captured persistent launch",
+                        f"{n_frames} frames each, graph-captured persistent launches",
             "bytes": total, "M_values": ms_list,
             "value": total / (ms_batch * 1e-3) / 1e9, "unit": UNIT, "ms": ms_batch,
+            "roofline_frac": (total + 5 * sum(d.n_frames for d in datasets))
+            / (ms_batch * 1e-3) / 1e9 / peaks()[0],
+            "launches_per_run": len({d.N for d in datasets}),
             "plain_value": total / (ms_plain * 1e-3) / 1e9, "plain_ms": ms_plain,
             "plain_launches": len(items), "speedup_vs_plain": ms_plain / ms_batch,
             "masks_identical": same}
