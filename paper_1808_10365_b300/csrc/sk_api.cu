@@ -99,11 +99,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Input-major fast paths, one-item launches only (batched and served launches
-// take input-major items through the general path).  G lanes per input; CH > 0
-// selects the grouped path for M = 16 G CH (PF: L2 prefetch of the next group),
-// CH = 0 the per-input path for any M that 16 G divides.
-template <int G, int CH, bool PF>
+// Input-major fast paths.  G lanes per input; CH > 0 selects the grouped path
+// for M = 16 G CH (PF: L2 prefetch of the next group), CH = 0 the per-input
+// path for any M that 16 G divides.  MODE 0: one item, a contiguous frame range
+// per CTA; MODE 1 (grouped path only): a chunk list of a batched launch whose
+// items all have this M.  Served launches take input-major items through the
+// general path.
+template <int G, int CH, bool PF, int MODE = 0, int SPLIT = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_imajor_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
                      const int32_t *__restrict__ cta_chunks, Item single)
@@ -112,6 +114,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ TeamSmem ts;
     const uint32_t lb = build_table(dyn_smem);
     int parity = 0;
+    if constexpr (MODE == 1) {
+        static_assert(CH > 0, "batched input-major launches use the grouped path");
+        const int32_t c0 = cta_chunks[blockIdx.x], c1 = cta_chunks[blockIdx.x + 1];
+        for (int32_t c = c0; c < c1; ++c) {
+            const Chunk ch = chunks[c];
+            __syncthreads();
+            const Item it = items[ch.item];
+            Item im = it;
+            im.team_log2 = it.imajor_team_log2;
+            if (it.fast == 2 && it.M == 16 * G * CH * SPLIT && im.team_log2 >= 5)
+                run_imajor_grouped<G, CH, PF, SPLIT>(im, ch.f_begin, ch.f_end, lb, ts, parity);
+            else
+                run_general<false>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+        }
+        return;
+    }
     const int64_t F = single.n_frames;
     const int64_t Gd = gridDim.x;
     const int64_t fb = F * (int64_t)blockIdx.x / Gd;
@@ -119,8 +137,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     Item im = single;  // the same item with the input-major team size
     im.team_log2 = single.imajor_team_log2;
     if constexpr (CH > 0) {
-        if (single.fast == 2 && single.M == 16 * G * CH && im.team_log2 >= 5)
-            run_imajor_grouped<G, CH, PF>(im, fb, fe, lb, ts, parity);
+        if (single.fast == 2 && single.M == 16 * G * CH * SPLIT && im.team_log2 >= 5)
+            run_imajor_grouped<G, CH, PF, SPLIT>(im, fb, fe, lb, ts, parity);
         else
             run_general<false>(single, fb, fe, lb, ts, parity);
     } else {
@@ -149,15 +167,18 @@ static const KernelFn kBatched[2][3] = {
      sk_fused_kernel<8, 2, false, 2048, 1>}};
 static const KernelFn kServed[2] = {sk_fused_kernel<16, 2, true, 0, 2>,
                                     sk_fused_kernel<8, 2, true, 0, 2>};
-// input-major: per-input path G = 2, 4, 8; grouped path G = 8, CH = 1, 2, 4, 8
-// without and with the L2 prefetch
-static const KernelFn kImajor[11] = {
-    sk_imajor_kernel<2, 0, false>,    sk_imajor_kernel<4, 0, false>,
-    sk_imajor_kernel<8, 0, false>,    sk_imajor_kernel<8, 1, false>,
-    sk_imajor_kernel<8, 2, false>,    sk_imajor_kernel<8, 4, false>,
-    sk_imajor_kernel<8, 8, false>,    sk_imajor_kernel<8, 1, true>,
-    sk_imajor_kernel<8, 2, true>,     sk_imajor_kernel<8, 4, true>,
-    sk_imajor_kernel<8, 8, true>};
+// input-major: per-input path G = 2, 4, 8; grouped path G = 8 for M = 128,
+// 256, 512 (CH = 1, 2, 4) and 1024, 2048, 4096 (CH = 4 on SPLIT = 2, 4, 8
+// sub-inputs), without and with the L2 prefetch
+static const KernelFn kImajor[15] = {
+    sk_imajor_kernel<2, 0, false>,          sk_imajor_kernel<4, 0, false>,
+    sk_imajor_kernel<8, 0, false>,          sk_imajor_kernel<8, 1, false>,
+    sk_imajor_kernel<8, 2, false>,          sk_imajor_kernel<8, 4, false>,
+    sk_imajor_kernel<8, 4, false, 0, 2>,    sk_imajor_kernel<8, 4, false, 0, 4>,
+    sk_imajor_kernel<8, 4, false, 0, 8>,    sk_imajor_kernel<8, 1, true>,
+    sk_imajor_kernel<8, 2, true>,           sk_imajor_kernel<8, 4, true>,
+    sk_imajor_kernel<8, 4, true, 0, 2>,     sk_imajor_kernel<8, 4, true, 0, 4>,
+    sk_imajor_kernel<8, 4, true, 0, 8>};
 
 // Lanes per input on the per-input input-major path: 4 up to M = 512, 8 above
 // (measured best on B300), or SK_IMAJOR_LANES (2, 4 or 8); reduced while 16 G
@@ -175,19 +196,23 @@ int imajor_lanes(int M)
     return g;
 }
 
-// Chunks per lane per input on the grouped input-major path (G = 8 lanes): M/128
-// for M in {128, 256, 512, 1024}, else 0 (the per-input path).
+// Shape index of M on the grouped input-major path (G = 8 lanes): 0..5 for M =
+// 128, 256, 512, 1024, 2048, 4096, else -1 (the per-input path).
 // SK_IMAJOR_GROUPED=0 turns the grouped path off.
-int imajor_chunks(int M)
+int imajor_shape(int M)
 {
     static const bool off = [] {
         const char *v = getenv("SK_IMAJOR_GROUPED");
         return v && atoi(v) == 0;
     }();
     if (off)
-        return 0;
-    return (M == 128 || M == 256 || M == 512 || M == 1024) ? M / 128 : 0;
+        return -1;
+    for (int sh = 0; sh < 6; ++sh)
+        if (M == (128 << sh))
+            return sh;
+    return -1;
 }
+
 
 static bool imajor_prefetch()
 {
@@ -198,13 +223,17 @@ static bool imajor_prefetch()
     return on;
 }
 
+// batched input-major launches: grouped path per M shape (batch classes 3..8)
+static const KernelFn kImajorBatched[6] = {
+    sk_imajor_kernel<8, 1, true, 1>,    sk_imajor_kernel<8, 2, true, 1>,
+    sk_imajor_kernel<8, 4, true, 1>,    sk_imajor_kernel<8, 4, true, 1, 2>,
+    sk_imajor_kernel<8, 4, true, 1, 4>, sk_imajor_kernel<8, 4, true, 1, 8>};
+
 static KernelFn imajor_kernel(int M)
 {
-    const int ch = imajor_chunks(M);
-    if (ch > 0) {
-        const int c = ch == 1 ? 0 : (ch == 2 ? 1 : (ch == 4 ? 2 : 3));
-        return kImajor[(imajor_prefetch() ? 7 : 3) + c];
-    }
+    const int sh = imajor_shape(M);
+    if (sh >= 0)
+        return kImajor[(imajor_prefetch() ? 9 : 3) + sh];
     const int g = imajor_lanes(M);
     return kImajor[g == 2 ? 0 : (g == 4 ? 1 : 2)];
 }
@@ -227,6 +256,8 @@ sk_status_t ensure_kernel_attrs(int device)
             return SK_OK;
     std::vector<KernelFn> fns;
     for (KernelFn f : kImajor)
+        fns.push_back(f);
+    for (KernelFn f : kImajorBatched)
         fns.push_back(f);
     for (int t = 0; t < 2; ++t) {
         fns.push_back(kServed[t]);
@@ -278,9 +309,13 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
 
 int batch_class(const Item &it)
 {
-    if (it.fast != 1)
-        return 0;
-    return it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
+    if (it.fast == 1)
+        return it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
+    if (it.fast == 2) {
+        const int sh = imajor_shape(it.M);
+        return sh >= 0 ? kFirstImajorClass + sh : 0;
+    }
+    return 0;
 }
 
 sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
@@ -294,7 +329,8 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
         return s;
     Item dummy;
     memset(&dummy, 0, sizeof dummy);
-    KernelFn fn = served ? kServed[tile] : kBatched[tile][nclass];
+    KernelFn fn = served ? kServed[tile]
+                         : (nclass < 3 ? kBatched[tile][nclass] : kImajorBatched[nclass - 3]);
     fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -482,7 +518,7 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
     pl->team_log2 = ceil_log2((N + kVec - 1) / kVec);
     pl->fast = (p.layout == SK_LAYOUT_TIME_MAJOR) && (N % kVec == 0) && (M % kFlushRows == 0);
     const int gl = imajor_lanes(M);
-    const bool grouped = imajor_chunks(M) > 0;
+    const bool grouped = imajor_shape(M) >= 0;
     pl->imajor = (p.layout == SK_LAYOUT_INPUT_MAJOR) && (grouped || M % (16 * gl) == 0);
     if (pl->imajor) {
         // grouped: about 2 KB of the frame per team thread, 32..256 threads (a

@@ -1,9 +1,10 @@
 // Batched persistent launch: one grid of one CTA per SM walks a static,
 // byte-balanced schedule of (item, frame range) chunks that mixes items of
 // different M (integration lengths 128..1024).  Items are split by kernel class
-// (N = 2048, N = 256, any other N or layout: the first two with the row stride
-// compiled in), and each non-empty class is one such launch; the launches are
-// captured once into a CUDA graph and replayed.
+// (time-major N = 2048 and N = 256 with the row stride compiled in, input-major
+// items by M on the grouped input-major path, and the rest), and each non-empty
+// class is one such launch; the launches are captured once into a CUDA graph and
+// replayed.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -16,8 +17,8 @@ struct sk_batch_s {
     std::vector<sk::Item> items;
     std::vector<sk::Chunk> chunks;  // all classes, concatenated
     std::vector<int32_t> cta;       // per class: grid + 1 offsets into chunks
-    int tile[sk::kBatchClasses] = {0, 0, 0};  // kernel tile (see launch_schedule)
-    bool used[sk::kBatchClasses] = {false, false, false};
+    int tile[sk::kBatchClasses] = {};   // kernel tile (see launch_schedule)
+    bool used[sk::kBatchClasses] = {};
     sk::Item *d_items = nullptr;
     sk::Chunk *d_chunks = nullptr;
     int32_t *d_cta = nullptr;
@@ -33,7 +34,7 @@ namespace sk {
 // before it and b bytes of its own goes to CTA floor((c + b/2) / (total/grid)).
 // Consecutive rounds of one item on one CTA merge into one chunk.
 void build_schedule(const std::vector<Item> &items, const std::vector<int32_t> &sel, int grid,
-                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta)
+                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta, bool imajor)
 {
     double total = 0.0;
     for (int32_t k : sel)
@@ -47,7 +48,7 @@ void build_schedule(const std::vector<Item> &items, const std::vector<int32_t> &
     double cum = 0.0;
     for (int32_t k : sel) {
         const Item &it = items[k];
-        const int64_t T = kThreads >> it.team_log2;
+        const int64_t T = kThreads >> (imajor ? it.imajor_team_log2 : it.team_log2);
         const double fbytes = (double)it.M * it.N;
         for (int64_t f0 = 0; f0 < it.n_frames; f0 += T) {
             const int64_t f1 = std::min(f0 + T, it.n_frames);
@@ -153,8 +154,9 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
     if (!b)
         return set_error(SK_ERR_OOM, "host allocation");
     b->device = device;
-    int rows[kBatchClasses] = {0, 0, 0};
-    bool all_m32[kBatchClasses] = {true, true, true};
+    int rows[kBatchClasses] = {};
+    bool all_m32[kBatchClasses];
+    std::fill(all_m32, all_m32 + kBatchClasses, true);
     std::vector<int32_t> sel[kBatchClasses];
     for (int32_t k = 0; k < n_items; ++k) {
         const sk_batch_item_t &bi = items[k];
@@ -182,7 +184,7 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
         b->tile[c] = pick_tile(rows[c] == 8 ? 8 : 16, all_m32[c]);
         std::vector<Chunk> ch;
         std::vector<int32_t> cta;
-        build_schedule(b->items, sel[c], b->grid, ch, cta);
+        build_schedule(b->items, sel[c], b->grid, ch, cta, c >= kFirstImajorClass);
         b->used[c] = !ch.empty();
         const int32_t base = (int32_t)b->chunks.size();
         for (int32_t &x : cta)

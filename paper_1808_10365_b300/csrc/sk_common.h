@@ -28,19 +28,22 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
                             const int32_t *d_cta_chunks, int grid, int tile, bool served,
                             int device, cudaStream_t st, int nclass = 0);
 // Kernel class of a batched item: 2 for time-major fast-path items of N = 2048,
-// 1 for N = 256, 0 for the rest (runtime row stride or the general path).
+// 1 for N = 256, 3..8 for input-major items on the grouped path with M = 128,
+// 256, ..., 4096, 0 for the rest (runtime row stride or the general path).
 int batch_class(const Item &it);
-constexpr int kBatchClasses = 3;
+constexpr int kBatchClasses = 9;
+constexpr int kFirstImajorClass = 3;
 int pick_tile(int rows, bool all_m32);
 int imajor_lanes(int M);
-int imajor_chunks(int M);
+int imajor_shape(int M);
 sk_status_t ensure_kernel_attrs(int device);
 int sm_count(int device);
 
 // Static byte-balanced schedule of the items listed in `sel` over `grid` CTAs;
-// chunk item indices refer to `items`.
+// chunk item indices refer to `items`.  imajor: rounds follow the input-major
+// kernel's team size.
 void build_schedule(const std::vector<Item> &items, const std::vector<int32_t> &sel, int grid,
-                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta);
+                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta, bool imajor = false);
 
 // Schedule for a batch of one-frame items; reorders items, returns the grid.
 int build_item_schedule(std::vector<Item> &items, int grid_max, std::vector<Chunk> &chunks,

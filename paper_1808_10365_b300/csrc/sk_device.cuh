@@ -779,27 +779,29 @@ __device__ __forceinline__ uint4 ldg_stream16_at(const uint8_t *base)
     return v;
 }
 
-// Batch nb of a group on the grouped input-major path: chunk t is chunk t % CH of
-// input nb IPB + t / CH; all offsets are load immediates.
-template <int M, int G, int CH, int IPB, int nb, int... Ts>
+// Batch nb of a group on the grouped input-major path: chunk t of the batch is
+// the group's chunk g = nb KB + t, i.e. chunk g % CH of input g / CH; all offsets
+// are load immediates.
+template <int M, int G, int CH, int KB, int nb, int... Ts>
 __device__ __forceinline__ void load_group_imm(uint4 *buf, const uint8_t *base,
                                                std::integer_sequence<int, Ts...>)
 {
-    ((buf[Ts] = ldg_stream16_at<(nb * IPB + Ts / CH) * M + (Ts % CH) * G * 16>(base)), ...);
+    ((buf[Ts] = ldg_stream16_at<((nb * KB + Ts) / CH) * M + ((nb * KB + Ts) % CH) * G * 16>(
+          base)),
+     ...);
 }
 
 template <int M, int G, int CH, int KB, int nb>
 __device__ __forceinline__ void load_group_batch(uint4 (&buf)[KB], const uint8_t *base, int live)
 {
-    constexpr int IPB = KB / CH;
     if (live == G) {
-        load_group_imm<M, G, CH, IPB, nb>(buf, base, std::make_integer_sequence<int, KB>{});
+        load_group_imm<M, G, CH, KB, nb>(buf, base, std::make_integer_sequence<int, KB>{});
     } else {
 #pragma unroll
         for (int t = 0; t < KB; ++t) {
-            const int u = nb * IPB + t / CH;
-            buf[t] = u < live ? ldg_stream16(base + u * M + (t % CH) * G * 16)
-                              : make_uint4(0u, 0u, 0u, 0u);
+            const int g = nb * KB + t;
+            buf[t] = g / CH < live ? ldg_stream16(base + (g / CH) * M + (g % CH) * G * 16)
+                                   : make_uint4(0u, 0u, 0u, 0u);
         }
     }
 }
@@ -813,7 +815,6 @@ __device__ __forceinline__ void group_batches(uint4 (&cur)[KB], uint4 (&nxt)[KB]
                                               uint32_t lb, int32_t (&s1)[G], int32_t (&s2)[G])
 {
     if constexpr (nb < NB) {
-        constexpr int IPB = KB / CH;
         if constexpr (nb + 1 < NB)
             load_group_batch<M, G, CH, KB, nb + 1>(nxt, cur_base, cur_live);
         else
@@ -821,8 +822,8 @@ __device__ __forceinline__ void group_batches(uint4 (&cur)[KB], uint4 (&nxt)[KB]
 #pragma unroll
         for (int t = 0; t < KB; ++t) {
             const uint32_t a = accum16(cur[t], lb);
-            s1[nb * IPB + t / CH] += (int32_t)(a >> kPackShift);
-            s2[nb * IPB + t / CH] += (int32_t)(a & kPackMask);
+            s1[(nb * KB + t) / CH] += (int32_t)(a >> kPackShift);
+            s2[(nb * KB + t) / CH] += (int32_t)(a & kPackMask);
         }
         group_batches<M, G, CH, NB, KB, nb + 1>(nxt, cur, cur_base, cur_live, nxt_base, nxt_live,
                                                 lb, s1, s2);
@@ -838,19 +839,25 @@ __device__ __forceinline__ void group_batches(uint4 (&cur)[KB], uint4 (&nxt)[KB]
 // input u's totals in lane u, so all lanes form an input term at once.  The
 // segment's groups are (k nseg + seg) G .. + G-1 for k = 0, 1, ...; a frame is
 // NG = ceil(N / team) groups per segment (team = threads per frame, which the
-// plan sets to about one per 2 KB of frame).  The group streams through two
+// plan sets to about one per 2 KB of frame).  Inputs longer than 512 samples are
+// read as SPLIT sub-inputs of 512 (measured: the 512-sample shape streams at
+// 6.2 TB/s, the 1024-sample one at 4.4).  The group streams through two
 // register batches of KB chunks (NB batches per group, NB even, so every group
 // starts in batch A); with PF the next group's bytes are requested into L2 while
 // this one is read.
-template <int G, int CH, bool PF>
+template <int G, int CH, bool PF, int SPLIT = 1>
 __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_begin,
                                                    int64_t f_end, uint32_t lb, TeamSmem &ts,
                                                    int &parity)
 {
+    // SPLIT > 1: each input is read as SPLIT consecutive sub-inputs of M / SPLIT
+    // bytes (the layout is the same bytes), whose sums are added after the
+    // reduce-scatter; M here is the sub-input length
+    static_assert(SPLIT >= 1 && G % SPLIT == 0, "sub-inputs of one input share a group");
     constexpr int M = 16 * G * CH;
     constexpr int NB = (G * CH / 8) < 2 ? 2 : G * CH / 8;  // batches per group
     constexpr int KB = G * CH / NB;                       // chunks per batch
-    static_assert(KB % CH == 0 && NB % 2 == 0, "batch shape");
+    static_assert(KB * NB == G * CH && NB % 2 == 0, "batch shape");
     const int team_log2 = it.team_log2;
     const int team = 1 << team_log2;
     const int T = kThreads >> team_log2;
@@ -859,14 +866,15 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
     const int nseg = team / G;
     const int seg = lit / G, j = lit % G;
     const int N = it.N;
-    const int NG = (N + team - 1) / team;
-    const int64_t fbytes = (int64_t)M * N;
+    const int NS = N * SPLIT;  // sub-inputs per frame
+    const int NG = (NS + team - 1) / team;
+    const int64_t fbytes = (int64_t)M * NS;
     const int64_t kmax = (f_end - f_begin + T - 1) / T;
 
-    // inputs of group (frame f, k) that this segment may read: 0..G
+    // sub-inputs of group (frame f, k) that this segment may read: 0..G
     auto live_of = [&](int64_t f, int k) -> int {
         const int i0 = (k * nseg + seg) * G;
-        const int r = N - i0;
+        const int r = NS - i0;
         return (f < f_end) ? (r < 0 ? 0 : (r > G ? G : r)) : 0;
     };
     auto base_of = [&](int64_t f, int k) -> const uint8_t * {
@@ -911,12 +919,19 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
                     s2[t] = keep2 + __shfl_xor_sync(0xFFFFFFFFu, send2, o);
                 }
             }
-            if (j < cur_live) {
-                const int i = (k * nseg + seg) * G + j;
+            // an input's sub-inputs sit in lanes j .. j + SPLIT - 1 (j % SPLIT == 0)
+#pragma unroll
+            for (int o = 1; o < SPLIT; o <<= 1) {
+                s1[0] += __shfl_xor_sync(0xFFFFFFFFu, s1[0], o);
+                s2[0] += __shfl_xor_sync(0xFFFFFFFFu, s2[0], o);
+            }
+            if (j < cur_live && j % SPLIT == 0) {
+                const int i = ((k * nseg + seg) * G + j) / SPLIT;
                 float r = 0.0f;
                 int64_t qi = 0;
-                const bool has = SK_EPILOGUE_ALU ? input_term_alu(s1[0], s2[0], M, r, qi)
-                                                 : input_term(s1[0], s2[0], M, r, qi);
+                const bool has = SK_EPILOGUE_ALU
+                                     ? input_term_alu(s1[0], s2[0], M * SPLIT, r, qi)
+                                     : input_term(s1[0], s2[0], M * SPLIT, r, qi);
                 if (has) {
                     q += qi;
                     cnt += 1;

@@ -26,6 +26,9 @@ def _dev():
     [(2048, 256, 23, 0), (256, 128, 70, 0), (2048, 1024, 5, 0), (256, 1024, 31, 0),
      (100, 48, 9, 0), (512, 256, 1, 0), (2048, 128, 0, 0), (256, 256, 64, 0),
      (2048, 48, 4, 0), (256, 256, 10, 1), (2048, 128, 3, 1)],
+    # input-major items only: the grouped path per M, ragged N, and the general path
+    [(2048, 256, 9, 1), (256, 1024, 7, 1), (512, 512, 5, 1), (100, 128, 6, 1), (64, 64, 4, 1),
+     (2048, 128, 11, 1)],
     # one class only
     [(256, 256, 40, 0), (256, 128, 17, 0)],
     [(2048, 256, 7, 0)],

@@ -352,10 +352,12 @@ def test_full_array_input_major_sampled():
     assert r["checked"] == len(sample)
 
 
-@pytest.mark.parametrize("N,M,F", [(4096, 1024, 2), (4096, 4096, 1), (9, 512, 4)])
+@pytest.mark.parametrize("N,M,F", [(4096, 1024, 2), (4096, 4096, 1), (9, 512, 4), (33, 2048, 3),
+                                   (5, 4096, 2), (1000, 1024, 3)])
 def test_input_major_maximum_and_ragged_sizes(N, M, F):
-    """Input-major at the largest N (grouped path, M = 1024; per-input path, M = 4096)
-    and a ragged N on the grouped path; worst-case bytes (every sample -8-8j) in one frame."""
+    """Input-major at the largest N and M (the grouped path reads inputs longer than 512
+    samples as 2, 4 or 8 sub-inputs) and ragged N; worst-case bytes (every sample
+    -8-8j) in one frame."""
     rng = np.random.default_rng(N + M + F)
     x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
     x[F - 1, : M * min(N, 64)] = 0x00

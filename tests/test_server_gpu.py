@@ -154,6 +154,22 @@ def test_input_major_stream_matches_time_major_stream(N, M):
     assert [m for _, m in got[1]] == [m for _, m in got[0]]
 
 
+@pytest.mark.parametrize("M", [64, 256, 1024])
+def test_plan_offset_table_matches_oracle_model(M):
+    """A running-offset plan without a caller table builds e[] from its own App. B model;
+    it must equal the oracle's table (entries may differ by one where rounding of
+    delta * 2^32 (M-1)/(M+1) falls on the other side of a half)."""
+    _need_gpu()
+    plan = sk.sk_plan_create(256, M, flags=sk.SK_RUNNING_OFFSET)
+    try:
+        e = sk.sk_plan_offset_table(plan)
+    finally:
+        sk.sk_plan_destroy(plan)
+    want = dg.offset_table(M)
+    d = np.abs(e - want)
+    assert d.max() <= 1 and (d == 0).mean() > 0.99
+
+
 def test_checkpoint_resume_continues_identically():
     _need_gpu()
     N, M, T = 512, 256, 24
