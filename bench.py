@@ -387,17 +387,23 @@ def batched_bench(reps: int = 10, dev_index: int = 0, n_frames: int = 500):
 
 
 def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
-                 pool: int = 32, threads: int = 8):
+                 pool: int = 32, threads: int = 0):
     """32 streams (24 x N=2048, 8 x N=256), M=256 frames arriving every 0.65536 ms per
     stream with exponential jitter (mean T/4), for `seconds` of simulated time, through
     the continuous-batching server with the running power state, driven by the
     library's load generator (sk_server_replay).  Frames cycle through a pool of
     pre-generated frames per stream.  Latency = submit -> result host-visible.
-    The plain reference is one synchronous sk_flag_host call per frame."""
+    The plain reference is one synchronous sk_flag_host call per frame.
+    threads: submitter threads of the load generator (0: 4 when paced -- enough
+    for the 20 GB/s of arrivals, and fewer spinning cores beside the server's
+    own threads -- and 8 flat out)."""
     import torch
 
     import paper_1808_10365_b300 as sk
     import synth
+
+    if threads <= 0:
+        threads = 4 if paced else 8
 
     specs = [2048] * 24 + [256] * 8
     M = 256
