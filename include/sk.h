@@ -23,6 +23,15 @@
  * sk_last_error() gives a message for the calling thread's last failure.
  * Calls taking a stream enqueue work and return without synchronising
  * unless stated otherwise.
+ *
+ * Environment (read once per process; none changes results, only speed):
+ *   SK_AUTOTUNE_CACHE    tile cache file ("N M layout rows grid" lines)
+ *   SK_IMAJOR_GROUPED=0  input-major: per-input path instead of the grouped one
+ *   SK_IMAJOR_PREFETCH=0 input-major grouped path without the L2 prefetch
+ *   SK_IMAJOR_LANES      input-major per-input path: lanes per input (2, 4, 8)
+ *   SK_SERVER_ZEROCOPY=0 server: upload each batch instead of zero-copy reads
+ *   SK_SERVER_INFLIGHT   server: launches in flight (1..8, default 2)
+ *   SK_SERVER_TRACE=1    server: per-launch stage times on destroy
  */
 #ifndef SK_H
 #define SK_H
