@@ -316,6 +316,57 @@ def input_major_bench(n_freq: int, ref_mask, reps: int = 10, dev_index: int = 0)
             "masks_identical_to_time_major": same}
 
 
+def variants_bench(d_in, F: int, delta: float, reps: int = 10, dev_index: int = 0):
+    """The benchmark workload (already on the device) through two variants of the plain
+    launch: per-input estimates with sk_compute_inputs (SK^_i and one-input flags for
+    every input, Eq. originalSK, besides SK~ and the mask), and sk_flag on a plan with
+    the Pearson type III false-alarm thresholds."""
+    import torch
+
+    import paper_1808_10365_b300 as sk
+
+    dev = torch.device("cuda", dev_index)
+    st = torch.cuda.Stream(dev)
+    peak, _ = peaks()
+    nbytes = F * M_T * N_IN
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record(st)
+            fn()
+            b.record(st)
+        st.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    out = {}
+    plan = sk.sk_plan_create(N_IN, M_T, 3.0, delta, device=dev_index)
+    sk_in = torch.empty((F, N_IN), dtype=torch.float32, device=dev)
+    m_in = torch.empty((F, N_IN), dtype=torch.uint8, device=dev)
+    d_sk = torch.empty(F, dtype=torch.float32, device=dev)
+    d_mask = torch.empty(F, dtype=torch.uint8, device=dev)
+    ms = timed(lambda: sk.sk_compute_inputs(plan, d_in, F, sk_in, m_in, d_sk, d_mask, st))
+    sk.sk_plan_destroy(plan)
+    alg = nbytes + F * N_IN * 5 + F * 5
+    out["independent_estimates"] = {
+        "call": "sk_compute_inputs (SK^_i float + one-input flag per input, SK~ + mask per frame)",
+        "value": nbytes / (ms * 1e-3) / 1e9, "unit": UNIT, "ms": ms,
+        "algorithmic_bytes": alg, "roofline_frac": alg / (ms * 1e-3) / 1e9 / peak}
+    del sk_in, m_in
+    plan = sk.sk_plan_create(N_IN, M_T, 3.0, delta, flags=sk.SK_THRESH_PEARSON3,
+                             device=dev_index)
+    ms = timed(lambda: sk.sk_flag(plan, d_in, F, d_sk, d_mask, st))
+    sk.sk_plan_destroy(plan)
+    out["pearson3_thresholds"] = {
+        "call": "sk_flag, SK_THRESH_PEARSON3 plan", "value": nbytes / (ms * 1e-3) / 1e9,
+        "unit": UNIT, "ms": ms, "roofline_frac": (nbytes + F * 5) / (ms * 1e-3) / 1e9 / peak,
+        "flag_rate": float(d_mask.float().mean().item())}
+    return out
+
+
 def batched_bench(reps: int = 10, dev_index: int = 0, n_frames: int = 500):
     """Mixed workload: 64 frequencies of N=2048 and 64 of N=256, M in {128, 256, 1024}
     per frequency from the seed, 500 frames each (n_frames: a smaller case for
@@ -387,7 +438,7 @@ def batched_bench(reps: int = 10, dev_index: int = 0, n_frames: int = 500):
 
 
 def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
-                 pool: int = 32, threads: int = 0):
+                 pool: int = 32, threads: int = 0, running_mu: bool = False):
     """32 streams (24 x N=2048, 8 x N=256), M=256 frames arriving every 0.65536 ms per
     stream with exponential jitter (mean T/4), for `seconds` of simulated time, through
     the continuous-batching server with the running power state, driven by the
@@ -396,7 +447,8 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
     The plain reference is one synchronous sk_flag_host call per frame.
     threads: submitter threads of the load generator (0: 4 when paced -- enough
     for the 20 GB/s of arrivals, and fewer spinning cores beside the server's
-    own threads -- and 8 flat out)."""
+    own threads -- and 8 flat out).  running_mu: the streams also normalise by the
+    running power (SK_RUNNING_MU) instead of each frame's own power."""
     import torch
 
     import paper_1808_10365_b300 as sk
@@ -415,13 +467,14 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
         pools.append(ds.generate_cpu())
     n_per = int(seconds / T)
     server = sk.sk_server_create(dev_index, 8 << 30)
-    sids = [sk.sk_stream_open(server, N, M, ring_frames=32, flags=sk.SK_RUNNING_OFFSET)
-            for N in specs]
+    flags = sk.SK_RUNNING_MU if running_mu else sk.SK_RUNNING_OFFSET
+    sids = [sk.sk_stream_open(server, N, M, ring_frames=32, flags=flags) for N in specs]
     r = sk.sk_server_replay(server, sids, pools, n_per, T, T / 4, paced=paced, threads=threads)
     for sid in sids:
         sk.sk_stream_close(server, sid)
     sk.sk_server_destroy(server)
-    out = {"streams": "24 x N=2048 + 8 x N=256, M=256, running power state",
+    out = {"streams": "24 x N=2048 + 8 x N=256, M=256, running power state"
+                      + (", running-mu normalisation" if running_mu else ""),
            "paced": paced, "simulated_s": seconds, "frames": r["frames"], "wall_s": r["wall_s"],
            "value": r["bytes"] / r["wall_s"] / 1e9, "unit": UNIT,
            "realtime_input_gbs": sum(specs) * M / T / 1e9,
@@ -429,7 +482,7 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
            "launches": r["launches"], "frames_per_launch": r["frames"] / max(1, r["launches"]),
            "submit_p50_us": r["submit_p50_us"], "busy_retries": r["busy_retries"],
            "driver": f"sk_server_replay, {threads} submitter threads"}
-    if paced:
+    if paced and not running_mu:
         # plain path on the same frames: one synchronous sk_flag_host per frame
         lat = []
         plans = {N: sk.sk_plan_create(N, M, 3.0, 0.0, device=dev_index) for N in set(specs)}
@@ -563,6 +616,8 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if ws == 1 and not args.no_extras:
+        if layout == 0:
+            line.update(variants_bench(d_in, F, delta, dev_index=dev.index))
         del d_in
         torch.cuda.empty_cache()
         if layout == 0:
@@ -570,6 +625,8 @@ def run_gpu(args):
         line["batched"] = batched_bench(dev_index=dev.index)
         line["served"] = served_bench(args.served_seconds, True, dev.index)
         line["served_replay"] = served_bench(min(args.served_seconds, 1.0), False, dev.index)
+        line["served_running_mu"] = served_bench(min(args.served_seconds, 1.0), True, dev.index,
+                                                 running_mu=True)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
