@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (it.fast == 2 && it.M == 16 * G * CH * SPLIT && im.team_log2 >= 5)
                 run_imajor_grouped<G, CH, PF, SPLIT>(im, ch.f_begin, ch.f_end, lb, ts, parity);
             else
-                run_general<false>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+                run_general<false, false>(it, ch.f_begin, ch.f_end, lb, ts, parity);
         }
         return;
     }
@@ -140,12 +140,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (single.fast == 2 && single.M == 16 * G * CH * SPLIT && im.team_log2 >= 5)
             run_imajor_grouped<G, CH, PF, SPLIT>(im, fb, fe, lb, ts, parity);
         else
-            run_general<false>(single, fb, fe, lb, ts, parity);
+            run_general<false, false>(single, fb, fe, lb, ts, parity);
     } else {
         if (single.fast == 2 && single.M % (16 * G) == 0 && im.team_log2 >= 5)
             run_imajor<G, 8>(im, fb, fe, lb, ts, parity);
         else
-            run_general<false>(single, fb, fe, lb, ts, parity);
+            run_general<false, false>(single, fb, fe, lb, ts, parity);
     }
 }
 
