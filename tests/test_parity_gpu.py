@@ -111,7 +111,8 @@ def test_fast_path_shapes_random_bytes(N, M, F):
 
 @pytest.mark.parametrize("N,M,F,layout", [
     (1, 2, 3, 0), (3, 17, 4, 0), (100, 100, 6, 0), (257, 33, 5, 0), (4095, 16, 2, 0),
-    (7, 64, 9, 0), (1, 2, 3, 1), (100, 100, 6, 1), (256, 256, 4, 1), (37, 5, 11, 1)])
+    (7, 64, 9, 0), (10, 6, 7, 0), (13, 3, 5, 0), (2046, 255, 2, 0), (4093, 7, 3, 0),
+    (1, 2, 3, 1), (100, 100, 6, 1), (256, 256, 4, 1), (37, 5, 11, 1)])
 def test_general_path_ragged_shapes(N, M, F, layout):
     rng = np.random.default_rng(N * 13 + M * 3 + F + layout)
     x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
