@@ -365,3 +365,27 @@ def test_input_major_maximum_and_ragged_sizes(N, M, F):
     want = oracle.flag(x, M, N, 3.0, 0.0, layout=1)
     got = run_compute(x, M, N, 3.0, 0.0, layout=1)
     assert_parity(got, want)
+
+
+def test_random_shapes_sweep():
+    """40 seeded random shapes (N, M, frames, layout) across every path: vector and
+    general time-major, grouped (with sub-inputs), per-input and general input-major.
+    Random bytes, nibble 0 included; everything bit-exact against the oracle."""
+    rng = np.random.default_rng(20261204)
+    Ms = [2, 3, 16, 32, 48, 64, 100, 128, 256, 384, 512, 1024, 2048, 4096]
+    for case in range(40):
+        layout = int(rng.integers(0, 2))
+        M = int(rng.choice(Ms)) if rng.random() < 0.7 else int(rng.integers(2, 700))
+        N = int(rng.integers(1, 4097)) if rng.random() < 0.5 else int(8 * rng.integers(1, 513))
+        F = int(rng.integers(1, 7))
+        while F > 1 and F * M * N > (6 << 20):
+            F -= 1
+        if M * N > (16 << 20):
+            N = max(1, (16 << 20) // M)
+        x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+        want = oracle.flag(x, M, N, 2.5, -0.02, layout=layout)
+        got = run_compute(x, M, N, 2.5, -0.02, layout=layout)
+        try:
+            assert_parity(got, want)
+        except AssertionError as e:
+            raise AssertionError(f"case {case}: N={N} M={M} F={F} layout={layout}") from e
