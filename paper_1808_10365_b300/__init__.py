@@ -161,6 +161,48 @@ def _ptr(x):
     return x.data_ptr()
 
 
+# (N, M) of the plans and served streams created through this binding, so that
+# buffer sizes can be checked before a kernel ever sees them
+_plan_shape = {}
+_stream_shape = {}
+
+
+def _buf(x, nbytes, where, what):
+    """Raw address of x after checking it.  A torch tensor or numpy array must be
+    contiguous, hold at least nbytes (when the shape is known) and live where the
+    call reads it: 'device' (a CUDA tensor, or a page-locked CPU tensor the device
+    can read) or 'host' (numpy, or a CPU tensor).  Plain integers pass unchecked."""
+    if x is None or isinstance(x, int):
+        return _ptr(x)
+    if isinstance(x, np.ndarray):
+        if where == "device":
+            raise SkError(SK_ERR_INVALID_ARG, f"{what}: a numpy array is host memory; "
+                                              "this call reads device memory")
+        if not x.flags.c_contiguous:
+            raise SkError(SK_ERR_INVALID_ARG, f"{what}: array is not contiguous")
+        size = x.nbytes
+    else:
+        if not x.is_contiguous():
+            raise SkError(SK_ERR_INVALID_ARG, f"{what}: tensor is not contiguous")
+        if where == "device" and not (x.is_cuda or x.is_pinned()):
+            raise SkError(SK_ERR_INVALID_ARG, f"{what}: tensor is in pageable host memory; "
+                                              "this call reads device memory")
+        if where == "host" and x.is_cuda:
+            raise SkError(SK_ERR_INVALID_ARG, f"{what}: CUDA tensor given to a host-buffer call")
+        size = x.numel() * x.element_size()
+    if nbytes is not None and size < nbytes:
+        raise SkError(SK_ERR_INVALID_ARG, f"{what}: {size} bytes, the call needs {nbytes}")
+    return _ptr(x)
+
+
+def _sizes(shape, n_frames, per_frame):
+    """Bytes of each buffer for n_frames frames (None if the shape is unknown)."""
+    if shape is None or n_frames < 0:
+        return [None] * len(per_frame)
+    N, M = shape
+    return [int(n_frames) * f(N, M) for f in per_frame]
+
+
 def _stream(s):
     if s is None:
         import torch
@@ -195,11 +237,13 @@ def sk_plan_create(n_inputs, n_time, n_sigma=3.0, mean_offset=0.0, layout=0, fla
     p, keep = _params(n_inputs, n_time, n_sigma, mean_offset, layout, flags, offset_table)
     h = ctypes.c_void_p()
     _check(library().sk_plan_create(ctypes.byref(p), int(device), ctypes.byref(h)))
+    _plan_shape[h.value] = (int(n_inputs), int(n_time))
     return h.value
 
 
 def sk_plan_destroy(plan):
     _check(library().sk_plan_destroy(plan))
+    _plan_shape.pop(plan, None)
 
 
 def sk_plan_thresholds(plan, n_inputs):
@@ -227,32 +271,54 @@ def sk_plan_get_tiles(plan):
 
 
 def sk_compute(plan, d_in, n_frames, s1=None, s2=None, q=None, sk=None, neff=None, stream=None):
-    _check(library().sk_compute(plan, _ptr(d_in), int(n_frames), _ptr(s1), _ptr(s2), _ptr(q),
-                                _ptr(sk), _ptr(neff), _stream(stream)))
+    F = int(n_frames)
+    b_in, b_s, b_q, b_4 = _sizes(_plan_shape.get(plan), F, [
+        lambda N, M: M * N, lambda N, M: 4 * N, lambda N, M: 8, lambda N, M: 4])
+    _check(library().sk_compute(plan, _buf(d_in, b_in, "device", "d_in"), F,
+                                _buf(s1, b_s, "device", "s1"), _buf(s2, b_s, "device", "s2"),
+                                _buf(q, b_q, "device", "q"), _buf(sk, b_4, "device", "sk"),
+                                _buf(neff, b_4, "device", "neff"), _stream(stream)))
 
 
 def sk_compute_inputs(plan, d_in, n_frames, sk_in, mask_in=None, sk=None, mask=None,
                       stream=None):
-    _check(library().sk_compute_inputs(plan, _ptr(d_in), int(n_frames), _ptr(sk_in),
-                                       _ptr(mask_in), _ptr(sk), _ptr(mask), _stream(stream)))
+    F = int(n_frames)
+    b_in, b_ski, b_mi, b_sk, b_m = _sizes(_plan_shape.get(plan), F, [
+        lambda N, M: M * N, lambda N, M: 4 * N, lambda N, M: N, lambda N, M: 4,
+        lambda N, M: 1])
+    _check(library().sk_compute_inputs(plan, _buf(d_in, b_in, "device", "d_in"), F,
+                                       _buf(sk_in, b_ski, "device", "sk_in"),
+                                       _buf(mask_in, b_mi, "device", "mask_in"),
+                                       _buf(sk, b_sk, "device", "sk"),
+                                       _buf(mask, b_m, "device", "mask"), _stream(stream)))
 
 
 def sk_flag(plan, d_in, n_frames, sk, mask, stream=None):
-    _check(library().sk_flag(plan, _ptr(d_in), int(n_frames), _ptr(sk), _ptr(mask),
+    F = int(n_frames)
+    b_in, b_sk, b_m = _sizes(_plan_shape.get(plan), F, [
+        lambda N, M: M * N, lambda N, M: 4, lambda N, M: 1])
+    _check(library().sk_flag(plan, _buf(d_in, b_in, "device", "d_in"), F,
+                             _buf(sk, b_sk, "device", "sk"), _buf(mask, b_m, "device", "mask"),
                              _stream(stream)))
 
 
+def _host_call(fn, plan, h_in, n_frames, h_sk, h_mask, stream):
+    F = int(n_frames)
+    b_in, b_sk, b_m = _sizes(_plan_shape.get(plan), F, [
+        lambda N, M: M * N, lambda N, M: 4, lambda N, M: 1])
+    _check(fn(plan, _buf(h_in, b_in, "host", "h_in"), F, _buf(h_sk, b_sk, "host", "h_sk"),
+              _buf(h_mask, b_m, "host", "h_mask"), _stream(stream)))
+
+
 def sk_flag_host(plan, h_in, n_frames, h_sk, h_mask, stream=None):
-    _check(library().sk_flag_host(plan, _ptr(h_in), int(n_frames), _ptr(h_sk), _ptr(h_mask),
-                                  _stream(stream)))
+    _host_call(library().sk_flag_host, plan, h_in, n_frames, h_sk, h_mask, stream)
 
 
 def sk_flag_host_noalloc(plan, h_in, n_frames, h_sk, h_mask, stream=None):
     """sk_flag_host for callers that cannot allocate device memory: stages through a
     fixed array inside the library (at most SK_NOALLOC_MAX_BYTES input bytes and
     SK_NOALLOC_MAX_FRAMES frames per call)."""
-    _check(library().sk_flag_host_noalloc(plan, _ptr(h_in), int(n_frames), _ptr(h_sk),
-                                          _ptr(h_mask), _stream(stream)))
+    _host_call(library().sk_flag_host_noalloc, plan, h_in, n_frames, h_sk, h_mask, stream)
 
 
 # ---------------------------------------------------------------- batched
@@ -261,11 +327,13 @@ def sk_batch_create(items, device=0) -> int:
     """items: sequence of (plan, d_in, n_frames, d_sk, d_mask)."""
     arr = (sk_batch_item_t * len(items))()
     for k, (plan, d_in, n, sk, mask) in enumerate(items):
+        b_in, b_sk, b_m = _sizes(_plan_shape.get(plan), int(n), [
+            lambda N, M: M * N, lambda N, M: 4, lambda N, M: 1])
         arr[k].plan = plan
-        arr[k].d_in = _ptr(d_in)
+        arr[k].d_in = _buf(d_in, b_in, "device", f"item {k} d_in")
         arr[k].n_frames = int(n)
-        arr[k].d_sk = _ptr(sk)
-        arr[k].d_mask = _ptr(mask)
+        arr[k].d_sk = _buf(sk, b_sk, "device", f"item {k} sk")
+        arr[k].d_mask = _buf(mask, b_m, "device", f"item {k} mask")
     h = ctypes.c_void_p()
     _check(library().sk_batch_create(arr, len(items), int(device), ctypes.byref(h)))
     return h.value
@@ -289,6 +357,8 @@ def sk_server_create(device=0, hbm_budget_bytes=1 << 34) -> int:
 
 def sk_server_destroy(server):
     _check(library().sk_server_destroy(server))
+    for key in [k for k in _stream_shape if k[0] == server]:
+        del _stream_shape[key]
 
 
 def sk_stream_open(server, n_inputs, n_time, ring_frames=16, n_sigma=3.0, mean_offset=0.0,
@@ -296,14 +366,16 @@ def sk_stream_open(server, n_inputs, n_time, ring_frames=16, n_sigma=3.0, mean_o
     p, keep = _params(n_inputs, n_time, n_sigma, mean_offset, layout, flags, offset_table)
     sid = ctypes.c_int32()
     _check(library().sk_stream_open(server, ctypes.byref(p), int(ring_frames), ctypes.byref(sid)))
+    _stream_shape[(server, sid.value)] = (int(n_inputs), int(n_time))
     return sid.value
 
 
 def sk_stream_submit(server, stream_id, frame, frame_index=0) -> int:
     """frame: host bytes (numpy uint8 or CPU tensor) of one frame; returns the ticket."""
+    (nb,) = _sizes(_stream_shape.get((server, int(stream_id))), 1, [lambda N, M: M * N])
     t = ctypes.c_int64()
-    _check(library().sk_stream_submit(server, int(stream_id), _ptr(frame), int(frame_index),
-                                      ctypes.byref(t)))
+    _check(library().sk_stream_submit(server, int(stream_id), _buf(frame, nb, "host", "frame"),
+                                      int(frame_index), ctypes.byref(t)))
     return t.value
 
 
@@ -334,6 +406,7 @@ def sk_stream_set_state(server, stream_id, state: bytes):
 
 def sk_stream_close(server, stream_id):
     _check(library().sk_stream_close(server, int(stream_id)))
+    _stream_shape.pop((server, int(stream_id)), None)
 
 
 def sk_server_stats(server) -> dict:

@@ -66,3 +66,41 @@ def test_no_device_is_an_error_not_a_crash():
     with pytest.raises(sk.SkError) as e:
         sk.sk_plan_create(256, 256)
     assert e.value.status in (sk.SK_ERR_CUDA, sk.SK_ERR_INVALID_ARG)
+
+
+def test_binding_rejects_buffers_before_any_call():
+    """Buffer checks of the binding: size against the plan's N and M, contiguity, and
+    host versus device memory.  They raise before the library is called (the plan
+    handle here is fake and must never reach it)."""
+    import torch
+
+    fake = 0x5EED
+    sk._plan_shape[fake] = (256, 256)
+    try:
+        F = 2
+        need = F * 256 * 256
+        cases = [
+            # device calls given host memory
+            lambda: sk.sk_flag(fake, np.zeros(need, np.uint8), F, None, np.zeros(F, np.uint8)),
+            lambda: sk.sk_flag(fake, torch.zeros(need, dtype=torch.uint8), F, None, None),
+            lambda: sk.sk_compute(fake, np.zeros(need, np.uint8), F),
+            # host calls: too small, not contiguous
+            lambda: sk.sk_flag_host(fake, np.zeros(need - 1, np.uint8), F, None,
+                                    np.zeros(F, np.uint8)),
+            lambda: sk.sk_flag_host(fake, np.zeros(need, np.uint8), F, np.zeros(1, np.float32),
+                                    np.zeros(F, np.uint8)),
+            lambda: sk.sk_flag_host(fake, np.zeros((F, 2 * 256 * 256), np.uint8)[:, ::2], F,
+                                    None, np.zeros(F, np.uint8)),
+            lambda: sk.sk_flag_host_noalloc(fake, np.zeros(need, np.uint8), F, None,
+                                            np.zeros(F - 1, np.uint8)),
+        ]
+        for k, call in enumerate(cases):
+            with pytest.raises(sk.SkError) as e:
+                call()
+            assert e.value.status == sk.SK_ERR_INVALID_ARG, k
+        sk._stream_shape[(fake, 3)] = (256, 256)
+        with pytest.raises(sk.SkError):
+            sk.sk_stream_submit(fake, 3, np.zeros(256 * 255, np.uint8))
+    finally:
+        sk._plan_shape.pop(fake, None)
+        sk._stream_shape.pop((fake, 3), None)
