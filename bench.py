@@ -40,6 +40,9 @@ UNIT = "Gsamples/s"
 N_IN, M_T, N_FREQ, N_FRAMES = 2048, 256, 4, 1525
 WORKLOAD = "full_array_plain: {f} freq x N=2048 x M=256 x 1525 frames, 4+4-bit, 3 sigma"
 KERNEL_SOURCES = ["paper_1808_10365_b300/csrc/sk_device.cuh",
+                  "paper_1808_10365_b300/csrc/sk_path_time.cuh",
+                  "paper_1808_10365_b300/csrc/sk_path_input.cuh",
+                  "paper_1808_10365_b300/csrc/sk_path_general.cuh",
                   "paper_1808_10365_b300/csrc/sk_api.cu"]
 PROFILE_SUMMARY = {0: os.path.join(ROOT, "profiles", "sk_fused_kernel_full_array.json"),
                    1: os.path.join(ROOT, "profiles", "sk_imajor_kernel_full_array.json")}

@@ -9,6 +9,9 @@
 #include <new>
 
 #include "sk_common.h"
+#include "sk_path_general.cuh"
+#include "sk_path_input.cuh"
+#include "sk_path_time.cuh"
 
 namespace sk {
 

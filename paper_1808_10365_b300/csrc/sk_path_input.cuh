@@ -1,0 +1,380 @@
+// Input-major paths of the fused kernel: the grouped path (8 lanes per group of
+// 8 inputs, reduce-scatter) and the per-input path for the other lengths.
+#pragma once
+
+#include "sk_device.cuh"
+
+namespace sk {
+
+__device__ __forceinline__ uint4 ldg_stream16(const uint8_t *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// 16 samples of one input (one 16-byte chunk) into one packed accumulator.
+__device__ __forceinline__ uint32_t accum16(uint4 w, uint32_t lb)
+{
+    uint32_t a = 0u;
+    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        a += lds_u32(prmt(ww[h], lb, 0x7604u)) + lds_u32(prmt(ww[h], lb, 0x7614u));
+        a += lds_u32(prmt(ww[h], lb, 0x7624u)) + lds_u32(prmt(ww[h], lb, 0x7634u));
+    }
+    return a;
+}
+
+// Input-major fast path: layout [frame][input][t], M % (16 G) == 0, team of at
+// least 32 threads.  A segment of G lanes owns one input at a time: lane j reads
+// the 16-byte chunks j, j+G, j+2G, ... of that input's M bytes, so one warp
+// instruction reads 32/G runs of 16 G contiguous bytes.  Each chunk (16 samples)
+// fills one packed accumulator, which is split into exact S1, S2 at once.  After
+// an input's last chunk the segment adds S1 and S2 over its G lanes with
+// log2(G) shuffles and its lane 0 forms the input's term.  The lane's chunks of
+// successive inputs, and of the team's next frame, form one flat sequence that
+// streams through two register batches of KB chunks; a frame's sequence is padded
+// to a multiple of KB so that frame ends fall on batch boundaries.
+template <int G, int KB>
+__device__ __forceinline__ void run_imajor(const Item &it, int64_t f_begin, int64_t f_end,
+                                           uint32_t lb, TeamSmem &ts, int &parity)
+{
+    const int team_log2 = it.team_log2;
+    const int T = kThreads >> team_log2;
+    const int team_idx = threadIdx.x >> team_log2;
+    const int lit = threadIdx.x & ((1 << team_log2) - 1);
+    const int nseg = (1 << team_log2) / G;
+    const int seg = lit / G, j = lit % G;
+    const int N = it.N, M = it.M;
+    const int C = M / (16 * G);                 // chunks per lane per input
+    const int K = (N + nseg - 1) / nseg;        // inputs per segment
+    const int per = ((K * C + KB - 1) / KB) * KB;  // padded flat chunks per frame
+    const int nbat = per / KB;
+    const int64_t fbytes = (int64_t)M * N;
+    const int64_t kmax = (f_end - f_begin + T - 1) / T;
+
+    // load cursor: frame, input slot k, chunk c, flat position g
+    int64_t lf = f_begin + team_idx;
+    int lk = 0, lc = 0, lg = 0;
+    auto load_batch = [&](uint4 (&buf)[KB]) {
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int i = seg + lk * nseg;
+            if (lf < f_end && lk < K && i < N)
+                buf[u] = ldg_stream16(it.in + lf * fbytes + (int64_t)i * M +
+                                      (int64_t)(j + lc * G) * 16);
+            if (++lc == C) {
+                lc = 0;
+                ++lk;
+            }
+        }
+        // frame ends fall on batch boundaries (per is a multiple of KB)
+        lg += KB;
+        if (lg >= per) {
+            lg = 0;
+            lk = 0;
+            lc = 0;
+            lf += T;
+        }
+    };
+
+    uint4 A[KB], B[KB];
+    load_batch(A);
+    int64_t frame = f_begin + team_idx;
+    for (int64_t kk = 0; kk < kmax; ++kk) {
+        const bool fvalid = frame < f_end;
+        int64_t q = 0, e = 0;
+        int32_t cnt = 0;
+        int32_t s1 = 0, s2 = 0;
+        int pk = 0, pc = 0;  // process cursor inside the frame
+        for (int b = 0; b < nbat; b += 2) {
+            const bool has_b = b + 1 < nbat;
+            if (has_b)
+                load_batch(B);
+            // process A then B; the same code for both buffers
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1 && !has_b)
+                    break;
+                uint4 (&buf)[KB] = half == 0 ? A : B;
+#pragma unroll
+                for (int u = 0; u < KB; ++u) {
+                    const int i = seg + pk * nseg;
+                    const bool live = fvalid && pk < K && i < N;
+                    if (live) {
+                        const uint32_t a = accum16(buf[u], lb);
+                        s1 += (int32_t)(a >> kPackShift);
+                        s2 += (int32_t)(a & kPackMask);
+                    }
+                    if (++pc == C) {
+                        // input done: combine the segment's lanes (all lanes of a
+                        // warp reach this point together)
+                        pc = 0;
+#pragma unroll
+                        for (int o = 1; o < G; o <<= 1) {
+                            s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+                            s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+                        }
+                        if (live && j == 0) {
+                            float r = 0.0f;
+                            int64_t qi = 0;
+                            const bool has = input_term(s1, s2, M, r, qi);
+                            if (has) {
+                                q += qi;
+                                cnt += 1;
+                            }
+                            const int64_t o = frame * N + i;
+                            if (it.s1) {
+                                it.s1[o] = s1;
+                                it.s2[o] = s2;
+                            }
+                            if (it.sk_in) {
+                                it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1])
+                                                  : __int_as_float(0x7FC00000);
+                                if (it.mask_in)
+                                    it.mask_in[o] =
+                                        has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+                            }
+                        }
+                        s1 = 0;
+                        s2 = 0;
+                        ++pk;
+                    }
+                }
+                if (half == 0)
+                    load_batch(A);
+            }
+        }
+        team_sum(q, cnt, e, team_log2, team_idx, parity, ts, false);
+        if (fvalid && lit == 0) {
+            uint8_t m = 1;
+            if (cnt > 0)
+                m = (q > it.t_hi[cnt] || q < it.t_lo[cnt]) ? 1 : 0;
+            if (it.sk) {
+                float skv = __int_as_float(0x7FC00000);
+                if (cnt > 0)
+                    skv = __fmul_rn(__fmul_rn(__ll2float_rn(q), 0x1p-32f), it.c_tab[cnt]);
+                it.sk[frame] = skv;
+            }
+            if (it.mask)
+                it.mask[frame] = m;
+            if (it.q)
+                it.q[frame] = q;
+            if (it.neff)
+                it.neff[frame] = cnt;
+        }
+        parity ^= 1;
+        frame += T;
+    }
+}
+
+// 16-byte streaming load at base + OFF, OFF an immediate of the instruction.
+template <int OFF>
+__device__ __forceinline__ uint4 ldg_stream16_at(const uint8_t *base)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4+%5];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(base), "n"(OFF));
+    return v;
+}
+
+// Batch nb of a group on the grouped input-major path: chunk t of the batch is
+// the group's chunk g = nb KB + t, i.e. chunk g % CH of input g / CH; all offsets
+// are load immediates.
+template <int M, int G, int CH, int KB, int nb, int... Ts>
+__device__ __forceinline__ void load_group_imm(uint4 *buf, const uint8_t *base,
+                                               std::integer_sequence<int, Ts...>)
+{
+    ((buf[Ts] = ldg_stream16_at<((nb * KB + Ts) / CH) * M + ((nb * KB + Ts) % CH) * G * 16>(
+          base)),
+     ...);
+}
+
+template <int M, int G, int CH, int KB, int nb>
+__device__ __forceinline__ void load_group_batch(uint4 (&buf)[KB], const uint8_t *base, int live)
+{
+    if (live == G) {
+        load_group_imm<M, G, CH, KB, nb>(buf, base, std::make_integer_sequence<int, KB>{});
+    } else {
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+            const int g = nb * KB + t;
+            buf[t] = g / CH < live ? ldg_stream16(base + (g / CH) * M + (g % CH) * G * 16)
+                                   : make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+}
+
+// Batches nb .. NB-1 of a group: load the following batch into nxt (the group's
+// next one, or batch 0 of the next group), then add cur into the sums.
+template <int M, int G, int CH, int NB, int KB, int nb>
+__device__ __forceinline__ void group_batches(uint4 (&cur)[KB], uint4 (&nxt)[KB],
+                                              const uint8_t *cur_base, int cur_live,
+                                              const uint8_t *nxt_base, int nxt_live,
+                                              uint32_t lb, int32_t (&s1)[G], int32_t (&s2)[G])
+{
+    if constexpr (nb < NB) {
+        if constexpr (nb + 1 < NB)
+            load_group_batch<M, G, CH, KB, nb + 1>(nxt, cur_base, cur_live);
+        else
+            load_group_batch<M, G, CH, KB, 0>(nxt, nxt_base, nxt_live);
+#pragma unroll
+        for (int t = 0; t < KB; ++t) {
+            const uint32_t a = accum16(cur[t], lb);
+            s1[(nb * KB + t) / CH] += (int32_t)(a >> kPackShift);
+            s2[(nb * KB + t) / CH] += (int32_t)(a & kPackMask);
+        }
+        group_batches<M, G, CH, NB, KB, nb + 1>(nxt, cur, cur_base, cur_live, nxt_base, nxt_live,
+                                                lb, s1, s2);
+    }
+}
+
+// Input-major path with grouped inputs: layout [frame][input][t] with
+// M = 16 G CH.  A segment of G lanes owns a group of G consecutive inputs; lane
+// j reads the 16-byte chunks j, j+G, ..., j+(CH-1)G of each of them (one warp
+// instruction reads 32/G whole 128-byte lines when G = 8), every offset inside
+// the group a load immediate.  Each lane keeps S1, S2 for all G inputs of the
+// group; a reduce-scatter over the segment's lanes (G-1 shuffle pairs) leaves
+// input u's totals in lane u, so all lanes form an input term at once.  The
+// segment's groups are (k nseg + seg) G .. + G-1 for k = 0, 1, ...; a frame is
+// NG = ceil(N / team) groups per segment (team = threads per frame, which the
+// plan sets to about one per 2 KB of frame).  Inputs longer than 512 samples are
+// read as SPLIT sub-inputs of 512 (measured: the 512-sample shape streams at
+// 6.2 TB/s, the 1024-sample one at 4.4).  The group streams through two
+// register batches of KB chunks (NB batches per group, NB even, so every group
+// starts in batch A); with PF the next group's bytes are requested into L2 while
+// this one is read.
+template <int G, int CH, bool PF, int SPLIT = 1>
+__device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_begin,
+                                                   int64_t f_end, uint32_t lb, TeamSmem &ts,
+                                                   int &parity)
+{
+    // SPLIT > 1: each input is read as SPLIT consecutive sub-inputs of M / SPLIT
+    // bytes (the layout is the same bytes), whose sums are added after the
+    // reduce-scatter; M here is the sub-input length
+    static_assert(SPLIT >= 1 && G % SPLIT == 0, "sub-inputs of one input share a group");
+    constexpr int M = 16 * G * CH;
+    constexpr int NB = (G * CH / 8) < 2 ? 2 : G * CH / 8;  // batches per group
+    constexpr int KB = G * CH / NB;                       // chunks per batch
+    static_assert(KB * NB == G * CH && NB % 2 == 0, "batch shape");
+    const int team_log2 = it.team_log2;
+    const int team = 1 << team_log2;
+    const int T = kThreads >> team_log2;
+    const int team_idx = threadIdx.x >> team_log2;
+    const int lit = threadIdx.x & (team - 1);
+    const int nseg = team / G;
+    const int seg = lit / G, j = lit % G;
+    const int N = it.N;
+    const int NS = N * SPLIT;  // sub-inputs per frame
+    const int NG = (NS + team - 1) / team;
+    const int64_t fbytes = (int64_t)M * NS;
+    const int64_t kmax = (f_end - f_begin + T - 1) / T;
+
+    // sub-inputs of group (frame f, k) that this segment may read: 0..G
+    auto live_of = [&](int64_t f, int k) -> int {
+        const int i0 = (k * nseg + seg) * G;
+        const int r = NS - i0;
+        return (f < f_end) ? (r < 0 ? 0 : (r > G ? G : r)) : 0;
+    };
+    auto base_of = [&](int64_t f, int k) -> const uint8_t * {
+        return it.in + f * fbytes + (int64_t)((k * nseg + seg) * G) * M + j * 16;
+    };
+    uint4 A[KB], B[KB];
+    int64_t frame = f_begin + team_idx;
+    const uint8_t *cur_base = base_of(frame, 0);
+    int cur_live = live_of(frame, 0);
+    load_group_batch<M, G, CH, KB, 0>(A, cur_base, cur_live);
+    for (int64_t kk = 0; kk < kmax; ++kk) {
+        const bool fvalid = frame < f_end;
+        int64_t q = 0, e = 0;
+        int32_t cnt = 0;
+        for (int k = 0; k < NG; ++k) {
+            // the group after this one: next k, else the team's next frame
+            const int64_t nf = (k + 1 < NG) ? frame : frame + T;
+            const int nk = (k + 1 < NG) ? k + 1 : 0;
+            const uint8_t *nxt_base = base_of(nf, nk);
+            const int nxt_live = live_of(nf, nk);
+            if (PF && nxt_live > 0 && j == 0)
+                prefetch_l2(nxt_base, (uint32_t)(nxt_live * M));
+            int32_t s1[G], s2[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                s1[u] = 0;
+                s2[u] = 0;
+            }
+            group_batches<M, G, CH, NB, KB, 0>(A, B, cur_base, cur_live, nxt_base, nxt_live, lb,
+                                               s1, s2);
+            // reduce-scatter: lane j ends with input j's sums in s1[0], s2[0]
+#pragma unroll
+            for (int o = G / 2; o >= 1; o >>= 1) {
+                const bool up = (j & o) != 0;
+#pragma unroll
+                for (int t = 0; t < o; ++t) {
+                    const int32_t send1 = up ? s1[t] : s1[t + o];
+                    const int32_t send2 = up ? s2[t] : s2[t + o];
+                    const int32_t keep1 = up ? s1[t + o] : s1[t];
+                    const int32_t keep2 = up ? s2[t + o] : s2[t];
+                    s1[t] = keep1 + __shfl_xor_sync(0xFFFFFFFFu, send1, o);
+                    s2[t] = keep2 + __shfl_xor_sync(0xFFFFFFFFu, send2, o);
+                }
+            }
+            // an input's sub-inputs sit in lanes j .. j + SPLIT - 1 (j % SPLIT == 0)
+#pragma unroll
+            for (int o = 1; o < SPLIT; o <<= 1) {
+                s1[0] += __shfl_xor_sync(0xFFFFFFFFu, s1[0], o);
+                s2[0] += __shfl_xor_sync(0xFFFFFFFFu, s2[0], o);
+            }
+            if (j < cur_live && j % SPLIT == 0) {
+                const int i = ((k * nseg + seg) * G + j) / SPLIT;
+                float r = 0.0f;
+                int64_t qi = 0;
+                const bool has = SK_EPILOGUE_ALU
+                                     ? input_term_alu(s1[0], s2[0], M * SPLIT, r, qi)
+                                     : input_term(s1[0], s2[0], M * SPLIT, r, qi);
+                if (has) {
+                    q += qi;
+                    cnt += 1;
+                }
+                const int64_t o = frame * N + i;
+                if (it.s1) {
+                    it.s1[o] = s1[0];
+                    it.s2[o] = s2[0];
+                }
+                if (it.sk_in) {
+                    it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
+                    if (it.mask_in)
+                        it.mask_in[o] =
+                            has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+                }
+            }
+            cur_base = nxt_base;
+            cur_live = nxt_live;
+        }
+        team_sum(q, cnt, e, team_log2, team_idx, parity, ts, false);
+        if (fvalid && lit == 0) {
+            uint8_t m = 1;
+            if (cnt > 0)
+                m = (q > it.t_hi[cnt] || q < it.t_lo[cnt]) ? 1 : 0;
+            if (it.sk) {
+                float skv = __int_as_float(0x7FC00000);
+                if (cnt > 0)
+                    skv = __fmul_rn(__fmul_rn(__ll2float_rn(q), 0x1p-32f), it.c_tab[cnt]);
+                it.sk[frame] = skv;
+            }
+            if (it.mask)
+                it.mask[frame] = m;
+            if (it.q)
+                it.q[frame] = q;
+            if (it.neff)
+                it.neff[frame] = cnt;
+        }
+        parity ^= 1;
+        frame += T;
+    }
+}
+
+}  // namespace sk
