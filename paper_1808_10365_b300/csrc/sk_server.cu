@@ -136,6 +136,7 @@ struct sk_server_s {
     size_t lat_next = 0;
     sk_status_t fault = SK_OK;
     std::string fault_msg;
+    int64_t inject_at = 0;  // SK_SERVER_INJECT_FAULT: the launch that fails on the host
     bool trace = false;
     double tr_n = 0, tr_frames = 0, tr_bytes = 0, tr_host_issue = 0, tr_host_total = 0,
            tr_copy = 0, tr_kernel = 0, tr_copy_to_kernel_end = 0;
@@ -160,8 +161,15 @@ static void set_fault(sk_server_s *s, sk_status_t st, const char *msg)
 }
 
 // Issue one batch (the lock is NOT held; `frames` were taken off the fifo).
-static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &frames)
+static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &frames,
+                        int64_t launch_no)
 {
+    if (s->inject_at > 0 && launch_no == s->inject_at) {
+        // host-side fault injection for tests: this launch fails before any CUDA call
+        std::lock_guard<std::mutex> g(s->mu);
+        set_fault(s, SK_ERR_CUDA, "injected launch failure (SK_SERVER_INJECT_FAULT)");
+        return;
+    }
     const int n = (int)frames.size();
     std::vector<Item> items(n);
     float *d_sk = (float *)L.d_res;
@@ -266,6 +274,21 @@ static void launcher_main(sk_server_s *s)
         const bool ready = !s->fifo.empty() && s->fifo.front().ready;
         if (s->stop)
             return;
+        if (s->fault != SK_OK && !s->fifo.empty()) {
+            // nothing launches after a fault: the queued frames' tickets complete
+            // with the fault status instead of waiting for ever
+            for (const Frame &f : s->fifo) {
+                auto t = s->tickets.find(f.ticket);
+                if (t != s->tickets.end()) {
+                    t->second.done = true;
+                    t->second.status = s->fault;
+                }
+                f.stream->outstanding -= 1;
+            }
+            s->fifo.clear();
+            s->cv_done.notify_all();
+            continue;
+        }
         if (slot < 0 || !ready || s->fault != SK_OK) {
             s->cv_work.wait(lk);
             continue;
@@ -299,9 +322,10 @@ static void launcher_main(sk_server_s *s)
             L.streams.push_back(f.stream);
         }
         s->launches += 1;
+        const int64_t launch_no = s->launches;
         lk.unlock();
         L.t_issue = Clock::now();
-        issue_batch(s, L, batch);
+        issue_batch(s, L, batch, launch_no);
         L.t_issued = Clock::now();
         lk.lock();
         s->flight.push_back(slot);
@@ -412,6 +436,8 @@ extern "C" sk_status_t sk_server_create(int device, size_t hbm_budget_bytes, sk_
         if (k >= 1 && k <= kLaunchSlots)
             s->nslots = k;
     }
+    if (const char *v = getenv("SK_SERVER_INJECT_FAULT"))
+        s->inject_at = atoll(v);
     sk_status_t st = SK_OK;
     {
         DeviceGuard dg(device);

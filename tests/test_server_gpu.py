@@ -384,3 +384,52 @@ def test_close_and_destroy_with_work_outstanding():
     sk.sk_flag(plan, d, 2, None, mask)
     torch.cuda.synchronize()
     sk.sk_plan_destroy(plan)
+
+
+def test_injected_launch_failure_fails_tickets_and_device_stays_usable(monkeypatch):
+    """Failure detection with the fault made on the host: SK_SERVER_INJECT_FAULT=3 makes
+    the third launch fail before any CUDA call.  The frames launched before it complete;
+    its frame, the frames queued behind it and later submits report SK_ERR_CUDA instead
+    of waiting; the server shuts down; a fresh plan then runs on the same device."""
+    _need_gpu()
+    N, M, T = 256, 256, 12
+    ds, x = _stream_data(33, N, M, T)
+    monkeypatch.setenv("SK_SERVER_INJECT_FAULT", "3")
+    server = sk.sk_server_create(0, 1 << 30)
+    monkeypatch.delenv("SK_SERVER_INJECT_FAULT")
+    ok, failed = 0, 0
+    try:
+        sid = sk.sk_stream_open(server, N, M, ring_frames=T, flags=sk.SK_RUNNING_OFFSET)
+        tickets = []
+        for f in range(T):
+            try:
+                tickets.append(sk.sk_stream_submit(server, sid, x[f], f))
+            except sk.SkError as e:
+                assert e.status == sk.SK_ERR_CUDA
+                failed += 1
+        for t in tickets:
+            try:
+                sk.sk_ticket_wait(server, t, 5_000_000)
+                ok += 1
+            except sk.SkError as e:
+                assert e.status == sk.SK_ERR_CUDA, e
+                assert "injected" in e.message
+                failed += 1
+        assert ok == 2 and failed == T - 2
+        with pytest.raises(sk.SkError) as e:
+            sk.sk_stream_submit(server, sid, x[0], T)
+        assert e.value.status == sk.SK_ERR_CUDA
+    finally:
+        sk.sk_server_destroy(server)
+    # the device still runs a fresh plan
+    want = oracle.flag(x[:4], M, N)
+    plan = sk.sk_plan_create(N, M)
+    try:
+        d = torch.from_numpy(x[:4].reshape(-1)).to("cuda")
+        mask = torch.empty(4, dtype=torch.uint8, device="cuda")
+        skv = torch.empty(4, dtype=torch.float32, device="cuda")
+        sk.sk_flag(plan, d, 4, skv, mask)
+        torch.cuda.synchronize()
+    finally:
+        sk.sk_plan_destroy(plan)
+    assert np.array_equal(mask.cpu().numpy(), want["mask"])
