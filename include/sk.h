@@ -303,6 +303,21 @@ typedef struct {
 } sk_server_stats_t;
 sk_status_t sk_server_stats(sk_server_t server, sk_server_stats_t *out);
 
+/* Counters of one open stream: frames retired, of which flagged; submits
+ * refused with SK_ERR_BUSY; frames outstanding; submit-to-result latency over
+ * its last 16384 frames.  INVALID_ARG for an unknown or closed stream. */
+typedef struct {
+    int64_t frames_done;
+    int64_t frames_flagged;
+    int64_t rejected;
+    int32_t outstanding;
+    int32_t pad;
+    double latency_p50_us;
+    double latency_p99_us;
+} sk_stream_stats_t;
+sk_status_t sk_stream_stats(sk_server_t server, sk_stream_id stream,
+                            sk_stream_stats_t *out);
+
 /*
  * Load generator for a server (measurement, not part of the method): replays
  * pools of frames into open streams from `threads` submitter threads.  Stream

@@ -47,7 +47,8 @@ EXPORTED = [
     "sk_batch_create", "sk_batch_run", "sk_batch_destroy", "sk_server_create",
     "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_ticket_wait",
     "sk_stream_drain", "sk_stream_get_state", "sk_stream_set_state", "sk_stream_close",
-    "sk_server_stats", "sk_server_replay", "sk_digitisation_offset", "sk_last_error",
+    "sk_server_stats", "sk_stream_stats", "sk_server_replay", "sk_digitisation_offset",
+    "sk_last_error",
 ]
 
 
@@ -85,6 +86,13 @@ class sk_replay_result_t(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("latency_p50_us", ctypes.c_double),
                 ("latency_p99_us", ctypes.c_double), ("submit_p50_us", ctypes.c_double),
                 ("submit_p99_us", ctypes.c_double)]
+
+
+class sk_stream_stats_t(ctypes.Structure):
+    _fields_ = [("frames_done", ctypes.c_int64), ("frames_flagged", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("outstanding", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("latency_p50_us", ctypes.c_double),
+                ("latency_p99_us", ctypes.c_double)]
 
 
 class sk_server_stats_t(ctypes.Structure):
@@ -132,6 +140,7 @@ def library():
         "sk_stream_set_state": [P, I32, P, ctypes.c_size_t],
         "sk_stream_close": [P, I32],
         "sk_server_stats": [P, ctypes.POINTER(sk_server_stats_t)],
+        "sk_stream_stats": [P, I32, ctypes.POINTER(sk_stream_stats_t)],
         "sk_server_replay": [P, ctypes.POINTER(sk_replay_t), ctypes.POINTER(sk_replay_result_t)],
         "sk_digitisation_offset": [ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
     }
@@ -413,6 +422,12 @@ def sk_server_stats(server) -> dict:
     s = sk_server_stats_t()
     _check(library().sk_server_stats(server, ctypes.byref(s)))
     return {k: getattr(s, k) for k, _ in sk_server_stats_t._fields_}
+
+
+def sk_stream_stats(server, stream_id) -> dict:
+    s = sk_stream_stats_t()
+    _check(library().sk_stream_stats(server, int(stream_id), ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in sk_stream_stats_t._fields_ if k != "pad"}
 
 
 def sk_server_replay(server, stream_ids, pools, frames_per_stream, cadence_s, jitter_mean_s,

@@ -61,7 +61,13 @@ struct StreamRec {
     size_t small = 0;            // state + tables bytes
     int32_t outstanding = 0;     // submitted, not yet retired
     bool closing = false;
+    // per-stream counters (sk_stream_stats)
+    int64_t frames_done = 0, frames_flagged = 0, rejected = 0;
+    std::vector<double> lat_us;  // last kStreamLatKeep submit-to-result times
+    size_t lat_next = 0;
 };
+
+static constexpr size_t kStreamLatKeep = 1 << 14;
 
 struct Frame {
     StreamRec *stream;
@@ -360,11 +366,19 @@ static void completer_main(sk_server_s *s)
                 t->second.status = s->fault;
                 t->second.sk = h_sk[k];
                 t->second.mask = h_mask[k];
-                record_latency(s, std::chrono::duration<double, std::micro>(
-                                      now - t->second.t_submit).count());
+                const double us =
+                    std::chrono::duration<double, std::micro>(now - t->second.t_submit).count();
+                record_latency(s, us);
+                StreamRec *r = L.streams[k];
+                if (r->lat_us.size() < kStreamLatKeep)
+                    r->lat_us.push_back(us);
+                else
+                    r->lat_us[r->lat_next++ % kStreamLatKeep] = us;
             }
             s->frames_done += 1;
             s->frames_flagged += h_mask[k] ? 1 : 0;
+            L.streams[k]->frames_done += 1;
+            L.streams[k]->frames_flagged += h_mask[k] ? 1 : 0;
             L.streams[k]->outstanding -= 1;
         }
         s->tail = std::max(s->tail, L.end);
@@ -632,6 +646,7 @@ extern "C" sk_status_t sk_stream_submit(sk_server_t s, sk_stream_id id, const ui
         return set_error(SK_ERR_CLOSED, "sk_stream_submit: stream %d closing", id);
     if (r->outstanding >= r->ring_frames) {
         s->rejected += 1;
+        r->rejected += 1;
         return set_error(SK_ERR_BUSY, "sk_stream_submit: stream %d has %d frames outstanding",
                          id, r->outstanding);
     }
@@ -641,6 +656,7 @@ extern "C" sk_status_t sk_stream_submit(sk_server_t s, sk_stream_id id, const ui
         off = (off / s->ring_cap + 1) * s->ring_cap;
     if (off + size - s->tail > s->ring_cap) {
         s->rejected += 1;
+        r->rejected += 1;
         return set_error(SK_ERR_BUSY, "sk_stream_submit: frame ring full");
     }
     s->head = off + size;
@@ -815,6 +831,32 @@ extern "C" sk_status_t sk_server_stats(sk_server_t s, sk_server_stats_t *out)
     }
     out->latency_p50_us = 0.0;
     out->latency_p99_us = 0.0;
+    if (!lat.empty()) {
+        std::sort(lat.begin(), lat.end());
+        out->latency_p50_us = lat[(size_t)(0.50 * (lat.size() - 1))];
+        out->latency_p99_us = lat[(size_t)(0.99 * (lat.size() - 1))];
+    }
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_stream_stats(sk_server_t s, sk_stream_id id, sk_stream_stats_t *out)
+{
+    if (!s || !out)
+        return set_error(SK_ERR_INVALID_ARG, "sk_stream_stats: null argument");
+    std::vector<double> lat;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        auto it = s->streams.find(id);
+        if (it == s->streams.end())
+            return set_error(SK_ERR_INVALID_ARG, "sk_stream_stats: unknown stream %d", id);
+        const StreamRec *r = it->second.get();
+        memset(out, 0, sizeof *out);
+        out->frames_done = r->frames_done;
+        out->frames_flagged = r->frames_flagged;
+        out->rejected = r->rejected;
+        out->outstanding = r->outstanding;
+        lat = r->lat_us;
+    }
     if (!lat.empty()) {
         std::sort(lat.begin(), lat.end());
         out->latency_p50_us = lat[(size_t)(0.50 * (lat.size() - 1))];

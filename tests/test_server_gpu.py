@@ -433,3 +433,38 @@ def test_injected_launch_failure_fails_tickets_and_device_stays_usable(monkeypat
     finally:
         sk.sk_plan_destroy(plan)
     assert np.array_equal(mask.cpu().numpy(), want["mask"])
+
+
+def test_stream_stats_count_frames_flags_and_rejections():
+    """sk_stream_stats: frames retired and flagged per stream, BUSY refusals, and
+    submit-to-result percentiles; a second stream's counters stay separate."""
+    _need_gpu()
+    N, M, T = 256, 256, 24
+    ds, x = _stream_data(7, N, M, T)
+    server = sk.sk_server_create(0, 1 << 30)
+    try:
+        a = sk.sk_stream_open(server, N, M, ring_frames=1, flags=sk.SK_RUNNING_OFFSET)
+        b = sk.sk_stream_open(server, N, M, ring_frames=8)
+        masks, busy, pending = [], 0, []
+        for f in range(T):
+            while True:
+                try:
+                    pending.append(sk.sk_stream_submit(server, a, x[f], f))
+                    break
+                except sk.SkError as e:
+                    assert e.status == sk.SK_ERR_BUSY
+                    busy += 1
+                    masks.append(sk.sk_ticket_wait(server, pending.pop(0))[1])
+        masks += [sk.sk_ticket_wait(server, t)[1] for t in pending]
+        for t in [sk.sk_stream_submit(server, b, x[f], f) for f in range(3)]:
+            sk.sk_ticket_wait(server, t)
+        sa, sb = sk.sk_stream_stats(server, a), sk.sk_stream_stats(server, b)
+        assert sa["frames_done"] == T and sa["frames_flagged"] == sum(masks)
+        assert sa["rejected"] == busy and sa["outstanding"] == 0
+        assert 0 < sa["latency_p50_us"] <= sa["latency_p99_us"]
+        assert sb["frames_done"] == 3 and sb["rejected"] == 0
+        sk.sk_stream_close(server, b)
+        with pytest.raises(sk.SkError):
+            sk.sk_stream_stats(server, b)
+    finally:
+        sk.sk_server_destroy(server)
