@@ -484,7 +484,7 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
            "latency_p50_us": r["latency_p50_us"], "latency_p99_us": r["latency_p99_us"],
            "launches": r["launches"], "frames_per_launch": r["frames"] / max(1, r["launches"]),
            "submit_p50_us": r["submit_p50_us"], "busy_retries": r["busy_retries"],
-           "driver": f"sk_server_replay, {threads} submitter threads"}
+           "load_generator": f"sk_server_replay, {threads} submitter threads"}
     if paced and not running_mu:
         # plain path on the same frames: one synchronous sk_flag_host per frame
         lat = []

@@ -49,7 +49,7 @@ extern "C" {
 typedef enum {
     SK_OK = 0,
     SK_ERR_INVALID_ARG = 1, /* null pointer, size out of range, misaligned */
-    SK_ERR_UNSUPPORTED = 2, /* valid request this build does not serve     */
+    SK_ERR_UNSUPPORTED = 2, /* valid request the library does not serve    */
     SK_ERR_OOM = 3,         /* device or host allocation failed            */
     SK_ERR_CUDA = 4,        /* a CUDA runtime call failed                  */
     SK_ERR_BUSY = 5,        /* admission refused: ring full or over budget */
