@@ -384,3 +384,30 @@ def test_pearson3_false_alarm_balance():
     up_p, lo_p = (sk > phi).mean(), (sk < plo).mean()
     assert up_s > 1.3 * p and lo_s < 0.5 * p                 # symmetric: unbalanced
     assert 0.7 * p < up_p < 1.4 * p and 0.7 * p < lo_p < 1.4 * p
+
+
+def test_pearson3_matches_exact_gamma_quantile():
+    """The Pearson III thresholds against the exact quantiles of the same shifted gamma
+    (shape m/25, scale 10/m, mean 1+delta) from scipy: the Wilson-Hilferty form the
+    oracle uses is within 1 % of the distance from the centre at m = M N_eff >= 256,
+    and its error shrinks as m grows."""
+    from scipy import stats
+
+    delta = -0.02
+    for a in (2.0, 3.0):
+        errs = []
+        for M, ne in ((256, 1), (128, 8), (256, 16), (256, 64)):
+            m = M * ne
+            t_lo, t_hi = oracle.thresholds(M, ne, a, delta, pearson3=True)
+            f = (M + 1) / ((M - 1) * ne * 2.0 ** 32)
+            k, scale, loc = m / 25.0, 10.0 / m, 1.0 + delta - 0.4
+            for t, p in ((t_hi[ne], stats.norm.cdf(a)), (t_lo[ne], stats.norm.cdf(-a))):
+                exact = loc + stats.gamma.ppf(p, k, scale=scale)
+                err = abs(t * f - exact) / abs(exact - (1.0 + delta))
+                assert err < 0.01, (a, M, ne, err)
+                errs.append((m, err))
+        by_m = {}
+        for m, e in errs:
+            by_m[m] = max(by_m.get(m, 0.0), e)
+        ms = sorted(by_m)
+        assert all(by_m[x] >= by_m[y] for x, y in zip(ms, ms[1:]))
