@@ -157,3 +157,20 @@ def test_running_mu_sees_a_power_step():
     assert 0.6 * (want - 1.0) < step_rm < 1.2 * (want - 1.0)
     assert abs(step_pf) < 0.04
     assert rm["mask"][-1] == 1 and pf["mask"][-1] == 0
+
+
+def test_repeated_frame_is_a_fixed_point_of_the_state():
+    """One frame served again and again: P = 2^6 S1 is the leaky integrator's fixed
+    point (P - P/64 + S1 = P exactly in integers), so the state never moves and every
+    frame gets the first frame's SK, E and mask, in both normalisations."""
+    M, N, T = 256, 64, 8
+    x1 = synth.Dataset(n_frames=1, M=M, N=N, seed=5).generate_cpu()
+    x = np.repeat(x1, T, axis=0)
+    e = dg.offset_table(M)
+    for rm in (False, True):
+        r = served.served_flags(x, M, N, e, running_mu=rm)
+        S1 = r["S1"][0] if np.ndim(r["S1"]) == 2 else r["S1"]
+        assert np.array_equal(np.asarray(r["P"], dtype=np.int64),
+                              np.asarray(S1, dtype=np.int64) << 6)
+        assert np.all(r["sk"].view(np.uint32) == r["sk"][0].view(np.uint32))
+        assert np.all(r["mask"] == r["mask"][0]) and np.all(r["E"] == r["E"][0])
