@@ -3,7 +3,7 @@
 A plain, slow CPU statement of the multi-receiver spectral-kurtosis RFI
 detector of Taylor et al., "Spectral Kurtosis Based RFI Mitigation for CHIME"
 (arXiv:1808.10365).  Only `tests/`, `__graft_entry__.smoke()` and the CPU
-baseline leg of `bench.py` may import it.  It shares no code with the CUDA
+baseline and reference-arm legs of `bench.py` may import it.  It shares no code with the CUDA
 library and never calls it; its inputs come from the `synth` generator or
 from the tests themselves.
 
@@ -18,16 +18,21 @@ Pieces and the passages they follow (every function cites its own):
                          point sum) so Q and masks compare bit for bit
   * `thresholds`, `mask` Sec. 3.2: flag outside mean +- a*sqrt(var), with
                          var = 4/(n N) (Eq. final moments) and the mean shifted
-                         by the digitisation offset (App. B)
+                         by the digitisation offset (App. B); `pearson3`: the
+                         false-alarm (shifted gamma) thresholds for small n N
+  * `flag_inputs`        Eq. (originalSK) per input (independent estimates)
   * `digitisation`       App. B: mean offset of SK for clipped 4-bit data
-  * `served_flags`       running per-input power state feeding the App. B offset
+  * `served_flags`       running per-input power state feeding the App. B offset,
+                         and the running-mu form of Eq. (avgSK)
   * `brute`              exact rational arithmetic on tiny inputs
 
 Parity status: S1, S2, Q, N_eff, SK and the static mask are pinned (closed
-forms, brute force, moments; tests/test_oracle_pins.py).  The integer
-threshold recipe and the digitisation-offset table are pinned only by
-Monte-Carlo false-alarm rates and by limits of the model (the paper prints no
-threshold numbers): parity for those is "partial" in the strict sense.
+forms, brute force, moments; tests/test_oracle_pins.py).  The Pearson III
+thresholds are pinned against exact gamma quantiles, the served state by its
+fixed point and a power step.  The integer threshold recipe and the
+digitisation-offset table are pinned only by Monte-Carlo false-alarm rates and
+by limits of the model (the paper prints no threshold numbers): parity for
+those is "partial" in the strict sense.
 """
 
 from __future__ import annotations
