@@ -32,6 +32,7 @@
  *   SK_SERVER_ZEROCOPY=0 server: upload each batch instead of zero-copy reads
  *   SK_SERVER_INFLIGHT   server: launches in flight (1..8, default 2)
  *   SK_SERVER_TRACE=1    server: per-launch stage times on destroy
+ *   SK_SERVER_SPLIT=0    server: no per-frame row split for small batches
  *   SK_SERVER_INJECT_FAULT=k  server (tests): launch k fails on the host, before
  *                        any CUDA call, as a failed launch would; its tickets and
  *                        the queued ones complete with SK_ERR_CUDA

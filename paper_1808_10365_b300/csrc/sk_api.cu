@@ -50,6 +50,9 @@ int sm_count(int device)
 //   0  one item, a contiguous frame range per CTA (sk_compute, sk_flag)
 //   1  chunk list of frame ranges (batched launch)
 //   2  chunk list of one-frame items, teams on different items (served batch)
+//   3  chunk list of one-frame items, one item per CTA at a time, its rows split
+//      over the CTA's teams (served batch smaller than the GPU: more loads in
+//      flight per frame)
 template <int R, int S, bool SRV, int NC, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_fused_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
@@ -80,6 +83,65 @@ __global__ void __launch_bounds__(kThreads, 1)
                 run_fast<R, S, SRV, NC>(it, ch.f_begin, ch.f_end, lb, ts, parity);
             else
                 run_general<SRV>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+        } else if (MODE == 3) {
+            const Item it = items[ch.item];
+            const int tl = it.team_log2;
+            const int team_idx = threadIdx.x >> tl;
+            const int lit = threadIdx.x & ((1 << tl) - 1);
+            const int col0 = lit * kVec;
+            if (it.fast == 1 && it.M % (R * S) == 0 && (NC == 0 || it.N == NC)) {
+                // teams 0..P-1 take equal shares of the ring iterations; teams 1..P-1
+                // leave their partial sums in the dynamic shared memory beside the
+                // table, and team 0 adds them and runs the epilogue
+                const int nit = it.M / (R * S);
+                const int T = kThreads >> tl;
+                const int P = T < nit ? T : nit;
+                int32_t s1[kVec], s2[kVec];
+#pragma unroll
+                for (int k = 0; k < kVec; ++k) {
+                    s1[k] = 0;
+                    s2[k] = 0;
+                }
+                if (team_idx < P && col0 < it.N) {
+                    const int i0 = nit * team_idx / P, i1 = nit * (team_idx + 1) / P;
+                    run_rows<R, S, NC>(it, 0, i0 * S, i1 * S, col0, lb, s1, s2);
+                }
+                if (P > 1) {
+                    // the larger free piece of the dynamic shared memory: below or
+                    // above the 64 KiB-aligned table, at least 32 KiB either way
+                    const uint32_t raw = (uint32_t)__cvta_generic_to_shared(dyn_smem);
+                    const uint32_t below = (lb & ~0xFFFFu) - raw;
+                    int32_t *part = (int32_t *)(below >= kLutBytes / 2
+                                                    ? dyn_smem
+                                                    : dyn_smem + below + kLutBytes);
+                    const int team = 1 << tl;
+                    int32_t *mine = part + ((team_idx - 1) * team + lit) * (2 * kVec);
+                    if (team_idx >= 1 && team_idx < P && col0 < it.N) {
+#pragma unroll
+                        for (int k = 0; k < kVec; ++k) {
+                            mine[k] = s1[k];
+                            mine[kVec + k] = s2[k];
+                        }
+                    }
+                    __syncthreads();
+                    if (team_idx == 0 && col0 < it.N) {
+                        for (int t = 1; t < P; ++t) {
+                            const int32_t *o = part + ((t - 1) * team + lit) * (2 * kVec);
+#pragma unroll
+                            for (int k = 0; k < kVec; ++k) {
+                                s1[k] += o[k];
+                                s2[k] += o[kVec + k];
+                            }
+                        }
+                    }
+                }
+                if (team_idx == 0) {
+                    frame_epilogue<SRV>(it, 0, true, col0, lit, 0, parity, s1, s2, ts);
+                    parity ^= 1;
+                }
+            } else if (team_idx == 0) {
+                run_general<SRV>(it, 0, 1, lb, ts, parity, true);  // toggles parity
+            }
         } else {
             // one frame per item, teams on different items; every item of the
             // chunk has the same shape, so all teams take the same path the same
@@ -170,6 +232,8 @@ static const KernelFn kBatched[2][3] = {
      sk_fused_kernel<8, 2, false, 2048, 1>}};
 static const KernelFn kServed[2] = {sk_fused_kernel<16, 2, true, 0, 2>,
                                     sk_fused_kernel<8, 2, true, 0, 2>};
+static const KernelFn kServedSplit[2] = {sk_fused_kernel<16, 2, true, 0, 3>,
+                                         sk_fused_kernel<8, 2, true, 0, 3>};
 // input-major: per-input path G = 2, 4, 8; grouped path G = 8 for M = 128,
 // 256, 512 (CH = 1, 2, 4) and 1024, 2048, 4096 (CH = 4 on SPLIT = 2, 4, 8
 // sub-inputs), without and with the L2 prefetch
@@ -264,6 +328,7 @@ sk_status_t ensure_kernel_attrs(int device)
         fns.push_back(f);
     for (int t = 0; t < 2; ++t) {
         fns.push_back(kServed[t]);
+        fns.push_back(kServedSplit[t]);
         for (int j = 0; j < 3; ++j) {
             fns.push_back(kSingle[t][j]);
             fns.push_back(kBatched[t][j]);
@@ -332,7 +397,7 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
         return s;
     Item dummy;
     memset(&dummy, 0, sizeof dummy);
-    KernelFn fn = served ? kServed[tile]
+    KernelFn fn = served ? (nclass == 1 ? kServedSplit[tile] : kServed[tile])
                          : (nclass < 3 ? kBatched[tile][nclass] : kImajorBatched[nclass - 3]);
     fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy);
     cudaError_t e = cudaGetLastError();

@@ -127,6 +127,29 @@ int build_item_schedule(std::vector<Item> &items, int grid_max, std::vector<Chun
     return grid;
 }
 
+int build_split_schedule(int n_items, int grid_max, std::vector<Chunk> &chunks,
+                         std::vector<int32_t> &cta)
+{
+    const int grid = std::max(1, std::min(grid_max, n_items));
+    std::vector<std::vector<Chunk>> per(grid);
+    for (int k = 0; k < n_items; ++k) {
+        Chunk ch;
+        ch.item = k;
+        ch.kind = 1;
+        ch.f_begin = k;
+        ch.f_end = k + 1;
+        per[k % grid].push_back(ch);
+    }
+    chunks.clear();
+    cta.assign(grid + 1, 0);
+    for (int c = 0; c < grid; ++c) {
+        cta[c] = (int32_t)chunks.size();
+        chunks.insert(chunks.end(), per[c].begin(), per[c].end());
+    }
+    cta[grid] = (int32_t)chunks.size();
+    return grid;
+}
+
 }  // namespace sk
 
 using namespace sk;

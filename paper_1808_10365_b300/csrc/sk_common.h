@@ -23,7 +23,9 @@ sk_status_t cuda_error(cudaError_t e, const char *what);
 sk_status_t launch_single(const Item &it, int rows, bool served, int device, cudaStream_t st,
                           int grid_cap = 0);
 // tile: 0 = 16 rows x 2 batches (M % 32 == 0), 1 = 8 x 2 (M % 16 == 0);
-// nclass (batched launches): the kernel for items of batch_class nclass
+// nclass: batched launches, the kernel for items of batch_class nclass; served
+// launches, 0 = teams on different frames, 1 = one frame per CTA with its rows
+// split over the CTA's teams
 sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
                             const int32_t *d_cta_chunks, int grid, int tile, bool served,
                             int device, cudaStream_t st, int nclass = 0);
@@ -44,6 +46,11 @@ int sm_count(int device);
 // kernel's team size.
 void build_schedule(const std::vector<Item> &items, const std::vector<int32_t> &sel, int grid,
                     std::vector<Chunk> &chunks, std::vector<int32_t> &cta, bool imajor = false);
+
+// One chunk per one-frame item, round-robin over at most grid_max CTAs (the
+// served launch that splits each frame's rows over a CTA); returns the grid.
+int build_split_schedule(int n_items, int grid_max, std::vector<Chunk> &chunks,
+                         std::vector<int32_t> &cta);
 
 // Schedule for a batch of one-frame items; reorders items, returns the grid.
 int build_item_schedule(std::vector<Item> &items, int grid_max, std::vector<Chunk> &chunks,

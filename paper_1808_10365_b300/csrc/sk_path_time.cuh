@@ -121,4 +121,49 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
     }
 }
 
+// Rows [b0 R, b1 R) of one frame for this thread's 8 columns, added into exact
+// s1, s2 (b1 - b0 a multiple of S).  The same ring of S register batches of R
+// rows as run_fast, without the frame epilogue: a frame whose rows are shared
+// by several teams sums their partial S1, S2 before its epilogue.
+template <int R, int S, int NC>
+__device__ __forceinline__ void run_rows(const Item &it, int64_t frame, int b0, int b1,
+                                         int col0, uint32_t lb, int32_t (&s1)[kVec],
+                                         int32_t (&s2)[kVec])
+{
+    static_assert((R * S) % kFlushRows == 0, "flush cadence");
+    const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
+    const uint8_t *fp = it.in + frame * (int64_t)it.M * N + col0;
+    uint2 buf[S][R];
+    uint32_t acc[kVec];
+#pragma unroll
+    for (int k = 0; k < kVec; ++k)
+        acc[k] = 0u;
+    auto load = [&](uint2 (&b)[R], int batch) {
+        const uint8_t *p = fp + (int64_t)batch * R * N;
+        if constexpr (NC > 0) {
+            load_rows_imm<NC>(b, p, std::make_integer_sequence<int, R>{});
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                b[r] = ldg_stream(p + (int64_t)r * N);
+        }
+    };
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+        if (b0 + j < b1)
+            load(buf[j], b0 + j);
+    for (int jb = b0; jb < b1; jb += S) {
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+#pragma unroll
+            for (int r = 0; r < R; r += 2)
+                accum_pair(buf[j][r], buf[j][r + 1], lb, acc);
+            if (((j + 1) * R) % kFlushRows == 0)
+                flush(acc, s1, s2);
+            if (jb + S + j < b1)
+                load(buf[j], jb + S + j);
+        }
+    }
+}
+
 }  // namespace sk

@@ -143,6 +143,7 @@ struct sk_server_s {
     sk_status_t fault = SK_OK;
     std::string fault_msg;
     int64_t inject_at = 0;  // SK_SERVER_INJECT_FAULT: the launch that fails on the host
+    bool split = true;      // SK_SERVER_SPLIT: small batches split each frame over a CTA
     bool trace = false;
     double tr_n = 0, tr_frames = 0, tr_bytes = 0, tr_host_issue = 0, tr_host_total = 0,
            tr_copy = 0, tr_kernel = 0, tr_copy_to_kernel_end = 0;
@@ -200,7 +201,18 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
     std::vector<Chunk> chunks;
     std::vector<int32_t> cta;
     std::vector<int32_t> perm;
-    const int grid = build_item_schedule(items, s->sms, chunks, cta, perm);
+    // a batch smaller than the GPU gives each frame a CTA of its own, its rows
+    // split over the CTA's teams; a larger one packs one frame per team
+    const bool split = s->split && n <= s->sms;
+    int grid;
+    if (split) {
+        perm.resize(n);
+        for (int k = 0; k < n; ++k)
+            perm[k] = k;
+        grid = build_split_schedule(n, s->sms, chunks, cta);
+    } else {
+        grid = build_item_schedule(items, s->sms, chunks, cta, perm);
+    }
     // result slot k now belongs to the frame items[k] came from
     {
         std::vector<sk_ticket_t> tk(n);
@@ -251,7 +263,8 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
     if (e == cudaSuccess)
         st = launch_schedule((const Item *)(L.d_work + o_items),
                              (const Chunk *)(L.d_work + o_chunks), (const int32_t *)L.d_work,
-                             grid, pick_tile(16, all_m32), true, s->device, s->s_compute);
+                             grid, pick_tile(16, all_m32), true, s->device, s->s_compute,
+                             split ? 1 : 0);
     if (e == cudaSuccess && st == SK_OK && s->trace)
         e = cudaEventRecord(L.t_k1, s->s_compute);
     if (e == cudaSuccess && st == SK_OK)
@@ -452,6 +465,8 @@ extern "C" sk_status_t sk_server_create(int device, size_t hbm_budget_bytes, sk_
     }
     if (const char *v = getenv("SK_SERVER_INJECT_FAULT"))
         s->inject_at = atoll(v);
+    if (const char *v = getenv("SK_SERVER_SPLIT"))
+        s->split = atoi(v) != 0;
     sk_status_t st = SK_OK;
     {
         DeviceGuard dg(device);

@@ -73,8 +73,12 @@ def _run_streams(server, specs, datas, interleave=True, ring=8, stateful=True, t
     return [(np.array(a, dtype=np.float32), np.array(b, dtype=np.uint8)) for a, b in out]
 
 
-def test_served_results_match_oracle_alone_and_in_mix():
+@pytest.mark.parametrize("split", ["1", "0"])
+def test_served_results_match_oracle_alone_and_in_mix(split, monkeypatch):
+    """Both served launch shapes: small batches with each frame's rows split over a
+    CTA (default) and teams on different frames (SK_SERVER_SPLIT=0)."""
     _need_gpu()
+    monkeypatch.setenv("SK_SERVER_SPLIT", split)
     specs = [(2048, 256), (256, 256), (256, 256), (2048, 256), (512, 128)]
     T = 30
     datas = [_stream_data(k, N, M, T) for k, (N, M) in enumerate(specs)]
