@@ -41,7 +41,6 @@ constexpr int kPackShift = 19;
 constexpr uint32_t kPackMask = (1u << kPackShift) - 1u;
 constexpr int kOffsetBuckets = 4096;
 constexpr int kStateShift = 6;
-constexpr int kImajorG = 8;                 // lanes per input on the input-major path
 
 // Output and table pointers of one work item: frames of one (N, M).
 struct Item {
