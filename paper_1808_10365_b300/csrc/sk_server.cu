@@ -95,6 +95,9 @@ struct Launch {
     // work block: items | chunks | cta (one copy); result block: sk | mask
     uint8_t *h_work = nullptr, *d_work = nullptr;
     uint8_t *h_res = nullptr, *d_res = nullptr;
+    // zero copy: device addresses of the mapped h_work and h_res, which the kernel
+    // then reads and writes directly (no work-list upload, no result download)
+    uint8_t *h_work_dev = nullptr, *h_res_dev = nullptr;
     cudaEvent_t uploaded = nullptr, done = nullptr;
     // tracing (SK_SERVER_TRACE=1): timing events and host times of one launch
     cudaEvent_t t_copy0 = nullptr, t_copy1 = nullptr, t_k0 = nullptr, t_k1 = nullptr;
@@ -179,8 +182,9 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
     }
     const int n = (int)frames.size();
     std::vector<Item> items(n);
-    float *d_sk = (float *)L.d_res;
-    uint8_t *d_mask = L.d_res + sizeof(float) * n;
+    uint8_t *res = s->zero_copy ? L.h_res_dev : L.d_res;
+    float *d_sk = (float *)res;
+    uint8_t *d_mask = res + sizeof(float) * n;
     bool all_m32 = true;
     for (int k = 0; k < n; ++k) {
         const Frame &f = frames[k];
@@ -240,8 +244,9 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
         e = cudaEventRecord(L.t_copy0, s->s_copy);
     L.bytes = b - a;
     // the work list goes first on the copy stream: a copy queued on the compute
-    // stream would wait on the copy engine behind the next batch's frames
-    if (e == cudaSuccess)
+    // stream would wait on the copy engine behind the next batch's frames.  With
+    // zero copy the kernel reads it from the mapped host buffer instead.
+    if (e == cudaSuccess && !s->zero_copy)
         e = cudaMemcpyAsync(L.d_work, L.h_work, used, cudaMemcpyHostToDevice, s->s_copy);
     uint64_t pos = s->zero_copy ? b : a;
     while (pos < b && e == cudaSuccess) {
@@ -251,23 +256,24 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
                             s->s_copy);
         pos += len;
     }
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !s->zero_copy)
         e = cudaEventRecord(L.uploaded, s->s_copy);
     if (e == cudaSuccess && s->trace)
         e = cudaEventRecord(L.t_copy1, s->s_copy);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !s->zero_copy)
         e = cudaStreamWaitEvent(s->s_compute, L.uploaded, 0);
     if (e == cudaSuccess && s->trace)
         e = cudaEventRecord(L.t_k0, s->s_compute);
     sk_status_t st = SK_OK;
+    uint8_t *work = s->zero_copy ? L.h_work_dev : L.d_work;
     if (e == cudaSuccess)
-        st = launch_schedule((const Item *)(L.d_work + o_items),
-                             (const Chunk *)(L.d_work + o_chunks), (const int32_t *)L.d_work,
+        st = launch_schedule((const Item *)(work + o_items),
+                             (const Chunk *)(work + o_chunks), (const int32_t *)work,
                              grid, pick_tile(16, all_m32), true, s->device, s->s_compute,
                              split ? 1 : 0);
     if (e == cudaSuccess && st == SK_OK && s->trace)
         e = cudaEventRecord(L.t_k1, s->s_compute);
-    if (e == cudaSuccess && st == SK_OK)
+    if (e == cudaSuccess && st == SK_OK && !s->zero_copy)
         e = cudaMemcpyAsync(L.h_res, L.d_res, (sizeof(float) + 1) * (size_t)n,
                             cudaMemcpyDeviceToHost, s->s_compute);
     if (e == cudaSuccess && st == SK_OK)
@@ -480,10 +486,14 @@ extern "C" sk_status_t sk_server_create(int device, size_t hbm_budget_bytes, sk_
         const size_t wb = work_bytes(s->sms), rb = sizeof(float) * kMaxBatch + kMaxBatch;
         for (int i = 0; i < s->nslots && st == SK_OK; ++i) {
             Launch &L = s->slots[i];
-            if (cudaHostAlloc(&L.h_work, wb, 0) != cudaSuccess ||
-                cudaHostAlloc(&L.h_res, rb, 0) != cudaSuccess ||
+            if (cudaHostAlloc(&L.h_work, wb, cudaHostAllocMapped) != cudaSuccess ||
+                cudaHostAlloc(&L.h_res, rb, cudaHostAllocMapped) != cudaSuccess ||
                 cudaMalloc(&L.d_work, wb) != cudaSuccess || cudaMalloc(&L.d_res, rb) != cudaSuccess)
                 st = set_error(SK_ERR_OOM, "server launch buffers");
+            else if (cudaHostGetDevicePointer((void **)&L.h_work_dev, L.h_work, 0) !=
+                         cudaSuccess ||
+                     cudaHostGetDevicePointer((void **)&L.h_res_dev, L.h_res, 0) != cudaSuccess)
+                st = set_error(SK_ERR_CUDA, "server launch buffer mapping");
             else if (cudaEventCreateWithFlags(&L.uploaded, cudaEventDisableTiming) != cudaSuccess ||
                      cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess)
                 st = set_error(SK_ERR_CUDA, "server events");
