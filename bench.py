@@ -441,7 +441,8 @@ def batched_bench(reps: int = 10, dev_index: int = 0, n_frames: int = 500):
 
 
 def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
-                 pool: int = 32, threads: int = 0, running_mu: bool = False):
+                 pool: int = 32, threads: int = 0, running_mu: bool = False,
+                 by_reference: bool = False):
     """32 streams (24 x N=2048, 8 x N=256), M=256 frames arriving every 0.65536 ms per
     stream with exponential jitter (mean T/4), for `seconds` of simulated time, through
     the continuous-batching server with the running power state, driven by the
@@ -451,7 +452,9 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
     threads: submitter threads of the load generator (0: 4 when paced -- enough
     for the 20 GB/s of arrivals, and fewer spinning cores beside the server's
     own threads -- and 8 flat out).  running_mu: the streams also normalise by the
-    running power (SK_RUNNING_MU) instead of each frame's own power."""
+    running power (SK_RUNNING_MU) instead of each frame's own power.  by_reference:
+    frames are submitted with sk_stream_submit_ref from page-locked pools (no copy
+    into the server's ring) instead of being copied by sk_stream_submit."""
     import torch
 
     import paper_1808_10365_b300 as sk
@@ -472,12 +475,17 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
     server = sk.sk_server_create(dev_index, 8 << 30)
     flags = sk.SK_RUNNING_MU if running_mu else sk.SK_RUNNING_OFFSET
     sids = [sk.sk_stream_open(server, N, M, ring_frames=32, flags=flags) for N in specs]
-    r = sk.sk_server_replay(server, sids, pools, n_per, T, T / 4, paced=paced, threads=threads)
+    if by_reference:
+        pools = [torch.from_numpy(p).pin_memory() for p in pools]
+    r = sk.sk_server_replay(server, sids, pools, n_per, T, T / 4, paced=paced, threads=threads,
+                            by_reference=by_reference)
     for sid in sids:
         sk.sk_stream_close(server, sid)
     sk.sk_server_destroy(server)
     out = {"streams": "24 x N=2048 + 8 x N=256, M=256, running power state"
-                      + (", running-mu normalisation" if running_mu else ""),
+                      + (", running-mu normalisation" if running_mu else "")
+                      + (", frames by reference from page-locked memory" if by_reference
+                         else ""),
            "paced": paced, "simulated_s": seconds, "frames": r["frames"], "wall_s": r["wall_s"],
            "value": r["bytes"] / r["wall_s"] / 1e9, "unit": UNIT,
            "realtime_input_gbs": sum(specs) * M / T / 1e9,
@@ -485,7 +493,7 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
            "launches": r["launches"], "frames_per_launch": r["frames"] / max(1, r["launches"]),
            "submit_p50_us": r["submit_p50_us"], "busy_retries": r["busy_retries"],
            "load_generator": f"sk_server_replay, {threads} submitter threads"}
-    if paced and not running_mu:
+    if paced and not running_mu and not by_reference:
         # plain path on the same frames: one synchronous sk_flag_host per frame
         lat = []
         plans = {N: sk.sk_plan_create(N, M, 3.0, 0.0, device=dev_index) for N in set(specs)}
@@ -630,6 +638,8 @@ def run_gpu(args):
         line["served_replay"] = served_bench(min(args.served_seconds, 1.0), False, dev.index)
         line["served_running_mu"] = served_bench(min(args.served_seconds, 1.0), True, dev.index,
                                                  running_mu=True)
+        line["served_by_reference"] = served_bench(min(args.served_seconds, 1.0), True,
+                                                   dev.index, by_reference=True)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:

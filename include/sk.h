@@ -273,6 +273,17 @@ sk_status_t sk_stream_submit(sk_server_t server, sk_stream_id stream,
                              const uint8_t *frame, int64_t frame_index,
                              sk_ticket_t *ticket);
 /*
+ * Queue one frame by reference: no copy.  frame (16-byte aligned) is device
+ * memory of the server's device, or page-locked host memory the device can
+ * read (mapped); the kernel reads it where it is, so it must stay unchanged
+ * until the ticket completes.  INVALID_ARG for pageable host memory.  Frames
+ * passed either way may be mixed in one stream; they are processed in
+ * submission order.
+ */
+sk_status_t sk_stream_submit_ref(sk_server_t server, sk_stream_id stream,
+                                 const uint8_t *frame, int64_t frame_index,
+                                 sk_ticket_t *ticket);
+/*
  * Wait up to timeout_us (< 0: no limit) for a ticket; fills *sk and *mask
  * (either may be NULL) and releases the ticket.  TIMEOUT if not done in
  * time, INVALID_ARG for an unknown or already collected ticket.
@@ -339,7 +350,8 @@ typedef struct {
     double cadence_s;
     double jitter_mean_s;
     int32_t paced;
-    int32_t pad;
+    int32_t by_reference;  /* submit with sk_stream_submit_ref (the pools must
+                              then be device-readable, e.g. page-locked) */
     uint64_t seed;
 } sk_replay_t;
 typedef struct {

@@ -45,7 +45,8 @@ EXPORTED = [
     "sk_plan_set_tiles", "sk_plan_get_tiles", "sk_compute", "sk_flag", "sk_flag_host",
     "sk_flag_host_noalloc", "sk_compute_inputs",
     "sk_batch_create", "sk_batch_run", "sk_batch_destroy", "sk_server_create",
-    "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_ticket_wait",
+    "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_stream_submit_ref",
+    "sk_ticket_wait",
     "sk_stream_drain", "sk_stream_get_state", "sk_stream_set_state", "sk_stream_close",
     "sk_server_stats", "sk_stream_stats", "sk_server_replay", "sk_digitisation_offset",
     "sk_last_error",
@@ -77,7 +78,8 @@ class sk_replay_t(ctypes.Structure):
                 ("streams", ctypes.c_void_p), ("frames", ctypes.c_void_p),
                 ("pool_frames", ctypes.c_void_p), ("frames_per_stream", ctypes.c_int64),
                 ("cadence_s", ctypes.c_double), ("jitter_mean_s", ctypes.c_double),
-                ("paced", ctypes.c_int32), ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("paced", ctypes.c_int32), ("by_reference", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 class sk_replay_result_t(ctypes.Structure):
@@ -134,6 +136,7 @@ def library():
         "sk_server_destroy": [P],
         "sk_stream_open": [P, ctypes.POINTER(sk_params_t), I32, ctypes.POINTER(I32)],
         "sk_stream_submit": [P, I32, P, I64, ctypes.POINTER(I64)],
+        "sk_stream_submit_ref": [P, I32, P, I64, ctypes.POINTER(I64)],
         "sk_ticket_wait": [P, I64, I64, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(U8)],
         "sk_stream_drain": [P, I32, I64],
         "sk_stream_get_state": [P, I32, P, ctypes.POINTER(ctypes.c_size_t)],
@@ -388,6 +391,17 @@ def sk_stream_submit(server, stream_id, frame, frame_index=0) -> int:
     return t.value
 
 
+def sk_stream_submit_ref(server, stream_id, frame, frame_index=0) -> int:
+    """frame: a CUDA tensor or a page-locked CPU tensor, read where it is (no copy);
+    it must stay unchanged until the ticket completes.  Returns the ticket."""
+    (nb,) = _sizes(_stream_shape.get((server, int(stream_id))), 1, [lambda N, M: M * N])
+    t = ctypes.c_int64()
+    _check(library().sk_stream_submit_ref(server, int(stream_id),
+                                          _buf(frame, nb, "device", "frame"),
+                                          int(frame_index), ctypes.byref(t)))
+    return t.value
+
+
 def sk_ticket_wait(server, ticket, timeout_us=-1):
     sk = ctypes.c_float()
     m = ctypes.c_uint8()
@@ -431,17 +445,26 @@ def sk_stream_stats(server, stream_id) -> dict:
 
 
 def sk_server_replay(server, stream_ids, pools, frames_per_stream, cadence_s, jitter_mean_s,
-                     paced=True, threads=8, seed=1):
-    """Replay frame pools (one uint8 numpy array [pool, M*N] per stream) into open streams."""
+                     paced=True, threads=8, seed=1, by_reference=False):
+    """Replay frame pools (one uint8 array [pool, M*N] per stream) into open streams.
+    by_reference: submit with sk_stream_submit_ref; the pools must then be page-locked
+    CPU tensors or CUDA tensors (2-D, contiguous)."""
     n = len(stream_ids)
-    pools = [np.ascontiguousarray(p, dtype=np.uint8) for p in pools]
+    if by_reference:
+        for p in pools:
+            _buf(p, None, "device", "pool")
+        ptrs = (ctypes.c_void_p * n)(*[p.data_ptr() for p in pools])
+        npool = (ctypes.c_int32 * n)(*[int(p.shape[0]) for p in pools])
+    else:
+        pools = [np.ascontiguousarray(p, dtype=np.uint8) for p in pools]
+        ptrs = (ctypes.c_void_p * n)(*[p.ctypes.data for p in pools])
+        npool = (ctypes.c_int32 * n)(*[p.shape[0] for p in pools])
     ids = (ctypes.c_int32 * n)(*stream_ids)
-    ptrs = (ctypes.c_void_p * n)(*[p.ctypes.data for p in pools])
-    npool = (ctypes.c_int32 * n)(*[p.shape[0] for p in pools])
     r = sk_replay_t(n, int(threads), ctypes.cast(ids, ctypes.c_void_p).value,
                     ctypes.cast(ptrs, ctypes.c_void_p).value,
                     ctypes.cast(npool, ctypes.c_void_p).value, int(frames_per_stream),
-                    float(cadence_s), float(jitter_mean_s), 1 if paced else 0, 0, int(seed))
+                    float(cadence_s), float(jitter_mean_s), 1 if paced else 0,
+                    1 if by_reference else 0, int(seed))
     out = sk_replay_result_t()
     _check(library().sk_server_replay(server, ctypes.byref(r), ctypes.byref(out)))
     return {k: getattr(out, k) for k, _ in sk_replay_result_t._fields_}

@@ -72,10 +72,11 @@ static constexpr size_t kStreamLatKeep = 1 << 14;
 struct Frame {
     StreamRec *stream;
     uint64_t off;   // monotonic ring offset
-    uint64_t size;  // bytes reserved (aligned)
+    uint64_t size;  // bytes reserved (aligned); 0 for a frame passed by reference
     sk_ticket_t ticket;
     bool ready;
     bool first;     // the stream's first frame with running state (set at launch)
+    const uint8_t *ref;  // device address of a frame passed by reference, else null
 };
 
 struct TicketRec {
@@ -190,7 +191,8 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
         const Frame &f = frames[k];
         StreamRec *r = f.stream;
         Item it = r->plan->item(
-            (s->zero_copy ? s->h_ring_dev : s->d_ring) + (f.off % s->ring_cap), 1);
+            f.ref ? f.ref : (s->zero_copy ? s->h_ring_dev : s->d_ring) + (f.off % s->ring_cap),
+            1);
         if (s->zero_copy)
             it.prefetch = 0;
         it.sk = d_sk + k;
@@ -236,9 +238,15 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
     memcpy(L.h_work, cta.data(), sizeof(int32_t) * cta.size());
     memcpy(L.h_work + o_chunks, chunks.data(), sizeof(Chunk) * chunks.size());
     memcpy(L.h_work + o_items, items.data(), sizeof(Item) * n);
-    // frames: one contiguous range of the ring, split at the wrap point
-    const uint64_t a = frames.front().off;
-    const uint64_t b = frames.back().off + frames.back().size;
+    // frames in the ring: one contiguous range, split at the wrap point (frames
+    // passed by reference are read where they are)
+    uint64_t a = 0, b = 0;
+    for (const Frame &f : frames)
+        if (!f.ref) {
+            if (b == 0)
+                a = f.off;
+            b = f.off + f.size;
+        }
     cudaError_t e = cudaSuccess;
     if (s->trace)
         e = cudaEventRecord(L.t_copy0, s->s_copy);
@@ -339,7 +347,10 @@ static void launcher_main(sk_server_s *s)
         Launch &L = s->slots[slot];
         L.busy = true;
         L.n = (int)batch.size();
-        L.end = batch.back().off + batch.back().size;
+        L.end = 0;
+        for (const Frame &f : batch)
+            if (!f.ref)
+                L.end = f.off + f.size;
         L.tickets.clear();
         L.streams.clear();
         for (const Frame &f : batch) {
@@ -690,7 +701,7 @@ extern "C" sk_status_t sk_stream_submit(sk_server_t s, sk_stream_id id, const ui
     TicketRec tr;
     tr.t_submit = t0;
     s->tickets.emplace(t, tr);
-    s->fifo.push_back(Frame{r, off, size, t, false, false});
+    s->fifo.push_back(Frame{r, off, size, t, false, false, nullptr});
     uint8_t *dst = s->h_ring + off % s->ring_cap;
     const int64_t fb = r->fbytes;
     lk.unlock();
@@ -701,6 +712,63 @@ extern "C" sk_status_t sk_stream_submit(sk_server_t s, sk_stream_id id, const ui
             f->ready = true;
             break;
         }
+    *ticket = t;
+    lk.unlock();
+    s->cv_work.notify_one();
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_stream_submit_ref(sk_server_t s, sk_stream_id id, const uint8_t *frame,
+                                            int64_t frame_index, sk_ticket_t *ticket)
+{
+    if (!s || !frame || !ticket)
+        return set_error(SK_ERR_INVALID_ARG, "sk_stream_submit_ref: null argument");
+    (void)frame_index;
+    if ((uintptr_t)frame & 15u)
+        return set_error(SK_ERR_INVALID_ARG, "sk_stream_submit_ref: frame not 16-byte aligned");
+    // the kernel reads the frame where it is: device memory of the server's
+    // device, or page-locked host memory mapped into its address space
+    cudaPointerAttributes pa;
+    const uint8_t *dev = nullptr;
+    {
+        DeviceGuard dg(s->device);
+        // a thread that has made no CUDA call yet has no current context until
+        // cudaSetDevice (which makes the device's primary context current)
+        cudaSetDevice(s->device);
+        if (cudaPointerGetAttributes(&pa, frame) == cudaSuccess) {
+            if ((pa.type == cudaMemoryTypeDevice && pa.device == s->device) ||
+                pa.type == cudaMemoryTypeManaged || pa.type == cudaMemoryTypeHost)
+                dev = (const uint8_t *)pa.devicePointer;
+        } else {
+            cudaGetLastError();  // clear the error a foreign pointer leaves behind
+        }
+    }
+    if (!dev)
+        return set_error(SK_ERR_INVALID_ARG,
+                         "sk_stream_submit_ref: frame is neither device memory nor "
+                         "page-locked host memory the device can read");
+    const Clock::time_point t0 = Clock::now();
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->fault != SK_OK)
+        return set_error(s->fault, "server fault: %s", s->fault_msg.c_str());
+    auto it = s->streams.find(id);
+    if (it == s->streams.end())
+        return set_error(SK_ERR_INVALID_ARG, "sk_stream_submit_ref: unknown stream %d", id);
+    StreamRec *r = it->second.get();
+    if (r->closing)
+        return set_error(SK_ERR_CLOSED, "sk_stream_submit_ref: stream %d closing", id);
+    if (r->outstanding >= r->ring_frames) {
+        s->rejected += 1;
+        r->rejected += 1;
+        return set_error(SK_ERR_BUSY, "sk_stream_submit_ref: stream %d has %d frames outstanding",
+                         id, r->outstanding);
+    }
+    r->outstanding += 1;
+    const sk_ticket_t t = s->next_ticket++;
+    TicketRec tr;
+    tr.t_submit = t0;
+    s->tickets.emplace(t, tr);
+    s->fifo.push_back(Frame{r, 0, 0, t, true, false, dev});
     *ticket = t;
     lk.unlock();
     s->cv_work.notify_one();
@@ -921,6 +989,7 @@ extern "C" sk_status_t sk_server_replay(sk_server_t s, const sk_replay_t *rp,
     std::vector<std::vector<double>> sub_us(nt);
     std::vector<int64_t> retries(nt, 0);
     std::vector<sk_status_t> status(nt, SK_OK);
+    std::vector<std::string> message(nt);
     const Clock::time_point t0 = Clock::now();
     auto worker = [&](int w) {
         std::mt19937_64 rng(rp->seed * 1000003ull + (uint64_t)w);
@@ -946,7 +1015,9 @@ extern "C" sk_status_t sk_server_replay(sk_server_t s, const sk_replay_t *rp,
             for (;;) {
                 sk_ticket_t t;
                 const Clock::time_point a = Clock::now();
-                sk_status_t st = sk_stream_submit(s, rp->streams[e.j], fr, e.k, &t);
+                sk_status_t st = rp->by_reference
+                                     ? sk_stream_submit_ref(s, rp->streams[e.j], fr, e.k, &t)
+                                     : sk_stream_submit(s, rp->streams[e.j], fr, e.k, &t);
                 sub_us[w].push_back(std::chrono::duration<double, std::micro>(Clock::now() - a).count());
                 if (st == SK_OK) {
                     pend[e.j].push_back(t);
@@ -954,6 +1025,7 @@ extern "C" sk_status_t sk_server_replay(sk_server_t s, const sk_replay_t *rp,
                 }
                 if (st != SK_ERR_BUSY || pend[e.j].empty()) {
                     status[w] = st;
+                    message[w] = sk_last_error();  // the message is per thread
                     return;
                 }
                 retries[w] += 1;
@@ -978,7 +1050,8 @@ extern "C" sk_status_t sk_server_replay(sk_server_t s, const sk_replay_t *rp,
     const double wall = std::chrono::duration<double>(Clock::now() - t0).count();
     for (int w = 0; w < nt; ++w)
         if (status[w] != SK_OK)
-            return set_error(status[w], "sk_server_replay: submit failed: %s", sk_last_error());
+            return set_error(status[w], "sk_server_replay: submit failed: %s",
+                             message[w].c_str());
     sk_server_stats_t after;
     sk_server_stats(s, &after);
     std::vector<double> all;

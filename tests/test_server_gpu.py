@@ -472,3 +472,39 @@ def test_stream_stats_count_frames_flags_and_rejections():
             sk.sk_stream_stats(server, b)
     finally:
         sk.sk_server_destroy(server)
+
+
+def test_submit_by_reference_mixed_with_copies():
+    """sk_stream_submit_ref reads frames where they are -- device memory, or page-locked
+    host memory -- and mixes in one stream with copied frames: the results follow the
+    served oracle frame by frame.  Pageable or misaligned frames are refused."""
+    _need_gpu()
+    N, M, T = 2048, 256, 12
+    ds, x = _stream_data(17, N, M, T)
+    e = dg.offset_table(M)
+    want = served.served_flags(x, M, N, e)
+    d_x = torch.from_numpy(x).to("cuda")
+    p_x = torch.from_numpy(x).pin_memory()
+    server = sk.sk_server_create(0, 1 << 30)
+    try:
+        sid = sk.sk_stream_open(server, N, M, ring_frames=T, flags=sk.SK_RUNNING_OFFSET,
+                                offset_table=e)
+        tickets = []
+        for f in range(T):
+            if f % 3 == 0:
+                tickets.append(sk.sk_stream_submit_ref(server, sid, d_x[f], f))
+            elif f % 3 == 1:
+                tickets.append(sk.sk_stream_submit_ref(server, sid, p_x[f], f))
+            else:
+                tickets.append(sk.sk_stream_submit(server, sid, x[f], f))
+        got = [sk.sk_ticket_wait(server, t, 10_000_000) for t in tickets]
+        for bad in (x[0].ctypes.data, d_x.data_ptr() + 8):
+            with pytest.raises(sk.SkError) as err:
+                sk.sk_stream_submit_ref(server, sid, bad, T)
+            assert err.value.status == sk.SK_ERR_INVALID_ARG
+        sk.sk_stream_close(server, sid)
+    finally:
+        sk.sk_server_destroy(server)
+    assert np.array_equal(np.array([m for _, m in got], dtype=np.uint8), want["mask"])
+    assert np.array_equal(np.array([v for v, _ in got], dtype=np.float32).view(np.uint32),
+                          want["sk"].view(np.uint32))
