@@ -129,7 +129,8 @@ def test_stateless_stream_matches_plain_flag():
                           want["sk"].view(np.uint32))
 
 
-@pytest.mark.parametrize("N,M", [(2048, 128), (256, 256), (100, 64), (37, 50), (2048, 48)])
+@pytest.mark.parametrize("N,M", [(2048, 128), (256, 256), (100, 64), (37, 50), (2048, 48),
+                                 (4096, 1024)])
 def test_input_major_stream_matches_time_major_stream(N, M):
     """The same frames served as [input][t] and as [t][input] give identical results,
     and the time-major stream matches the served-state oracle."""
