@@ -405,10 +405,12 @@ static void completer_main(sk_server_s *s)
                 else
                     r->lat_us[r->lat_next++ % kStreamLatKeep] = us;
             }
-            s->frames_done += 1;
-            s->frames_flagged += h_mask[k] ? 1 : 0;
-            L.streams[k]->frames_done += 1;
-            L.streams[k]->frames_flagged += h_mask[k] ? 1 : 0;
+            if (s->fault == SK_OK) {  // a failed launch has no results to count
+                s->frames_done += 1;
+                s->frames_flagged += h_mask[k] ? 1 : 0;
+                L.streams[k]->frames_done += 1;
+                L.streams[k]->frames_flagged += h_mask[k] ? 1 : 0;
+            }
             L.streams[k]->outstanding -= 1;
         }
         s->tail = std::max(s->tail, L.end);

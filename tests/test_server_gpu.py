@@ -424,6 +424,7 @@ def test_injected_launch_failure_fails_tickets_and_device_stays_usable(monkeypat
         with pytest.raises(sk.SkError) as e:
             sk.sk_stream_submit(server, sid, x[0], T)
         assert e.value.status == sk.SK_ERR_CUDA
+        assert sk.sk_server_stats(server)["frames_done"] == 2   # failed frames not counted
     finally:
         sk.sk_server_destroy(server)
     # the device still runs a fresh plan
