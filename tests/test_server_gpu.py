@@ -510,3 +510,81 @@ def test_submit_by_reference_mixed_with_copies():
     assert np.array_equal(np.array([m for _, m in got], dtype=np.uint8), want["mask"])
     assert np.array_equal(np.array([v for v, _ in got], dtype=np.float32).view(np.uint32),
                           want["sk"].view(np.uint32))
+
+
+def test_randomised_streams_against_the_oracle():
+    """Seeded stress of the server's bookkeeping: streams of different N, M and flags,
+    frames copied or passed by reference (device or page-locked memory), submitted in
+    a random interleaving against small rings (BUSY and ring wrap-around), one stream
+    closed and another opened half way.  Every result equals the served oracle's."""
+    _need_gpu()
+    rng = np.random.default_rng(2026)
+    shapes = [(2048, 256), (37, 64), (256, 256), (512, 128), (2048, 64), (100, 256)]
+    flag_of = [sk.SK_RUNNING_OFFSET, 0, sk.SK_RUNNING_MU, sk.SK_RUNNING_OFFSET, 0,
+               sk.SK_RUNNING_OFFSET]
+    T = 15
+    datas, wants, tables = [], [], []
+    for k, ((N, M), fl) in enumerate(zip(shapes, flag_of)):
+        ds, x = _stream_data(100 + k, N, M, T)
+        e = dg.offset_table(M)
+        if fl:
+            w = served.served_flags(x, M, N, e, running_mu=bool(fl & sk.SK_RUNNING_MU))
+        else:
+            w = oracle.flag(x, M, N, 3.0, 0.0)
+        datas.append((x, torch.from_numpy(x).to("cuda"), torch.from_numpy(x).pin_memory()))
+        wants.append(w)
+        tables.append(e)
+    server = sk.sk_server_create(0, 64 << 20)      # a 32 MiB ring: it wraps
+    try:
+        sids = {}
+        opened = list(range(5))                    # the sixth opens half way
+        for k in opened:
+            N, M = shapes[k]
+            sids[k] = sk.sk_stream_open(server, N, M, ring_frames=int(rng.integers(2, 5)),
+                                        flags=flag_of[k], offset_table=tables[k])
+        nxt = {k: 0 for k in range(6)}
+        pend = {k: [] for k in range(6)}
+        got = {k: [] for k in range(6)}
+        closed = set()
+
+        def collect(k):
+            got[k].append(sk.sk_ticket_wait(server, pend[k].pop(0), 10_000_000))
+
+        while any(nxt[k] < T for k in sids if k not in closed):
+            live = [k for k in sids if k not in closed and nxt[k] < T]
+            k = int(rng.choice(live))
+            f = nxt[k]
+            x, dx, px = datas[k]
+            how = int(rng.integers(0, 3))
+            try:
+                if how == 0:
+                    t = sk.sk_stream_submit(server, sids[k], x[f], f)
+                elif how == 1:
+                    t = sk.sk_stream_submit_ref(server, sids[k], dx[f], f)
+                else:
+                    t = sk.sk_stream_submit_ref(server, sids[k], px[f], f)
+            except sk.SkError as e:
+                assert e.status == sk.SK_ERR_BUSY
+                if pend[k]:
+                    collect(k)
+                continue
+            pend[k].append(t)
+            nxt[k] += 1
+            if k == 1 and nxt[k] == T:             # finish and close stream 1 ...
+                while pend[k]:
+                    collect(k)
+                sk.sk_stream_close(server, sids[k])
+                closed.add(k)
+                N, M = shapes[5]                    # ... and open stream 5 instead
+                sids[5] = sk.sk_stream_open(server, N, M, ring_frames=3, flags=flag_of[5],
+                                            offset_table=tables[5])
+        for k in sids:
+            while pend[k]:
+                collect(k)
+    finally:
+        sk.sk_server_destroy(server)
+    for k in range(6):
+        skv = np.array([v for v, _ in got[k]], dtype=np.float32)
+        m = np.array([b for _, b in got[k]], dtype=np.uint8)
+        assert np.array_equal(m, wants[k]["mask"]), k
+        assert np.array_equal(skv.view(np.uint32), wants[k]["sk"].view(np.uint32)), k
