@@ -86,3 +86,47 @@ def test_batch_rejects_bad_items():
             sk.sk_batch_create([])
     finally:
         sk.sk_plan_destroy(plan)
+
+
+def test_randomised_batches_against_the_oracle():
+    """Three seeded random batches of 12 items each: N, M, frame counts and layouts
+    drawn at random (every kernel class appears), replayed twice; every item equals
+    the oracle."""
+    dev = _dev()
+    rng = np.random.default_rng(404)
+    Ns = [8, 37, 100, 256, 512, 1000, 2048, 4096]
+    Ms = [16, 48, 64, 100, 128, 256, 512, 1024, 2048]
+    for rep in range(3):
+        items, plans, bufs, wants = [], [], [], []
+        for k in range(12):
+            N, M = int(rng.choice(Ns)), int(rng.choice(Ms))
+            layout = int(rng.integers(0, 2))
+            F = int(rng.integers(0, 9))
+            while F > 1 and F * M * N > (8 << 20):
+                F -= 1
+            x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+            delta = float(rng.uniform(-0.1, 0.0))
+            wants.append(oracle.flag(x, M, N, 3.0, delta, layout=layout) if F else None)
+            plan = sk.sk_plan_create(N, M, 3.0, delta, layout=layout)
+            d_in = (torch.from_numpy(x.reshape(-1)).to(dev) if F
+                    else torch.empty(16, dtype=torch.uint8, device=dev))
+            skv = torch.full((max(F, 1),), -1.0, dtype=torch.float32, device=dev)
+            mask = torch.full((max(F, 1),), 9, dtype=torch.uint8, device=dev)
+            plans.append(plan)
+            bufs.append((F, skv, mask))
+            items.append((plan, d_in, F, skv, mask))
+        batch = sk.sk_batch_create(items)
+        try:
+            for _ in range(2):
+                sk.sk_batch_run(batch)
+                torch.cuda.synchronize()
+                for k, ((F, skv, mask), w) in enumerate(zip(bufs, wants)):
+                    if not F:
+                        continue
+                    assert np.array_equal(mask.cpu().numpy()[:F], w["mask"]), (rep, k)
+                    assert np.array_equal(skv.cpu().numpy()[:F].view(np.uint32),
+                                          w["sk"].view(np.uint32)), (rep, k)
+        finally:
+            sk.sk_batch_destroy(batch)
+            for p in plans:
+                sk.sk_plan_destroy(p)
