@@ -56,10 +56,13 @@ int sm_count(int device)
 template <int R, int S, bool SRV, int NC, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_fused_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
-                    const int32_t *__restrict__ cta_chunks, Item single)
+                    const int32_t *__restrict__ cta_chunks, Item single,
+                    const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     __shared__ TeamSmem ts;
+    if (MODE == 0)
+        init_wi_slots(ts);  // ordered before first use by build_table's barrier
     const uint32_t lb = build_table(dyn_smem);
     int parity = 0;
     if (MODE == 0) {
@@ -67,7 +70,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t G = gridDim.x;
         const int64_t fb = F * (int64_t)blockIdx.x / G;
         const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
-        if (single.fast == 1 && single.M % (R * S) == 0 && (NC == 0 || single.N == NC))
+        const bool fast =
+            single.fast == 1 && single.M % (R * S) == 0 && (NC == 0 || single.N == NC);
+        if constexpr (R * S == 32 && !SRV) {
+            if (fast && single.wi) {
+                run_fast_wi<R, S, NC>(single, fb, fe, lb, ts, &tmap);
+                return;
+            }
+        }
+        if (fast)
             run_fast<R, S, SRV, NC>(single, fb, fe, lb, ts, parity);
         else
             run_general<SRV>(single, fb, fe, lb, ts, parity);
@@ -173,7 +184,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int G, int CH, bool PF, int MODE = 0, int SPLIT = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_imajor_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
-                     const int32_t *__restrict__ cta_chunks, Item single)
+                     const int32_t *__restrict__ cta_chunks, Item single,
+                     const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     __shared__ TeamSmem ts;
@@ -214,7 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-using KernelFn = void (*)(const Item *, const Chunk *, const int32_t *, Item);
+using KernelFn = void (*)(const Item *, const Chunk *, const int32_t *, Item,
+                          const CUtensorMap);
 
 // one-item launches: [tile][0 -> runtime N, 1 -> N = 256, 2 -> N = 2048]
 static const KernelFn kSingle[2][3] = {
@@ -345,6 +358,48 @@ sk_status_t ensure_kernel_attrs(int device)
     return SK_OK;
 }
 
+// Shapes of the warp-slice path: a team of N/8 threads (N/8 a power of two) of at
+// least two warps, each warp a 256-column slice.  SK_WARP_SLICE=0 turns it off.
+static bool warp_slice_shape(int N, int M)
+{
+    static const bool off = [] {
+        const char *v = getenv("SK_WARP_SLICE");
+        return v && atoi(v) == 0;
+    }();
+    return !off && N >= 512 && (N & (N - 1)) == 0 && N <= 4096 && M % 32 == 0;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map of a time-major input for the warp-slice path's prefetch: rows of N
+// bytes, boxes of 32 rows x 256 bytes.  False if the driver cannot make one (the
+// launch then takes the team path).
+static bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out)
+{
+    static const EncodeTiledFn encode = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return (EncodeTiledFn)f;
+    }();
+    if (!encode || rows <= 0 || rows > 0x7FFFFFFFLL || ((uintptr_t)in & 15u))
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)N};
+    const cuuint32_t box[2] = {256, 32};
+    const cuuint32_t es[2] = {1, 1};
+    return encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, (void *)in, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 sk_status_t launch_single(const Item &it, int rows, bool served, int device, cudaStream_t st,
                           int grid_cap)
 {
@@ -365,10 +420,18 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     if (served)
         return set_error(SK_ERR_UNSUPPORTED, "served items go through launch_schedule");
     const int nci = it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
-    KernelFn fn = kSingle[pick_tile(rows, it.M % 32 == 0)][nci];
+    const int tile = pick_tile(rows, it.M % 32 == 0);
+    KernelFn fn = kSingle[tile][nci];
     if (it.fast == 2)
         fn = imajor_kernel(it.M);
-    fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, it);
+    Item run = it;
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof tmap);
+    run.wi = (it.fast == 1 && tile == 0 && warp_slice_shape(it.N, it.M) &&
+              encode_input_map(it.in, it.N, it.n_frames * it.M, &tmap))
+                 ? 1
+                 : 0;
+    fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, run, tmap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_error(e, "sk kernel launch");
@@ -397,9 +460,12 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
         return s;
     Item dummy;
     memset(&dummy, 0, sizeof dummy);
+    CUtensorMap no_map;
+    memset(&no_map, 0, sizeof no_map);
     KernelFn fn = served ? (nclass == 1 ? kServedSplit[tile] : kServed[tile])
                          : (nclass < 3 ? kBatched[tile][nclass] : kImajorBatched[nclass - 3]);
-    fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy);
+    fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy,
+                                                   no_map);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_error(e, "sk batched kernel launch");
@@ -518,6 +584,8 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.running_mu = (p.flags & SK_RUNNING_MU) ? 1 : 0;
     it.n_sigma = p.n_sigma;
     it.mean_offset = p.mean_offset;
+    it.wi = 0;
+    it.err = d_err;
     return it;
 }
 
@@ -533,6 +601,8 @@ extern "C" sk_status_t sk_digitisation_offset(double sigma, double *delta)
 
 static void free_plan_device(sk_plan_s *pl)
 {
+    if (pl->h_err)
+        cudaFreeHost(pl->h_err);
     cudaFree(pl->d_t_lo);
     cudaFree(pl->d_t_hi);
     cudaFree(pl->d_c);
@@ -647,8 +717,11 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
         if (cudaMalloc(&pl->d_t_lo, tb) != cudaSuccess ||
             cudaMalloc(&pl->d_t_hi, tb) != cudaSuccess ||
             cudaMalloc(&pl->d_c, sizeof(float) * (N + 1)) != cudaSuccess ||
-            cudaMalloc(&pl->d_e, sizeof(int64_t) * kOffsetBuckets) != cudaSuccess) {
+            cudaMalloc(&pl->d_e, sizeof(int64_t) * kOffsetBuckets) != cudaSuccess ||
+            cudaHostAlloc(&pl->h_err, sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess) {
             st = set_error(SK_ERR_OOM, "device allocation of plan tables");
+        } else if (cudaHostGetDevicePointer((void **)&pl->d_err, pl->h_err, 0) != cudaSuccess) {
+            st = set_error(SK_ERR_CUDA, "mapping of the plan's error word");
         } else if (cudaMemcpy(pl->d_t_lo, pl->t_lo.data(), tb, cudaMemcpyHostToDevice) !=
                        cudaSuccess ||
                    cudaMemcpy(pl->d_t_hi, pl->t_hi.data(), tb, cudaMemcpyHostToDevice) !=
@@ -659,6 +732,7 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
                               cudaMemcpyHostToDevice) != cudaSuccess) {
             st = set_error(SK_ERR_CUDA, "copy of plan tables");
         } else {
+            *pl->h_err = 0;
             st = ensure_kernel_attrs(device);
         }
         if (st != SK_OK)
@@ -721,11 +795,25 @@ extern "C" sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows, int32_t 
     return SK_OK;
 }
 
+// A bounded wait inside an earlier launch of this plan gave up (its results are
+// void): report it once, on the next call.
+sk_status_t sk::pending_fault(sk_plan_t plan, const char *who)
+{
+    if (plan->h_err && *reinterpret_cast<volatile int32_t *>(plan->h_err)) {
+        *plan->h_err = 0;
+        return set_error(SK_ERR_CUDA, "%s: a wait inside an earlier launch timed out; "
+                                      "that launch's results are void", who);
+    }
+    return SK_OK;
+}
+
 static sk_status_t check_call(sk_plan_t plan, const void *d_in, int64_t n_frames,
                               const char *who)
 {
     if (!plan)
         return set_error(SK_ERR_INVALID_ARG, "%s: plan is NULL", who);
+    if (sk_status_t f = pending_fault(plan, who))
+        return f;
     if (n_frames < 0)
         return set_error(SK_ERR_INVALID_ARG, "%s: n_frames < 0", who);
     if (n_frames > 0 && !d_in)
@@ -824,6 +912,8 @@ extern "C" sk_status_t sk_flag_host(sk_plan_t plan, const uint8_t *h_in, int64_t
 {
     if (!plan)
         return set_error(SK_ERR_INVALID_ARG, "sk_flag_host: plan is NULL");
+    if (sk_status_t f = pending_fault(plan, "sk_flag_host"))
+        return f;
     if (n_frames < 0 || (n_frames > 0 && (!h_in || !h_mask)))
         return set_error(SK_ERR_INVALID_ARG, "sk_flag_host: bad arguments");
     if (n_frames == 0)

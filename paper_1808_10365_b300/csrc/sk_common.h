@@ -33,6 +33,8 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
 // 1 for N = 256, 3..8 for input-major items on the grouped path with M = 128,
 // 256, ..., 4096, 0 for the rest (runtime row stride or the general path).
 int batch_class(const Item &it);
+// SK_ERR_CUDA once if a bounded wait in an earlier launch of the plan gave up.
+sk_status_t pending_fault(sk_plan_t plan, const char *who);
 constexpr int kBatchClasses = 9;
 constexpr int kFirstImajorClass = 3;
 int pick_tile(int rows, bool all_m32);
@@ -88,6 +90,8 @@ struct sk_plan_s {
     std::vector<float> c_tab;
     int64_t *d_t_lo = nullptr, *d_t_hi = nullptr, *d_e = nullptr;
     float *d_c = nullptr;
+    // a word in mapped host memory that a kernel sets when a bounded wait gives up
+    int32_t *h_err = nullptr, *d_err = nullptr;
     // staging for sk_flag_host
     std::mutex host_mu;
     uint8_t *d_stage[2] = {nullptr, nullptr};

@@ -22,6 +22,7 @@
 // 16 p <= 2^11), after which it is split into the exact S1 and S2.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the 2D tensor prefetch of the warp-slice path)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -69,6 +70,8 @@ struct Item {
     int32_t running_mu;      // served: normalise by the running power in the state
     double n_sigma;          // running-mu decision (double domain)
     double mean_offset;
+    int32_t wi;              // 1: one-item launch on the warp-slice path (tensor map given)
+    int32_t *err;            // mapped host word: set when a bounded wait gives up
 };
 
 // Work of one CTA.  kind 0: frames [f_begin, f_end) of item `item`, the CTA's
@@ -266,6 +269,17 @@ __device__ __forceinline__ bool input_term_alu(int32_t s1, int32_t s2, int32_t M
     return true;
 }
 
+// Per-frame accumulators of the warp-slice path: each team has a ring of kWiSlots
+// slots; slot j holds the sums of the team's frame with counter `tag`.
+constexpr int kWiSlots = 4;
+struct WiSlot {
+    unsigned long long q;
+    int cnt;
+    int arrive;
+    unsigned tag;
+    int pad;
+};
+
 struct TeamSmem {
     long long q[2][kSlots];
     long long e[2][kSlots];
@@ -273,6 +287,7 @@ struct TeamSmem {
     long long rb[2][kSlots];
     int cnt[2][kSlots];
     int rn[2][kSlots];
+    WiSlot wi[kThreads / 64][kWiSlots];  // warp-slice path: teams of >= 2 warps
 };
 
 // Sum of the running-mu terms (A, B, n) over the team, every thread gets them.

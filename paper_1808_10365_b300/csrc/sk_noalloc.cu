@@ -61,6 +61,8 @@ extern "C" sk_status_t sk_flag_host_noalloc(sk_plan_t plan, const uint8_t *h_in,
 {
     if (!plan)
         return set_error(SK_ERR_INVALID_ARG, "sk_flag_host_noalloc: plan is NULL");
+    if (sk_status_t f = pending_fault(plan, "sk_flag_host_noalloc"))
+        return f;
     if (n_frames < 0 || (n_frames > 0 && (!h_in || !h_mask)))
         return set_error(SK_ERR_INVALID_ARG, "sk_flag_host_noalloc: bad arguments");
     if (n_frames == 0)

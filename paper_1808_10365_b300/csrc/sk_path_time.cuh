@@ -166,4 +166,199 @@ __device__ __forceinline__ void run_rows(const Item &it, int64_t frame, int b0, 
     }
 }
 
+// L2 prefetch of a box of the input through its tensor map (rows y .. y+31 of
+// columns x .. x+255 for the warp-slice path); a hint, results never depend on it.
+__device__ __forceinline__ void prefetch_box(const CUtensorMap *tm, int x, int y)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
+{
+    return *reinterpret_cast<const volatile unsigned *>(p);
+}
+
+// Warp-slice path: one-item launches, time-major, N a multiple of 256 and at
+// least 512, 16 x 2 tiles.  The team of a frame (N/8 threads) is cut into its
+// warps, and each warp owns a 256-column slice of the team's frames and runs on
+// its own: no barrier per frame.  Lane 0 of each warp asks L2 for the rows the
+// warp will load two ring turns ahead with one 2D tensor prefetch (32 rows x 256
+// bytes) through the launch's tensor map.  After a frame, the warp adds its
+// slice's Q and N_eff into the team's slot for that frame (shared-memory
+// atomics); the warp that arrives last forms the frame's mask and SK and frees
+// the slot.  A team's slots form a ring of kWiSlots frames; a warp that gets
+// that far ahead of a slow one waits, bounded, for its slot.
+template <int R, int S, int NC>
+__device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int64_t f_end,
+                                            uint32_t lb, TeamSmem &ts, const CUtensorMap *tmap)
+{
+    static_assert(R * S == 32, "one prefetch box per ring turn");
+    const int team_log2 = it.team_log2;
+    const int T = kThreads >> team_log2;
+    const int team_idx = threadIdx.x >> team_log2;
+    const int lit = threadIdx.x & ((1 << team_log2) - 1);
+    const int W = (1 << team_log2) >> 5;  // warps per frame
+    const int lane = threadIdx.x & 31;
+    const int xs = (lit >> 5) * 256;      // the warp's first column
+    const int col0 = lit * kVec;
+    const int M = it.M;
+    const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
+    const int64_t fbytes = (int64_t)M * N;
+    const int nb = M / R;
+    const int64_t kmax = (f_end - f_begin + T - 1) / T;
+    WiSlot *slots = ts.wi[team_idx];
+
+    uint2 buf[S][R];
+    int64_t frame = f_begin + team_idx;
+    bool ok = frame < f_end;
+    const uint8_t *fp = it.in + frame * fbytes + col0;
+    // R rows from p, row stride N (a load immediate when NC > 0)
+    auto load = [&](uint2 (&b)[R], const uint8_t *p) {
+        if constexpr (NC > 0) {
+            load_rows_imm<NC>(b, p, std::make_integer_sequence<int, R>{});
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                b[r] = ldg_stream(p + (int64_t)r * N);
+        }
+    };
+    if (ok) {
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            load(buf[j], fp + (int64_t)j * R * N);
+    }
+    for (int64_t kk = 0; kk < kmax; ++kk) {
+        const int64_t nframe = frame + T;
+        const bool nok = nframe < f_end;
+        const uint8_t *nfp = it.in + nframe * fbytes + col0;
+        uint32_t acc[kVec];
+        int32_t s1[kVec], s2[kVec];
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            acc[j] = 0u;
+            s1[j] = 0;
+            s2[j] = 0;
+        }
+        for (int jb = 0; jb < nb; jb += S) {
+            if (lane == 0) {
+                const int ba = jb + 2 * S;  // two ring turns ahead
+                if (ba < nb) {
+                    if (ok)
+                        prefetch_box(tmap, xs, (int)(frame * M + ba * R));
+                } else if (nok && ba - nb + S <= nb) {
+                    prefetch_box(tmap, xs, (int)(nframe * M + (ba - nb) * R));
+                }
+            }
+            const bool same_frame = jb + S < nb;
+            const uint8_t *pn = same_frame ? fp + (int64_t)(jb + S) * R * N : nfp;
+            const bool lok = same_frame ? ok : nok;
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                if (ok) {
+#pragma unroll
+                    for (int r = 0; r < R; r += 2)
+                        accum_pair(buf[j][r], buf[j][r + 1], lb, acc);
+                    if (((j + 1) * R) % kFlushRows == 0)
+                        flush(acc, s1, s2);
+                }
+                if (lok)
+                    load(buf[j], pn + (int64_t)j * R * N);
+            }
+        }
+        if (ok) {
+            // the slice's terms and per-input outputs
+            int64_t q = 0;
+            int32_t cnt = 0;
+#pragma unroll
+            for (int k = 0; k < kVec; ++k) {
+                float r = 0.0f;
+                int64_t qi = 0;
+                const bool has = SK_EPILOGUE_ALU ? input_term_alu(s1[k], s2[k], M, r, qi)
+                                                 : input_term(s1[k], s2[k], M, r, qi);
+                if (has) {
+                    q += qi;
+                    cnt += 1;
+                }
+                if (it.sk_in) {
+                    const int64_t o = frame * it.N + col0 + k;
+                    it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
+                    if (it.mask_in)
+                        it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+                }
+            }
+            if (it.s1) {
+                int32_t *o1 = it.s1 + frame * it.N + col0;
+                int32_t *o2 = it.s2 + frame * it.N + col0;
+#pragma unroll
+                for (int k = 0; k < kVec; ++k) {
+                    o1[k] = s1[k];
+                    o2[k] = s2[k];
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+                cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+            }
+            if (lane == 0) {
+                WiSlot &sl = slots[kk % kWiSlots];
+                // the slot is this frame's once the frame kWiSlots back is done
+                for (int spins = 0; ld_volatile_u32(&sl.tag) != (unsigned)kk; ++spins) {
+                    if (spins > (1 << 22)) {
+                        atomicExch(it.err, 1);  // gave up: results of this launch are void
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                atomicAdd(&sl.q, (unsigned long long)q);
+                atomicAdd(&sl.cnt, cnt);
+                __threadfence_block();
+                if (atomicAdd(&sl.arrive, 1) == W - 1) {
+                    __threadfence_block();
+                    const int64_t Q = (int64_t)atomicAdd(&sl.q, 0ull);
+                    const int32_t C = atomicAdd(&sl.cnt, 0);
+                    uint8_t m = 1;
+                    if (C > 0)
+                        m = (Q > it.t_hi[C] || Q < it.t_lo[C]) ? 1 : 0;
+                    if (it.sk) {
+                        float skv = __int_as_float(0x7FC00000);
+                        if (C > 0)
+                            skv = __fmul_rn(__fmul_rn(__ll2float_rn(Q), 0x1p-32f), it.c_tab[C]);
+                        it.sk[frame] = skv;
+                    }
+                    if (it.mask)
+                        it.mask[frame] = m;
+                    if (it.q)
+                        it.q[frame] = Q;
+                    if (it.neff)
+                        it.neff[frame] = C;
+                    sl.q = 0ull;
+                    sl.cnt = 0;
+                    sl.arrive = 0;
+                    __threadfence_block();
+                    *reinterpret_cast<volatile unsigned *>(&sl.tag) = (unsigned)(kk + kWiSlots);
+                }
+            }
+            __syncwarp();
+        }
+        frame = nframe;
+        fp = nfp;
+        ok = nok;
+    }
+}
+
+// Slots of the warp-slice path before first use: slot j expects frame counter j.
+__device__ __forceinline__ void init_wi_slots(TeamSmem &ts)
+{
+    for (int i = threadIdx.x; i < (kThreads / 64) * kWiSlots; i += blockDim.x) {
+        WiSlot &sl = ts.wi[i / kWiSlots][i % kWiSlots];
+        sl.q = 0ull;
+        sl.cnt = 0;
+        sl.arrive = 0;
+        sl.tag = (unsigned)(i % kWiSlots);
+    }
+}
+
 }  // namespace sk
