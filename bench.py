@@ -618,8 +618,10 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": (f"sk_fused_kernel<{rows},2,false,2048>" if layout == 0
-                                else "sk_imajor_kernel<8,2,true>"),
+                     "kernel": ((f"sk_fused_kernel<{rows},2,false,2048,0>"
+                                 + (", team path" if os.environ.get("SK_WARP_SLICE") == "0" or rows != 16
+                                    else ", warp-slice path"))
+                                if layout == 0 else "sk_imajor_kernel<8,2,1,0,1>"),
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": mean_launch_s * 1e3},
         "e2e": line_tail["e2e"],
