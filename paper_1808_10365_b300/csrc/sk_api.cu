@@ -189,6 +189,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 {
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     __shared__ TeamSmem ts;
+    if (MODE == 0)
+        init_wi_slots(ts);  // ordered before first use by build_table's barrier
     const uint32_t lb = build_table(dyn_smem);
     int parity = 0;
     if constexpr (MODE == 1) {
@@ -200,6 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const Item it = items[ch.item];
             Item im = it;
             im.team_log2 = it.imajor_team_log2;
+            im.wi = 0;
             if (it.fast == 2 && it.M == 16 * G * CH * SPLIT && im.team_log2 >= 5)
                 run_imajor_grouped<G, CH, PF, SPLIT>(im, ch.f_begin, ch.f_end, lb, ts, parity);
             else
@@ -360,13 +363,18 @@ sk_status_t ensure_kernel_attrs(int device)
 
 // Shapes of the warp-slice path: a team of N/8 threads (N/8 a power of two) of at
 // least two warps, each warp a 256-column slice.  SK_WARP_SLICE=0 turns it off.
-static bool warp_slice_shape(int N, int M)
+static bool warp_slice_on()
 {
     static const bool off = [] {
         const char *v = getenv("SK_WARP_SLICE");
         return v && atoi(v) == 0;
     }();
-    return !off && N >= 512 && (N & (N - 1)) == 0 && N <= 4096 && M % 32 == 0;
+    return !off;
+}
+
+static bool warp_slice_shape(int N, int M)
+{
+    return warp_slice_on() && N >= 512 && (N & (N - 1)) == 0 && N <= 4096 && M % 32 == 0;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -431,6 +439,9 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
               encode_input_map(it.in, it.N, it.n_frames * it.M, &tmap))
                  ? 1
                  : 0;
+    // input-major teams of two or more warps combine through the same slot ring
+    if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6)
+        run.wi = 1;
     fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, run, tmap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

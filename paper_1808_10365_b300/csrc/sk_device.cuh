@@ -70,7 +70,8 @@ struct Item {
     int32_t running_mu;      // served: normalise by the running power in the state
     double n_sigma;          // running-mu decision (double domain)
     double mean_offset;
-    int32_t wi;              // 1: one-item launch on the warp-slice path (tensor map given)
+    int32_t wi;              // 1: one-item launch whose warps combine through the slot ring
+                             // (time-major: warp-slice path, tensor map given)
     int32_t *err;            // mapped host word: set when a bounded wait gives up
 };
 
@@ -289,6 +290,71 @@ struct TeamSmem {
     int rn[2][kSlots];
     WiSlot wi[kThreads / 64][kWiSlots];  // warp-slice path: teams of >= 2 warps
 };
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
+{
+    return *reinterpret_cast<const volatile unsigned *>(p);
+}
+
+// Slots of the warp-slice combine before first use: slot j expects frame counter j.
+__device__ __forceinline__ void init_wi_slots(TeamSmem &ts)
+{
+    for (int i = threadIdx.x; i < (kThreads / 64) * kWiSlots; i += blockDim.x) {
+        WiSlot &sl = ts.wi[i / kWiSlots][i % kWiSlots];
+        sl.q = 0ull;
+        sl.cnt = 0;
+        sl.arrive = 0;
+        sl.tag = (unsigned)(i % kWiSlots);
+    }
+}
+
+// Lane 0 of a warp adds the warp's part (q, cnt) of the team's frame with counter
+// kk (the frame's index `frame`) into the team's slot for it; the warp that arrives
+// last of the team's W writes the frame's outputs (Sec. 3.2 test on Q against the
+// integer thresholds of N_eff = cnt, SK of Eq. final) and frees the slot for frame
+// counter kk + kWiSlots.  The wait for the slot is bounded: past the bound the
+// warp sets the plan's error word and goes on, and the launch's results are void.
+__device__ __forceinline__ void wi_commit(const Item &it, WiSlot *slots, int64_t kk, int W,
+                                          int64_t frame, int64_t q, int32_t cnt)
+{
+    WiSlot &sl = slots[kk % kWiSlots];
+    // the slot is this frame's once the frame kWiSlots back is done
+    for (int spins = 0; ld_volatile_u32(&sl.tag) != (unsigned)kk; ++spins) {
+        if (spins > (1 << 22)) {
+            atomicExch(it.err, 1);
+            break;
+        }
+        __nanosleep(64);
+    }
+    atomicAdd(&sl.q, (unsigned long long)q);
+    atomicAdd(&sl.cnt, cnt);
+    __threadfence_block();
+    if (atomicAdd(&sl.arrive, 1) == W - 1) {
+        __threadfence_block();
+        const int64_t Q = (int64_t)atomicAdd(&sl.q, 0ull);
+        const int32_t C = atomicAdd(&sl.cnt, 0);
+        uint8_t m = 1;
+        if (C > 0)
+            m = (Q > it.t_hi[C] || Q < it.t_lo[C]) ? 1 : 0;
+        if (it.sk) {
+            float skv = __int_as_float(0x7FC00000);
+            if (C > 0)
+                skv = __fmul_rn(__fmul_rn(__ll2float_rn(Q), 0x1p-32f), it.c_tab[C]);
+            it.sk[frame] = skv;
+        }
+        if (it.mask)
+            it.mask[frame] = m;
+        if (it.q)
+            it.q[frame] = Q;
+        if (it.neff)
+            it.neff[frame] = C;
+        sl.q = 0ull;
+        sl.cnt = 0;
+        sl.arrive = 0;
+        __threadfence_block();
+        *reinterpret_cast<volatile unsigned *>(&sl.tag) = (unsigned)(kk + kWiSlots);
+    }
+}
 
 // Sum of the running-mu terms (A, B, n) over the team, every thread gets them.
 // Called by every thread of a served kernel whatever its item's flags, so that

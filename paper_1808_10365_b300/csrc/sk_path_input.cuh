@@ -273,6 +273,9 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
     const int NG = (NS + team - 1) / team;
     const int64_t fbytes = (int64_t)M * NS;
     const int64_t kmax = (f_end - f_begin + T - 1) / T;
+    // teams of two or more warps in a single-item launch combine a frame's warps
+    // through the team's slot ring instead of a barrier per frame
+    const bool wi = it.wi && team >= 64;
 
     // sub-inputs of group (frame f, k) that this segment may read: 0..G
     auto live_of = [&](int64_t f, int k) -> int {
@@ -353,6 +356,20 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
             }
             cur_base = nxt_base;
             cur_live = nxt_live;
+        }
+        if (wi) {
+            // warp-slice combine: the warp's part goes into the team's slot, no barrier
+            if (fvalid) {
+                for (int o = 16; o > 0; o >>= 1) {
+                    q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+                    cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+                }
+                if ((lit & 31) == 0)
+                    wi_commit(it, ts.wi[team_idx], kk, team >> 5, frame, q, cnt);
+                __syncwarp();
+            }
+            frame += T;
+            continue;
         }
         team_sum(q, cnt, e, team_log2, team_idx, parity, ts, false);
         if (fvalid && lit == 0) {

@@ -176,11 +176,6 @@ __device__ __forceinline__ void prefetch_box(const CUtensorMap *tm, int x, int y
                  : "memory");
 }
 
-__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
-{
-    return *reinterpret_cast<const volatile unsigned *>(p);
-}
-
 // Warp-slice path: one-item launches, time-major, N a multiple of 256 and at
 // least 512, 16 x 2 tiles.  The team of a frame (N/8 threads) is cut into its
 // warps, and each warp owns a 256-column slice of the team's frames and runs on
@@ -302,62 +297,13 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
                 q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
                 cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
             }
-            if (lane == 0) {
-                WiSlot &sl = slots[kk % kWiSlots];
-                // the slot is this frame's once the frame kWiSlots back is done
-                for (int spins = 0; ld_volatile_u32(&sl.tag) != (unsigned)kk; ++spins) {
-                    if (spins > (1 << 22)) {
-                        atomicExch(it.err, 1);  // gave up: results of this launch are void
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-                atomicAdd(&sl.q, (unsigned long long)q);
-                atomicAdd(&sl.cnt, cnt);
-                __threadfence_block();
-                if (atomicAdd(&sl.arrive, 1) == W - 1) {
-                    __threadfence_block();
-                    const int64_t Q = (int64_t)atomicAdd(&sl.q, 0ull);
-                    const int32_t C = atomicAdd(&sl.cnt, 0);
-                    uint8_t m = 1;
-                    if (C > 0)
-                        m = (Q > it.t_hi[C] || Q < it.t_lo[C]) ? 1 : 0;
-                    if (it.sk) {
-                        float skv = __int_as_float(0x7FC00000);
-                        if (C > 0)
-                            skv = __fmul_rn(__fmul_rn(__ll2float_rn(Q), 0x1p-32f), it.c_tab[C]);
-                        it.sk[frame] = skv;
-                    }
-                    if (it.mask)
-                        it.mask[frame] = m;
-                    if (it.q)
-                        it.q[frame] = Q;
-                    if (it.neff)
-                        it.neff[frame] = C;
-                    sl.q = 0ull;
-                    sl.cnt = 0;
-                    sl.arrive = 0;
-                    __threadfence_block();
-                    *reinterpret_cast<volatile unsigned *>(&sl.tag) = (unsigned)(kk + kWiSlots);
-                }
-            }
+            if (lane == 0)
+                wi_commit(it, slots, kk, W, frame, q, cnt);
             __syncwarp();
         }
         frame = nframe;
         fp = nfp;
         ok = nok;
-    }
-}
-
-// Slots of the warp-slice path before first use: slot j expects frame counter j.
-__device__ __forceinline__ void init_wi_slots(TeamSmem &ts)
-{
-    for (int i = threadIdx.x; i < (kThreads / 64) * kWiSlots; i += blockDim.x) {
-        WiSlot &sl = ts.wi[i / kWiSlots][i % kWiSlots];
-        sl.q = 0ull;
-        sl.cnt = 0;
-        sl.arrive = 0;
-        sl.tag = (unsigned)(i % kWiSlots);
     }
 }
 
