@@ -90,10 +90,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         if (MODE == 1) {
             const Item it = items[ch.item];
-            if (it.fast == 1 && it.M % (R * S) == 0 && (NC == 0 || it.N == NC))
+            const bool fast = it.fast == 1 && it.M % (R * S) == 0 && (NC == 0 || it.N == NC);
+            if (fast)
                 run_fast<R, S, SRV, NC>(it, ch.f_begin, ch.f_end, lb, ts, parity);
             else
                 run_general<SRV>(it, ch.f_begin, ch.f_end, lb, ts, parity);
+        } else if (MODE == 4) {
+            // batched items on the warp-slice path (each with its input's tensor map
+            // in device memory), a fresh slot ring per chunk
+            if constexpr (R * S == 32 && !SRV && NC >= 512) {
+                // by reference: a copy of the item would hold its fields in registers
+                // through the loop
+                const Item &it = items[ch.item];
+                init_wi_slots(ts);
+                if ((threadIdx.x & 31) == 0)
+                    tensormap_acquire(it.tmap);
+                __syncthreads();
+                run_fast_wi<R, S, NC>(it, ch.f_begin, ch.f_end, lb, ts, it.tmap);
+            }
         } else if (MODE == 3) {
             const Item it = items[ch.item];
             const int tl = it.team_log2;
@@ -246,6 +260,8 @@ static const KernelFn kBatched[2][3] = {
      sk_fused_kernel<16, 2, false, 2048, 1>},
     {sk_fused_kernel<8, 2, false, 0, 1>, sk_fused_kernel<8, 2, false, 256, 1>,
      sk_fused_kernel<8, 2, false, 2048, 1>}};
+// batched time-major N = 2048 items on the warp-slice path
+static const KernelFn kBatchedWi = sk_fused_kernel<16, 2, false, 2048, 4>;
 static const KernelFn kServed[2] = {sk_fused_kernel<16, 2, true, 0, 2>,
                                     sk_fused_kernel<8, 2, true, 0, 2>};
 static const KernelFn kServedSplit[2] = {sk_fused_kernel<16, 2, true, 0, 3>,
@@ -342,6 +358,7 @@ sk_status_t ensure_kernel_attrs(int device)
         fns.push_back(f);
     for (KernelFn f : kImajorBatched)
         fns.push_back(f);
+    fns.push_back(kBatchedWi);
     for (int t = 0; t < 2; ++t) {
         fns.push_back(kServed[t]);
         fns.push_back(kServedSplit[t]);
@@ -372,7 +389,7 @@ static bool warp_slice_on()
     return !off;
 }
 
-static bool warp_slice_shape(int N, int M)
+bool warp_slice_shape(int N, int M)
 {
     return warp_slice_on() && N >= 512 && (N & (N - 1)) == 0 && N <= 4096 && M % 32 == 0;
 }
@@ -385,7 +402,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 // Tensor map of a time-major input for the warp-slice path's prefetch: rows of N
 // bytes, boxes of 32 rows x 256 bytes.  False if the driver cannot make one (the
 // launch then takes the team path).
-static bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out)
+bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out)
 {
     static const EncodeTiledFn encode = [] {
         void *f = nullptr;
@@ -474,7 +491,11 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
     CUtensorMap no_map;
     memset(&no_map, 0, sizeof no_map);
     KernelFn fn = served ? (nclass == 1 ? kServedSplit[tile] : kServed[tile])
-                         : (nclass < 3 ? kBatched[tile][nclass] : kImajorBatched[nclass - 3]);
+                         : (nclass < kWarpSliceClass
+                                ? kBatched[tile][nclass]
+                                : (nclass == kWarpSliceClass
+                                       ? kBatchedWi
+                                       : kImajorBatched[nclass - kFirstImajorClass]));
     fn<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks, d_cta_chunks, dummy,
                                                    no_map);
     cudaError_t e = cudaGetLastError();
@@ -597,6 +618,7 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.mean_offset = p.mean_offset;
     it.wi = 0;
     it.err = d_err;
+    it.tmap = nullptr;
     return it;
 }
 

@@ -22,6 +22,8 @@ struct sk_batch_s {
     sk::Item *d_items = nullptr;
     sk::Chunk *d_chunks = nullptr;
     int32_t *d_cta = nullptr;
+    CUtensorMap *d_maps = nullptr;  // tensor maps of the warp-slice items' inputs
+    std::vector<sk_plan_t> plans;   // the items' plans, each once
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -163,6 +165,7 @@ static void free_batch(sk_batch_s *b)
     cudaFree(b->d_items);
     cudaFree(b->d_chunks);
     cudaFree(b->d_cta);
+    cudaFree(b->d_maps);
 }
 
 extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_items,
@@ -181,6 +184,8 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
     bool all_m32[kBatchClasses];
     std::fill(all_m32, all_m32 + kBatchClasses, true);
     std::vector<int32_t> sel[kBatchClasses];
+    std::vector<CUtensorMap> maps;
+    std::vector<int32_t> map_of;
     for (int32_t k = 0; k < n_items; ++k) {
         const sk_batch_item_t &bi = items[k];
         if (!bi.plan || bi.n_frames < 0 || (bi.n_frames > 0 && !bi.d_in) ||
@@ -196,7 +201,23 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
         Item it = bi.plan->item(bi.d_in, bi.n_frames);
         it.sk = bi.d_sk;
         it.mask = bi.d_mask;
-        const int c = batch_class(it);
+        if (std::find(b->plans.begin(), b->plans.end(), bi.plan) == b->plans.end())
+            b->plans.push_back(bi.plan);
+        int c = batch_class(it);
+        // time-major N = 2048 items of M <= 128 on 16-row tiles take the warp-slice
+        // path (measured 5-6 % faster there; at M = 256 and 1024 the team path is
+        // 1.5 % and 8 % faster in a batch): each gets a tensor map of its input, in
+        // device memory, for the per-warp prefetch
+        CUtensorMap m;
+        if (c == 2 && bi.plan->rows == 16 && it.M % 32 == 0 && it.M <= 128 &&
+            it.n_frames > 0 && warp_slice_shape(it.N, it.M) &&
+            encode_input_map(it.in, it.N, it.n_frames * it.M, &m)) {
+            c = kWarpSliceClass;
+            map_of.push_back((int32_t)maps.size());
+            maps.push_back(m);
+        } else {
+            map_of.push_back(-1);
+        }
         b->items.push_back(it);
         sel[c].push_back(k);
         rows[c] = std::max(rows[c], bi.plan->rows);
@@ -218,12 +239,27 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
     sk_status_t s = SK_OK;
     {
         DeviceGuard dg(device);
+        if (!maps.empty()) {
+            if (cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * maps.size()) != cudaSuccess ||
+                cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                           cudaMemcpyHostToDevice) != cudaSuccess) {
+                s = set_error(SK_ERR_OOM, "batch tensor maps");
+            } else {
+                for (size_t k = 0; k < b->items.size(); ++k)
+                    if (map_of[k] >= 0) {
+                        b->items[k].wi = 1;
+                        b->items[k].tmap = b->d_maps + map_of[k];
+                    }
+            }
+        }
         size_t ni = sizeof(Item) * b->items.size();
         size_t nc = sizeof(Chunk) * std::max<size_t>(1, b->chunks.size());
         size_t nt = sizeof(int32_t) * b->cta.size();
-        if (cudaMalloc(&b->d_items, ni) != cudaSuccess ||
-            cudaMalloc(&b->d_chunks, nc) != cudaSuccess ||
-            cudaMalloc(&b->d_cta, nt) != cudaSuccess) {
+        if (s != SK_OK) {
+            // no room for the tensor maps
+        } else if (cudaMalloc(&b->d_items, ni) != cudaSuccess ||
+                   cudaMalloc(&b->d_chunks, nc) != cudaSuccess ||
+                   cudaMalloc(&b->d_cta, nt) != cudaSuccess) {
             s = set_error(SK_ERR_OOM, "batch schedule");
         } else if (cudaMemcpy(b->d_items, b->items.data(), ni, cudaMemcpyHostToDevice) !=
                        cudaSuccess ||
@@ -253,6 +289,10 @@ extern "C" sk_status_t sk_batch_run(sk_batch_t b, sk_cuda_stream_t stream)
         return set_error(SK_ERR_INVALID_ARG, "sk_batch_run: batch is NULL");
     DeviceGuard dg(b->device);
     sk_status_t s = SK_OK;
+    // a bounded wait of an earlier run that gave up voids that run's results
+    for (sk_plan_t p : b->plans)
+        if ((s = pending_fault(p, "sk_batch_run")) != SK_OK)
+            return s;
     if (b->chunks.empty())
         return SK_OK;  // no frames in any item
     if (!b->exec) {

@@ -2,6 +2,7 @@
 // launch helpers).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -30,13 +31,22 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
                             const int32_t *d_cta_chunks, int grid, int tile, bool served,
                             int device, cudaStream_t st, int nclass = 0);
 // Kernel class of a batched item: 2 for time-major fast-path items of N = 2048,
-// 1 for N = 256, 3..8 for input-major items on the grouped path with M = 128,
+// 1 for N = 256, 4..9 for input-major items on the grouped path with M = 128,
 // 256, ..., 4096, 0 for the rest (runtime row stride or the general path).
+// sk_batch_create moves class-2 items with a tensor map to class 3 (the
+// warp-slice path).
 int batch_class(const Item &it);
+// Time-major shapes of the warp-slice path (N a power of two from 512 to 4096,
+// M % 32 == 0), unless SK_WARP_SLICE=0.
+bool warp_slice_shape(int N, int M);
+// Tensor map of a time-major input for the warp-slice path's prefetch: rows of N
+// bytes, boxes of 32 rows x 256 bytes.  False if the driver cannot make one.
+bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out);
 // SK_ERR_CUDA once if a bounded wait in an earlier launch of the plan gave up.
 sk_status_t pending_fault(sk_plan_t plan, const char *who);
-constexpr int kBatchClasses = 9;
-constexpr int kFirstImajorClass = 3;
+constexpr int kBatchClasses = 10;
+constexpr int kWarpSliceClass = 3;
+constexpr int kFirstImajorClass = 4;
 int pick_tile(int rows, bool all_m32);
 int imajor_lanes(int M);
 int imajor_shape(int M);

@@ -70,9 +70,10 @@ struct Item {
     int32_t running_mu;      // served: normalise by the running power in the state
     double n_sigma;          // running-mu decision (double domain)
     double mean_offset;
-    int32_t wi;              // 1: one-item launch whose warps combine through the slot ring
+    int32_t wi;              // 1: the warps of a frame combine through the slot ring
                              // (time-major: warp-slice path, tensor map given)
     int32_t *err;            // mapped host word: set when a bounded wait gives up
+    const CUtensorMap *tmap;  // batched time-major items: the input's map in device memory
 };
 
 // Work of one CTA.  kind 0: frames [f_begin, f_end) of item `item`, the CTA's

@@ -176,12 +176,22 @@ __device__ __forceinline__ void prefetch_box(const CUtensorMap *tm, int x, int y
                  : "memory");
 }
 
-// Warp-slice path: one-item launches, time-major, N a multiple of 256 and at
-// least 512, 16 x 2 tiles.  The team of a frame (N/8 threads) is cut into its
+// Orders a tensor map in device memory, written by a host copy before the launch,
+// before this thread's first use of it through the tensor-map proxy.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *tm)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                     reinterpret_cast<uint64_t>(tm))
+                 : "memory");
+}
+
+// Warp-slice path: one-item launches and batched items with a tensor map,
+// time-major, N a power of two from 512 to 4096, 16 x 2 tiles.  The team of a frame (N/8 threads) is cut into its
 // warps, and each warp owns a 256-column slice of the team's frames and runs on
 // its own: no barrier per frame.  Lane 0 of each warp asks L2 for the rows the
 // warp will load two ring turns ahead with one 2D tensor prefetch (32 rows x 256
-// bytes) through the launch's tensor map.  After a frame, the warp adds its
+// bytes) through the input's tensor map (a kernel parameter of a one-item
+// launch, or the item's map in device memory).  After a frame, the warp adds its
 // slice's Q and N_eff into the team's slot for that frame (shared-memory
 // atomics); the warp that arrives last forms the frame's mask and SK and frees
 // the slot.  A team's slots form a ring of kWiSlots frames; a warp that gets
@@ -205,11 +215,12 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     const int nb = M / R;
     const int64_t kmax = (f_end - f_begin + T - 1) / T;
     WiSlot *slots = ts.wi[team_idx];
+    const uint8_t *const in = it.in;
 
     uint2 buf[S][R];
     int64_t frame = f_begin + team_idx;
     bool ok = frame < f_end;
-    const uint8_t *fp = it.in + frame * fbytes + col0;
+    const uint8_t *fp = in + frame * fbytes + col0;
     // R rows from p, row stride N (a load immediate when NC > 0)
     auto load = [&](uint2 (&b)[R], const uint8_t *p) {
         if constexpr (NC > 0) {
@@ -228,7 +239,7 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     for (int64_t kk = 0; kk < kmax; ++kk) {
         const int64_t nframe = frame + T;
         const bool nok = nframe < f_end;
-        const uint8_t *nfp = it.in + nframe * fbytes + col0;
+        const uint8_t *nfp = in + nframe * fbytes + col0;
         uint32_t acc[kVec];
         int32_t s1[kVec], s2[kVec];
 #pragma unroll

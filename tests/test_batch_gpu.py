@@ -29,6 +29,10 @@ def _dev():
     # input-major items only: the grouped path per M, ragged N, and the general path
     [(2048, 256, 9, 1), (256, 1024, 7, 1), (512, 512, 5, 1), (100, 128, 6, 1), (64, 64, 4, 1),
      (2048, 128, 11, 1)],
+    # time-major N = 2048 items of M <= 128 (the warp-slice class, one item long
+    # enough that each team's slot ring wraps), beside N = 2048 items of larger M
+    [(2048, 128, 19, 0), (2048, 64, 33, 0), (2048, 32, 3000, 0), (2048, 96, 7, 0),
+     (2048, 256, 5, 0), (2048, 128, 1, 0), (2048, 1024, 2, 0)],
     # one class only
     [(256, 256, 40, 0), (256, 128, 17, 0)],
     [(2048, 256, 7, 0)],
