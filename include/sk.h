@@ -29,6 +29,8 @@
  *   SK_WARP_SLICE=0      one-item launches: team path (one barrier per frame)
  *                        instead of the warp-slice path (time-major, N >= 512)
  *                        and the slot-ring combine (input-major teams of >= 2 warps)
+ *   SK_ROW_BALANCE=0     warp-slice launches hand out whole frames instead of
+ *                        equal row ranges (no plan scratch)
  *   SK_IMAJOR_GROUPED=0  input-major: per-input path instead of the grouped one
  *   SK_IMAJOR_PREFETCH=0 input-major grouped path without the L2 prefetch
  *   SK_IMAJOR_LANES      input-major per-input path: lanes per input (2, 4, 8)

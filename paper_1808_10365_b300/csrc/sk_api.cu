@@ -74,7 +74,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             single.fast == 1 && single.M % (R * S) == 0 && (NC == 0 || single.N == NC);
         if constexpr (R * S == 32 && !SRV) {
             if (fast && single.wi) {
-                run_fast_wi<R, S, NC>(single, fb, fe, lb, ts, &tmap);
+                if (single.rb)
+                    run_fast_rb<R, S, NC>(single, lb, ts, &tmap);
+                else
+                    run_fast_wi<R, S, NC>(single, fb, fe, lb, ts, &tmap);
                 return;
             }
         }
@@ -425,25 +428,67 @@ bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out)
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+static bool row_balance_on()
+{
+    static const bool off = [] {
+        const char *v = getenv("SK_ROW_BALANCE");
+        return v && atoi(v) == 0;
+    }();
+    return !off;
+}
+
+// The plan's scratch for a row-balanced launch of `need` bytes on stream st, or
+// nullptr (the launch then hands out whole frames).  Called with plan->rb_mu held.
+// Not while st is being captured; a launch on another stream than the last one
+// waits for that one, since launches share the scratch.
+static int32_t *rb_acquire(sk_plan_t plan, cudaStream_t st, size_t need, bool may_alloc)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+        return nullptr;
+    if (plan->rb_bytes < need) {
+        if (!may_alloc || plan->rb_failed)
+            return nullptr;
+        cudaFree(plan->rb);  // waits for the launches that used it
+        plan->rb = nullptr;
+        plan->rb_bytes = 0;
+        plan->rb_used = false;
+        if ((!plan->rb_ev &&
+             cudaEventCreateWithFlags(&plan->rb_ev, cudaEventDisableTiming) != cudaSuccess) ||
+            cudaMalloc(&plan->rb, need) != cudaSuccess ||
+            cudaMemsetAsync(plan->rb, 0, need, st) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(plan->rb);
+            plan->rb = nullptr;
+            plan->rb_failed = true;  // whole frames from now on
+            return nullptr;
+        }
+        plan->rb_bytes = need;
+    }
+    if (plan->rb_used && plan->rb_last != st &&
+        cudaStreamWaitEvent(st, plan->rb_ev, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return plan->rb;
+}
+
 sk_status_t launch_single(const Item &it, int rows, bool served, int device, cudaStream_t st,
-                          int grid_cap)
+                          int grid_cap, sk_plan_t plan, bool may_alloc)
 {
     if (it.n_frames == 0)
         return SK_OK;
     sk_status_t s = ensure_kernel_attrs(device);
     if (s != SK_OK)
         return s;
-    const int64_t T = kThreads >> (it.fast == 2 ? it.imajor_team_log2 : it.team_log2);
-    int64_t need = (it.n_frames + T - 1) / T;
-    int64_t g = sm_count(device);
-    if (grid_cap > 0)
-        g = grid_cap;
-    if (need < g)
-        g = need;
-    if (g < 1)
-        g = 1;
     if (served)
         return set_error(SK_ERR_UNSUPPORTED, "served items go through launch_schedule");
+    const int64_t T = kThreads >> (it.fast == 2 ? it.imajor_team_log2 : it.team_log2);
+    const int64_t gmax = grid_cap > 0 ? grid_cap : sm_count(device);
     const int nci = it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
     const int tile = pick_tile(rows, it.M % 32 == 0);
     KernelFn fn = kSingle[tile][nci];
@@ -459,10 +504,39 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // input-major teams of two or more warps combine through the same slot ring
     if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6)
         run.wi = 1;
+    // frames per team decide the grid, unless rows are balanced over the grid
+    int64_t g = std::min<int64_t>(gmax, (it.n_frames + T - 1) / T);
+    std::unique_lock<std::mutex> lk;
+    bool rb = false;
+    if (run.wi && it.fast == 1 && plan && row_balance_on()) {
+        const int64_t turns = it.n_frames * (it.M / 32);
+        const int64_t grb = std::max<int64_t>(1, std::min<int64_t>(gmax, turns / T));
+        const int64_t K = grb * T;
+        const int64_t W = it.N / 256;
+        const size_t need = (size_t)K * (size_t)(2 * it.N + W) * 4 + (size_t)K * 16;
+        lk = std::unique_lock<std::mutex>(plan->rb_mu);
+        run.rb = rb_acquire(plan, st, need, may_alloc);
+        if (run.rb) {
+            rb = true;
+            g = grb;
+        } else {
+            lk.unlock();
+        }
+    }
+    if (g < 1)
+        g = 1;
     fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, run, tmap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_error(e, "sk kernel launch");
+    if (rb) {
+        plan->rb_used = true;
+        plan->rb_last = st;
+        if ((e = cudaEventRecord(plan->rb_ev, st)) != cudaSuccess) {
+            plan->rb_failed = true;  // no later launch uses the scratch
+            return cuda_error(e, "sk scratch event");
+        }
+    }
     return SK_OK;
 }
 
@@ -619,6 +693,7 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.wi = 0;
     it.err = d_err;
     it.tmap = nullptr;
+    it.rb = nullptr;
     return it;
 }
 
@@ -651,6 +726,9 @@ static void free_plan_device(sk_plan_s *pl)
     }
     if (pl->s_copy)
         cudaStreamDestroy(pl->s_copy);
+    cudaFree(pl->rb);
+    if (pl->rb_ev)
+        cudaEventDestroy(pl->rb_ev);
 }
 
 extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_plan_t *out)
@@ -875,7 +953,7 @@ extern "C" sk_status_t sk_compute(sk_plan_t plan, const uint8_t *d_in, int64_t n
     it.neff = d_neff;
     DeviceGuard dg(plan->device);
     return launch_single(it, plan->rows, false, plan->device, (cudaStream_t)stream,
-                         plan->grid_ctas);
+                         plan->grid_ctas, plan);
 }
 
 extern "C" sk_status_t sk_flag(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
@@ -891,7 +969,7 @@ extern "C" sk_status_t sk_flag(sk_plan_t plan, const uint8_t *d_in, int64_t n_fr
     it.mask = d_mask;
     DeviceGuard dg(plan->device);
     return launch_single(it, plan->rows, false, plan->device, (cudaStream_t)stream,
-                         plan->grid_ctas);
+                         plan->grid_ctas, plan);
 }
 
 extern "C" sk_status_t sk_compute_inputs(sk_plan_t plan, const uint8_t *d_in,
@@ -910,7 +988,7 @@ extern "C" sk_status_t sk_compute_inputs(sk_plan_t plan, const uint8_t *d_in,
     it.mask = d_mask;
     DeviceGuard dg(plan->device);
     return launch_single(it, plan->rows, false, plan->device, (cudaStream_t)stream,
-                         plan->grid_ctas);
+                         plan->grid_ctas, plan);
 }
 
 // Host-buffer path: chunks of stage_frames frames alternate between two device
@@ -974,7 +1052,7 @@ extern "C" sk_status_t sk_flag_host(sk_plan_t plan, const uint8_t *h_in, int64_t
         Item it = plan->item(plan->d_stage[b], nf);
         it.sk = h_sk ? plan->d_sk_stage[b] : nullptr;
         it.mask = plan->d_mask_stage[b];
-        s = launch_single(it, plan->rows, false, plan->device, st, plan->grid_ctas);
+        s = launch_single(it, plan->rows, false, plan->device, st, plan->grid_ctas, plan);
         if (s != SK_OK)
             break;
         e = cudaMemcpyAsync(h_mask + f0, plan->d_mask_stage[b], (size_t)nf,

@@ -20,9 +20,11 @@ sk_status_t set_error(sk_status_t s, const char *fmt, ...);
 sk_status_t cuda_error(cudaError_t e, const char *what);
 
 // Kernel launch over one item with a contiguous frame range per CTA, or over
-// a prebuilt chunk schedule (items/chunks/cta_chunks on the device).
+// a prebuilt chunk schedule (items/chunks/cta_chunks on the device).  Given its
+// plan, a time-major launch of the warp-slice shapes balances rows over the
+// grid through the plan's scratch (allocated on first use when may_alloc).
 sk_status_t launch_single(const Item &it, int rows, bool served, int device, cudaStream_t st,
-                          int grid_cap = 0);
+                          int grid_cap = 0, sk_plan_t plan = nullptr, bool may_alloc = true);
 // tile: 0 = 16 rows x 2 batches (M % 32 == 0), 1 = 8 x 2 (M % 16 == 0);
 // nclass: batched launches, the kernel for items of batch_class nclass; served
 // launches, 0 = teams on different frames, 1 = one frame per CTA with its rows
@@ -102,6 +104,14 @@ struct sk_plan_s {
     float *d_c = nullptr;
     // a word in mapped host memory that a kernel sets when a bounded wait gives up
     int32_t *h_err = nullptr, *d_err = nullptr;
+    // scratch of the row-balanced launch (zero between launches); rb_ev follows its
+    // last launch, on stream rb_last, so that a launch on another stream waits
+    std::mutex rb_mu;
+    int32_t *rb = nullptr;
+    size_t rb_bytes = 0;
+    bool rb_failed = false, rb_used = false;
+    cudaEvent_t rb_ev = nullptr;
+    cudaStream_t rb_last = nullptr;
     // staging for sk_flag_host
     std::mutex host_mu;
     uint8_t *d_stage[2] = {nullptr, nullptr};

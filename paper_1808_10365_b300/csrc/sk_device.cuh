@@ -74,6 +74,7 @@ struct Item {
                              // (time-major: warp-slice path, tensor map given)
     int32_t *err;            // mapped host word: set when a bounded wait gives up
     const CUtensorMap *tmap;  // batched time-major items: the input's map in device memory
+    int32_t *rb;              // row-balanced warp-slice launch: the plan's zeroed scratch
 };
 
 // Work of one CTA.  kind 0: frames [f_begin, f_end) of item `item`, the CTA's
@@ -309,6 +310,27 @@ __device__ __forceinline__ void init_wi_slots(TeamSmem &ts)
     }
 }
 
+// The outputs of one frame from its Q and N_eff = C: the mask (Sec. 3.2 test of Q
+// against the integer thresholds of C), SK (Eq. final), Q and N_eff.
+__device__ __forceinline__ void write_frame(const Item &it, int64_t frame, int64_t Q, int32_t C)
+{
+    uint8_t m = 1;
+    if (C > 0)
+        m = (Q > it.t_hi[C] || Q < it.t_lo[C]) ? 1 : 0;
+    if (it.sk) {
+        float skv = __int_as_float(0x7FC00000);
+        if (C > 0)
+            skv = __fmul_rn(__fmul_rn(__ll2float_rn(Q), 0x1p-32f), it.c_tab[C]);
+        it.sk[frame] = skv;
+    }
+    if (it.mask)
+        it.mask[frame] = m;
+    if (it.q)
+        it.q[frame] = Q;
+    if (it.neff)
+        it.neff[frame] = C;
+}
+
 // Lane 0 of a warp adds the warp's part (q, cnt) of the team's frame with counter
 // kk (the frame's index `frame`) into the team's slot for it; the warp that arrives
 // last of the team's W writes the frame's outputs (Sec. 3.2 test on Q against the
@@ -332,23 +354,7 @@ __device__ __forceinline__ void wi_commit(const Item &it, WiSlot *slots, int64_t
     __threadfence_block();
     if (atomicAdd(&sl.arrive, 1) == W - 1) {
         __threadfence_block();
-        const int64_t Q = (int64_t)atomicAdd(&sl.q, 0ull);
-        const int32_t C = atomicAdd(&sl.cnt, 0);
-        uint8_t m = 1;
-        if (C > 0)
-            m = (Q > it.t_hi[C] || Q < it.t_lo[C]) ? 1 : 0;
-        if (it.sk) {
-            float skv = __int_as_float(0x7FC00000);
-            if (C > 0)
-                skv = __fmul_rn(__fmul_rn(__ll2float_rn(Q), 0x1p-32f), it.c_tab[C]);
-            it.sk[frame] = skv;
-        }
-        if (it.mask)
-            it.mask[frame] = m;
-        if (it.q)
-            it.q[frame] = Q;
-        if (it.neff)
-            it.neff[frame] = C;
+        write_frame(it, frame, (int64_t)atomicAdd(&sl.q, 0ull), atomicAdd(&sl.cnt, 0));
         sl.q = 0ull;
         sl.cnt = 0;
         sl.arrive = 0;

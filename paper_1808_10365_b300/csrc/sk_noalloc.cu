@@ -92,7 +92,8 @@ extern "C" sk_status_t sk_flag_host_noalloc(sk_plan_t plan, const uint8_t *h_in,
     Item it = plan->item(base, n_frames);
     it.sk = h_sk ? d_sk : nullptr;
     it.mask = d_mask;
-    s = launch_single(it, plan->rows, false, plan->device, st, plan->grid_ctas);
+    // the plan's row-balancing scratch only if an earlier call allocated it
+    s = launch_single(it, plan->rows, false, plan->device, st, plan->grid_ctas, plan, false);
     if (s != SK_OK)
         return s;
     e = cudaMemcpyAsync(h_mask, d_mask, (size_t)n_frames, cudaMemcpyDeviceToHost, st);

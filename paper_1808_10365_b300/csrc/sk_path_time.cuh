@@ -185,6 +185,48 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *tm)
                  : "memory");
 }
 
+// The input terms (Eq. normedSum2 per input) of one lane's 8 inputs of a frame,
+// with the per-input outputs the item asks for (S1, S2, SK_i and its one-input
+// flag), and the sum over the warp of their fixed-point q_i and count.
+__device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int col0, int M,
+                                            const int32_t (&s1)[kVec],
+                                            const int32_t (&s2)[kVec], int64_t &q,
+                                            int32_t &cnt)
+{
+    q = 0;
+    cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+        float r = 0.0f;
+        int64_t qi = 0;
+        const bool has = SK_EPILOGUE_ALU ? input_term_alu(s1[k], s2[k], M, r, qi)
+                                         : input_term(s1[k], s2[k], M, r, qi);
+        if (has) {
+            q += qi;
+            cnt += 1;
+        }
+        if (it.sk_in) {
+            const int64_t o = frame * it.N + col0 + k;
+            it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
+            if (it.mask_in)
+                it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+        }
+    }
+    if (it.s1) {
+        int32_t *o1 = it.s1 + frame * it.N + col0;
+        int32_t *o2 = it.s2 + frame * it.N + col0;
+#pragma unroll
+        for (int k = 0; k < kVec; ++k) {
+            o1[k] = s1[k];
+            o2[k] = s2[k];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+        cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    }
+}
+
 // Warp-slice path: one-item launches and batched items with a tensor map,
 // time-major, N a power of two from 512 to 4096, 16 x 2 tiles.  The team of a frame (N/8 threads) is cut into its
 // warps, and each warp owns a 256-column slice of the team's frames and runs on
@@ -275,39 +317,10 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
             }
         }
         if (ok) {
-            // the slice's terms and per-input outputs
-            int64_t q = 0;
-            int32_t cnt = 0;
-#pragma unroll
-            for (int k = 0; k < kVec; ++k) {
-                float r = 0.0f;
-                int64_t qi = 0;
-                const bool has = SK_EPILOGUE_ALU ? input_term_alu(s1[k], s2[k], M, r, qi)
-                                                 : input_term(s1[k], s2[k], M, r, qi);
-                if (has) {
-                    q += qi;
-                    cnt += 1;
-                }
-                if (it.sk_in) {
-                    const int64_t o = frame * it.N + col0 + k;
-                    it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
-                    if (it.mask_in)
-                        it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
-                }
-            }
-            if (it.s1) {
-                int32_t *o1 = it.s1 + frame * it.N + col0;
-                int32_t *o2 = it.s2 + frame * it.N + col0;
-#pragma unroll
-                for (int k = 0; k < kVec; ++k) {
-                    o1[k] = s1[k];
-                    o2[k] = s2[k];
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
-                cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-            }
+            // the slice's terms and per-input outputs, summed over the warp
+            int64_t q;
+            int32_t cnt;
+            slice_terms(it, frame, col0, M, s1, s2, q, cnt);
             if (lane == 0)
                 wi_commit(it, slots, kk, W, frame, q, cnt);
             __syncwarp();
@@ -315,6 +328,159 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
         frame = nframe;
         fp = nfp;
         ok = nok;
+    }
+}
+
+// Row-balanced warp-slice path (one-item time-major launches of the warp-slice
+// shapes, given the plan's scratch).  The input is one sequence of F*M rows (a
+// frame is a block of M consecutive rows), cut into TT = F*M/32 ring turns of 32
+// rows.  Team k of the grid's K teams takes the turns [TT*k/K, TT*(k+1)/K), so
+// teams differ by at most one turn whatever F is, and each of its warps runs its
+// 256-column slice of those rows.  A frame that lies inside the range goes through
+// the team's slot ring as on the warp-slice path.  A frame that a range boundary
+// cuts is shared with the neighbouring team(s): each part adds its S1, S2 into the
+// frame's slot in the scratch (device memory), the warp that completes a column's
+// rows forms that column's terms, and the warp that completes the last column
+// writes the frame.  Whoever reads a scratch word back leaves it zero, so the
+// scratch is all zero before and after every launch.  Scratch layout for K teams
+// of W warps: int32 S[K][2][N], int32 turns[K][W], uint64 Q[K], int32 cnt[K],
+// int32 arrive[K]; the slot of a cut frame is the index of the first team boundary
+// inside it.
+template <int R, int S, int NC>
+__device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSmem &ts,
+                                            const CUtensorMap *tmap)
+{
+    static_assert(R * S == 32, "one turn per ring revolution");
+    const int team_log2 = it.team_log2;
+    const int T = kThreads >> team_log2;
+    const int team_idx = threadIdx.x >> team_log2;
+    const int lit = threadIdx.x & ((1 << team_log2) - 1);
+    const int W = (1 << team_log2) >> 5;  // warps (256-column slices) per frame
+    const int lane = threadIdx.x & 31;
+    const int c = lit >> 5;
+    const int xs = c * 256;
+    const int col0 = lit * kVec;
+    const int M = it.M;
+    const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
+    const int64_t tpf = M / 32;  // turns per frame
+    const int64_t TT = it.n_frames * tpf;
+    const int64_t K = (int64_t)gridDim.x * T;
+    const int64_t kt = (int64_t)blockIdx.x * T + team_idx;
+    const int64_t t0 = TT * kt / K, t1 = TT * (kt + 1) / K;
+    int32_t *const ps = it.rb;
+    int32_t *const pturn = ps + 2 * K * N;
+    unsigned long long *const pq = reinterpret_cast<unsigned long long *>(pturn + K * W);
+    int32_t *const pcnt = reinterpret_cast<int32_t *>(pq + K);
+    int32_t *const parr = pcnt + K;
+    WiSlot *slots = ts.wi[team_idx];
+    const uint8_t *const in = it.in + col0;
+
+    // R rows from p, row stride N (a load immediate when NC > 0)
+    auto load = [&](uint2 (&b)[R], const uint8_t *p) {
+        if constexpr (NC > 0) {
+            load_rows_imm<NC>(b, p, std::make_integer_sequence<int, R>{});
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                b[r] = ldg_stream(p + (int64_t)r * N);
+        }
+    };
+    uint2 buf[S][R];
+    if (t0 < t1) {
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            load(buf[j], in + (t0 * 32 + j * R) * N);
+    }
+    uint32_t acc[kVec];
+    int32_t s1[kVec], s2[kVec];
+#pragma unroll
+    for (int j = 0; j < kVec; ++j) {
+        acc[j] = 0u;
+        s1[j] = 0;
+        s2[j] = 0;
+    }
+    int64_t kk = 0;     // whole frames this team has committed
+    int64_t seg0 = t0;  // first turn of the current frame part
+    for (int64_t g = t0; g < t1; ++g) {
+        if (lane == 0 && g + 2 < t1)
+            prefetch_box(tmap, xs, (int)((g + 2) * 32));  // two turns ahead
+        const bool more = g + 1 < t1;
+        const uint8_t *pn = in + (g + 1) * 32 * N;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+#pragma unroll
+            for (int r = 0; r < R; r += 2)
+                accum_pair(buf[j][r], buf[j][r + 1], lb, acc);
+            if (((j + 1) * R) % kFlushRows == 0)
+                flush(acc, s1, s2);
+            if (more)
+                load(buf[j], pn + (int64_t)j * R * N);
+        }
+        const bool fend = (g + 1) % tpf == 0;
+        if (!fend && more)
+            continue;
+        const int64_t frame = g / tpf;
+        if (fend && seg0 % tpf == 0) {
+            // a whole frame: the slice's part goes into the team's slot ring
+            int64_t q;
+            int32_t cnt;
+            slice_terms(it, frame, col0, M, s1, s2, q, cnt);
+            if (lane == 0)
+                wi_commit(it, slots, kk, W, frame, q, cnt);
+            __syncwarp();
+            ++kk;
+        } else {
+            // part of a cut frame: add the column's sums into the frame's slot
+            const int64_t slot = ((frame * tpf + 1) * K + TT - 1) / TT;
+            int32_t *sp = ps + slot * 2 * N + col0;
+#pragma unroll
+            for (int k = 0; k < kVec; ++k) {
+                atomicAdd(sp + k, s1[k]);
+                atomicAdd(sp + N + k, s2[k]);
+            }
+            __threadfence();
+            __syncwarp();
+            int fin = 0;
+            if (lane == 0) {
+                const int part = (int)(g + 1 - seg0);
+                fin = atomicAdd(pturn + slot * W + c, part) + part == (int)tpf;
+            }
+            fin = __shfl_sync(0xFFFFFFFFu, fin, 0);
+            if (fin) {
+                // this warp completed the column: its totals, and the slot words zero
+                __threadfence();
+#pragma unroll
+                for (int k = 0; k < kVec; ++k) {
+                    s1[k] = atomicExch(sp + k, 0);
+                    s2[k] = atomicExch(sp + N + k, 0);
+                }
+                int64_t q;
+                int32_t cnt;
+                slice_terms(it, frame, col0, M, s1, s2, q, cnt);
+                if (lane == 0) {
+                    atomicExch(pturn + slot * W + c, 0);
+                    atomicAdd(pq + slot, (unsigned long long)q);
+                    atomicAdd(pcnt + slot, cnt);
+                    __threadfence();
+                    if (atomicAdd(parr + slot, 1) == W - 1) {
+                        // the last column: the frame's outputs
+                        __threadfence();
+                        const int64_t Q = (int64_t)atomicExch(pq + slot, 0ull);
+                        const int32_t C = atomicExch(pcnt + slot, 0);
+                        atomicExch(parr + slot, 0);
+                        write_frame(it, frame, Q, C);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            acc[j] = 0u;
+            s1[j] = 0;
+            s2[j] = 0;
+        }
+        seg0 = g + 1;
     }
 }
 

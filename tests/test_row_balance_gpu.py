@@ -1,0 +1,146 @@
+"""Row-balanced launches: a one-item time-major launch of the warp-slice shapes
+hands every team an equal range of 32-row turns, and frames cut by a range
+boundary are combined through the plan's scratch in device memory.  Against the
+oracle: cut frames of every kind (a frame shared by two teams, a frame spread
+over many teams, a team inside one frame), per-input outputs written by the
+warp that completes a column, one plan on two streams, a captured launch (which
+hands out whole frames), and the no-allocation call before and after the plan
+has its scratch."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1808_10365_b300 as sk  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch.device("cuda:0")
+
+
+def _bytes(N, M, F, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    if F > 1:
+        x[1, : N * 4] = 0x88          # a few dead rows
+        x[F - 1, :] = 0x00            # a frame of -8-8j everywhere
+    return x
+
+
+@pytest.mark.parametrize("N,M,F", [
+    (2048, 256, 299),    # 299 frames over 296 teams: most frames cut in two
+    (2048, 1024, 37),    # frames spread over 8 teams each
+    (4096, 4096, 3),     # 384 turns over 148 teams: several teams inside a frame
+    (512, 4096, 5),      # 640 turns over 640 two-warp teams: one turn each
+    (1024, 32, 3001),    # one turn per frame
+    (4096, 96, 150),     # 3 turns per frame
+    (512, 64, 1)])       # fewer turns than teams
+def test_cut_frames_bit_exact(N, M, F):
+    dev = _dev()
+    x = _bytes(N, M, F, N + 7 * M + F)
+    want = oracle.flag(x, M, N, 3.0, 0.02)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    s1 = torch.full((F, N), -1, dtype=torch.int32, device=dev)
+    s2 = torch.full_like(s1, -1)
+    q = torch.full((F,), -1, dtype=torch.int64, device=dev)
+    skv = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+    ne = torch.full((F,), -1, dtype=torch.int32, device=dev)
+    mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.02)
+    try:
+        for _ in range(3):   # the scratch is left zero for the next launch
+            sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
+            sk.sk_flag(plan, d_in, F, None, mask)
+            torch.cuda.synchronize()
+            assert np.array_equal(s1.cpu().numpy(), want["S1"])
+            assert np.array_equal(s2.cpu().numpy(), want["S2"])
+            assert np.array_equal(q.cpu().numpy(), want["Q"])
+            assert np.array_equal(ne.cpu().numpy(), want["neff"])
+            assert np.array_equal(skv.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32))
+            assert np.array_equal(mask.cpu().numpy(), want["mask"])
+        # per-input estimates on the same cut frames
+        wi = oracle.flag_inputs(x, M, N, 3.0, 0.02)
+        sk_in = torch.empty((F, N), dtype=torch.float32, device=dev)
+        m_in = torch.empty((F, N), dtype=torch.uint8, device=dev)
+        sk.sk_compute_inputs(plan, d_in, F, sk_in, m_in)
+        torch.cuda.synchronize()
+        assert np.array_equal(sk_in.cpu().numpy().view(np.uint32), wi["sk_in"].view(np.uint32))
+        assert np.array_equal(m_in.cpu().numpy(), wi["mask_in"])
+    finally:
+        sk.sk_plan_destroy(plan)
+
+
+def test_one_plan_on_two_streams():
+    """Launches of one plan on two streams take turns on the scratch."""
+    dev = _dev()
+    N, M = 2048, 128
+    xs = [_bytes(N, M, F, 100 + F) for F in (301, 97, 450)]
+    wants = [oracle.flag(x, M, N, 2.5, 0.0)["mask"] for x in xs]
+    d_ins = [torch.from_numpy(x.reshape(-1)).to(dev) for x in xs]
+    streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+    plan = sk.sk_plan_create(N, M, 2.5, 0.0)
+    try:
+        masks = [torch.full((x.shape[0],), 7, dtype=torch.uint8, device=dev) for x in xs]
+        for rep in range(4):
+            for k, (d_in, m) in enumerate(zip(d_ins, masks)):
+                sk.sk_flag(plan, d_in, xs[k].shape[0], None, m, streams[(k + rep) % 2])
+        torch.cuda.synchronize()
+        for m, w in zip(masks, wants):
+            assert np.array_equal(m.cpu().numpy(), w)
+    finally:
+        sk.sk_plan_destroy(plan)
+
+
+def test_captured_launch_hands_out_whole_frames():
+    """A launch captured into a CUDA graph does not use the scratch; the replayed
+    graph and the plain launch give the oracle's results."""
+    dev = _dev()
+    N, M, F = 2048, 256, 299
+    x = _bytes(N, M, F, 5)
+    want = oracle.flag(x, M, N, 3.0, 0.0)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.0)
+    try:
+        m0 = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+        sk.sk_flag(plan, d_in, F, None, m0)      # plain launch: allocates the scratch
+        torch.cuda.synchronize()
+        m1 = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+        sk1 = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            sk.sk_flag(plan, d_in, F, sk1, m1, torch.cuda.current_stream())
+        for _ in range(2):
+            m1.fill_(7)
+            g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(m0.cpu().numpy(), want["mask"])
+        assert np.array_equal(m1.cpu().numpy(), want["mask"])
+        assert np.array_equal(sk1.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32))
+    finally:
+        sk.sk_plan_destroy(plan)
+
+
+def test_no_alloc_call_before_and_after_scratch():
+    """The no-allocation call balances rows only once the plan has its scratch
+    from an earlier call; either way its results are the oracle's."""
+    _dev()
+    N, M, F = 2048, 256, 31
+    x = _bytes(N, M, F, 11)
+    want = oracle.flag(x, M, N, 3.0, 0.0)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.0)
+    try:
+        for _ in range(2):   # first without scratch, then with the scratch of sk_flag_host
+            h_sk = np.full(F, -1.0, dtype=np.float32)
+            h_mask = np.full(F, 7, dtype=np.uint8)
+            sk.sk_flag_host_noalloc(plan, x, F, h_sk, h_mask)
+            assert np.array_equal(h_mask, want["mask"])
+            assert np.array_equal(h_sk.view(np.uint32), want["sk"].view(np.uint32))
+            sk.sk_flag_host(plan, x, F, np.zeros(F, dtype=np.float32), np.zeros(F, dtype=np.uint8))
+    finally:
+        sk.sk_plan_destroy(plan)

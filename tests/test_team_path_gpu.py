@@ -1,7 +1,8 @@
-"""The team path (one barrier per frame) that SK_WARP_SLICE=0 selects for one-item
-launches, against the oracle: the parity cases of the time-major vector path and
-of the grouped input-major path run again in a child process with the switch set
-(it is read once per process)."""
+"""The paths that switches select for one-item launches, against the oracle: the
+team path (one barrier per frame, SK_WARP_SLICE=0) and the warp-slice path
+handing out whole frames (SK_ROW_BALANCE=0).  The parity cases of the time-major
+vector path and of the grouped input-major path run again in a child process
+with the switch set (switches are read once per process)."""
 
 import os
 import subprocess
@@ -14,11 +15,12 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def test_team_path_parity():
+@pytest.mark.parametrize("switch", ["SK_WARP_SLICE", "SK_ROW_BALANCE"])
+def test_switched_path_parity(switch):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    env = dict(os.environ, SK_WARP_SLICE="0")
+    env = dict(os.environ, **{switch: "0"})
     sel = ("fast_path_shapes or input_major_fast_path or input_major_maximum "
            "or full_array_workload_sampled or full_array_input_major_sampled")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu",
