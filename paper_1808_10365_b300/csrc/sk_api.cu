@@ -234,9 +234,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     Item im = single;  // the same item with the input-major team size
     im.team_log2 = single.imajor_team_log2;
     if constexpr (CH > 0) {
-        if (single.fast == 2 && single.M == 16 * G * CH * SPLIT && im.team_log2 >= 5)
+        if (single.fast == 2 && single.M == 16 * G * CH * SPLIT && im.team_log2 >= 5) {
+            // balanced rows only where they pay: at M = 512 .. 2048 the path's
+            // registers spill (measured 12 % slower than whole frames)
+            if constexpr (CH <= 2 || SPLIT == 8) {
+                if (single.rb) {
+                    run_imajor_rb<G, CH, PF, SPLIT>(im, lb, ts);
+                    return;
+                }
+            }
             run_imajor_grouped<G, CH, PF, SPLIT>(im, fb, fe, lb, ts, parity);
-        else
+        } else
             run_general<false, false>(single, fb, fe, lb, ts, parity);
     } else {
         if (single.fast == 2 && single.M % (16 * G) == 0 && im.team_log2 >= 5)
@@ -508,12 +516,26 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     int64_t g = std::min<int64_t>(gmax, (it.n_frames + T - 1) / T);
     std::unique_lock<std::mutex> lk;
     bool rb = false;
-    if (run.wi && it.fast == 1 && plan && row_balance_on()) {
-        const int64_t turns = it.n_frames * (it.M / 32);
-        const int64_t grb = std::max<int64_t>(1, std::min<int64_t>(gmax, turns / T));
-        const int64_t K = grb * T;
-        const int64_t W = it.N / 256;
-        const size_t need = (size_t)K * (size_t)(2 * it.N + W) * 4 + (size_t)K * 16;
+    // time-major: 32-row turns, scratch for partial sums of cut frames; grouped
+    // input-major (sub-inputs of a frame a multiple of the team): group rows of
+    // team*M bytes, scratch for Q and N_eff of cut frames
+    int64_t units = 0;
+    size_t need = 0;
+    if (run.wi && it.fast == 1) {
+        units = it.n_frames * (it.M / 32);
+        const int64_t K = std::max<int64_t>(1, std::min<int64_t>(gmax, units / T)) * T;
+        need = (size_t)K * (size_t)(2 * it.N + it.N / 256) * 4 + (size_t)K * 16;
+    } else if (run.wi && it.fast == 2 && imajor_shape(it.M) >= 0 &&
+               (it.M <= 256 || it.M == 4096)) {
+        const int64_t split = it.M >= 1024 ? it.M / 512 : 1;
+        if ((it.N * split) % (kThreads / T) == 0 &&
+            it.n_frames * (it.N * split / (kThreads / T)) < (int64_t)1 << 31) {
+            units = it.n_frames * (it.N * split / (kThreads / T));
+            need = (size_t)std::max<int64_t>(1, std::min<int64_t>(gmax, units / T)) * T * 16;
+        }
+    }
+    if (units > 0 && plan && row_balance_on()) {
+        const int64_t grb = std::max<int64_t>(1, std::min<int64_t>(gmax, units / T));
         lk = std::unique_lock<std::mutex>(plan->rb_mu);
         run.rb = rb_acquire(plan, st, need, may_alloc);
         if (run.rb) {

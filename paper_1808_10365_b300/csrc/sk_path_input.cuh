@@ -233,6 +233,60 @@ __device__ __forceinline__ void group_batches(uint4 (&cur)[KB], uint4 (&nxt)[KB]
     }
 }
 
+// The sums of a segment's group once its chunks are read (the balanced path; the
+// grouped path spells the same steps out, which ptxas allocates with fewer
+// spills in the batched kernels): a reduce-scatter over
+// the G lanes leaves input j's S1, S2 in lane j (the sub-inputs of an input are
+// added), and lane j adds its input's term (Eq. normedSum2) to q, cnt and writes
+// the per-input outputs the item asks for.  i0 is the group's first sub-input in
+// the frame, M the sub-input length.
+template <int G, int SPLIT>
+__device__ __forceinline__ void group_terms(const Item &it, int32_t (&s1)[G], int32_t (&s2)[G],
+                                            int j, int live, int64_t frame, int i0, int M,
+                                            int64_t &q, int32_t &cnt)
+{
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        const bool up = (j & o) != 0;
+#pragma unroll
+        for (int t = 0; t < o; ++t) {
+            const int32_t send1 = up ? s1[t] : s1[t + o];
+            const int32_t send2 = up ? s2[t] : s2[t + o];
+            const int32_t keep1 = up ? s1[t + o] : s1[t];
+            const int32_t keep2 = up ? s2[t + o] : s2[t];
+            s1[t] = keep1 + __shfl_xor_sync(0xFFFFFFFFu, send1, o);
+            s2[t] = keep2 + __shfl_xor_sync(0xFFFFFFFFu, send2, o);
+        }
+    }
+    // an input's sub-inputs sit in lanes j .. j + SPLIT - 1 (j % SPLIT == 0)
+#pragma unroll
+    for (int o = 1; o < SPLIT; o <<= 1) {
+        s1[0] += __shfl_xor_sync(0xFFFFFFFFu, s1[0], o);
+        s2[0] += __shfl_xor_sync(0xFFFFFFFFu, s2[0], o);
+    }
+    if (j < live && j % SPLIT == 0) {
+        const int i = (i0 + j) / SPLIT;
+        float r = 0.0f;
+        int64_t qi = 0;
+        const bool has = SK_EPILOGUE_ALU ? input_term_alu(s1[0], s2[0], M * SPLIT, r, qi)
+                                         : input_term(s1[0], s2[0], M * SPLIT, r, qi);
+        if (has) {
+            q += qi;
+            cnt += 1;
+        }
+        const int64_t o = frame * it.N + i;
+        if (it.s1) {
+            it.s1[o] = s1[0];
+            it.s2[o] = s2[0];
+        }
+        if (it.sk_in) {
+            it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
+            if (it.mask_in)
+                it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+        }
+    }
+}
+
 // Input-major path with grouped inputs: layout [frame][input][t] with
 // M = 16 G CH.  A segment of G lanes owns a group of G consecutive inputs; lane
 // j reads the 16-byte chunks j, j+G, ..., j+(CH-1)G of each of them (one warp
@@ -391,6 +445,108 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
         }
         parity ^= 1;
         frame += T;
+    }
+}
+
+// The grouped input-major path with rows balanced over the grid (one-item
+// launches given the plan's scratch, teams of two or more warps whose sub-inputs
+// divide a frame's).  A group row is one group per segment of a team, team*M
+// consecutive bytes, and the input is one sequence of TT = F*NG group rows (NG
+// per frame).  Team k of the grid's K teams takes the group rows
+// [TT*k/K, TT*(k+1)/K), and each of its warps runs its segments' groups of those
+// rows.  A group holds whole inputs, so a frame that a range boundary cuts needs
+// only its Q and N_eff combined: every warp adds its part into the frame's slot in
+// the scratch and counts its group rows, and the warp that brings the count to NG
+// times the team's warps writes the frame and zeroes the slot.  Frames inside the
+// range go through the team's slot ring.  Scratch layout for K teams: uint64 Q[K],
+// int32 cnt[K], int32 rows[K]; the slot of a cut frame is the index of the first
+// team boundary inside it.
+template <int G, int CH, bool PF, int SPLIT = 1>
+__device__ __forceinline__ void run_imajor_rb(const Item &it, uint32_t lb, TeamSmem &ts)
+{
+    static_assert(SPLIT >= 1 && G % SPLIT == 0, "sub-inputs of one input share a group");
+    constexpr int M = 16 * G * CH;
+    constexpr int NB = (G * CH / 8) < 2 ? 2 : G * CH / 8;  // batches per group
+    constexpr int KB = G * CH / NB;                       // chunks per batch
+    static_assert(KB * NB == G * CH && NB % 2 == 0, "batch shape");
+    // 32-bit counters (the host keeps TT below 2^31): fewer live registers beside
+    // the two register batches
+    const int team_log2 = it.team_log2;
+    const int team = 1 << team_log2;
+    const int T = kThreads >> team_log2;
+    const int team_idx = threadIdx.x >> team_log2;
+    const int lit = threadIdx.x & (team - 1);
+    const int nseg = team / G;
+    const int seg = lit / G, j = lit % G;
+    const int NG = it.N * SPLIT / team;  // group rows per frame
+    const int TT = (int)it.n_frames * NG;
+    const int K = (int)gridDim.x * T;
+    const int kt = (int)blockIdx.x * T + team_idx;
+    const int u0 = (int)((int64_t)TT * kt / K), u1 = (int)((int64_t)TT * (kt + 1) / K);
+    const int64_t step = (int64_t)team * M;  // bytes per group row
+    const uint8_t *cur = it.in + (int64_t)u0 * step + seg * G * M + j * 16;
+
+    uint4 A[KB], B[KB];
+    if (u0 < u1)
+        load_group_batch<M, G, CH, KB, 0>(A, cur, G);
+    int64_t q = 0;
+    int32_t cnt = 0;
+    int frame = u0 / NG, ku = u0 % NG;  // the group row's frame and row in it
+    int ku0 = ku;                       // first row of the current frame part
+    int kk = 0;                         // whole frames this team has committed
+    for (int u = u0; u < u1; ++u) {
+        const bool more = u + 1 < u1;
+        const uint8_t *nxt = more ? cur + step : cur;
+        if (PF && more && j == 0)
+            prefetch_l2(nxt, (uint32_t)(G * M));
+        int32_t s1[G], s2[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) {
+            s1[t] = 0;
+            s2[t] = 0;
+        }
+        group_batches<M, G, CH, NB, KB, 0>(A, B, cur, G, nxt, more ? G : 0, lb, s1, s2);
+        group_terms<G, SPLIT>(it, s1, s2, j, G, frame, (ku * nseg + seg) * G, M, q, cnt);
+        cur = nxt;
+        ++ku;
+        const bool fend = ku == NG;
+        if (!fend && more)
+            continue;
+        for (int o = 16; o > 0; o >>= 1) {
+            q += __shfl_xor_sync(0xFFFFFFFFu, q, o);
+            cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+        }
+        const int W = team >> 5;
+        if (fend && ku0 == 0) {
+            if ((lit & 31) == 0)
+                wi_commit(it, ts.wi[team_idx], kk, W, frame, q, cnt);
+            ++kk;
+        } else if ((lit & 31) == 0) {
+            // part of a cut frame: the warp's Q, N_eff and group rows into the slot
+            unsigned long long *pq = reinterpret_cast<unsigned long long *>(it.rb);
+            int32_t *pcnt = reinterpret_cast<int32_t *>(pq + K);
+            int32_t *prow = pcnt + K;
+            const int64_t slot = (((int64_t)frame * NG + 1) * K + TT - 1) / TT;
+            atomicAdd(pq + slot, (unsigned long long)q);
+            atomicAdd(pcnt + slot, cnt);
+            __threadfence();
+            const int part = ku - ku0;
+            if (atomicAdd(prow + slot, part) + part == NG * W) {
+                __threadfence();
+                const int64_t Q = (int64_t)atomicExch(pq + slot, 0ull);
+                const int32_t C = atomicExch(pcnt + slot, 0);
+                atomicExch(prow + slot, 0);
+                write_frame(it, frame, Q, C);
+            }
+        }
+        __syncwarp();
+        q = 0;
+        cnt = 0;
+        if (fend) {
+            ku = 0;
+            ++frame;
+        }
+        ku0 = ku;
     }
 }
 

@@ -1,6 +1,7 @@
 """Row-balanced launches: a one-item time-major launch of the warp-slice shapes
-hands every team an equal range of 32-row turns, and frames cut by a range
-boundary are combined through the plan's scratch in device memory.  Against the
+hands every team an equal range of 32-row turns (an input-major one, of group
+rows), and frames cut by a range boundary are combined through the plan's
+scratch in device memory.  Against the
 oracle: cut frames of every kind (a frame shared by two teams, a frame spread
 over many teams, a team inside one frame), per-input outputs written by the
 warp that completes a column, one plan on two streams, a captured launch (which
@@ -33,18 +34,25 @@ def _bytes(N, M, F, seed):
     return x
 
 
-@pytest.mark.parametrize("N,M,F", [
-    (2048, 256, 299),    # 299 frames over 296 teams: most frames cut in two
-    (2048, 1024, 37),    # frames spread over 8 teams each
-    (4096, 4096, 3),     # 384 turns over 148 teams: several teams inside a frame
-    (512, 4096, 5),      # 640 turns over 640 two-warp teams: one turn each
-    (1024, 32, 3001),    # one turn per frame
-    (4096, 96, 150),     # 3 turns per frame
-    (512, 64, 1)])       # fewer turns than teams
-def test_cut_frames_bit_exact(N, M, F):
+@pytest.mark.parametrize("N,M,F,layout", [
+    (2048, 256, 299, 0),    # 299 frames over 296 teams: most frames cut in two
+    (2048, 1024, 37, 0),    # frames spread over 8 teams each
+    (4096, 4096, 3, 0),     # 384 turns over 148 teams: several teams inside a frame
+    (512, 4096, 5, 0),      # 640 turns over 640 two-warp teams: one turn each
+    (1024, 32, 3001, 0),    # one turn per frame
+    (4096, 96, 150, 0),     # 3 turns per frame
+    (512, 64, 1, 0),        # fewer turns than teams
+    # input-major: group rows of team*M bytes balanced over the grid (M = 128,
+    # 256 and 4096; other M hand out whole frames)
+    (2048, 256, 299, 1),    # 8 group rows per frame
+    (2048, 4096, 3, 1),     # sub-inputs: 8 per input
+    (4096, 128, 150, 1),
+    (512, 1024, 37, 1),
+    (256, 512, 7, 1)])
+def test_cut_frames_bit_exact(N, M, F, layout):
     dev = _dev()
     x = _bytes(N, M, F, N + 7 * M + F)
-    want = oracle.flag(x, M, N, 3.0, 0.02)
+    want = oracle.flag(x, M, N, 3.0, 0.02, layout=layout)
     d_in = torch.from_numpy(x.reshape(-1)).to(dev)
     s1 = torch.full((F, N), -1, dtype=torch.int32, device=dev)
     s2 = torch.full_like(s1, -1)
@@ -52,7 +60,7 @@ def test_cut_frames_bit_exact(N, M, F):
     skv = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
     ne = torch.full((F,), -1, dtype=torch.int32, device=dev)
     mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
-    plan = sk.sk_plan_create(N, M, 3.0, 0.02)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.02, layout=layout)
     try:
         for _ in range(3):   # the scratch is left zero for the next launch
             sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
@@ -65,7 +73,7 @@ def test_cut_frames_bit_exact(N, M, F):
             assert np.array_equal(skv.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32))
             assert np.array_equal(mask.cpu().numpy(), want["mask"])
         # per-input estimates on the same cut frames
-        wi = oracle.flag_inputs(x, M, N, 3.0, 0.02)
+        wi = oracle.flag_inputs(x, M, N, 3.0, 0.02, layout=layout)
         sk_in = torch.empty((F, N), dtype=torch.float32, device=dev)
         m_in = torch.empty((F, N), dtype=torch.uint8, device=dev)
         sk.sk_compute_inputs(plan, d_in, F, sk_in, m_in)
