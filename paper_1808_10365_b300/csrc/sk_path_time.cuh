@@ -343,7 +343,7 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
 // rows forms that column's terms, and the warp that completes the last column
 // writes the frame.  Whoever reads a scratch word back leaves it zero, so the
 // scratch is all zero before and after every launch.  Scratch layout for K teams
-// of W warps: int32 S[K][2][N], int32 turns[K][W], uint64 Q[K], int32 cnt[K],
+// of W warps: uint64 S2:S1[K][N], int32 turns[K][W], uint64 Q[K], int32 cnt[K],
 // int32 arrive[K]; the slot of a cut frame is the index of the first team boundary
 // inside it.
 template <int R, int S, int NC>
@@ -367,8 +367,8 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
     const int64_t K = (int64_t)gridDim.x * T;
     const int64_t kt = (int64_t)blockIdx.x * T + team_idx;
     const int64_t t0 = TT * kt / K, t1 = TT * (kt + 1) / K;
-    int32_t *const ps = it.rb;
-    int32_t *const pturn = ps + 2 * K * N;
+    unsigned long long *const ps = reinterpret_cast<unsigned long long *>(it.rb);
+    int32_t *const pturn = reinterpret_cast<int32_t *>(ps + K * N);
     unsigned long long *const pq = reinterpret_cast<unsigned long long *>(pturn + K * W);
     int32_t *const pcnt = reinterpret_cast<int32_t *>(pq + K);
     int32_t *const parr = pcnt + K;
@@ -430,29 +430,35 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
             __syncwarp();
             ++kk;
         } else {
-            // part of a cut frame: add the column's sums into the frame's slot
+            // part of a cut frame: add the column's sums into the frame's slot, S2 in
+            // the high and S1 in the low half of one word per input (S1 <= 2^19 and
+            // S2 <= 2^26 for M <= 4096, so the halves never carry into each other)
             const int64_t slot = ((frame * tpf + 1) * K + TT - 1) / TT;
-            int32_t *sp = ps + slot * 2 * N + col0;
+            unsigned long long *sp = ps + slot * N + col0;
 #pragma unroll
-            for (int k = 0; k < kVec; ++k) {
-                atomicAdd(sp + k, s1[k]);
-                atomicAdd(sp + N + k, s2[k]);
-            }
-            __threadfence();
+            for (int k = 0; k < kVec; ++k)
+                atomicAdd(sp + k, ((unsigned long long)(uint32_t)s2[k] << 32) | (uint32_t)s1[k]);
             __syncwarp();
             int fin = 0;
             if (lane == 0) {
+                // one fence for the warp: it orders the lanes' adds, which the
+                // __syncwarp put before it, ahead of the count
+                __threadfence();
                 const int part = (int)(g + 1 - seg0);
                 fin = atomicAdd(pturn + slot * W + c, part) + part == (int)tpf;
+                if (fin)
+                    __threadfence();
             }
             fin = __shfl_sync(0xFFFFFFFFu, fin, 0);
             if (fin) {
                 // this warp completed the column: its totals, and the slot words zero
-                __threadfence();
+                // (the __syncwarp orders the lanes' reads after lane 0's fence)
+                __syncwarp();
 #pragma unroll
                 for (int k = 0; k < kVec; ++k) {
-                    s1[k] = atomicExch(sp + k, 0);
-                    s2[k] = atomicExch(sp + N + k, 0);
+                    const unsigned long long v = atomicExch(sp + k, 0ull);
+                    s1[k] = (int32_t)(uint32_t)v;
+                    s2[k] = (int32_t)(v >> 32);
                 }
                 int64_t q;
                 int32_t cnt;
