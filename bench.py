@@ -623,7 +623,9 @@ def run_gpu(args):
                                     else ", warp-slice path"))
                                 if layout == 0 else "sk_imajor_kernel<8,2,1,0,1>"),
                      "algorithmic_bytes_per_launch": alg_bytes,
-                     "mean_launch_ms": mean_launch_s * 1e3},
+                     "mean_launch_ms": mean_launch_s * 1e3,
+                     "launch_ms_min_median_max": [min(launch_ms), statistics.median(launch_ms),
+                                                  max(launch_ms)]},
         "e2e": line_tail["e2e"],
         "gpu_launches": args.steps,
         "clocks": clocks,

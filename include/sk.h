@@ -167,6 +167,19 @@ sk_status_t sk_compute(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
                        float *d_sk, int32_t *d_neff, sk_cuda_stream_t stream);
 
 /*
+ * Scratch of the device calls (sk_compute, sk_flag, sk_compute_inputs and
+ * the chunks of sk_flag_host).  Time-major plans of N = 512, 1024, 2048 or
+ * 4096 with M % 32 == 0, and input-major plans of M = 128, 256 or 4096, give
+ * every team of the launch an equal share of rows; frames cut between teams
+ * are combined in a scratch of the plan (about 5 MB time-major, a few KB
+ * input-major) that every launch leaves zero.  The first such call that is
+ * not being captured into a graph allocates it; a call that cannot allocate
+ * it, or is being captured, hands out whole frames instead (same results).
+ * Calls of one plan on two streams take turns on the scratch: the later one
+ * waits, on the device, for the earlier one.  SK_ROW_BALANCE=0 turns it off.
+ */
+
+/*
  * Fused compute + threshold: mask[f] = 1 when Q lies above T_hi[neff] or
  * below T_lo[neff] (SK~ strictly outside the centre +- a*sigma interval,
  * Sec. 3.2) or neff = 0.  d_sk may be NULL.  Same rules as sk_compute.
