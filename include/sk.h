@@ -395,6 +395,18 @@ sk_status_t sk_server_replay(sk_server_t server, const sk_replay_t *replay,
  */
 sk_status_t sk_digitisation_offset(double sigma, double *delta);
 
+/*
+ * Self-test on `device` of the exact conversions the kernels use instead of
+ * the int64 <-> fp32 conversion instructions (the input term of Eqs.
+ * discreteMean and normedSum2 with M S2 - S1^2 exact in int64 and one fp32
+ * divide): each is compared bit for bit with CUDA's conversion intrinsics on
+ * every non-negative fp32 below 2^62, on every halfway case below 2^43 and its
+ * neighbours, and on hashed samples of int64 values and of (S1, S2, M).
+ * *n_checked gets the number of cases, *n_bad the mismatches (0 expected).
+ * Takes about a second.  Errors: INVALID_ARG (NULL output), CUDA.
+ */
+sk_status_t sk_selftest_conversions(int device, int64_t *n_checked, int64_t *n_bad);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char *sk_last_error(void);
 

@@ -49,7 +49,7 @@ EXPORTED = [
     "sk_ticket_wait",
     "sk_stream_drain", "sk_stream_get_state", "sk_stream_set_state", "sk_stream_close",
     "sk_server_stats", "sk_stream_stats", "sk_server_replay", "sk_digitisation_offset",
-    "sk_last_error",
+    "sk_selftest_conversions", "sk_last_error",
 ]
 
 
@@ -146,6 +146,7 @@ def library():
         "sk_stream_stats": [P, I32, ctypes.POINTER(sk_stream_stats_t)],
         "sk_server_replay": [P, ctypes.POINTER(sk_replay_t), ctypes.POINTER(sk_replay_result_t)],
         "sk_digitisation_offset": [ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
+        "sk_selftest_conversions": [ctypes.c_int, ctypes.POINTER(I64), ctypes.POINTER(I64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -476,6 +477,15 @@ def sk_digitisation_offset(sigma) -> float:
     d = ctypes.c_double()
     _check(library().sk_digitisation_offset(float(sigma), ctypes.byref(d)))
     return d.value
+
+
+def sk_selftest_conversions(device: int = 0):
+    """(cases checked, mismatches) of the kernels' exact conversions against CUDA's
+    conversion intrinsics on `device`."""
+    n = ctypes.c_int64()
+    bad = ctypes.c_int64()
+    _check(library().sk_selftest_conversions(int(device), ctypes.byref(n), ctypes.byref(bad)))
+    return n.value, bad.value
 
 
 def sk_last_error() -> str:

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsk.so")
-SOURCES = ["sk_api.cu", "sk_batch.cu", "sk_server.cu", "sk_noalloc.cu"]
+SOURCES = ["sk_api.cu", "sk_batch.cu", "sk_server.cu", "sk_noalloc.cu", "sk_selftest.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

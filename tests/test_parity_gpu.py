@@ -72,6 +72,17 @@ def assert_parity(got, want, check_sums=True):
     assert np.all(np.isnan(got["sk"][~ok]))
 
 
+def test_exact_conversions_match_cuda_intrinsics():
+    """The epilogue's own int64 -> fp32 and fp32 -> int64 roundings (and the input
+    term built on them) agree bit for bit with CUDA's conversion intrinsics: every
+    non-negative fp32 below 2^62, every halfway case below 2^43 with its
+    neighbours, and hashed samples."""
+    _dev()
+    n, bad = sk.sk_selftest_conversions(0)
+    assert n == 0x5E800000 + (1 << 25) + 19 * (1 << 23) * 3 + (1 << 28) + (1 << 26)
+    assert bad == 0
+
+
 def test_pathfinder_workload_bit_exact():
     """N=256, M=256, 64 frames, CW frames 10-19, 50 % pulse frames 40-44, 3 sigma."""
     ds = synth.pathfinder_config()
