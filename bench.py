@@ -625,7 +625,15 @@ def run_gpu(args):
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": mean_launch_s * 1e3,
                      "launch_ms_min_median_max": [min(launch_ms), statistics.median(launch_ms),
-                                                  max(launch_ms)]},
+                                                  max(launch_ms)],
+                     # medians of the four quarters of the timed launches: after about
+                     # 70 ms of back-to-back streaming the launches settle about 6 %
+                     # slower (sw_power_cap), which the mean includes
+                     "launch_ms_quarter_medians": [
+                         statistics.median(launch_ms[q * len(launch_ms) // 4:
+                                                     max((q + 1) * len(launch_ms) // 4,
+                                                         q * len(launch_ms) // 4 + 1)])
+                         for q in range(4)]},
         "e2e": line_tail["e2e"],
         "gpu_launches": args.steps,
         "clocks": clocks,
