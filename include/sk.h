@@ -167,6 +167,24 @@ sk_status_t sk_compute(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
                        float *d_sk, int32_t *d_neff, sk_cuda_stream_t stream);
 
 /*
+ * Input sharding: the inputs of one frequency split over several devices.  Each
+ * device holds its own inputs' bytes as a contiguous array of n_frames frames
+ * (its own N and M, in a plan of its own), and sk_compute gives its per-frame Q
+ * and neff.  The per-input terms of Eq. final do not depend on the other
+ * inputs, so the frame's Q and N_eff are the exact int64 / int32 sums of the
+ * shards' values; once they are summed (one all-reduce of 12 bytes a frame),
+ * sk_finish forms SK and the mask with the plan of the whole array (its N is
+ * the total).  The result is bit-identical to sk_flag on the whole array.
+ * d_q [n_frames] int64 and d_neff [n_frames] int32 are required, d_sk may be
+ * NULL, d_mask is required.  A neff outside 0..N gives mask 1 and SK NaN.
+ * Errors: INVALID_ARG, UNSUPPORTED (plans with SK_RUNNING_OFFSET or
+ * SK_RUNNING_MU: their state belongs to served streams), CUDA.
+ */
+sk_status_t sk_finish(sk_plan_t plan, const int64_t *d_q, const int32_t *d_neff,
+                      int64_t n_frames, float *d_sk, uint8_t *d_mask,
+                      sk_cuda_stream_t stream);
+
+/*
  * Scratch of the device calls (sk_compute, sk_flag, sk_compute_inputs and
  * the chunks of sk_flag_host).  Time-major plans of N = 512, 1024, 2048 or
  * 4096 with M % 32 == 0, and input-major plans of M = 128, 256 or 4096, give

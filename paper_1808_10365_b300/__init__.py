@@ -43,7 +43,7 @@ SK_NOALLOC_MAX_FRAMES = 65536
 EXPORTED = [
     "sk_plan_create", "sk_plan_destroy", "sk_plan_thresholds", "sk_plan_offset_table",
     "sk_plan_set_tiles", "sk_plan_get_tiles", "sk_compute", "sk_flag", "sk_flag_host",
-    "sk_flag_host_noalloc", "sk_compute_inputs",
+    "sk_flag_host_noalloc", "sk_compute_inputs", "sk_finish",
     "sk_batch_create", "sk_batch_run", "sk_batch_destroy", "sk_server_create",
     "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_stream_submit_ref",
     "sk_ticket_wait",
@@ -147,6 +147,7 @@ def library():
         "sk_server_replay": [P, ctypes.POINTER(sk_replay_t), ctypes.POINTER(sk_replay_result_t)],
         "sk_digitisation_offset": [ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
         "sk_selftest_conversions": [ctypes.c_int, ctypes.POINTER(I64), ctypes.POINTER(I64)],
+        "sk_finish": [P, P, P, I64, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -313,6 +314,18 @@ def sk_flag(plan, d_in, n_frames, sk, mask, stream=None):
     _check(library().sk_flag(plan, _buf(d_in, b_in, "device", "d_in"), F,
                              _buf(sk, b_sk, "device", "sk"), _buf(mask, b_m, "device", "mask"),
                              _stream(stream)))
+
+
+def sk_finish(plan, d_q, d_neff, n_frames, sk, mask, stream=None):
+    """SK and mask per frame from Q and neff summed over input shards, with the
+    whole array's plan (input sharding; see sharding.py)."""
+    F = int(n_frames)
+    b_q, b_n, b_sk, b_m = _sizes(_plan_shape.get(plan), F, [
+        lambda N, M: 8, lambda N, M: 4, lambda N, M: 4, lambda N, M: 1])
+    _check(library().sk_finish(plan, _buf(d_q, b_q, "device", "q"),
+                               _buf(d_neff, b_n, "device", "neff"), F,
+                               _buf(sk, b_sk, "device", "sk"), _buf(mask, b_m, "device", "mask"),
+                               _stream(stream)))
 
 
 def _host_call(fn, plan, h_in, n_frames, h_sk, h_mask, stream):

@@ -994,6 +994,61 @@ extern "C" sk_status_t sk_flag(sk_plan_t plan, const uint8_t *d_in, int64_t n_fr
                          plan->grid_ctas, plan);
 }
 
+namespace sk {
+
+// Per frame: SK and the mask from a frame's Q and N_eff summed over input shards
+// (write_frame: Sec. 3.2 test against the plan's integer thresholds, Eq. final).
+// An N_eff outside 0..N cannot come from shards of this plan's inputs: mask 1,
+// SK NaN.
+__global__ void finish_kernel(const int64_t *__restrict__ q, const int32_t *__restrict__ neff,
+                              int64_t n_frames, Item it)
+{
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < n_frames;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t C = neff[f];
+        if (C < 0 || C > it.N) {
+            if (it.sk)
+                it.sk[f] = __int_as_float(0x7FC00000);
+            if (it.mask)
+                it.mask[f] = 1;
+            continue;
+        }
+        write_frame(it, f, q[f], C);
+    }
+}
+
+}  // namespace sk
+
+extern "C" sk_status_t sk_finish(sk_plan_t plan, const int64_t *d_q, const int32_t *d_neff,
+                                 int64_t n_frames, float *d_sk, uint8_t *d_mask,
+                                 sk_cuda_stream_t stream)
+{
+    if (!plan)
+        return set_error(SK_ERR_INVALID_ARG, "sk_finish: plan is NULL");
+    if (sk_status_t f = pending_fault(plan, "sk_finish"))
+        return f;
+    if (n_frames < 0)
+        return set_error(SK_ERR_INVALID_ARG, "sk_finish: n_frames < 0");
+    if (n_frames > 0 && (!d_q || !d_neff || !d_mask))
+        return set_error(SK_ERR_INVALID_ARG, "sk_finish: q, neff and mask are required");
+    if (plan->p.flags & (SK_RUNNING_OFFSET | SK_RUNNING_MU))
+        return set_error(SK_ERR_UNSUPPORTED,
+                         "sk_finish: running state belongs to served streams, not to shards");
+    if (n_frames == 0)
+        return SK_OK;
+    Item it = plan->item(nullptr, n_frames);
+    it.sk = d_sk;
+    it.mask = d_mask;
+    DeviceGuard dg(plan->device);
+    const int64_t blocks =
+        std::min<int64_t>((n_frames + 255) / 256, (int64_t)sm_count(plan->device) * 8);
+    finish_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(d_q, d_neff, n_frames, it);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_error(e, "sk_finish launch");
+    return SK_OK;
+}
+
 extern "C" sk_status_t sk_compute_inputs(sk_plan_t plan, const uint8_t *d_in,
                                          int64_t n_frames, float *d_sk_in, uint8_t *d_mask_in,
                                          float *d_sk, uint8_t *d_mask, sk_cuda_stream_t stream)

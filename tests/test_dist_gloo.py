@@ -1,6 +1,8 @@
-"""Multi-rank host logic of bench.py on CPU (gloo, world size 2): barrier,
-max-over-ranks timing, and per-rank frequency sharding (independent seeds, no
-data-path collective)."""
+"""Multi-rank host logic on CPU (gloo, world size 2): bench.py's barrier,
+max-over-ranks timing and per-rank frequency sharding (independent seeds, no
+data-path collective), and the input-sharding exchange (exact integer sums of
+the ranks' per-frame Q and N_eff) checked against the oracle on the whole
+array."""
 
 import os
 import socket
@@ -79,3 +81,52 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert line["impl"] == "reference" and line["n_gpus"] == 2
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def _shard_worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    import numpy as np
+
+    import oracle
+    from paper_1808_10365_b300 import sharding
+
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        N, M, F = 96, 64, 23
+        rng = np.random.default_rng(4242)           # every rank draws the whole array
+        x = rng.integers(0, 256, size=(F, M, N), dtype=np.uint8)
+        x[3, :, :40] = 0x88                          # dead inputs, both shards
+        bounds = [0, 40, N][rank:rank + 2]           # uneven shards: 40 and 56 inputs
+        mine = np.ascontiguousarray(x[:, :, bounds[0]:bounds[1]])
+        n_mine = bounds[1] - bounds[0]
+        S1, S2 = oracle.power_sums(mine.reshape(F, -1), M, n_mine)
+        Qr, ner, _ = oracle.sk_spec(S1, S2, M)
+        qt = torch.from_numpy(np.asarray(Qr, dtype=np.int64).copy())
+        nt = torch.from_numpy(np.asarray(ner, dtype=np.int32).copy())
+        sharding.exchange_partials(qt, nt)
+        whole = oracle.flag(x.reshape(F, -1), M, N, 3.0, 0.01)
+        m = oracle.mask(qt.numpy(), nt.numpy(), whole["t_lo"], whole["t_hi"])
+        q.put((rank, bool(np.array_equal(qt.numpy(), whole["Q"])),
+               bool(np.array_equal(nt.numpy(), whole["neff"])),
+               bool(np.array_equal(m, whole["mask"])), int(whole["neff"][3])))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_input_sharding_exchange():
+    """Two ranks hold 40 and 56 of 96 inputs; after the exchange each has the whole
+    array's Q, N_eff and mask exactly."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=240) for _ in procs]
+    for p in procs:
+        p.join(60)
+        assert p.exitcode == 0
+    for rank, q_ok, n_ok, m_ok, neff3 in out:
+        assert q_ok and n_ok and m_ok, rank
+        assert neff3 == 96 - 40
