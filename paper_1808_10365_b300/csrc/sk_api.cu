@@ -389,8 +389,9 @@ sk_status_t ensure_kernel_attrs(int device)
     return SK_OK;
 }
 
-// Shapes of the warp-slice path: a team of N/8 threads (N/8 a power of two) of at
-// least two warps, each warp a 256-column slice.  SK_WARP_SLICE=0 turns it off.
+// Shapes of the warp-slice path: N a multiple of 16 (the tensor map's row stride)
+// from 512 to 4096, a team of ceil(N/256) >= 2 warps, each warp a 256-column
+// slice.  SK_WARP_SLICE=0 turns it off.
 static bool warp_slice_on()
 {
     static const bool off = [] {
@@ -402,7 +403,7 @@ static bool warp_slice_on()
 
 bool warp_slice_shape(int N, int M)
 {
-    return warp_slice_on() && N >= 512 && (N & (N - 1)) == 0 && N <= 4096 && M % 32 == 0;
+    return warp_slice_on() && N >= 512 && N % 16 == 0 && N <= 4096 && M % 32 == 0;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -512,8 +513,10 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // input-major teams of two or more warps combine through the same slot ring
     if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6)
         run.wi = 1;
+    // teams per CTA: 16 / ceil(N/256) on the warp-slice paths
+    const int64_t Tl = (run.wi && it.fast == 1) ? (kThreads / 32) / ((it.N + 255) / 256) : T;
     // frames per team decide the grid, unless rows are balanced over the grid
-    int64_t g = std::min<int64_t>(gmax, (it.n_frames + T - 1) / T);
+    int64_t g = std::min<int64_t>(gmax, (it.n_frames + Tl - 1) / Tl);
     std::unique_lock<std::mutex> lk;
     bool rb = false;
     // time-major: 32-row turns, scratch for partial sums of cut frames; grouped
@@ -523,8 +526,9 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     size_t need = 0;
     if (run.wi && it.fast == 1) {
         units = it.n_frames * (it.M / 32);
-        const int64_t K = std::max<int64_t>(1, std::min<int64_t>(gmax, units / T)) * T;
-        need = (size_t)K * (size_t)(2 * it.N + it.N / 256) * 4 + (size_t)K * 16;
+        const int64_t K = std::max<int64_t>(1, std::min<int64_t>(gmax, units / Tl)) * Tl;
+        const int64_t W = (it.N + 255) / 256;
+        need = (size_t)K * it.N * 8 + (size_t)((K * W + 1) & ~(int64_t)1) * 4 + (size_t)K * 16;
     } else if (run.wi && it.fast == 2 && imajor_shape(it.M) >= 0 &&
                (it.M <= 256 || it.M == 4096)) {
         const int64_t split = it.M >= 1024 ? it.M / 512 : 1;
@@ -535,7 +539,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         }
     }
     if (units > 0 && plan && row_balance_on()) {
-        const int64_t grb = std::max<int64_t>(1, std::min<int64_t>(gmax, units / T));
+        const int64_t grb = std::max<int64_t>(1, std::min<int64_t>(gmax, units / Tl));
         lk = std::unique_lock<std::mutex>(plan->rb_mu);
         run.rb = rb_acquire(plan, st, need, may_alloc);
         if (run.rb) {

@@ -185,9 +185,22 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *tm)
                  : "memory");
 }
 
+// Register batches of a lane past the last input: bytes 0x88 (re = im = 0) have
+// no power, so the lane's sums stay zero and its inputs count for nothing.
+template <int S, int R>
+__device__ __forceinline__ void fill_zero_power(uint2 (&buf)[S][R])
+{
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            buf[j][r] = make_uint2(0x88888888u, 0x88888888u);
+}
+
 // The input terms (Eq. normedSum2 per input) of one lane's 8 inputs of a frame,
 // with the per-input outputs the item asks for (S1, S2, SK_i and its one-input
-// flag), and the sum over the warp of their fixed-point q_i and count.
+// flag), and the sum over the warp of their fixed-point q_i and count.  A lane
+// past the last input (its sums zero) adds nothing and writes nothing.
 __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int col0, int M,
                                             const int32_t (&s1)[kVec],
                                             const int32_t (&s2)[kVec], int64_t &q,
@@ -205,14 +218,14 @@ __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int c
             q += qi;
             cnt += 1;
         }
-        if (it.sk_in) {
+        if (it.sk_in && col0 < it.N) {
             const int64_t o = frame * it.N + col0 + k;
             it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
             if (it.mask_in)
                 it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
         }
     }
-    if (it.s1) {
+    if (it.s1 && col0 < it.N) {
         int32_t *o1 = it.s1 + frame * it.N + col0;
         int32_t *o2 = it.s2 + frame * it.N + col0;
 #pragma unroll
@@ -243,16 +256,21 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
                                             uint32_t lb, TeamSmem &ts, const CUtensorMap *tmap)
 {
     static_assert(R * S == 32, "one prefetch box per ring turn");
-    const int team_log2 = it.team_log2;
-    const int T = kThreads >> team_log2;
-    const int team_idx = threadIdx.x >> team_log2;
-    const int lit = threadIdx.x & ((1 << team_log2) - 1);
-    const int W = (1 << team_log2) >> 5;  // warps per frame
-    const int lane = threadIdx.x & 31;
-    const int xs = (lit >> 5) * 256;      // the warp's first column
-    const int col0 = lit * kVec;
     const int M = it.M;
     const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
+    // teams of W warps, one 256-column slice each (the last one partial when 256
+    // does not divide N); the CTA's last 16 - T W warps have nothing to do
+    const int W = (int)((N + 255) >> 8);
+    const int T = (kThreads / 32) / W;
+    const int warp = threadIdx.x >> 5;
+    const int team_idx = warp / W;
+    if (team_idx >= T)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int xs = (warp - team_idx * W) * 256;  // the warp's first column
+    const int col0 = xs + lane * kVec;
+    // lanes past N read nothing (none when N is a compiled multiple of 256)
+    const bool col_ok = (NC > 0 && NC % 256 == 0) || col0 < N;
     const int64_t fbytes = (int64_t)M * N;
     const int nb = M / R;
     const int64_t kmax = (f_end - f_begin + T - 1) / T;
@@ -260,6 +278,8 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     const uint8_t *const in = it.in;
 
     uint2 buf[S][R];
+    if (!col_ok)
+        fill_zero_power(buf);
     int64_t frame = f_begin + team_idx;
     bool ok = frame < f_end;
     const uint8_t *fp = in + frame * fbytes + col0;
@@ -273,7 +293,7 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
                 b[r] = ldg_stream(p + (int64_t)r * N);
         }
     };
-    if (ok) {
+    if (ok && col_ok) {
 #pragma unroll
         for (int j = 0; j < S; ++j)
             load(buf[j], fp + (int64_t)j * R * N);
@@ -312,7 +332,7 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
                     if (((j + 1) * R) % kFlushRows == 0)
                         flush(acc, s1, s2);
                 }
-                if (lok)
+                if (lok && col_ok)
                     load(buf[j], pn + (int64_t)j * R * N);
             }
         }
@@ -343,25 +363,30 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
 // rows forms that column's terms, and the warp that completes the last column
 // writes the frame.  Whoever reads a scratch word back leaves it zero, so the
 // scratch is all zero before and after every launch.  Scratch layout for K teams
-// of W warps: uint64 S2:S1[K][N], int32 turns[K][W], uint64 Q[K], int32 cnt[K],
-// int32 arrive[K]; the slot of a cut frame is the index of the first team boundary
-// inside it.
+// of W warps: uint64 S2:S1[K][N], int32 turns[K][W] (padded to an even count),
+// uint64 Q[K], int32 cnt[K], int32 arrive[K]; the slot of a cut frame is the
+// index of the first team boundary inside it.
 template <int R, int S, int NC>
 __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSmem &ts,
                                             const CUtensorMap *tmap)
 {
     static_assert(R * S == 32, "one turn per ring revolution");
-    const int team_log2 = it.team_log2;
-    const int T = kThreads >> team_log2;
-    const int team_idx = threadIdx.x >> team_log2;
-    const int lit = threadIdx.x & ((1 << team_log2) - 1);
-    const int W = (1 << team_log2) >> 5;  // warps (256-column slices) per frame
-    const int lane = threadIdx.x & 31;
-    const int c = lit >> 5;
-    const int xs = c * 256;
-    const int col0 = lit * kVec;
     const int M = it.M;
     const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
+    // teams of W warps (256-column slices, the last one partial when 256 does not
+    // divide N); the CTA's last 16 - T W warps have nothing to do
+    const int W = (int)((N + 255) >> 8);
+    const int T = (kThreads / 32) / W;
+    const int warp = threadIdx.x >> 5;
+    const int team_idx = warp / W;
+    if (team_idx >= T)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int c = warp - team_idx * W;
+    const int xs = c * 256;
+    const int col0 = xs + lane * kVec;
+    // lanes past N read and add nothing (none when N is a compiled multiple of 256)
+    const bool col_ok = (NC > 0 && NC % 256 == 0) || col0 < N;
     const int64_t tpf = M / 32;  // turns per frame
     const int64_t TT = it.n_frames * tpf;
     const int64_t K = (int64_t)gridDim.x * T;
@@ -369,7 +394,9 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
     const int64_t t0 = TT * kt / K, t1 = TT * (kt + 1) / K;
     unsigned long long *const ps = reinterpret_cast<unsigned long long *>(it.rb);
     int32_t *const pturn = reinterpret_cast<int32_t *>(ps + K * N);
-    unsigned long long *const pq = reinterpret_cast<unsigned long long *>(pturn + K * W);
+    // the turn counters padded to an even count keep the 64-bit words aligned
+    unsigned long long *const pq =
+        reinterpret_cast<unsigned long long *>(pturn + ((K * W + 1) & ~(int64_t)1));
     int32_t *const pcnt = reinterpret_cast<int32_t *>(pq + K);
     int32_t *const parr = pcnt + K;
     WiSlot *slots = ts.wi[team_idx];
@@ -386,7 +413,9 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
         }
     };
     uint2 buf[S][R];
-    if (t0 < t1) {
+    if (!col_ok)
+        fill_zero_power(buf);
+    if (t0 < t1 && col_ok) {
 #pragma unroll
         for (int j = 0; j < S; ++j)
             load(buf[j], in + (t0 * 32 + j * R) * N);
@@ -399,8 +428,10 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
         s1[j] = 0;
         s2[j] = 0;
     }
-    int64_t kk = 0;     // whole frames this team has committed
-    int64_t seg0 = t0;  // first turn of the current frame part
+    int64_t kk = 0;               // whole frames this team has committed
+    int64_t frame = t0 / tpf;     // the current turn's frame ...
+    int gf = (int)(t0 - frame * tpf);  // ... and turn in it (counters: no division per turn)
+    int gf0 = gf;                 // first turn of the current frame part
     for (int64_t g = t0; g < t1; ++g) {
         if (lane == 0 && g + 2 < t1)
             prefetch_box(tmap, xs, (int)((g + 2) * 32));  // two turns ahead
@@ -413,14 +444,14 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
                 accum_pair(buf[j][r], buf[j][r + 1], lb, acc);
             if (((j + 1) * R) % kFlushRows == 0)
                 flush(acc, s1, s2);
-            if (more)
+            if (more && col_ok)
                 load(buf[j], pn + (int64_t)j * R * N);
         }
-        const bool fend = (g + 1) % tpf == 0;
+        ++gf;
+        const bool fend = gf == (int)tpf;
         if (!fend && more)
             continue;
-        const int64_t frame = g / tpf;
-        if (fend && seg0 % tpf == 0) {
+        if (fend && gf0 == 0) {
             // a whole frame: the slice's part goes into the team's slot ring
             int64_t q;
             int32_t cnt;
@@ -435,16 +466,19 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
             // S2 <= 2^26 for M <= 4096, so the halves never carry into each other)
             const int64_t slot = ((frame * tpf + 1) * K + TT - 1) / TT;
             unsigned long long *sp = ps + slot * N + col0;
+            if (col_ok) {
 #pragma unroll
-            for (int k = 0; k < kVec; ++k)
-                atomicAdd(sp + k, ((unsigned long long)(uint32_t)s2[k] << 32) | (uint32_t)s1[k]);
+                for (int k = 0; k < kVec; ++k)
+                    atomicAdd(sp + k,
+                              ((unsigned long long)(uint32_t)s2[k] << 32) | (uint32_t)s1[k]);
+            }
             __syncwarp();
             int fin = 0;
             if (lane == 0) {
                 // one fence for the warp: it orders the lanes' adds, which the
                 // __syncwarp put before it, ahead of the count
                 __threadfence();
-                const int part = (int)(g + 1 - seg0);
+                const int part = gf - gf0;
                 fin = atomicAdd(pturn + slot * W + c, part) + part == (int)tpf;
                 if (fin)
                     __threadfence();
@@ -454,11 +488,13 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
                 // this warp completed the column: its totals, and the slot words zero
                 // (the __syncwarp orders the lanes' reads after lane 0's fence)
                 __syncwarp();
+                if (col_ok) {
 #pragma unroll
-                for (int k = 0; k < kVec; ++k) {
-                    const unsigned long long v = atomicExch(sp + k, 0ull);
-                    s1[k] = (int32_t)(uint32_t)v;
-                    s2[k] = (int32_t)(v >> 32);
+                    for (int k = 0; k < kVec; ++k) {
+                        const unsigned long long v = atomicExch(sp + k, 0ull);
+                        s1[k] = (int32_t)(uint32_t)v;
+                        s2[k] = (int32_t)(v >> 32);
+                    }
                 }
                 int64_t q;
                 int32_t cnt;
@@ -486,7 +522,11 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
             s1[j] = 0;
             s2[j] = 0;
         }
-        seg0 = g + 1;
+        if (fend) {
+            gf = 0;
+            ++frame;
+        }
+        gf0 = gf;
     }
 }
 

@@ -42,6 +42,11 @@ def _bytes(N, M, F, seed):
     (1024, 32, 3001, 0),    # one turn per frame
     (4096, 96, 150, 0),     # 3 turns per frame
     (512, 64, 1, 0),        # fewer turns than teams
+    (768, 256, 101, 0),     # 3-warp teams, 5 per CTA (one warp idle)
+    (1040, 64, 61, 0),      # a last slice of 16 columns: lanes past N idle
+    (1536, 96, 29, 0),      # 6-warp teams, 2 per CTA
+    (3008, 32, 17, 0),      # 12-warp teams, one per CTA
+    (528, 128, 9, 0),       # 3 warps, the last one with 2 of 32 lanes busy
     # input-major: group rows of team*M bytes balanced over the grid (M = 128,
     # 256 and 4096; other M hand out whole frames)
     (2048, 256, 299, 1),    # 8 group rows per frame
