@@ -104,6 +104,7 @@ struct Launch {
     cudaEvent_t t_copy0 = nullptr, t_copy1 = nullptr, t_k0 = nullptr, t_k1 = nullptr;
     Clock::time_point t_issue, t_issued;
     uint64_t bytes = 0;
+    bool failed = false;  // this launch failed to issue (its tickets get the fault)
 };
 
 size_t round16(size_t v) { return (v + 15) / 16 * 16; }
@@ -179,6 +180,7 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
         // host-side fault injection for tests: this launch fails before any CUDA call
         std::lock_guard<std::mutex> g(s->mu);
         set_fault(s, SK_ERR_CUDA, "injected launch failure (SK_SERVER_INJECT_FAULT)");
+        L.failed = true;
         return;
     }
     const int n = (int)frames.size();
@@ -290,6 +292,7 @@ static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &fra
         std::lock_guard<std::mutex> g(s->mu);
         set_fault(s, e != cudaSuccess ? SK_ERR_CUDA : st,
                   e != cudaSuccess ? cudaGetErrorString(e) : "batch launch failed");
+        L.failed = true;
     }
 }
 
@@ -359,6 +362,7 @@ static void launcher_main(sk_server_s *s)
         }
         s->launches += 1;
         const int64_t launch_no = s->launches;
+        L.failed = false;
         lk.unlock();
         L.t_issue = Clock::now();
         issue_batch(s, L, batch, launch_no);
@@ -387,13 +391,16 @@ static void completer_main(sk_server_s *s)
         s->flight.pop_front();
         if (e != cudaSuccess)
             set_fault(s, SK_ERR_CUDA, cudaGetErrorString(e));
+        // a launch that completed keeps its results even when a later launch has
+        // failed since; a launch that failed itself gets the server's fault
+        const sk_status_t lst = (e != cudaSuccess || L.failed) ? s->fault : SK_OK;
         const float *h_sk = (const float *)L.h_res;
         const uint8_t *h_mask = L.h_res + sizeof(float) * L.n;
         for (int k = 0; k < L.n; ++k) {
             auto t = s->tickets.find(L.tickets[k]);
             if (t != s->tickets.end()) {
                 t->second.done = true;
-                t->second.status = s->fault;
+                t->second.status = lst;
                 t->second.sk = h_sk[k];
                 t->second.mask = h_mask[k];
                 const double us =
@@ -405,7 +412,7 @@ static void completer_main(sk_server_s *s)
                 else
                     r->lat_us[r->lat_next++ % kStreamLatKeep] = us;
             }
-            if (s->fault == SK_OK) {  // a failed launch has no results to count
+            if (lst == SK_OK) {  // a failed launch has no results to count
                 s->frames_done += 1;
                 s->frames_flagged += h_mask[k] ? 1 : 0;
                 L.streams[k]->frames_done += 1;
