@@ -389,9 +389,9 @@ sk_status_t ensure_kernel_attrs(int device)
     return SK_OK;
 }
 
-// Shapes of the warp-slice path: N a multiple of 16 (the tensor map's row stride)
-// from 512 to 4096, a team of ceil(N/256) >= 2 warps, each warp a 256-column
-// slice.  SK_WARP_SLICE=0 turns it off.
+// Shapes of the warp-slice path: N a multiple of 8 from 512 to 4096, a team of
+// ceil(N/256) >= 2 warps, each warp a 256-column slice.  SK_WARP_SLICE=0 turns it
+// off.
 static bool warp_slice_on()
 {
     static const bool off = [] {
@@ -403,7 +403,7 @@ static bool warp_slice_on()
 
 bool warp_slice_shape(int N, int M)
 {
-    return warp_slice_on() && N >= 512 && N % 16 == 0 && N <= 4096 && M % 32 == 0;
+    return warp_slice_on() && N >= 512 && N % 8 == 0 && N <= 4096 && M % 32 == 0;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -412,8 +412,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 // Tensor map of a time-major input for the warp-slice path's prefetch: rows of N
-// bytes, boxes of 32 rows x 256 bytes.  False if the driver cannot make one (the
-// launch then takes the team path).
+// bytes (N % 16 == 0: the map's row stride must be a multiple of 16), boxes of 32
+// rows x 256 bytes.  False if no map can be made.
 bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out)
 {
     static const EncodeTiledFn encode = [] {
@@ -425,7 +425,7 @@ bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out)
             f = nullptr;
         return (EncodeTiledFn)f;
     }();
-    if (!encode || rows <= 0 || rows > 0x7FFFFFFFLL || ((uintptr_t)in & 15u))
+    if (!encode || rows <= 0 || rows > 0x7FFFFFFFLL || ((uintptr_t)in & 15u) || N % 16 != 0)
         return false;
     const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)N};
@@ -506,10 +506,14 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     Item run = it;
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof tmap);
-    run.wi = (it.fast == 1 && tile == 0 && warp_slice_shape(it.N, it.M) &&
-              encode_input_map(it.in, it.N, it.n_frames * it.M, &tmap))
-                 ? 1
-                 : 0;
+    // warp-slice path: 1 with the tensor map of the prefetch, 2 without one (N % 16
+    // != 0; measured faster than a map of row pairs, whose prefetch slowed N = 1000
+    // from 6.0 to 4.2 TB/s), 0 not taken (or the map failed)
+    run.wi = 0;
+    if (it.fast == 1 && tile == 0 && warp_slice_shape(it.N, it.M))
+        run.wi = it.N % 16 != 0
+                     ? 2
+                     : (encode_input_map(it.in, it.N, it.n_frames * it.M, &tmap) ? 1 : 0);
     // input-major teams of two or more warps combine through the same slot ring
     if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6)
         run.wi = 1;

@@ -38,11 +38,11 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
 // sk_batch_create moves class-2 items with a tensor map to class 3 (the
 // warp-slice path).
 int batch_class(const Item &it);
-// Time-major shapes of the warp-slice path (N a power of two from 512 to 4096,
+// Time-major shapes of the warp-slice path (N a multiple of 8 from 512 to 4096,
 // M % 32 == 0), unless SK_WARP_SLICE=0.
 bool warp_slice_shape(int N, int M);
 // Tensor map of a time-major input for the warp-slice path's prefetch: rows of N
-// bytes, boxes of 32 rows x 256 bytes.  False if the driver cannot make one.
+// bytes (N % 16 == 0), boxes of 32 rows x 256 bytes.  False if none can be made.
 bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out);
 // SK_ERR_CUDA once if a bounded wait in an earlier launch of the plan gave up.
 sk_status_t pending_fault(sk_plan_t plan, const char *who);

@@ -70,8 +70,9 @@ struct Item {
     int32_t running_mu;      // served: normalise by the running power in the state
     double n_sigma;          // running-mu decision (double domain)
     double mean_offset;
-    int32_t wi;              // 1: the warps of a frame combine through the slot ring
-                             // (time-major: warp-slice path, tensor map given)
+    int32_t wi;              // nonzero: the warps of a frame combine through the slot ring
+                             // (time-major: warp-slice path, 1 with the tensor map for
+                             // the L2 prefetch, 2 without, when N % 16 != 0)
     int32_t *err;            // mapped host word: set when a bounded wait gives up
     const CUtensorMap *tmap;  // batched time-major items: the input's map in device memory
     int32_t *rb;              // row-balanced warp-slice launch: the plan's zeroed scratch

@@ -271,6 +271,9 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     const int col0 = xs + lane * kVec;
     // lanes past N read nothing (none when N is a compiled multiple of 256)
     const bool col_ok = (NC > 0 && NC % 256 == 0) || col0 < N;
+    // no tensor map when N is not a multiple of 16 (the map's row stride must
+    // be): those launches stream without the L2 prefetch
+    const bool pf = NC > 0 || it.wi != 2;
     const int64_t fbytes = (int64_t)M * N;
     const int nb = M / R;
     const int64_t kmax = (f_end - f_begin + T - 1) / T;
@@ -311,7 +314,7 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
             s2[j] = 0;
         }
         for (int jb = 0; jb < nb; jb += S) {
-            if (lane == 0) {
+            if (lane == 0 && pf) {
                 const int ba = jb + 2 * S;  // two ring turns ahead
                 if (ba < nb) {
                     if (ok)
@@ -387,6 +390,9 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
     const int col0 = xs + lane * kVec;
     // lanes past N read and add nothing (none when N is a compiled multiple of 256)
     const bool col_ok = (NC > 0 && NC % 256 == 0) || col0 < N;
+    // no tensor map when N is not a multiple of 16 (the map's row stride must
+    // be): those launches stream without the L2 prefetch
+    const bool pf = NC > 0 || it.wi != 2;
     const int64_t tpf = M / 32;  // turns per frame
     const int64_t TT = it.n_frames * tpf;
     const int64_t K = (int64_t)gridDim.x * T;
@@ -433,7 +439,7 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
     int gf = (int)(t0 - frame * tpf);  // ... and turn in it (counters: no division per turn)
     int gf0 = gf;                 // first turn of the current frame part
     for (int64_t g = t0; g < t1; ++g) {
-        if (lane == 0 && g + 2 < t1)
+        if (lane == 0 && pf && g + 2 < t1)
             prefetch_box(tmap, xs, (int)((g + 2) * 32));  // two turns ahead
         const bool more = g + 1 < t1;
         const uint8_t *pn = in + (g + 1) * 32 * N;

@@ -110,7 +110,8 @@ def test_pathfinder_25pct_pulse_flags_high():
 @pytest.mark.parametrize("N,M,F", [
     (8, 16, 5), (16, 32, 33), (24, 48, 17), (256, 128, 40), (1000, 64, 9),
     (2048, 256, 7), (4096, 32, 5), (2048, 1024, 3), (512, 4096, 2), (64, 16, 70),
-    (4096, 4096, 2), (768, 256, 7), (1040, 64, 9), (3008, 32, 5)])
+    (4096, 4096, 2), (768, 256, 7), (1040, 64, 9), (3008, 32, 5), (2056, 256, 5),
+    (520, 32, 11)])
 def test_fast_path_shapes_random_bytes(N, M, F):
     rng = np.random.default_rng(N * 7 + M + F)
     x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)

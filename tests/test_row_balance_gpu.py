@@ -47,6 +47,9 @@ def _bytes(N, M, F, seed):
     (1536, 96, 29, 0),      # 6-warp teams, 2 per CTA
     (3008, 32, 17, 0),      # 12-warp teams, one per CTA
     (528, 128, 9, 0),       # 3 warps, the last one with 2 of 32 lanes busy
+    (1000, 64, 61, 0),      # N = 8 mod 16: no tensor map, no L2 prefetch
+    (2056, 32, 33, 0),
+    (3000, 96, 11, 0),
     # input-major: group rows of team*M bytes balanced over the grid (M = 128,
     # 256 and 4096; other M hand out whole frames)
     (2048, 256, 299, 1),    # 8 group rows per frame
