@@ -251,7 +251,9 @@ def run_reference(args):
 
     layout = 1 if args.layout == "input" else 0
     ds = workload_datasets(0, 1, layout)[0]
-    nf = 64
+    # 256 frames (134 MB) a step, the cpu_baseline leg's sample: the oracle's
+    # per-call set-up (threshold tables) weighs little against the sums at that size
+    nf = 256
     x = ds.generate_cpu(0, nf)
     delta = float(np.mean(oracle.digitisation.delta_of_sigma(ds.sigma)))
     for _ in range(args.warmup):
