@@ -28,7 +28,7 @@
  *   SK_AUTOTUNE_CACHE    tile cache file ("N M layout rows grid" lines)
  *   SK_WARP_SLICE=0      one-item launches: team path (one barrier per frame)
  *                        instead of the warp-slice path (time-major, N a multiple
- *                        of 8 from 512 to 4096)
+ *                        of 8 from 256 to 4096)
  *                        and the slot-ring combine (input-major teams of >= 2 warps)
  *   SK_ROW_BALANCE=0     warp-slice launches hand out whole frames instead of
  *                        equal row ranges (no plan scratch)
@@ -188,7 +188,7 @@ sk_status_t sk_finish(sk_plan_t plan, const int64_t *d_q, const int32_t *d_neff,
 /*
  * Scratch of the device calls (sk_compute, sk_flag, sk_compute_inputs and
  * the chunks of sk_flag_host).  Time-major plans with N a multiple of 8 from
- * 512 to 4096 and M % 32 == 0, and input-major plans of M = 128, 256 or 4096, give
+ * 256 to 4096 and M % 32 == 0, and input-major plans of M = 128, 256 or 4096, give
  * every team of the launch an equal share of rows; frames cut between teams
  * are combined in a scratch of the plan (about 5 MB time-major, a few KB
  * input-major) that every launch leaves zero.  The first such call that is

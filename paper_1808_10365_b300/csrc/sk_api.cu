@@ -389,9 +389,9 @@ sk_status_t ensure_kernel_attrs(int device)
     return SK_OK;
 }
 
-// Shapes of the warp-slice path: N a multiple of 8 from 512 to 4096, a team of
-// ceil(N/256) >= 2 warps, each warp a 256-column slice.  SK_WARP_SLICE=0 turns it
-// off.
+// Shapes of the warp-slice path: N a multiple of 8 from 256 to 4096, a team of
+// ceil(N/256) warps (one at N = 256), each warp a 256-column slice.
+// SK_WARP_SLICE=0 turns it off.
 static bool warp_slice_on()
 {
     static const bool off = [] {
@@ -403,7 +403,7 @@ static bool warp_slice_on()
 
 bool warp_slice_shape(int N, int M)
 {
-    return warp_slice_on() && N >= 512 && N % 8 == 0 && N <= 4096 && M % 32 == 0;
+    return warp_slice_on() && N >= 256 && N % 8 == 0 && N <= 4096 && M % 32 == 0;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -510,7 +510,11 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // != 0; measured faster than a map of row pairs, whose prefetch slowed N = 1000
     // from 6.0 to 4.2 TB/s), 0 not taken (or the map failed)
     run.wi = 0;
-    if (it.fast == 1 && tile == 0 && warp_slice_shape(it.N, it.M))
+    // one-warp teams (N = 256) have no barrier to remove: there the warp-slice path
+    // pays only when too few frames to occupy the grid would leave most warps idle
+    // (64 frames: 16 against 30 us); with more it measured 1-15 % slower
+    const bool ws_n256 = it.N > 256 || it.n_frames * 4 < (int64_t)gmax * (kThreads / 32);
+    if (it.fast == 1 && tile == 0 && warp_slice_shape(it.N, it.M) && ws_n256)
         run.wi = it.N % 16 != 0
                      ? 2
                      : (encode_input_map(it.in, it.N, it.n_frames * it.M, &tmap) ? 1 : 0);

@@ -38,7 +38,7 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
 // sk_batch_create moves class-2 items with a tensor map to class 3 (the
 // warp-slice path).
 int batch_class(const Item &it);
-// Time-major shapes of the warp-slice path (N a multiple of 8 from 512 to 4096,
+// Time-major shapes of the warp-slice path (N a multiple of 8 from 256 to 4096,
 // M % 32 == 0), unless SK_WARP_SLICE=0.
 bool warp_slice_shape(int N, int M);
 // Tensor map of a time-major input for the warp-slice path's prefetch: rows of N

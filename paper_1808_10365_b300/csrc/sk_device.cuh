@@ -291,7 +291,7 @@ struct TeamSmem {
     long long rb[2][kSlots];
     int cnt[2][kSlots];
     int rn[2][kSlots];
-    WiSlot wi[kThreads / 64][kWiSlots];  // warp-slice path: teams of >= 2 warps
+    WiSlot wi[kThreads / 32][kWiSlots];  // warp-slice paths: up to 16 teams (of one warp)
 };
 
 __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
@@ -302,7 +302,7 @@ __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned *p)
 // Slots of the warp-slice combine before first use: slot j expects frame counter j.
 __device__ __forceinline__ void init_wi_slots(TeamSmem &ts)
 {
-    for (int i = threadIdx.x; i < (kThreads / 64) * kWiSlots; i += blockDim.x) {
+    for (int i = threadIdx.x; i < (kThreads / 32) * kWiSlots; i += blockDim.x) {
         WiSlot &sl = ts.wi[i / kWiSlots][i % kWiSlots];
         sl.q = 0ull;
         sl.cnt = 0;

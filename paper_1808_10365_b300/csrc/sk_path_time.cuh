@@ -241,12 +241,12 @@ __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int c
 }
 
 // Warp-slice path: one-item launches and batched items with a tensor map,
-// time-major, N a power of two from 512 to 4096, 16 x 2 tiles.  The team of a frame (N/8 threads) is cut into its
-// warps, and each warp owns a 256-column slice of the team's frames and runs on
-// its own: no barrier per frame.  Lane 0 of each warp asks L2 for the rows the
-// warp will load two ring turns ahead with one 2D tensor prefetch (32 rows x 256
-// bytes) through the input's tensor map (a kernel parameter of a one-item
-// launch, or the item's map in device memory).  After a frame, the warp adds its
+// time-major, N a multiple of 8 from 256 to 4096, 16 x 2 tiles.  The team of a
+// frame is ceil(N/256) warps, each owning a 256-column slice of the team's frames
+// and running on its own: no barrier per frame.  Lane 0 of each warp asks L2 for
+// the rows the warp will load two ring turns ahead with one 2D tensor prefetch
+// (32 rows x 256 bytes) through the input's tensor map (a kernel parameter of a
+// one-item launch, or the item's map in device memory; none when N % 16 != 0).  After a frame, the warp adds its
 // slice's Q and N_eff into the team's slot for that frame (shared-memory
 // atomics); the warp that arrives last forms the frame's mask and SK and frees
 // the slot.  A team's slots form a ring of kWiSlots frames; a warp that gets

@@ -50,6 +50,9 @@ def _bytes(N, M, F, seed):
     (1000, 64, 61, 0),      # N = 8 mod 16: no tensor map, no L2 prefetch
     (2056, 32, 33, 0),
     (3000, 96, 11, 0),
+    (256, 256, 64, 0),      # one-warp teams, 16 per CTA: 512 turns over 2368 teams
+    (256, 128, 3001, 0),
+    (264, 64, 77, 0),       # two warps, the second with one lane busy
     # input-major: group rows of team*M bytes balanced over the grid (M = 128,
     # 256 and 4096; other M hand out whole frames)
     (2048, 256, 299, 1),    # 8 group rows per frame
