@@ -163,3 +163,46 @@ def test_no_alloc_call_before_and_after_scratch():
             sk.sk_flag_host(plan, x, F, np.zeros(F, dtype=np.float32), np.zeros(F, dtype=np.uint8))
     finally:
         sk.sk_plan_destroy(plan)
+
+
+def test_random_balanced_shapes_sweep():
+    """40 seeded random shapes on the balanced paths (N a multiple of 8 from 256 to
+    4096, M a multiple of 32, 1 to a few hundred frames, so frames cut between
+    teams in every way; some input-major with M = 128 or 256), each against the
+    oracle: S1, S2, Q, N_eff, SK bits and masks."""
+    dev = _dev()
+    rng = np.random.default_rng(18081036)
+    for case in range(40):
+        layout = 1 if rng.random() < 0.2 else 0
+        if layout == 0:
+            N = int(8 * rng.integers(32, 513))
+            M = int(32 * rng.integers(1, 33))
+        else:
+            N = int(256 * rng.integers(1, 9))
+            M = int(rng.choice([128, 256]))
+        F = int(rng.integers(1, 400))
+        while F > 1 and F * M * N > (24 << 20):
+            F //= 2
+        x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+        want = oracle.flag(x, M, N, 2.5, 0.01, layout=layout)
+        d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+        s1 = torch.full((F, N), -1, dtype=torch.int32, device=dev)
+        s2 = torch.full_like(s1, -1)
+        q = torch.full((F,), -1, dtype=torch.int64, device=dev)
+        skv = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+        ne = torch.full((F,), -1, dtype=torch.int32, device=dev)
+        mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+        plan = sk.sk_plan_create(N, M, 2.5, 0.01, layout=layout)
+        try:
+            sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
+            sk.sk_flag(plan, d_in, F, None, mask)
+            torch.cuda.synchronize()
+        finally:
+            sk.sk_plan_destroy(plan)
+        tag = f"case {case}: N={N} M={M} F={F} layout={layout}"
+        assert np.array_equal(s1.cpu().numpy(), want["S1"]), tag
+        assert np.array_equal(s2.cpu().numpy(), want["S2"]), tag
+        assert np.array_equal(q.cpu().numpy(), want["Q"]), tag
+        assert np.array_equal(ne.cpu().numpy(), want["neff"]), tag
+        assert np.array_equal(skv.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32)), tag
+        assert np.array_equal(mask.cpu().numpy(), want["mask"]), tag
