@@ -161,7 +161,10 @@ sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows_per_batch,
  * Every output pointer may be NULL (not written); S1 and S2 go together and
  * must be 16-byte aligned.  Device pointers only.
  * Errors: INVALID_ARG (null plan or d_in, misaligned pointer, n_frames < 0),
- * CUDA (launch failure).
+ * CUDA (launch failure), TIMEOUT (a bounded wait inside an earlier launch of
+ * this plan ran out: that launch's outputs are void; reported once, by the
+ * plan's next call, which then runs normally -- every call that takes a plan
+ * reports it the same way).
  */
 sk_status_t sk_compute(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
                        int32_t *d_s1, int32_t *d_s2, int64_t *d_q,
@@ -242,12 +245,17 @@ sk_status_t sk_flag_host(sk_plan_t plan, const uint8_t *h_in, int64_t n_frames,
  * buffers sk_flag_host allocates, so it allocates nothing (the plan itself is
  * made beforehand with sk_plan_create).  One call takes at most
  * SK_NOALLOC_MAX_BYTES input bytes (n_frames*M*N) and SK_NOALLOC_MAX_FRAMES
- * frames; larger requests get INVALID_ARG and must be split.  Every device
- * that loads the library keeps the array (about 16.3 MiB) until the process
- * exits.  The first call on a device looks up the array's device address;
- * make it before any stream capture.  Calls on one device share the array:
- * this process serialises them and each returns after its results are in
- * h_sk/h_mask, but other work that overlaps a call on the GPU would race.
+ * frames; larger requests get INVALID_ARG and must be split.  The array
+ * (about 16.3 MiB) is set up when sk_plan_create makes a plan on the device:
+ * the plan looks up its device address, which loads the part of the library
+ * holding it, and the device keeps it until the process exits.  So create the
+ * plan before handing the device's memory to another allocator; if that
+ * set-up failed, the first call on the device retries it and reports its
+ * error.  Calls on one device share the array: this process serialises them
+ * and each returns after its results are in h_sk/h_mask, but other work that
+ * overlaps a call on the GPU would race.  Like sk_flag_host, the call returns
+ * the plan's pending fault (SK_ERR_TIMEOUT) if a bounded wait inside its own
+ * launch gave up.
  */
 #define SK_NOALLOC_MAX_BYTES (16 * 1024 * 1024)
 #define SK_NOALLOC_MAX_FRAMES 65536
@@ -425,6 +433,24 @@ sk_status_t sk_digitisation_offset(double sigma, double *delta);
  * Takes about a second.  Errors: INVALID_ARG (NULL output), CUDA.
  */
 sk_status_t sk_selftest_conversions(int device, int64_t *n_checked, int64_t *n_bad);
+
+/*
+ * Self-test of the one bounded wait inside the kernels (the paper has no
+ * failure model; this exercises the library's own error path).  Warps of a
+ * frame's team combine their parts through a ring of slots in shared memory,
+ * and a warp that runs a whole ring ahead waits for its slot to be freed, for
+ * at most a bounded number of 64 ns polls, then sets the plan's error word and
+ * returns.  This entry launches one warp of a two-warp team (1 CTA, on the
+ * plan's device and `stream`) whose slot is held by a frame that never
+ * completes, with a bound of spin_limit polls (1 .. 2^22), so the wait runs
+ * out and the kernel returns.  It synchronises the stream and sets *gave_up to
+ * 1 if the kernel raised the plan's error word (it does not consume it): the
+ * plan's next call then returns SK_ERR_TIMEOUT.  The kernel writes nothing
+ * else and allocates nothing.  Errors: INVALID_ARG (null plan or output,
+ * spin_limit out of range), CUDA.
+ */
+sk_status_t sk_selftest_slot_wait(sk_plan_t plan, int32_t spin_limit, int32_t *gave_up,
+                                  sk_cuda_stream_t stream);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char *sk_last_error(void);

@@ -84,3 +84,30 @@ def outside(sk: Fraction, n: int, ne: int, n_sigma: float, mean_offset: float = 
     half = Decimal(n_sigma) * Decimal(2) / (Decimal(n * ne).sqrt())
     v = Decimal(sk.numerator) / Decimal(sk.denominator)
     return 1 if (v > centre + half or v < centre - half) else 0
+
+
+def sk_running_mu(S1, S2, mu, n: int):
+    """SK~ with each receiver normalised by a given mean power per sample mu_i
+    instead of its frame's own S1_i/n (the running-mu reading of the served path).
+
+    Eq. (avgSK) 1st line over M' = n N_eff samples, with S1bar = sum S1_i/mu_i and
+    S2bar = sum S2_i/mu_i^2 (Eq. normedSum1/normedSum2 with mu_i given), then
+    rescaled to SK~ by Eq. (final) 1st line.  Receivers with S1_i = 0 or mu_i = 0
+    are left out.  Returns (SK~ as a Fraction or None, N_eff, n' S2bar / S1bar^2).
+    """
+    s1bar = Fraction(0)
+    s2bar = Fraction(0)
+    ne = 0
+    for s1, s2, m in zip(S1, S2, mu):
+        m = Fraction(m)
+        if s1 == 0 or m == 0:
+            continue
+        s1bar += Fraction(s1) / m
+        s2bar += Fraction(s2) / (m * m)
+        ne += 1
+    if ne == 0:
+        return None, 0, None
+    Mp = n * ne
+    ratio = Mp * s2bar / (s1bar * s1bar)
+    sk_hat = Fraction(Mp + 1, Mp - 1) * (ratio - 1)
+    return rescale_hat(sk_hat, n, ne), ne, ratio

@@ -49,7 +49,7 @@ EXPORTED = [
     "sk_ticket_wait",
     "sk_stream_drain", "sk_stream_get_state", "sk_stream_set_state", "sk_stream_close",
     "sk_server_stats", "sk_stream_stats", "sk_server_replay", "sk_digitisation_offset",
-    "sk_selftest_conversions", "sk_last_error",
+    "sk_selftest_conversions", "sk_selftest_slot_wait", "sk_last_error",
 ]
 
 
@@ -147,6 +147,7 @@ def library():
         "sk_server_replay": [P, ctypes.POINTER(sk_replay_t), ctypes.POINTER(sk_replay_result_t)],
         "sk_digitisation_offset": [ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
         "sk_selftest_conversions": [ctypes.c_int, ctypes.POINTER(I64), ctypes.POINTER(I64)],
+        "sk_selftest_slot_wait": [P, I32, ctypes.POINTER(I32), P],
         "sk_finish": [P, P, P, I64, P, P, P],
     }
     for name, args in sig.items():
@@ -499,6 +500,16 @@ def sk_selftest_conversions(device: int = 0):
     bad = ctypes.c_int64()
     _check(library().sk_selftest_conversions(int(device), ctypes.byref(n), ctypes.byref(bad)))
     return n.value, bad.value
+
+
+def sk_selftest_slot_wait(plan, spin_limit: int = 16, stream=None) -> bool:
+    """Runs the kernels' bounded slot wait against a slot that is never freed, with
+    a bound of spin_limit polls; True if the wait gave up and raised the plan's
+    error word (the plan's next call then reports SK_ERR_TIMEOUT)."""
+    out = ctypes.c_int32()
+    _check(library().sk_selftest_slot_wait(plan, int(spin_limit), ctypes.byref(out),
+                                           _stream(stream)))
+    return bool(out.value)
 
 
 def sk_last_error() -> str:

@@ -879,6 +879,8 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
         } else {
             *pl->h_err = 0;
             st = ensure_kernel_attrs(device);
+            if (st == SK_OK)
+                noalloc_prepare(device);
         }
         if (st != SK_OK)
             free_plan_device(pl);
@@ -941,13 +943,13 @@ extern "C" sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows, int32_t 
 }
 
 // A bounded wait inside an earlier launch of this plan gave up (its results are
-// void): report it once, on the next call.
+// void): report it once, as SK_ERR_TIMEOUT, on the next call.
 sk_status_t sk::pending_fault(sk_plan_t plan, const char *who)
 {
     if (plan->h_err && *reinterpret_cast<volatile int32_t *>(plan->h_err)) {
         *plan->h_err = 0;
-        return set_error(SK_ERR_CUDA, "%s: a wait inside an earlier launch timed out; "
-                                      "that launch's results are void", who);
+        return set_error(SK_ERR_TIMEOUT, "%s: a bounded wait inside an earlier launch "
+                                         "ran out; that launch's results are void", who);
     }
     return SK_OK;
 }
@@ -1157,5 +1159,8 @@ extern "C" sk_status_t sk_flag_host(sk_plan_t plan, const uint8_t *h_in, int64_t
     cudaError_t e = cudaStreamSynchronize(st);
     if (s == SK_OK && e != cudaSuccess)
         s = cuda_error(e, "sk_flag_host synchronize");
+    // the launches are complete: a bounded wait of their own that gave up voids them
+    if (s == SK_OK)
+        s = pending_fault(plan, "sk_flag_host");
     return s;
 }

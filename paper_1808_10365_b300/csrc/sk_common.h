@@ -44,8 +44,11 @@ bool warp_slice_shape(int N, int M);
 // Tensor map of a time-major input for the warp-slice path's prefetch: rows of N
 // bytes (N % 16 == 0), boxes of 32 rows x 256 bytes.  False if none can be made.
 bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out);
-// SK_ERR_CUDA once if a bounded wait in an earlier launch of the plan gave up.
+// SK_ERR_TIMEOUT once if a bounded wait in an earlier launch of the plan gave up.
 sk_status_t pending_fault(sk_plan_t plan, const char *who);
+// Set-up of sk_flag_host_noalloc on `device` (current): looks up the device
+// address of its fixed staging array, which loads the module holding it.
+void noalloc_prepare(int device);
 constexpr int kBatchClasses = 10;
 constexpr int kWarpSliceClass = 3;
 constexpr int kFirstImajorClass = 4;

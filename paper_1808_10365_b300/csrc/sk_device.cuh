@@ -336,15 +336,18 @@ __device__ __forceinline__ void write_frame(const Item &it, int64_t frame, int64
 // kk (the frame's index `frame`) into the team's slot for it; the warp that arrives
 // last of the team's W writes the frame's outputs (Sec. 3.2 test on Q against the
 // integer thresholds of N_eff = cnt, SK of Eq. final) and frees the slot for frame
-// counter kk + kWiSlots.  The wait for the slot is bounded: past the bound the
-// warp sets the plan's error word and goes on, and the launch's results are void.
+// counter kk + kWiSlots.  The wait for the slot is bounded: past spin_limit polls
+// (64 ns apart; the default is about a quarter of a second) the warp sets the
+// plan's error word and goes on, and the launch's results are void.
+constexpr int kWiSpinLimit = 1 << 22;
 __device__ __forceinline__ void wi_commit(const Item &it, WiSlot *slots, int64_t kk, int W,
-                                          int64_t frame, int64_t q, int32_t cnt)
+                                          int64_t frame, int64_t q, int32_t cnt,
+                                          int spin_limit = kWiSpinLimit)
 {
     WiSlot &sl = slots[kk % kWiSlots];
     // the slot is this frame's once the frame kWiSlots back is done
     for (int spins = 0; ld_volatile_u32(&sl.tag) != (unsigned)kk; ++spins) {
-        if (spins > (1 << 22)) {
+        if (spins >= spin_limit) {
             atomicExch(it.err, 1);
             break;
         }

@@ -9,17 +9,22 @@
 // allocation could synchronise the device and miss a deadline.  Such callers
 // create their plan at start-up and then use only this call.
 //
-// The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (SK_NOALLOC_MAX_BYTES + 5 * SK_NOALLOC_MAX_FRAMES bytes) until
-// the process exits.  Host code cannot use the array's name as a device
-// address (on the host it names a stand-in), so its device address is looked
-// up with cudaGetSymbolAddress once per device, on that device's first call.
-// Make that first call before any stream capture.  All calls on a device
-// share the array and each call leaves its data there; nothing in it has to
-// start at zero, because the kernel writes every output it reads back.  Calls
-// from this process are serialised per device (the call synchronises its
-// stream before returning); work issued elsewhere that overlaps on the GPU
-// with a call would race on the array.
+// The array is a file-scope __device__ variable: every GPU on which the module
+// holding it is loaded keeps it (SK_NOALLOC_MAX_BYTES + 5 * SK_NOALLOC_MAX_FRAMES
+// bytes) until the process exits.  Host code cannot use the array's name as a
+// device address (on the host it names a stand-in), so its device address is
+// looked up with cudaGetSymbolAddress once per device, with that device
+// current.  The look-up is part of set-up: sk_plan_create does it for the
+// plan's device (noalloc_prepare), because with lazy module loading it is the
+// look-up that loads this file's module and so takes the array's memory from
+// the driver.  A plan created before the device's memory is handed to another
+// allocator therefore leaves nothing for this call to allocate.  If that
+// look-up failed at plan creation, the first call on the device retries it and
+// reports its error.  All calls on a device share the array and each call leaves
+// its data there; nothing in it has to start at zero, because the kernel writes
+// every output it reads back.  Calls from this process are serialised per device
+// (the call synchronises its stream before returning); work issued elsewhere
+// that overlaps on the GPU with a call would race on the array.
 #include <mutex>
 
 #include "sk_common.h"
@@ -39,7 +44,8 @@ constexpr int kMaxDevices = 64;
 std::mutex g_dev_mu[kMaxDevices];
 uint8_t *g_dev_ptr[kMaxDevices] = {};
 
-// Device address of the array on `device` (current); looked up once.
+// Device address of the array on `device` (current); looked up once.  Called
+// with g_dev_mu[device] held.
 sk_status_t scratch_address(int device, uint8_t **out)
 {
     if (!g_dev_ptr[device]) {
@@ -54,6 +60,19 @@ sk_status_t scratch_address(int device, uint8_t **out)
 }
 
 }  // namespace
+
+// Set-up at plan creation (device current): the array's address on `device`,
+// which loads the module that holds it.  A failure here is left for the first
+// sk_flag_host_noalloc call on the device to report.
+void sk::noalloc_prepare(int device)
+{
+    if (device < 0 || device >= kMaxDevices)
+        return;
+    std::lock_guard<std::mutex> g(g_dev_mu[device]);
+    uint8_t *p = nullptr;
+    if (scratch_address(device, &p) != SK_OK)
+        cudaGetLastError();
+}
 
 extern "C" sk_status_t sk_flag_host_noalloc(sk_plan_t plan, const uint8_t *h_in,
                                             int64_t n_frames, float *h_sk, uint8_t *h_mask,
@@ -104,5 +123,6 @@ extern "C" sk_status_t sk_flag_host_noalloc(sk_plan_t plan, const uint8_t *h_in,
         e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
         return cuda_error(e, "sk_flag_host_noalloc: download");
-    return SK_OK;
+    // the launch is complete: a bounded wait of its own that gave up voids it
+    return pending_fault(plan, "sk_flag_host_noalloc");
 }

@@ -8,6 +8,10 @@
 //     neighbours; a hashed sample of 2^28 values below 2^43.
 //   input term (Eqs. discreteMean, normedSum2): a hashed sample of 2^26 valid
 //     (S1, S2, M) with M from 2 to 4096 and 0 < S1 <= 128 M, S1^2 <= M S2 <= 128 M S1.
+//
+// And a self-test of the bounded slot wait of the warp-slice combine
+// (wi_commit): one warp of a two-warp team commits frame counter 0 into a slot
+// still held by the frame a ring back, which never completes.
 #include "sk_common.h"
 
 namespace sk {
@@ -123,5 +127,57 @@ extern "C" sk_status_t sk_selftest_conversions(int device, int64_t *n_checked, i
         return cuda_error(e, "sk_selftest_conversions");
     *n_checked = (int64_t)n_f32 + (int64_t)n_u43 + (int64_t)n_term;
     *n_bad = (int64_t)(h_bad[0] + h_bad[1] + h_bad[2]);
+    return SK_OK;
+}
+
+namespace sk {
+
+namespace {
+
+// One warp (the first of a team of W = 2) commits its part of frame counter 0.
+// Slot 0 is initialised as held by counter -kWiSlots (its tag is kWiSlots, not
+// 0), the state a ring turn behind a slow warp leaves; nobody frees it, so the
+// wait gives up after spin_limit polls and raises it.err.  The part is added
+// into the slot afterwards, as on the real path, but the second warp never
+// arrives, so no frame is written.
+__global__ void slot_wait_kernel(Item it, int spin_limit)
+{
+    __shared__ WiSlot slots[kWiSlots];
+    if (threadIdx.x < kWiSlots) {
+        slots[threadIdx.x].q = 0ull;
+        slots[threadIdx.x].cnt = 0;
+        slots[threadIdx.x].arrive = 0;
+        slots[threadIdx.x].tag = (unsigned)(threadIdx.x + kWiSlots);
+    }
+    __syncwarp();
+    if (threadIdx.x == 0)
+        wi_commit(it, slots, 0, 2, 0, 0, 0, spin_limit);
+    __syncwarp();
+}
+
+}  // namespace
+
+}  // namespace sk
+
+extern "C" sk_status_t sk_selftest_slot_wait(sk_plan_t plan, int32_t spin_limit,
+                                             int32_t *gave_up, sk_cuda_stream_t stream)
+{
+    using namespace sk;
+    if (!plan || !gave_up)
+        return set_error(SK_ERR_INVALID_ARG, "sk_selftest_slot_wait: null argument");
+    if (spin_limit < 1 || spin_limit > kWiSpinLimit)
+        return set_error(SK_ERR_INVALID_ARG, "sk_selftest_slot_wait: spin_limit %d outside 1..%d",
+                         spin_limit, kWiSpinLimit);
+    DeviceGuard dg(plan->device);
+    const int32_t before = *reinterpret_cast<volatile int32_t *>(plan->h_err);
+    Item it = plan->item(nullptr, 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    slot_wait_kernel<<<1, 32, 0, st>>>(it, spin_limit);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cuda_error(e, "sk_selftest_slot_wait");
+    *gave_up = (!before && *reinterpret_cast<volatile int32_t *>(plan->h_err)) ? 1 : 0;
     return SK_OK;
 }

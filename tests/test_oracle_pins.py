@@ -239,14 +239,6 @@ def test_digitisation_limits():
         assert abs(float(dg.sigma_of_power(2 * m2)[0]) - s) < 1e-9
 
 
-def test_offset_table_matches_delta():
-    M = 256
-    e = dg.offset_table(M, B=256)
-    mu = (np.arange(256) + 0.5) * 128 / 256
-    d = dg.delta_of_power(mu)
-    assert np.allclose(e, np.round(d * 2 ** 32 * (M - 1) / (M + 1)), rtol=0, atol=1)
-
-
 @pytest.mark.slow
 def test_digitised_mean_offset_monte_carlo():
     """Quantised Gaussian data: mean(SK~) - 1 converges to delta(sigma) (App. B)."""

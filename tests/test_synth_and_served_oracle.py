@@ -174,3 +174,134 @@ def test_repeated_frame_is_a_fixed_point_of_the_state():
                               np.asarray(S1, dtype=np.int64) << 6)
         assert np.all(r["sk"].view(np.uint32) == r["sk"][0].view(np.uint32))
         assert np.all(r["mask"] == r["mask"][0]) and np.all(r["E"] == r["E"][0])
+
+
+def test_running_mu_against_exact_rationals():
+    """The running-mu estimator of the served oracle (its 2^24 fixed-point sums and
+    double-precision steps) against the exact rational statement of Eq. (avgSK) 1st
+    line with mu_i = P_i / (2^6 n), rescaled by Eq. (final) 1st line (brute.py), on
+    tiny arrays with random bytes (nibble 0 included) and random states.
+
+    Error bound: a_i and b_i carry at most three fp32 roundings each (two
+    conversions and the divide, 2^-24 relative apiece), so X = n' B / A^2 is within
+    about 6e-7 relative of its exact value, and SK~ = (n+1)/(n-1) (X - 1) within
+    (n+1)/(n-1) 6e-7 X; the fixed-point rounding (2^-25 per term) is far below."""
+    from fractions import Fraction
+
+    from oracle import brute
+
+    rng = np.random.default_rng(1808)
+    k = 6
+    worst = 0.0
+    for case in range(120):
+        M = int(rng.integers(2, 17))
+        N = int(rng.integers(1, 9))
+        x = rng.integers(0, 256, size=M * N, dtype=np.uint8)
+        if case % 7 == 0:
+            x[0::N] = 0x88                      # input 0 has no power
+        S1, S2 = brute.sums(x, M, N)
+        P = []
+        for s1 in S1:
+            base = s1 if s1 > 0 else int(rng.integers(1, 60))
+            P.append(max(1, int(round(base * (1 << k) * 2.0 ** rng.uniform(-2.0, 2.0)))))
+        A, B, ne, skd = served._running_mu_sk(np.array(S1, dtype=np.int64),
+                                             np.array(S2, dtype=np.int64),
+                                             np.array(P, dtype=np.int64), M, k)
+        mu = [Fraction(p, (1 << k) * M) for p in P]
+        want, ne_w, ratio = brute.sk_running_mu(S1, S2, mu, M)
+        assert ne == ne_w
+        if want is None:
+            assert skd != skd
+            continue
+        err = abs(skd - float(want))
+        tol = (M + 1) / (M - 1) * 1e-6 * float(ratio) + 1e-9
+        worst = max(worst, err / tol)
+        assert err <= tol, (case, M, N, skd, float(want))
+    assert worst < 1.0
+
+
+def test_bucket_edges_from_mean_power():
+    """bucket(P) is the index b of the power bucket [b, b+1) * 128 / B that holds the
+    running mean power per sample mu = P / (2^k n): checked at both sides of every
+    bucket edge found by exact rationals, at n where P * B exceeds 2^32 (n = 4096),
+    at the top (mu >= 128 clips to B - 1) and at P = 0."""
+    from fractions import Fraction
+
+    B, k = 4096, 6
+    rng = np.random.default_rng(3)
+    wide = 0
+    for M in (2, 16, 256, 1024, 4096):
+        scale = (1 << k) * M
+        edges = sorted(set([1, 2, B - 1] + rng.integers(1, B, 40).tolist()))
+        for b in edges:
+            # smallest P with P / scale >= b * 128 / B
+            lo = Fraction(b * 128, B) * scale
+            p_edge = lo.numerator // lo.denominator + (lo.denominator != 1)
+            got = served.bucket(np.array([p_edge - 1, p_edge], dtype=np.int64), M, B, k)
+            assert got.tolist() == [b - 1, b], (M, b)
+            wide += p_edge * B > 2 ** 32              # the uint64 product path
+        top = served.bucket(np.array([128 * scale - 1, 128 * scale, 2 ** 32 - 1, 0],
+                                     dtype=np.int64), M, B, k)
+        assert top.tolist() == [B - 1, B - 1, B - 1, 0]
+    assert wide >= 20
+
+
+def test_offset_table_against_quadrature():
+    """The offset table e[b] (the App. B digitisation offset of bucket b's mean power,
+    in Q units) against an independent computation at a spread of buckets: the
+    moments of clip(round(sigma g), -7, 7) by adaptive quadrature of the normal
+    density over each level's interval (scipy.integrate.quad, not the erfc tail
+    formula), sigma solved by Brent's method (not bisection), and the Q-unit scale
+    taken from the threshold recipe itself: e[b] must equal the shift of the one-input
+    upper threshold when the centre moves by delta (Sec. 3.2 interval in Q units)."""
+    import math
+
+    from scipy import integrate, optimize
+
+    def moments_quad(sigma):
+        pdf = lambda t: math.exp(-0.5 * (t / sigma) ** 2) / (sigma * math.sqrt(2 * math.pi))
+        m2 = m4 = 0.0
+        for v in range(1, 8):
+            a = v - 0.5
+            b = v + 0.5 if v < 7 else math.inf
+            p = integrate.quad(pdf, a, b, epsabs=1e-15, epsrel=1e-13, limit=200)[0]
+            m2 += 2 * p * v ** 2
+            m4 += 2 * p * v ** 4
+        return m2, m4
+
+    M = 256
+    e = dg.offset_table(M)
+    # buckets above 2 m2(inf) = 98 (all samples clipped to +-7) have no sigma: the
+    # table clamps them to sigma = 1000 (delta near -1, two-level data)
+    for b in (3, 40, 300, 700, 1500, 2200, 3000, 3100, 3600, 4095):
+        mu = (b + 0.5) * 128 / 4096
+        if mu < 98.0:
+            sig = optimize.brentq(lambda s: 2 * moments_quad(s)[0] - mu, 1e-2, 1e3,
+                                  xtol=1e-14, rtol=1e-15, maxiter=500)
+        else:
+            sig = 1000.0
+        m2, m4 = moments_quad(sig)
+        delta = m4 / (2 * m2 * m2) - 1.5
+        lo0, hi0 = oracle.thresholds(M, 1, 3.0, 0.0)
+        lo1, hi1 = oracle.thresholds(M, 1, 3.0, delta)
+        assert abs(int(e[b]) - int(hi1[1] - hi0[1])) <= 2, (b, int(e[b]), int(hi1[1] - hi0[1]))
+        assert abs(int(e[b]) - int(lo1[1] - lo0[1])) <= 2
+
+
+def test_offset_table_monte_carlo():
+    """Two buckets of the table against a Monte Carlo run: complex samples with
+    components round(sigma g) clipped to [-7, 7], sigma chosen so the mean power per
+    sample is the bucket's centre; the sample kurtosis E|x|^4 / (E|x|^2)^2 - 2 is the
+    large-n offset of SK (App. B), 4e6 samples."""
+    rng = np.random.default_rng(11)
+    M = 256
+    e = dg.offset_table(M)
+    scale = 2 ** 32 * (M - 1) / (M + 1)
+    for b in (900, 2600):
+        mu = (b + 0.5) * 128 / 4096
+        sig = float(dg.sigma_of_power(mu)[0])
+        v = np.clip(np.round(sig * rng.standard_normal((2, 4_000_000))), -7, 7)
+        p = v[0] ** 2 + v[1] ** 2
+        assert abs(p.mean() - mu) < 0.01 * mu
+        d_mc = (p ** 2).mean() / p.mean() ** 2 - 2.0
+        assert abs(float(e[b]) / scale - d_mc) < 0.01 * (1 + abs(d_mc)) * 0.3, (b, d_mc)
