@@ -9,6 +9,10 @@ the L2 size, so no flush is needed between steps.
 metric: Gsamples/s (1 sample = 1 byte); value = whole-job throughput with
 inputs resident in HBM; e2e = the same call on host (pinned) buffers with the
 host-to-device upload and the mask/SK download inside the timed region.
+After the timed steps a sustained leg streams the same launch back to back for
+a few seconds (the regime after the power cap engages: roofline.frac_sustained),
+and the extras time off-benchmark shapes (`shapes`), the batched mixed
+workload, and the serving workload (its full 10 s paced, plus shorter legs).
 
 Under torchrun each rank runs its own 4 frequencies (weak scaling, no
 collective in the data path); the timed region is bracketed by barriers and
@@ -401,6 +405,7 @@ def batched_bench(reps: int = 10, dev_index: int = 0, n_frames: int = 500):
         views.append((v, skv, mask))
         items.append((plan, v, d.n_frames, skv, mask))
     batch = sk.sk_batch_create(items, dev_index)
+    launches = sk.sk_batch_launches(batch)
     st = torch.cuda.Stream(dev)
 
     def timed(fn):
@@ -436,7 +441,7 @@ def batched_bench(reps: int = 10, dev_index: int = 0, n_frames: int = 500):
             "value": total / (ms_batch * 1e-3) / 1e9, "unit": UNIT, "ms": ms_batch,
             "roofline_frac": (total + 5 * sum(d.n_frames for d in datasets))
             / (ms_batch * 1e-3) / 1e9 / peaks()[0],
-            "launches_per_run": len({d.N for d in datasets}),
+            "launches_per_run": launches,
             "plain_value": total / (ms_plain * 1e-3) / 1e9, "plain_ms": ms_plain,
             "plain_launches": len(items), "speedup_vs_plain": ms_plain / ms_batch,
             "masks_identical": same}
@@ -492,6 +497,7 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
            "value": r["bytes"] / r["wall_s"] / 1e9, "unit": UNIT,
            "realtime_input_gbs": sum(specs) * M / T / 1e9,
            "latency_p50_us": r["latency_p50_us"], "latency_p99_us": r["latency_p99_us"],
+           "p99_over_p50": r["latency_p99_us"] / max(r["latency_p50_us"], 1e-9),
            "launches": r["launches"], "frames_per_launch": r["frames"] / max(1, r["launches"]),
            "submit_p50_us": r["submit_p50_us"], "busy_retries": r["busy_retries"],
            "load_generator": f"sk_server_replay, {threads} submitter threads"}
@@ -512,9 +518,103 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
         lat = np.sort(np.array(lat[32:]))
         out["plain_latency_p50_us"] = float(lat[len(lat) // 2])
         out["plain_latency_p99_us"] = float(lat[int(0.99 * (len(lat) - 1))])
+        out["plain_p99_over_p50"] = out["plain_latency_p99_us"] / out["plain_latency_p50_us"]
         out["plain_max_frames_per_s"] = float(1e6 / lat.mean())
         out["realtime_frames_per_s"] = len(specs) / T
     return out
+
+
+# Shapes off the benchmark's own: ragged N on the general path, N = 8 (mod 16),
+# a short integration (8-row tile) and input-major integration lengths at both
+# ends.  (label, N, M, layout); each runs on about 1 GB of random bytes.
+OFF_SHAPES = [
+    ("time-major N=2047 M=256 (ragged N, general path)", 2047, 256, 0),
+    ("time-major N=100 M=100 (general path)", 100, 100, 0),
+    ("time-major N=2056 M=256 (N = 8 mod 16)", 2056, 256, 0),
+    ("time-major N=520 M=256 (N = 8 mod 16)", 520, 256, 0),
+    ("time-major N=2048 M=48 (M = 16 mod 32)", 2048, 48, 0),
+    ("input-major N=2048 M=64", 2048, 64, 1),
+    ("input-major N=2048 M=4096", 2048, 4096, 1),
+]
+
+
+def shapes_bench(reps: int = 10, dev_index: int = 0, target_bytes: int = 1 << 30):
+    """sk_flag on each OFF_SHAPES case: about 1 GB of random bytes (8x L2), 3 warm-up
+    launches, then `reps` launches each between its own CUDA events on the launching
+    stream; throughput and fraction of the measured copy bandwidth per shape."""
+    import torch
+
+    import paper_1808_10365_b300 as sk
+
+    dev = torch.device("cuda", dev_index)
+    st = torch.cuda.Stream(dev)
+    peak, kind = peaks()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1808)
+    out = []
+    for label, N, M, layout in OFF_SHAPES:
+        F = max(1, target_bytes // (M * N))
+        nbytes = F * M * N
+        d_in = torch.randint(0, 256, (nbytes,), dtype=torch.uint8, device=dev, generator=gen)
+        d_sk = torch.empty(F, dtype=torch.float32, device=dev)
+        d_mask = torch.empty(F, dtype=torch.uint8, device=dev)
+        plan = sk.sk_plan_create(N, M, 3.0, 0.0, layout=layout, device=dev_index)
+        try:
+            for _ in range(3):
+                sk.sk_flag(plan, d_in, F, d_sk, d_mask, st)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(reps)]
+            for a, b in ev:
+                a.record(st)
+                sk.sk_flag(plan, d_in, F, d_sk, d_mask, st)
+                b.record(st)
+            st.synchronize()
+        finally:
+            sk.sk_plan_destroy(plan)
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        out.append({"shape": label, "N": N, "M": M, "layout": layout, "frames": F,
+                    "bytes": nbytes, "ms": ms, "tb_s": nbytes / (ms * 1e-3) / 1e12,
+                    "roofline_frac": (nbytes + 5 * F) / (ms * 1e-3) / 1e9 / peak})
+        del d_in, d_sk, d_mask
+    torch.cuda.empty_cache()
+    return {"peak_gbs": peak, "peak_kind": f"{kind} copy bandwidth", "cases": out}
+
+
+def sustained_leg(sk, plan, d_in, F, d_sk, d_mask, stream, alg_bytes, seconds, dev_index,
+                  est_launch_s):
+    """Back-to-back sk_flag launches of the benchmark workload for about `seconds`, as a
+    deployment that streams continuously runs it: the board's power cap engages after
+    tens of milliseconds and the SM clock dips.  Each launch between its own events on
+    the launching stream; SM clocks sampled during the leg."""
+    import torch
+
+    n = max(20, int(seconds / max(est_launch_s, 1e-5)))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(n)]
+    torch.cuda.synchronize(d_in.device)
+    with ClockSampler(physical_index(dev_index)) as clk:
+        t0 = time.perf_counter()
+        for a, b in ev:
+            a.record(stream)
+            sk.sk_flag(plan, d_in, F, d_sk, d_mask, stream)
+            b.record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    mean_ms = statistics.mean(ms)
+    peak, _ = peaks()
+    q = len(ms) // 4
+    quarters = [statistics.median(ms[i * q:(i + 1) * q]) for i in range(4)]
+    mhz = clocks.get("sm_mhz")
+    return {"seconds": wall, "launches": n, "mean_launch_ms": mean_ms,
+            "achieved_gbs": alg_bytes / (mean_ms * 1e-3) / 1e9,
+            "frac": alg_bytes / (mean_ms * 1e-3) / 1e9 / peak,
+            "launch_ms_quarter_medians": quarters,
+            "launch_ms_min_median_max": [min(ms), statistics.median(ms), max(ms)],
+            # launch time x median SM clock: flat across runs if the time follows the clock
+            "mean_launch_ms_x_median_sm_mhz": mean_ms * mhz if mhz else None,
+            "clocks": clocks}
 
 
 def run_e2e(sk, plan, d_in, d_mask, F, fb, bytes_per_step, e2e_steps, stream, ws):
@@ -605,6 +705,10 @@ def run_gpu(args):
     e2e_steps = min(args.e2e_steps, args.steps)
     if e2e_steps > 0:
         e2e = run_e2e(sk, plan, d_in, d_mask, F, fb, bytes_per_step, e2e_steps, stream, ws)
+    sustained = None
+    if args.sustained_seconds > 0:
+        sustained = sustained_leg(sk, plan, d_in, F, d_sk, d_mask, stream, alg_bytes,
+                                  args.sustained_seconds, dev.index, mean_launch_s)
     sk.sk_plan_destroy(plan)
     line_tail = dict(e2e=e2e)
     line = {
@@ -640,6 +744,9 @@ def run_gpu(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if sustained is not None:
+        line["roofline"]["frac_sustained"] = sustained["frac"]
+        line["sustained"] = sustained
     if ws == 1 and not args.no_extras:
         if layout == 0:
             line.update(variants_bench(d_in, F, delta, dev_index=dev.index))
@@ -647,13 +754,13 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         if layout == 0:
             line["input_major"] = input_major_bench(args.freqs, d_mask, dev_index=dev.index)
+        line["shapes"] = shapes_bench(dev_index=dev.index)
         line["batched"] = batched_bench(dev_index=dev.index)
         line["served"] = served_bench(args.served_seconds, True, dev.index)
-        line["served_replay"] = served_bench(min(args.served_seconds, 1.0), False, dev.index)
-        line["served_running_mu"] = served_bench(min(args.served_seconds, 1.0), True, dev.index,
-                                                 running_mu=True)
-        line["served_by_reference"] = served_bench(min(args.served_seconds, 1.0), True,
-                                                   dev.index, by_reference=True)
+        short = min(args.served_seconds, 2.0)
+        line["served_replay"] = served_bench(min(short, 1.0), False, dev.index)
+        line["served_running_mu"] = served_bench(short, True, dev.index, running_mu=True)
+        line["served_by_reference"] = served_bench(short, True, dev.index, by_reference=True)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -680,7 +787,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and served measurements")
-    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-seconds", type=float, default=10.0,
+                    help="simulated seconds of the paced 32-stream served leg (the serving "
+                         "workload's full 10 s by default); the other served legs run "
+                         "at most 2 s")
+    ap.add_argument("--sustained-seconds", type=float, default=3.0,
+                    help="seconds of back-to-back launches of the sustained leg (0: skip)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -283,6 +283,9 @@ typedef struct {
 sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_items,
                             int device, sk_batch_t *out);
 sk_status_t sk_batch_run(sk_batch_t batch, sk_cuda_stream_t stream);
+/* Kernel launches one sk_batch_run replays: one persistent launch per
+ * non-empty kernel class of the batch's items (0 if no item has frames). */
+sk_status_t sk_batch_launches(sk_batch_t batch, int32_t *launches);
 sk_status_t sk_batch_destroy(sk_batch_t batch);
 
 /* ------------------------------------------------------------ serving */
@@ -297,8 +300,11 @@ sk_status_t sk_batch_destroy(sk_batch_t batch);
  * from the host ring directly (zero copy); SK_SERVER_ZEROCOPY=0 selects a
  * device mirror of the ring with one upload per batch instead.  The ring is
  * half of hbm_budget_bytes (at most 4 GiB); a stream is admitted while its
- * ring share (ring_frames frames) fits the ring and its device state and
- * tables fit the rest of the budget.  SK_SERVER_INFLIGHT (1..8, default 2)
+ * ring share (ring_frames frames) fits the ring, its device state and
+ * tables fit the rest of the budget, and they fit the device's free memory
+ * at the time of sk_stream_open (cudaMemGetInfo) less a headroom of
+ * 256 MiB kept for the launches: admission follows the lesser of the
+ * caller's budget and the memory really free.  SK_SERVER_INFLIGHT (1..8, default 2)
  * sets how many launches may be in flight; SK_SERVER_TRACE=1 prints per-launch
  * timing averages when the server is destroyed.
  */

@@ -44,7 +44,7 @@ EXPORTED = [
     "sk_plan_create", "sk_plan_destroy", "sk_plan_thresholds", "sk_plan_offset_table",
     "sk_plan_set_tiles", "sk_plan_get_tiles", "sk_compute", "sk_flag", "sk_flag_host",
     "sk_flag_host_noalloc", "sk_compute_inputs", "sk_finish",
-    "sk_batch_create", "sk_batch_run", "sk_batch_destroy", "sk_server_create",
+    "sk_batch_create", "sk_batch_run", "sk_batch_launches", "sk_batch_destroy", "sk_server_create",
     "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_stream_submit_ref",
     "sk_ticket_wait",
     "sk_stream_drain", "sk_stream_get_state", "sk_stream_set_state", "sk_stream_close",
@@ -131,6 +131,7 @@ def library():
         "sk_compute_inputs": [P, P, I64, P, P, P, P, P],
         "sk_batch_create": [ctypes.POINTER(sk_batch_item_t), I32, ctypes.c_int, ctypes.POINTER(P)],
         "sk_batch_run": [P, P],
+        "sk_batch_launches": [P, ctypes.POINTER(I32)],
         "sk_batch_destroy": [P],
         "sk_server_create": [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(P)],
         "sk_server_destroy": [P],
@@ -368,6 +369,12 @@ def sk_batch_create(items, device=0) -> int:
 
 def sk_batch_run(batch, stream=None):
     _check(library().sk_batch_run(batch, _stream(stream)))
+
+
+def sk_batch_launches(batch) -> int:
+    n = ctypes.c_int32()
+    _check(library().sk_batch_launches(batch, ctypes.byref(n)))
+    return n.value
 
 
 def sk_batch_destroy(batch):

@@ -28,7 +28,7 @@ def build(verbose: bool = False):
             cmd.insert(1, "-Xptxas=-v")
         subprocess.run(cmd, check=True)
         objs.append(o)
-    subprocess.run([nvcc(), ARCH, "-shared", "-o", LIB] + objs + ["-lcudart", "-lpthread"],
+    subprocess.run([nvcc(), ARCH, "-shared", "-o", LIB] + objs + ["-lcudart", "-lpthread", "-ldl"],
                    check=True)
     return LIB
 

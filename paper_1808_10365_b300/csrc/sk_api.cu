@@ -491,6 +491,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
 {
     if (it.n_frames == 0)
         return SK_OK;
+    NvtxRange nv("sk launch");
     sk_status_t s = ensure_kernel_attrs(device);
     if (s != SK_OK)
         return s;
@@ -591,6 +592,7 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
 {
     if (grid <= 0)
         return SK_OK;
+    NvtxRange nv(served ? "sk served launch" : "sk batched launch");
     sk_status_t s = ensure_kernel_attrs(device);
     if (s != SK_OK)
         return s;
@@ -790,6 +792,7 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
         return cuda_error(ce, "cudaGetDeviceCount");
     if (device < 0 || device >= ndev)
         return set_error(SK_ERR_INVALID_ARG, "device %d not present", device);
+    NvtxRange nv("sk_plan_create");
 
     sk_plan_s *pl = new (std::nothrow) sk_plan_s();
     if (!pl)
@@ -974,6 +977,7 @@ extern "C" sk_status_t sk_compute(sk_plan_t plan, const uint8_t *d_in, int64_t n
                                   int32_t *d_s1, int32_t *d_s2, int64_t *d_q, float *d_sk,
                                   int32_t *d_neff, sk_cuda_stream_t stream)
 {
+    NvtxRange nv("sk_compute");
     sk_status_t s = check_call(plan, d_in, n_frames, "sk_compute");
     if (s != SK_OK)
         return s;
@@ -995,6 +999,7 @@ extern "C" sk_status_t sk_compute(sk_plan_t plan, const uint8_t *d_in, int64_t n
 extern "C" sk_status_t sk_flag(sk_plan_t plan, const uint8_t *d_in, int64_t n_frames,
                                float *d_sk, uint8_t *d_mask, sk_cuda_stream_t stream)
 {
+    NvtxRange nv("sk_flag");
     sk_status_t s = check_call(plan, d_in, n_frames, "sk_flag");
     if (s != SK_OK)
         return s;
@@ -1037,6 +1042,7 @@ extern "C" sk_status_t sk_finish(sk_plan_t plan, const int64_t *d_q, const int32
                                  int64_t n_frames, float *d_sk, uint8_t *d_mask,
                                  sk_cuda_stream_t stream)
 {
+    NvtxRange nv("sk_finish");
     if (!plan)
         return set_error(SK_ERR_INVALID_ARG, "sk_finish: plan is NULL");
     if (sk_status_t f = pending_fault(plan, "sk_finish"))
@@ -1067,6 +1073,7 @@ extern "C" sk_status_t sk_compute_inputs(sk_plan_t plan, const uint8_t *d_in,
                                          int64_t n_frames, float *d_sk_in, uint8_t *d_mask_in,
                                          float *d_sk, uint8_t *d_mask, sk_cuda_stream_t stream)
 {
+    NvtxRange nv("sk_compute_inputs");
     sk_status_t s = check_call(plan, d_in, n_frames, "sk_compute_inputs");
     if (s != SK_OK)
         return s;
@@ -1112,6 +1119,7 @@ static sk_status_t ensure_staging(sk_plan_s *pl)
 extern "C" sk_status_t sk_flag_host(sk_plan_t plan, const uint8_t *h_in, int64_t n_frames,
                                     float *h_sk, uint8_t *h_mask, sk_cuda_stream_t stream)
 {
+    NvtxRange nv("sk_flag_host");
     if (!plan)
         return set_error(SK_ERR_INVALID_ARG, "sk_flag_host: plan is NULL");
     if (sk_status_t f = pending_fault(plan, "sk_flag_host"))

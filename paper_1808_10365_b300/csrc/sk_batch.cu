@@ -171,6 +171,7 @@ static void free_batch(sk_batch_s *b)
 extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_items,
                                        int device, sk_batch_t *out)
 {
+    NvtxRange nv("sk_batch_create");
     if (!out)
         return set_error(SK_ERR_INVALID_ARG, "sk_batch_create: out is NULL");
     *out = nullptr;
@@ -285,6 +286,7 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
 
 extern "C" sk_status_t sk_batch_run(sk_batch_t b, sk_cuda_stream_t stream)
 {
+    NvtxRange nv("sk_batch_run");
     if (!b)
         return set_error(SK_ERR_INVALID_ARG, "sk_batch_run: batch is NULL");
     DeviceGuard dg(b->device);
@@ -327,6 +329,18 @@ extern "C" sk_status_t sk_batch_run(sk_batch_t b, sk_cuda_stream_t stream)
             s = cuda_error(e, "cudaGraphLaunch");
     }
     return s;
+}
+
+extern "C" sk_status_t sk_batch_launches(sk_batch_t b, int32_t *launches)
+{
+    if (!b || !launches)
+        return set_error(SK_ERR_INVALID_ARG, "sk_batch_launches: null argument");
+    int32_t n = 0;
+    if (!b->chunks.empty())
+        for (int c = 0; c < kBatchClasses; ++c)
+            n += b->used[c] ? 1 : 0;
+    *launches = n;
+    return SK_OK;
 }
 
 extern "C" sk_status_t sk_batch_destroy(sk_batch_t b)

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sk.h"
 #include "sk_device.cuh"
 
@@ -77,6 +79,15 @@ int build_item_schedule(std::vector<Item> &items, int grid_max, std::vector<Chun
 double digitisation_delta(double sigma);
 double sigma_of_power(double mu);
 void build_offset_table(int32_t M, int64_t *e);
+
+// Scoped NVTX range (plan creation, launches, batch replay, served launches), seen
+// by profilers that trace NVTX (ncu --nvtx); a function-pointer test otherwise.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Scoped switch of the current device.
 struct DeviceGuard {

@@ -78,6 +78,7 @@ extern "C" sk_status_t sk_flag_host_noalloc(sk_plan_t plan, const uint8_t *h_in,
                                             int64_t n_frames, float *h_sk, uint8_t *h_mask,
                                             sk_cuda_stream_t stream)
 {
+    NvtxRange nv("sk_flag_host_noalloc");
     if (!plan)
         return set_error(SK_ERR_INVALID_ARG, "sk_flag_host_noalloc: plan is NULL");
     if (sk_status_t f = pending_fault(plan, "sk_flag_host_noalloc"))

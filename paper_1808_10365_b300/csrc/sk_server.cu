@@ -19,7 +19,8 @@
 // device mirror and each batch is one contiguous host-to-device copy before its
 // kernel.  The ring is sized to half of the server's budget (at most 4 GiB);
 // streams are admitted while their ring share (ring_frames frames) fits the
-// ring and their device state and tables fit the other half of the budget.
+// ring and their device state and tables fit both the other half of the budget
+// and the device's memory free at sk_stream_open, less a headroom.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -47,6 +48,9 @@ constexpr int kLaunchSlots = 8;  // at most this many launches in flight
 constexpr int kMaxBatch = 1024;        // frames per launch
 constexpr uint64_t kAlign = 256;       // ring placement granularity
 constexpr size_t kMaxRing = (size_t)4 << 30;
+// device memory kept free beside admitted streams (kernel local memory, driver
+// bookkeeping): a stream is refused if its state and tables would leave less
+constexpr size_t kHbmHeadroom = (size_t)256 << 20;
 
 struct StreamRec {
     sk_stream_id id = -1;
@@ -176,6 +180,7 @@ static void set_fault(sk_server_s *s, sk_status_t st, const char *msg)
 static void issue_batch(sk_server_s *s, Launch &L, const std::vector<Frame> &frames,
                         int64_t launch_no)
 {
+    NvtxRange nv("sk_server issue_batch");
     if (s->inject_at > 0 && launch_no == s->inject_at) {
         // host-side fault injection for tests: this launch fails before any CUDA call
         std::lock_guard<std::mutex> g(s->mu);
@@ -634,8 +639,26 @@ extern "C" sk_status_t sk_stream_open(sk_server_t s, const sk_params_t *params,
     const size_t small = sizeof(uint32_t) * params->n_inputs +
                          sizeof(int64_t) * (2 * (params->n_inputs + 1) + SK_OFFSET_BUCKETS) +
                          sizeof(float) * (params->n_inputs + 1);
+    // the device's real free memory, less a headroom for the launches (kernel
+    // local memory, driver bookkeeping): admission takes the lesser of it and the
+    // caller's budget
+    size_t dev_free = SIZE_MAX, dev_total = 0;
+    {
+        DeviceGuard dg(s->device);
+        if (cudaMemGetInfo(&dev_free, &dev_total) != cudaSuccess) {
+            cudaGetLastError();
+            dev_free = SIZE_MAX;
+        }
+    }
     {
         std::lock_guard<std::mutex> g(s->mu);
+        if (dev_free < kHbmHeadroom || small > dev_free - kHbmHeadroom) {
+            s->rejected += 1;
+            return set_error(SK_ERR_BUSY,
+                             "sk_stream_open: the device has %zu bytes free; the stream needs "
+                             "%zu beside a headroom of %zu",
+                             dev_free, small, kHbmHeadroom);
+        }
         if (s->ring_reserved + share > s->ring_cap ||
             s->small_in_use + small > s->budget - s->ring_cap) {
             s->rejected += 1;

@@ -282,6 +282,20 @@ def test_full_array_workload_every_frame():
     assert r["mask"].mean() < 0.06
 
 
+@pytest.mark.parametrize("N,M,layout,F", [
+    (2047, 256, 0, 23), (100, 100, 0, 301), (2056, 256, 0, 19), (520, 256, 0, 77),
+    (2048, 48, 0, 61), (2048, 64, 1, 45), (2048, 4096, 1, 3)])
+def test_benchmarked_off_shapes_bit_exact(N, M, layout, F):
+    """The shapes the benchmark times besides its own (ragged N, N = 8 mod 16, a short
+    integration, input-major M = 64 and 4096), each over several CTAs' worth of
+    frames with a ragged tail: everything bit-exact against the oracle."""
+    rng = np.random.default_rng(N * 11 + M * 3 + layout)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    want = oracle.flag(x, M, N, 3.0, 0.0, layout=layout)
+    got = run_compute(x, M, N, 3.0, 0.0, layout=layout)
+    assert_parity(got, want)
+
+
 @pytest.mark.parametrize("N,M,F", [(256, 256, 40), (2048, 128, 6), (100, 64, 9)])
 def test_independent_estimates_bit_exact(N, M, F):
     """sk_compute_inputs: per-input SK^_i and one-input flags against the oracle."""

@@ -246,6 +246,54 @@ def test_admission_budget_and_ring_full():
         sk.sk_server_destroy(server)
 
 
+def test_admission_by_device_free_memory():
+    """Admission takes the lesser of the caller's budget and the device's real free
+    memory (cudaMemGetInfo at each sk_stream_open, less the server's 256 MiB headroom):
+    with a budget far above the device, a stream is refused while other allocations
+    hold the device's memory, and admitted once they are released."""
+    _need_gpu()
+    N, M = 2048, 256
+    server = sk.sk_server_create(0, 1 << 40)
+    hold = []
+    try:
+        a = sk.sk_stream_open(server, N, M, ring_frames=4)
+        # hold device memory until less than the headroom is free (plain allocations)
+        step = 1 << 30
+        while True:
+            free = torch.cuda.mem_get_info()[0]
+            if free < (160 << 20):
+                break
+            want = min(step, free - (96 << 20))
+            if want < (8 << 20):
+                break
+            try:
+                hold.append(torch.empty(want, dtype=torch.uint8, device="cuda:0"))
+            except RuntimeError:
+                step //= 4
+                if step < (8 << 20):
+                    break
+        assert torch.cuda.mem_get_info()[0] < (256 << 20)
+        with pytest.raises(sk.SkError) as e:
+            sk.sk_stream_open(server, N, M, ring_frames=4)
+        assert e.value.status == sk.SK_ERR_BUSY
+        assert "free" in e.value.message
+        hold.clear()
+        torch.cuda.empty_cache()
+        b = sk.sk_stream_open(server, N, M, ring_frames=4)
+        # the admitted streams still serve frames
+        frame = np.full(N * M, 0x99, dtype=np.uint8)
+        for sid in (a, b):
+            t = sk.sk_stream_submit(server, sid, frame, 0)
+            sk.sk_ticket_wait(server, t)
+        sk.sk_stream_close(server, a)
+        sk.sk_stream_close(server, b)
+        assert sk.sk_server_stats(server)["rejected"] >= 1
+    finally:
+        hold.clear()
+        torch.cuda.empty_cache()
+        sk.sk_server_destroy(server)
+
+
 def test_ticket_timeout_and_concurrent_submitters():
     _need_gpu()
     N, M, T = 256, 256, 40
