@@ -51,6 +51,8 @@ KERNEL_SOURCES = ["paper_1808_10365_b300/csrc/sk_device.cuh",
 PROFILE_SUMMARY = {0: os.path.join(ROOT, "profiles", "sk_fused_kernel_full_array.json"),
                    1: os.path.join(ROOT, "profiles", "sk_imajor_kernel_full_array.json")}
 LAYOUT_SUFFIX = {0: "", 1: ", input-major [frame][input][t]"}
+PATH_NAMES = {1: "team", 2: "warp-slice", 3: "row-balanced warp-slice", 4: "general",
+              5: "per-input"}
 
 
 def kernel_hash() -> str:
@@ -705,6 +707,8 @@ def run_gpu(args):
     e2e_steps = min(args.e2e_steps, args.steps)
     if e2e_steps > 0:
         e2e = run_e2e(sk, plan, d_in, d_mask, F, fb, bytes_per_step, e2e_steps, stream, ws)
+    # the read path the benchmark launch took (sk_launch_config_t.last_path)
+    taken = sk.sk_plan_get_config(plan)["last_path"]
     sustained = None
     if args.sustained_seconds > 0:
         sustained = sustained_leg(sk, plan, d_in, F, d_sk, d_mask, stream, alg_bytes,
@@ -724,10 +728,9 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": ((f"sk_fused_kernel<{rows},2,false,2048,0>"
-                                 + (", team path" if os.environ.get("SK_WARP_SLICE") == "0" or rows != 16
-                                    else ", warp-slice path"))
-                                if layout == 0 else "sk_imajor_kernel<8,2,1,0,1>"),
+                     "kernel": ((f"sk_fused_kernel<{rows},2,false,2048,0>" if layout == 0
+                                 else "sk_imajor_kernel<8,2,true,0,1>")
+                                + f", {PATH_NAMES.get(taken, 'unknown')} path"),
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": mean_launch_s * 1e3,
                      "launch_ms_min_median_max": [min(launch_ms), statistics.median(launch_ms),

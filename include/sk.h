@@ -25,7 +25,10 @@
  * unless stated otherwise.
  *
  * Environment (read once per process; none changes results, only speed):
- *   SK_AUTOTUNE_CACHE    tile cache file ("N M layout rows grid" lines)
+ *   SK_AUTOTUNE_CACHE    launch configuration cache file, read at each plan
+ *                        creation (lines "N M layout rows grid path team_log2
+ *                        prefetch batch_path", see sk_launch_config_t; older
+ *                        "N M layout rows grid" lines are still read)
  *   SK_WARP_SLICE=0      one-item launches: team path (one barrier per frame)
  *                        instead of the warp-slice path (time-major, N a multiple
  *                        of 8 from 256 to 4096)
@@ -121,10 +124,10 @@ typedef int64_t sk_ticket_t;
  * thresholds on Q for N_eff = 1..N (Sec. 3.2: outside mean +- a*sqrt(var),
  * var = 4/(M N_eff) from the moments below Eq. final; mean 1 + delta, App.
  * B), the fp32 scale (M+1)/((M-1) N_eff) of Eq. final, and, with
- * SK_RUNNING_OFFSET, the offset table.  Copies them to `device`.  Tile
- * choice (rows per register batch) comes from the autotune cache file named
+ * SK_RUNNING_OFFSET, the offset table.  Copies them to `device`.  The launch
+ * configuration (sk_launch_config_t) comes from the autotune cache file named
  * by the environment variable SK_AUTOTUNE_CACHE when it has an entry for
- * (N, M, layout), else from the built-in default.
+ * (N, M, layout), else from the built-in defaults.
  * Errors: INVALID_ARG (null, N or M out of range, bad layout, n_sigma < 0),
  * CUDA, OOM.  *out is NULL on error.
  */
@@ -148,6 +151,63 @@ sk_status_t sk_plan_set_tiles(sk_plan_t plan, int32_t rows_per_batch,
                               int32_t grid_ctas);
 sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows_per_batch,
                               int32_t *grid_ctas);
+
+/*
+ * Read paths of the fused kernel.  Requested (sk_launch_config_t.path,
+ * .batch_path): AUTO lets the library choose by shape; TEAM takes the team
+ * path (the threads of a frame meet at one barrier per frame); WARP_SLICE
+ * has the warps of a frame combine through a ring of shared-memory slots
+ * (whole frames per team); ROW_BALANCED adds equal row ranges over the grid
+ * through the plan's scratch.  A path the shape cannot take (or the launch:
+ * a captured launch has no row balancing) falls back to the one it can.
+ * Reported (sk_launch_config_t.last_path) besides those: GENERAL (any N and
+ * M, either layout) and PER_INPUT (input-major lengths of the per-input path).
+ */
+typedef enum {
+    SK_PATH_AUTO = 0,
+    SK_PATH_TEAM = 1,
+    SK_PATH_WARP_SLICE = 2,
+    SK_PATH_ROW_BALANCED = 3,
+    SK_PATH_GENERAL = 4,
+    SK_PATH_PER_INPUT = 5
+} sk_path_t;
+
+/*
+ * Launch configuration of a plan, the space the autotuner searches.  None of
+ * it changes results (the combination over inputs and rows is exact integer
+ * arithmetic), only speed.
+ *   rows       rows of 8 bytes per register batch of the time-major vector
+ *              paths: 16 (needs M % 32 == 0) or 8; the warp-slice paths run
+ *              32-row turns on 16 and, only where M = 16 mod 32, 16-row
+ *              turns on 8
+ *   grid_ctas  CTAs of a one-item launch (0: one per SM)
+ *   path       sk_path_t requested for one-item launches (0..3)
+ *   team_log2  input-major layout: threads per frame as a power of two,
+ *              5..8 (5..9 on the per-input path); set 0 for the plan's own
+ *              choice (about 2 KB of frame per thread); get returns the size
+ *              in use (0 for plans without an input-major fast path)
+ *   prefetch   0: the L2 prefetch of the read paths, 1: none
+ *   batch_path sk_path_t requested for this plan's items in sk_batch_create:
+ *              time-major N = 2048 items take the warp-slice class for
+ *              WARP_SLICE or ROW_BALANCED, the team class for TEAM, and by
+ *              their M for AUTO (warp slices at M <= 128)
+ *   last_path  (get only) the path the plan's latest one-item launch took
+ *              (0 before any)
+ */
+typedef struct {
+    int32_t rows;
+    int32_t grid_ctas;
+    int32_t path;
+    int32_t team_log2;
+    int32_t prefetch;
+    int32_t batch_path;
+    int32_t last_path;
+} sk_launch_config_t;
+
+/* Set the plan's launch configuration (last_path is ignored).  INVALID_ARG
+ * for values outside the ranges above. */
+sk_status_t sk_plan_set_config(sk_plan_t plan, const sk_launch_config_t *cfg);
+sk_status_t sk_plan_get_config(sk_plan_t plan, sk_launch_config_t *cfg);
 
 /*
  * Raw statistics of n_frames frames at d_in (device, 16-byte aligned,
@@ -191,7 +251,7 @@ sk_status_t sk_finish(sk_plan_t plan, const int64_t *d_q, const int32_t *d_neff,
 /*
  * Scratch of the device calls (sk_compute, sk_flag, sk_compute_inputs and
  * the chunks of sk_flag_host).  Time-major plans with N a multiple of 8 from
- * 256 to 4096 and M % 32 == 0, and input-major plans of M = 128, 256 or 4096, give
+ * 256 to 4096 and M % 16 == 0, and input-major plans of M = 128, 256 or 4096, give
  * every team of the launch an equal share of rows; frames cut between teams
  * are combined in a scratch of the plan (about 5 MB time-major, a few KB
  * input-major) that every launch leaves zero.  The first such call that is

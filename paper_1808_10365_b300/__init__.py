@@ -16,7 +16,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsk.so")
+# SK_DEBUG_LIBRARY=1 loads the debug build (bounds-checked loads and stores)
+LIB_PATH = os.path.join(HERE, "libsk_debug.so" if os.environ.get("SK_DEBUG_LIBRARY") == "1"
+                        else "libsk.so")
 # tile choices measured on B300 by autotune.py; a caller's SK_AUTOTUNE_CACHE wins
 os.environ.setdefault("SK_AUTOTUNE_CACHE", os.path.join(HERE, "tiles_b300.txt"))
 
@@ -37,12 +39,19 @@ SK_RUNNING_MU = 0x4
 SK_OFFSET_BUCKETS = 4096
 SK_MAX_INPUTS = 4096
 SK_MAX_TIME = 4096
+SK_PATH_AUTO = 0
+SK_PATH_TEAM = 1
+SK_PATH_WARP_SLICE = 2
+SK_PATH_ROW_BALANCED = 3
+SK_PATH_GENERAL = 4
+SK_PATH_PER_INPUT = 5
 SK_NOALLOC_MAX_BYTES = 16 * 1024 * 1024
 SK_NOALLOC_MAX_FRAMES = 65536
 
 EXPORTED = [
     "sk_plan_create", "sk_plan_destroy", "sk_plan_thresholds", "sk_plan_offset_table",
-    "sk_plan_set_tiles", "sk_plan_get_tiles", "sk_compute", "sk_flag", "sk_flag_host",
+    "sk_plan_set_tiles", "sk_plan_get_tiles", "sk_plan_set_config", "sk_plan_get_config",
+    "sk_compute", "sk_flag", "sk_flag_host",
     "sk_flag_host_noalloc", "sk_compute_inputs", "sk_finish",
     "sk_batch_create", "sk_batch_run", "sk_batch_launches", "sk_batch_destroy", "sk_server_create",
     "sk_server_destroy", "sk_stream_open", "sk_stream_submit", "sk_stream_submit_ref",
@@ -65,6 +74,13 @@ class sk_params_t(ctypes.Structure):
                 ("layout", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("n_sigma", ctypes.c_double), ("mean_offset", ctypes.c_double),
                 ("offset_table", ctypes.c_void_p)]
+
+
+class sk_launch_config_t(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+                ("path", ctypes.c_int32), ("team_log2", ctypes.c_int32),
+                ("prefetch", ctypes.c_int32), ("batch_path", ctypes.c_int32),
+                ("last_path", ctypes.c_int32)]
 
 
 class sk_batch_item_t(ctypes.Structure):
@@ -124,6 +140,8 @@ def library():
         "sk_plan_offset_table": [P, P],
         "sk_plan_set_tiles": [P, I32, I32],
         "sk_plan_get_tiles": [P, ctypes.POINTER(I32), ctypes.POINTER(I32)],
+        "sk_plan_set_config": [P, ctypes.POINTER(sk_launch_config_t)],
+        "sk_plan_get_config": [P, ctypes.POINTER(sk_launch_config_t)],
         "sk_compute": [P, P, I64, P, P, P, P, P, P],
         "sk_flag": [P, P, I64, P, P, P],
         "sk_flag_host": [P, P, I64, P, P, P],
@@ -284,6 +302,20 @@ def sk_plan_get_tiles(plan):
     g = ctypes.c_int32()
     _check(library().sk_plan_get_tiles(plan, ctypes.byref(r), ctypes.byref(g)))
     return r.value, g.value
+
+
+def sk_plan_get_config(plan) -> dict:
+    """The plan's launch configuration (sk_launch_config_t) as a dict."""
+    c = sk_launch_config_t()
+    _check(library().sk_plan_get_config(plan, ctypes.byref(c)))
+    return {k: getattr(c, k) for k, _ in sk_launch_config_t._fields_}
+
+
+def sk_plan_set_config(plan, rows=16, grid_ctas=0, path=SK_PATH_AUTO, team_log2=0, prefetch=0,
+                       batch_path=SK_PATH_AUTO):
+    c = sk_launch_config_t(int(rows), int(grid_ctas), int(path), int(team_log2), int(prefetch),
+                           int(batch_path), 0)
+    _check(library().sk_plan_set_config(plan, ctypes.byref(c)))
 
 
 def sk_compute(plan, d_in, n_frames, s1=None, s2=None, q=None, sk=None, neff=None, stream=None):

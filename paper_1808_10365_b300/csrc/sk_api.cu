@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
         const bool fast =
             single.fast == 1 && single.M % (R * S) == 0 && (NC == 0 || single.N == NC);
-        if constexpr (R * S == 32 && !SRV) {
+        if constexpr ((R * S == 32 || R * S == 16) && !SRV) {
             if (fast && single.wi) {
                 if (single.rb)
                     run_fast_rb<R, S, NC>(single, lb, ts, &tmap);
@@ -279,16 +279,19 @@ static const KernelFn kServedSplit[2] = {sk_fused_kernel<16, 2, true, 0, 3>,
                                          sk_fused_kernel<8, 2, true, 0, 3>};
 // input-major: per-input path G = 2, 4, 8; grouped path G = 8 for M = 128,
 // 256, 512 (CH = 1, 2, 4) and 1024, 2048, 4096 (CH = 4 on SPLIT = 2, 4, 8
-// sub-inputs), without and with the L2 prefetch
-static const KernelFn kImajor[15] = {
+// sub-inputs), and G = 4 for M = 64 (CH = 1), without and with the L2 prefetch
+constexpr int kImajorShapes = 7;
+constexpr int kImajorGroupedNoPf = 3, kImajorGroupedPf = 3 + kImajorShapes;
+static const KernelFn kImajor[3 + 2 * kImajorShapes] = {
     sk_imajor_kernel<2, 0, false>,          sk_imajor_kernel<4, 0, false>,
     sk_imajor_kernel<8, 0, false>,          sk_imajor_kernel<8, 1, false>,
     sk_imajor_kernel<8, 2, false>,          sk_imajor_kernel<8, 4, false>,
     sk_imajor_kernel<8, 4, false, 0, 2>,    sk_imajor_kernel<8, 4, false, 0, 4>,
-    sk_imajor_kernel<8, 4, false, 0, 8>,    sk_imajor_kernel<8, 1, true>,
-    sk_imajor_kernel<8, 2, true>,           sk_imajor_kernel<8, 4, true>,
-    sk_imajor_kernel<8, 4, true, 0, 2>,     sk_imajor_kernel<8, 4, true, 0, 4>,
-    sk_imajor_kernel<8, 4, true, 0, 8>};
+    sk_imajor_kernel<8, 4, false, 0, 8>,    sk_imajor_kernel<4, 1, false>,
+    sk_imajor_kernel<8, 1, true>,           sk_imajor_kernel<8, 2, true>,
+    sk_imajor_kernel<8, 4, true>,           sk_imajor_kernel<8, 4, true, 0, 2>,
+    sk_imajor_kernel<8, 4, true, 0, 4>,     sk_imajor_kernel<8, 4, true, 0, 8>,
+    sk_imajor_kernel<4, 1, true>};
 
 // Lanes per input on the per-input input-major path: 4 up to M = 512, 8 above
 // (measured best on B300), or SK_IMAJOR_LANES (2, 4 or 8); reduced while 16 G
@@ -306,9 +309,10 @@ int imajor_lanes(int M)
     return g;
 }
 
-// Shape index of M on the grouped input-major path (G = 8 lanes): 0..5 for M =
-// 128, 256, 512, 1024, 2048, 4096, else -1 (the per-input path).
-// SK_IMAJOR_GROUPED=0 turns the grouped path off.
+// Shape index of M on the grouped input-major path: 0..5 for M = 128, 256, 512,
+// 1024, 2048, 4096 (groups of 8 inputs on 8 lanes), 6 for M = 64 (groups of 4 on
+// 4 lanes), else -1 (the per-input path).  SK_IMAJOR_GROUPED=0 turns the grouped
+// path off.
 int imajor_shape(int M)
 {
     static const bool off = [] {
@@ -320,7 +324,7 @@ int imajor_shape(int M)
     for (int sh = 0; sh < 6; ++sh)
         if (M == (128 << sh))
             return sh;
-    return -1;
+    return M == 64 ? 6 : -1;
 }
 
 
@@ -333,17 +337,21 @@ static bool imajor_prefetch()
     return on;
 }
 
-// batched input-major launches: grouped path per M shape (batch classes 3..8)
-static const KernelFn kImajorBatched[6] = {
+// batched input-major launches: grouped path per M shape (batch classes
+// kFirstImajorClass + shape index)
+static const KernelFn kImajorBatched[kImajorShapes] = {
     sk_imajor_kernel<8, 1, true, 1>,    sk_imajor_kernel<8, 2, true, 1>,
     sk_imajor_kernel<8, 4, true, 1>,    sk_imajor_kernel<8, 4, true, 1, 2>,
-    sk_imajor_kernel<8, 4, true, 1, 4>, sk_imajor_kernel<8, 4, true, 1, 8>};
+    sk_imajor_kernel<8, 4, true, 1, 4>, sk_imajor_kernel<8, 4, true, 1, 8>,
+    sk_imajor_kernel<4, 1, true, 1>};
+static_assert(kFirstImajorClass + kImajorShapes == kBatchClasses, "batch classes");
 
-static KernelFn imajor_kernel(int M)
+static KernelFn imajor_kernel(int M, bool prefetch)
 {
     const int sh = imajor_shape(M);
     if (sh >= 0)
-        return kImajor[(imajor_prefetch() ? 9 : 3) + sh];
+        return kImajor[(prefetch && imajor_prefetch() ? kImajorGroupedPf : kImajorGroupedNoPf) +
+                       sh];
     const int g = imajor_lanes(M);
     return kImajor[g == 2 ? 0 : (g == 4 ? 1 : 2)];
 }
@@ -403,7 +411,7 @@ static bool warp_slice_on()
 
 bool warp_slice_shape(int N, int M)
 {
-    return warp_slice_on() && N >= 256 && N % 8 == 0 && N <= 4096 && M % 32 == 0;
+    return warp_slice_on() && N >= 256 && N % 8 == 0 && N <= 4096 && M % 16 == 0;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -501,26 +509,38 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     const int64_t gmax = grid_cap > 0 ? grid_cap : sm_count(device);
     const int nci = it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
     const int tile = pick_tile(rows, it.M % 32 == 0);
+    // the plan's requested path and prefetch (autotuned launch configuration)
+    const int req = plan ? plan->path : SK_PATH_AUTO;
+    const bool pf_off = plan && plan->prefetch_off;
     KernelFn fn = kSingle[tile][nci];
     if (it.fast == 2)
-        fn = imajor_kernel(it.M);
+        fn = imajor_kernel(it.M, !pf_off);
     Item run = it;
+    if (pf_off)
+        run.prefetch = 0;
     CUtensorMap tmap;
     memset(&tmap, 0, sizeof tmap);
     // warp-slice path: 1 with the tensor map of the prefetch, 2 without one (N % 16
     // != 0; measured faster than a map of row pairs, whose prefetch slowed N = 1000
-    // from 6.0 to 4.2 TB/s), 0 not taken (or the map failed)
+    // from 6.0 to 4.2 TB/s; or the prefetch turned off), 0 not taken (or the map
+    // failed)
     run.wi = 0;
     // one-warp teams (N = 256) have no barrier to remove: there the warp-slice path
     // pays only when too few frames to occupy the grid would leave most warps idle
     // (64 frames: 16 against 30 us); with more it measured 1-15 % slower
     const bool ws_n256 = it.N > 256 || it.n_frames * 4 < (int64_t)gmax * (kThreads / 32);
-    if (it.fast == 1 && tile == 0 && warp_slice_shape(it.N, it.M) && ws_n256)
-        run.wi = it.N % 16 != 0
+    const bool want_ws = req == SK_PATH_AUTO
+                             ? ws_n256
+                             : (req == SK_PATH_WARP_SLICE || req == SK_PATH_ROW_BALANCED);
+    // 16-row turns on the 8-row tile only where 32-row turns do not fit (M = 16
+    // mod 32): an 8-row tile requested for M % 32 == 0 keeps the team path
+    const bool ws_tile = tile == 0 || it.M % 32 != 0;
+    if (it.fast == 1 && ws_tile && warp_slice_shape(it.N, it.M) && want_ws)
+        run.wi = (it.N % 16 != 0 || pf_off)
                      ? 2
                      : (encode_input_map(it.in, it.N, it.n_frames * it.M, &tmap) ? 1 : 0);
     // input-major teams of two or more warps combine through the same slot ring
-    if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6)
+    if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6 && req != SK_PATH_TEAM)
         run.wi = 1;
     // teams per CTA: 16 / ceil(N/256) on the warp-slice paths
     const int64_t Tl = (run.wi && it.fast == 1) ? (kThreads / 32) / ((it.N + 255) / 256) : T;
@@ -534,7 +554,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     int64_t units = 0;
     size_t need = 0;
     if (run.wi && it.fast == 1) {
-        units = it.n_frames * (it.M / 32);
+        units = it.n_frames * (it.M / (tile == 0 ? 32 : 16));
         const int64_t K = std::max<int64_t>(1, std::min<int64_t>(gmax, units / Tl)) * Tl;
         const int64_t W = (it.N + 255) / 256;
         need = (size_t)K * it.N * 8 + (size_t)((K * W + 1) & ~(int64_t)1) * 4 + (size_t)K * 16;
@@ -547,7 +567,8 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
             need = (size_t)std::max<int64_t>(1, std::min<int64_t>(gmax, units / T)) * T * 16;
         }
     }
-    if (units > 0 && plan && row_balance_on()) {
+    if (units > 0 && plan && row_balance_on() &&
+        (req == SK_PATH_AUTO || req == SK_PATH_ROW_BALANCED)) {
         const int64_t grb = std::max<int64_t>(1, std::min<int64_t>(gmax, units / Tl));
         lk = std::unique_lock<std::mutex>(plan->rb_mu);
         run.rb = rb_acquire(plan, st, need, may_alloc);
@@ -560,6 +581,21 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     }
     if (g < 1)
         g = 1;
+#ifdef SK_DEBUG
+    // slots of the row-balancing scratch: one per team of the grid
+    run.dbg_rb_slots = rb ? g * (it.fast == 1 ? Tl : T) : 0;
+#endif
+    if (plan) {
+        // the path the kernel takes for this item (sk_fused_kernel, sk_imajor_kernel)
+        int taken = SK_PATH_GENERAL;
+        const bool grouped = imajor_shape(it.M) >= 0;
+        if ((it.fast == 1 && it.M % (tile == 0 ? 32 : 16) == 0) ||
+            (it.fast == 2 && grouped && it.imajor_team_log2 >= 5))
+            taken = run.wi ? (rb ? SK_PATH_ROW_BALANCED : SK_PATH_WARP_SLICE) : SK_PATH_TEAM;
+        else if (it.fast == 2 && !grouped && it.imajor_team_log2 >= 5)
+            taken = SK_PATH_PER_INPUT;
+        plan->last_path.store(taken, std::memory_order_relaxed);
+    }
     fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(nullptr, nullptr, nullptr, run, tmap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -678,8 +714,24 @@ static int ceil_log2(int64_t v)
     return l;
 }
 
-// Autotune cache: lines "N M layout rows grid" (grid 0 = one CTA per SM).
-static bool cached_tiles(int32_t N, int32_t M, int32_t layout, int *rows, int *grid)
+// Autotune cache: lines "N M layout rows grid path team_log2 prefetch batch_path"
+// (sk_launch_config_t; grid 0 = one CTA per SM), or the older "N M layout rows
+// grid" (the rest AUTO / default).  The last valid line for (N, M, layout) wins.
+struct CachedConfig {
+    int rows = 16, grid = 0, path = SK_PATH_AUTO, team_log2 = 0, prefetch = 0,
+        batch_path = SK_PATH_AUTO;
+};
+
+static bool config_valid(const CachedConfig &c)
+{
+    return (c.rows == 8 || c.rows == 16) && c.grid >= 0 && c.grid <= 65535 && c.path >= 0 &&
+           c.path <= SK_PATH_ROW_BALANCED && (c.team_log2 == 0 ||
+                                              (c.team_log2 >= 5 && c.team_log2 <= 9)) &&
+           (c.prefetch == 0 || c.prefetch == 1) && c.batch_path >= 0 &&
+           c.batch_path <= SK_PATH_ROW_BALANCED;
+}
+
+static bool cached_config(int32_t N, int32_t M, int32_t layout, CachedConfig *out)
 {
     const char *path = getenv("SK_AUTOTUNE_CACHE");
     if (!path || !*path)
@@ -687,19 +739,33 @@ static bool cached_tiles(int32_t N, int32_t M, int32_t layout, int *rows, int *g
     FILE *f = fopen(path, "r");
     if (!f)
         return false;
-    int n, m, l, r, g;
     bool found = false;
     char line[256];
     while (fgets(line, sizeof line, f)) {
-        if (sscanf(line, "%d %d %d %d %d", &n, &m, &l, &r, &g) == 5 && n == N && m == M &&
-            l == layout && (r == 8 || r == 16) && g >= 0) {
-            *rows = r;
-            *grid = g;
+        int n, m, l;
+        CachedConfig c;
+        const int k = sscanf(line, "%d %d %d %d %d %d %d %d %d", &n, &m, &l, &c.rows, &c.grid,
+                             &c.path, &c.team_log2, &c.prefetch, &c.batch_path);
+        if ((k == 5 || k == 9) && n == N && m == M && l == layout && config_valid(c)) {
+            if (k == 5)
+                c.path = c.team_log2 = c.prefetch = c.batch_path = 0;
+            *out = c;
             found = true;
         }
     }
     fclose(f);
     return found;
+}
+
+// Valid input-major team size override for a plan (grouped path 5..8, per-input
+// path 5..9).
+static bool team_override_ok(const sk_plan_s *pl, int t)
+{
+    if (t == 0)
+        return true;
+    if (!pl->imajor)
+        return false;
+    return t >= 5 && t <= (imajor_shape(pl->p.n_time) >= 0 ? 8 : 9);
 }
 
 }  // namespace sk
@@ -716,7 +782,7 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.N = p.n_inputs;
     it.layout = p.layout;
     it.team_log2 = team_log2;
-    it.imajor_team_log2 = imajor_team_log2;
+    it.imajor_team_log2 = team_override ? team_override : imajor_team_log2;
     it.t_lo = d_t_lo;
     it.t_hi = d_t_hi;
     it.c_tab = d_c;
@@ -730,6 +796,16 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.err = d_err;
     it.tmap = nullptr;
     it.rb = nullptr;
+#ifdef SK_DEBUG
+    // SK_DEBUG_SHRINK_INPUT=k (debug builds, tests): the checks take the input as
+    // k bytes shorter than it is, so that the last bytes' loads fail their check
+    static const int64_t shrink = [] {
+        const char *v = getenv("SK_DEBUG_SHRINK_INPUT");
+        return v ? (int64_t)atoll(v) : (int64_t)0;
+    }();
+    it.dbg_in_bytes = n_frames * (int64_t)p.n_time * p.n_inputs - shrink;
+    it.dbg_rb_slots = 0;
+#endif
     return it;
 }
 
@@ -819,7 +895,15 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
     }
     pl->rows = 16;
     pl->grid_ctas = 0;
-    cached_tiles(N, M, p.layout, &pl->rows, &pl->grid_ctas);
+    CachedConfig cc;
+    if (cached_config(N, M, p.layout, &cc)) {
+        pl->rows = cc.rows;
+        pl->grid_ctas = cc.grid;
+        pl->path = cc.path;
+        pl->team_override = team_override_ok(pl, cc.team_log2) ? cc.team_log2 : 0;
+        pl->prefetch_off = cc.prefetch == 1;
+        pl->batch_path = cc.batch_path;
+    }
 
     // thresholds on Q, one pair per N_eff (Sec. 3.2); order of operations fixed
     pl->t_lo.assign(N + 1, 0);
@@ -945,12 +1029,58 @@ extern "C" sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows, int32_t 
     return SK_OK;
 }
 
+extern "C" sk_status_t sk_plan_set_config(sk_plan_t plan, const sk_launch_config_t *cfg)
+{
+    if (!plan || !cfg)
+        return set_error(SK_ERR_INVALID_ARG, "sk_plan_set_config: null argument");
+    CachedConfig c;
+    c.rows = cfg->rows;
+    c.grid = cfg->grid_ctas;
+    c.path = cfg->path;
+    c.team_log2 = cfg->team_log2;
+    c.prefetch = cfg->prefetch;
+    c.batch_path = cfg->batch_path;
+    if (!config_valid(c) || !team_override_ok(plan, c.team_log2))
+        return set_error(SK_ERR_INVALID_ARG,
+                         "sk_plan_set_config: rows 8 or 16, grid 0..65535, path and batch_path "
+                         "0..3, team_log2 0 or 5..8 (5..9 on the per-input path; input-major "
+                         "plans only), prefetch 0 or 1");
+    plan->rows = c.rows;
+    plan->grid_ctas = c.grid;
+    plan->path = c.path;
+    plan->team_override = c.team_log2;
+    plan->prefetch_off = c.prefetch == 1;
+    plan->batch_path = c.batch_path;
+    return SK_OK;
+}
+
+extern "C" sk_status_t sk_plan_get_config(sk_plan_t plan, sk_launch_config_t *cfg)
+{
+    if (!plan || !cfg)
+        return set_error(SK_ERR_INVALID_ARG, "sk_plan_get_config: null argument");
+    cfg->rows = plan->rows;
+    cfg->grid_ctas = plan->grid_ctas;
+    cfg->path = plan->path;
+    cfg->team_log2 = plan->imajor ? (plan->team_override ? plan->team_override
+                                                         : plan->imajor_team_log2)
+                                  : 0;
+    cfg->prefetch = plan->prefetch_off ? 1 : 0;
+    cfg->batch_path = plan->batch_path;
+    cfg->last_path = plan->last_path.load(std::memory_order_relaxed);
+    return SK_OK;
+}
+
 // A bounded wait inside an earlier launch of this plan gave up (its results are
 // void): report it once, as SK_ERR_TIMEOUT, on the next call.
 sk_status_t sk::pending_fault(sk_plan_t plan, const char *who)
 {
-    if (plan->h_err && *reinterpret_cast<volatile int32_t *>(plan->h_err)) {
+    const int32_t err = plan->h_err ? *reinterpret_cast<volatile int32_t *>(plan->h_err) : 0;
+    if (err) {
         *plan->h_err = 0;
+        if (err == kErrBounds)
+            return set_error(SK_ERR_CUDA, "%s: a bounds check inside an earlier launch failed "
+                                          "(debug build); the access was skipped and that "
+                                          "launch's results are void", who);
         return set_error(SK_ERR_TIMEOUT, "%s: a bounded wait inside an earlier launch "
                                          "ran out; that launch's results are void", who);
     }

@@ -205,12 +205,15 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
         if (std::find(b->plans.begin(), b->plans.end(), bi.plan) == b->plans.end())
             b->plans.push_back(bi.plan);
         int c = batch_class(it);
-        // time-major N = 2048 items of M <= 128 on 16-row tiles take the warp-slice
-        // path (measured 5-6 % faster there; at M = 256 and 1024 the team path is
-        // 1.5 % and 8 % faster in a batch): each gets a tensor map of its input, in
-        // device memory, for the per-warp prefetch
+        // time-major N = 2048 items on 16-row tiles take the warp-slice path when
+        // the plan's batch path asks for it, or by default at M <= 128 (measured
+        // 5-6 % faster there; at M = 256 and 1024 the team path was 1.5 % and 8 %
+        // faster in a batch): each gets a tensor map of its input, in device
+        // memory, for the per-warp prefetch
+        const int bp = bi.plan->batch_path;
+        const bool want_ws = bp == SK_PATH_AUTO ? it.M <= 128 : bp != SK_PATH_TEAM;
         CUtensorMap m;
-        if (c == 2 && bi.plan->rows == 16 && it.M % 32 == 0 && it.M <= 128 &&
+        if (c == 2 && bi.plan->rows == 16 && it.M % 32 == 0 && want_ws &&
             it.n_frames > 0 && warp_slice_shape(it.N, it.M) &&
             encode_input_map(it.in, it.N, it.n_frames * it.M, &m)) {
             c = kWarpSliceClass;

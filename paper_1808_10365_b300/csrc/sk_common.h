@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdarg>
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -36,12 +37,14 @@ sk_status_t launch_schedule(const Item *d_items, const Chunk *d_chunks,
                             int device, cudaStream_t st, int nclass = 0);
 // Kernel class of a batched item: 2 for time-major fast-path items of N = 2048,
 // 1 for N = 256, 4..9 for input-major items on the grouped path with M = 128,
-// 256, ..., 4096, 0 for the rest (runtime row stride or the general path).
+// 256, ..., 4096 and 10 for M = 64, 0 for the rest (runtime row stride or the
+// general path).
 // sk_batch_create moves class-2 items with a tensor map to class 3 (the
 // warp-slice path).
 int batch_class(const Item &it);
 // Time-major shapes of the warp-slice path (N a multiple of 8 from 256 to 4096,
-// M % 32 == 0), unless SK_WARP_SLICE=0.
+// M % 16 == 0: 32-row turns, or 16-row turns when M = 16 mod 32), unless
+// SK_WARP_SLICE=0.
 bool warp_slice_shape(int N, int M);
 // Tensor map of a time-major input for the warp-slice path's prefetch: rows of N
 // bytes (N % 16 == 0), boxes of 32 rows x 256 bytes.  False if none can be made.
@@ -51,7 +54,7 @@ sk_status_t pending_fault(sk_plan_t plan, const char *who);
 // Set-up of sk_flag_host_noalloc on `device` (current): looks up the device
 // address of its fixed staging array, which loads the module holding it.
 void noalloc_prepare(int device);
-constexpr int kBatchClasses = 10;
+constexpr int kBatchClasses = 11;
 constexpr int kWarpSliceClass = 3;
 constexpr int kFirstImajorClass = 4;
 int pick_tile(int rows, bool all_m32);
@@ -112,6 +115,14 @@ struct sk_plan_s {
     bool imajor = false;  // input-major fast path applies
     int rows = 16;      // register batch rows of the fast path
     int grid_ctas = 0;  // 0: one CTA per SM
+    // launch configuration (sk_launch_config_t): requested read path of one-item
+    // launches and of batched items, input-major team size override (0: none),
+    // L2 prefetch off; the path the latest one-item launch took
+    int path = SK_PATH_AUTO;
+    int batch_path = SK_PATH_AUTO;
+    int team_override = 0;
+    bool prefetch_off = false;
+    std::atomic<int> last_path{0};
     std::vector<int64_t> t_lo, t_hi, etab;
     std::vector<float> c_tab;
     int64_t *d_t_lo = nullptr, *d_t_hi = nullptr, *d_e = nullptr;

@@ -76,7 +76,51 @@ struct Item {
     int32_t *err;            // mapped host word: set when a bounded wait gives up
     const CUtensorMap *tmap;  // batched time-major items: the input's map in device memory
     int32_t *rb;              // row-balanced warp-slice launch: the plan's zeroed scratch
+#ifdef SK_DEBUG
+    int64_t dbg_in_bytes;     // debug builds: bytes of `in` the kernel may read
+    int64_t dbg_rb_slots;     // debug builds: slots of the row-balancing scratch
+#endif
 };
+
+// Debug builds (-DSK_DEBUG) check every global load and every output store of
+// the kernels against the item's buffers before making it: an access outside
+// them is skipped (a load gives bytes without power) and sets the plan's error
+// word to kErrBounds, which the plan's next call reports.  No trap: the launch
+// runs to its end.  Release builds compile the checks to nothing.
+constexpr int32_t kErrBounds = 2;
+#ifdef SK_DEBUG
+__device__ __forceinline__ bool dbg_fail(const Item &it)
+{
+    if (it.err)
+        atomicExch(it.err, kErrBounds);
+    return false;
+}
+// [p, p + bytes) inside the item's input
+__device__ __forceinline__ bool dbg_in(const Item &it, const void *p, int64_t bytes)
+{
+    const uint8_t *b = (const uint8_t *)p;
+    return (b >= it.in && bytes >= 0 && b + bytes <= it.in + it.dbg_in_bytes) ? true
+                                                                              : dbg_fail(it);
+}
+// frame f of the item's per-frame outputs, and input i of its per-input ones
+__device__ __forceinline__ bool dbg_out(const Item &it, int64_t f, int64_t i = 0)
+{
+    return (f >= 0 && f < it.n_frames && i >= 0 && i < it.N) ? true : dbg_fail(it);
+}
+__device__ __forceinline__ bool dbg_slot(const Item &it, int64_t slot)
+{
+    return (slot >= 0 && slot < it.dbg_rb_slots) ? true : dbg_fail(it);
+}
+#define SK_DBG_IN(it, p, bytes) ::sk::dbg_in((it), (p), (int64_t)(bytes))
+#define SK_DBG_OUT(it, f) ::sk::dbg_out((it), (int64_t)(f))
+#define SK_DBG_OUT_IN(it, f, i) ::sk::dbg_out((it), (int64_t)(f), (int64_t)(i))
+#define SK_DBG_SLOT(it, s) ::sk::dbg_slot((it), (int64_t)(s))
+#else
+#define SK_DBG_IN(it, p, bytes) true
+#define SK_DBG_OUT(it, f) true
+#define SK_DBG_OUT_IN(it, f, i) true
+#define SK_DBG_SLOT(it, s) true
+#endif
 
 // Work of one CTA.  kind 0: frames [f_begin, f_end) of item `item`, the CTA's
 // teams striding through them.  kind 1: items [f_begin, f_end), one frame each
@@ -315,6 +359,8 @@ __device__ __forceinline__ void init_wi_slots(TeamSmem &ts)
 // against the integer thresholds of C), SK (Eq. final), Q and N_eff.
 __device__ __forceinline__ void write_frame(const Item &it, int64_t frame, int64_t Q, int32_t C)
 {
+    if (!SK_DBG_OUT(it, frame))
+        return;
     uint8_t m = 1;
     if (C > 0)
         m = (Q > it.t_hi[C] || Q < it.t_lo[C]) ? 1 : 0;
@@ -470,7 +516,7 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
                     q += qi;
                     cnt += 1;
                 }
-                if (it.sk_in) {
+                if (it.sk_in && SK_DBG_OUT_IN(it, frame, col0 + k)) {
                     // single-receiver estimate SK^_i = (M+1)/(M-1) r_i and its own
                     // flag against the one-input thresholds (Sec. 2.2.3, independent
                     // estimates)
@@ -481,7 +527,7 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
                 }
             }
         }
-        if (it.s1) {
+        if (it.s1 && SK_DBG_OUT_IN(it, frame, col0)) {
             int32_t *o1 = it.s1 + frame * it.N + col0;
             int32_t *o2 = it.s2 + frame * it.N + col0;
 #pragma unroll
@@ -549,7 +595,7 @@ __device__ __forceinline__ void frame_epilogue(const Item &it, int64_t frame, bo
         int64_t hi = it.t_hi[cnt] + (stateful ? e : 0);
         m = (q > hi || q < lo) ? 1 : 0;
     }
-    if (fvalid && lit == 0) {
+    if (fvalid && lit == 0 && SK_DBG_OUT(it, frame)) {
         if (it.sk) {
             float skv = __int_as_float(0x7FC00000);
             if (SERVED && it.running_mu && stateful)

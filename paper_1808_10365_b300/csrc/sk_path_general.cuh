@@ -62,13 +62,16 @@ __device__ __forceinline__ void run_general(const Item &it, int64_t f_begin, int
                         const int d = (int)((uintptr_t)a & 7u);
                         const uint8_t *w = a - d;
                         sh[r] = d;
-                        if (w >= lo_lim && w + 16 <= hi_lim) {
+                        if (w >= lo_lim && w + 16 <= hi_lim && SK_DBG_IN(it, w, 16)) {
                             lo[r] = __ldg((const unsigned long long *)w);
                             hi[r] = __ldg((const unsigned long long *)(w + 8));
                         } else {
-                            uint64_t v = 0;
-                            for (int j = 0; j < keep; ++j)
-                                v |= (uint64_t)a[j] << (8 * j);
+                            uint64_t v = 0x8888888888888888ull;
+                            if (SK_DBG_IN(it, a, keep)) {
+                                v = 0;
+                                for (int j = 0; j < keep; ++j)
+                                    v |= (uint64_t)a[j] << (8 * j);
+                            }
                             lo[r] = v;  // already aligned to the thread's columns
                             sh[r] = -1;
                         }
@@ -97,7 +100,8 @@ __device__ __forceinline__ void run_general(const Item &it, int64_t f_begin, int
                 for (int j = 0; j < kVec; ++j) {
                     const int64_t c = col0 + j;
                     if (c < N) {
-                        uint32_t b = it.layout == 0 ? fb[(int64_t)t * N + c] : fb[c * M + t];
+                        const uint8_t *pb = fb + (it.layout == 0 ? (int64_t)t * N + c : c * M + t);
+                        const uint32_t b = SK_DBG_IN(it, pb, 1) ? *pb : 0x88u;
                         const uint32_t sh = 8u * (uint32_t)(j & 3);
                         if (j < 4)
                             w0 = (w0 & ~(0xFFu << sh)) | (b << sh);

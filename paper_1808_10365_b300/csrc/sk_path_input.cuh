@@ -63,9 +63,12 @@ __device__ __forceinline__ void run_imajor(const Item &it, int64_t f_begin, int6
 #pragma unroll
         for (int u = 0; u < KB; ++u) {
             const int i = seg + lk * nseg;
-            if (lf < f_end && lk < K && i < N)
-                buf[u] = ldg_stream16(it.in + lf * fbytes + (int64_t)i * M +
-                                      (int64_t)(j + lc * G) * 16);
+            if (lf < f_end && lk < K && i < N) {
+                const uint8_t *a = it.in + lf * fbytes + (int64_t)i * M + (int64_t)(j + lc * G) * 16;
+                buf[u] = SK_DBG_IN(it, a, 16) ? ldg_stream16(a)
+                                              : make_uint4(0x88888888u, 0x88888888u,
+                                                           0x88888888u, 0x88888888u);
+            }
             if (++lc == C) {
                 lc = 0;
                 ++lk;
@@ -127,11 +130,11 @@ __device__ __forceinline__ void run_imajor(const Item &it, int64_t f_begin, int6
                                 cnt += 1;
                             }
                             const int64_t o = frame * N + i;
-                            if (it.s1) {
+                            if (it.s1 && SK_DBG_OUT_IN(it, frame, i)) {
                                 it.s1[o] = s1;
                                 it.s2[o] = s2;
                             }
-                            if (it.sk_in) {
+                            if (it.sk_in && SK_DBG_OUT_IN(it, frame, i)) {
                                 it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1])
                                                   : __int_as_float(0x7FC00000);
                                 if (it.mask_in)
@@ -149,7 +152,7 @@ __device__ __forceinline__ void run_imajor(const Item &it, int64_t f_begin, int6
             }
         }
         team_sum(q, cnt, e, team_log2, team_idx, parity, ts, false);
-        if (fvalid && lit == 0) {
+        if (fvalid && lit == 0 && SK_DBG_OUT(it, frame)) {
             uint8_t m = 1;
             if (cnt > 0)
                 m = (q > it.t_hi[cnt] || q < it.t_lo[cnt]) ? 1 : 0;
@@ -275,11 +278,11 @@ __device__ __forceinline__ void group_terms(const Item &it, int32_t (&s1)[G], in
             cnt += 1;
         }
         const int64_t o = frame * it.N + i;
-        if (it.s1) {
+        if (it.s1 && SK_DBG_OUT_IN(it, frame, i)) {
             it.s1[o] = s1[0];
             it.s2[o] = s2[0];
         }
-        if (it.sk_in) {
+        if (it.sk_in && SK_DBG_OUT_IN(it, frame, i)) {
             it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
             if (it.mask_in)
                 it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
@@ -340,10 +343,16 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
     auto base_of = [&](int64_t f, int k) -> const uint8_t * {
         return it.in + f * fbytes + (int64_t)((k * nseg + seg) * G) * M + j * 16;
     };
+    // debug builds: a group whose chunks would leave the input is not read
+    auto dbg_live = [&](const uint8_t *base, int live) -> int {
+        return (live > 0 && !SK_DBG_IN(it, base, (int64_t)(live - 1) * M + (CH - 1) * G * 16 + 16))
+                   ? 0
+                   : live;
+    };
     uint4 A[KB], B[KB];
     int64_t frame = f_begin + team_idx;
     const uint8_t *cur_base = base_of(frame, 0);
-    int cur_live = live_of(frame, 0);
+    int cur_live = dbg_live(cur_base, live_of(frame, 0));
     load_group_batch<M, G, CH, KB, 0>(A, cur_base, cur_live);
     for (int64_t kk = 0; kk < kmax; ++kk) {
         const bool fvalid = frame < f_end;
@@ -354,7 +363,7 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
             const int64_t nf = (k + 1 < NG) ? frame : frame + T;
             const int nk = (k + 1 < NG) ? k + 1 : 0;
             const uint8_t *nxt_base = base_of(nf, nk);
-            const int nxt_live = live_of(nf, nk);
+            const int nxt_live = dbg_live(nxt_base, live_of(nf, nk));
             if (PF && nxt_live > 0 && j == 0)
                 prefetch_l2(nxt_base, (uint32_t)(nxt_live * M));
             int32_t s1[G], s2[G];
@@ -397,11 +406,11 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
                     cnt += 1;
                 }
                 const int64_t o = frame * N + i;
-                if (it.s1) {
+                if (it.s1 && SK_DBG_OUT_IN(it, frame, i)) {
                     it.s1[o] = s1[0];
                     it.s2[o] = s2[0];
                 }
-                if (it.sk_in) {
+                if (it.sk_in && SK_DBG_OUT_IN(it, frame, i)) {
                     it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
                     if (it.mask_in)
                         it.mask_in[o] =
@@ -426,7 +435,7 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
             continue;
         }
         team_sum(q, cnt, e, team_log2, team_idx, parity, ts, false);
-        if (fvalid && lit == 0) {
+        if (fvalid && lit == 0 && SK_DBG_OUT(it, frame)) {
             uint8_t m = 1;
             if (cnt > 0)
                 m = (q > it.t_hi[cnt] || q < it.t_lo[cnt]) ? 1 : 0;
@@ -486,9 +495,11 @@ __device__ __forceinline__ void run_imajor_rb(const Item &it, uint32_t lb, TeamS
     const int64_t step = (int64_t)team * M;  // bytes per group row
     const uint8_t *cur = it.in + (int64_t)u0 * step + seg * G * M + j * 16;
 
+    // debug builds: a group row whose chunks would leave the input is not read
+    [[maybe_unused]] const int64_t gext = (int64_t)(G - 1) * M + (CH - 1) * G * 16 + 16;
     uint4 A[KB], B[KB];
     if (u0 < u1)
-        load_group_batch<M, G, CH, KB, 0>(A, cur, G);
+        load_group_batch<M, G, CH, KB, 0>(A, cur, SK_DBG_IN(it, cur, gext) ? G : 0);
     int64_t q = 0;
     int32_t cnt = 0;
     int frame = u0 / NG, ku = u0 % NG;  // the group row's frame and row in it
@@ -505,7 +516,9 @@ __device__ __forceinline__ void run_imajor_rb(const Item &it, uint32_t lb, TeamS
             s1[t] = 0;
             s2[t] = 0;
         }
-        group_batches<M, G, CH, NB, KB, 0>(A, B, cur, G, nxt, more ? G : 0, lb, s1, s2);
+        group_batches<M, G, CH, NB, KB, 0>(A, B, cur, G, nxt,
+                                           (more && SK_DBG_IN(it, nxt, gext)) ? G : 0, lb, s1,
+                                           s2);
         group_terms<G, SPLIT>(it, s1, s2, j, G, frame, (ku * nseg + seg) * G, M, q, cnt);
         cur = nxt;
         ++ku;
@@ -527,16 +540,18 @@ __device__ __forceinline__ void run_imajor_rb(const Item &it, uint32_t lb, TeamS
             int32_t *pcnt = reinterpret_cast<int32_t *>(pq + K);
             int32_t *prow = pcnt + K;
             const int64_t slot = (((int64_t)frame * NG + 1) * K + TT - 1) / TT;
-            atomicAdd(pq + slot, (unsigned long long)q);
-            atomicAdd(pcnt + slot, cnt);
-            __threadfence();
-            const int part = ku - ku0;
-            if (atomicAdd(prow + slot, part) + part == NG * W) {
+            if (SK_DBG_SLOT(it, slot)) {
+                atomicAdd(pq + slot, (unsigned long long)q);
+                atomicAdd(pcnt + slot, cnt);
                 __threadfence();
-                const int64_t Q = (int64_t)atomicExch(pq + slot, 0ull);
-                const int32_t C = atomicExch(pcnt + slot, 0);
-                atomicExch(prow + slot, 0);
-                write_frame(it, frame, Q, C);
+                const int part = ku - ku0;
+                if (atomicAdd(prow + slot, part) + part == NG * W) {
+                    __threadfence();
+                    const int64_t Q = (int64_t)atomicExch(pq + slot, 0ull);
+                    const int32_t C = atomicExch(pcnt + slot, 0);
+                    atomicExch(prow + slot, 0);
+                    write_frame(it, frame, Q, C);
+                }
             }
         }
         __syncwarp();

@@ -6,6 +6,15 @@
 
 namespace sk {
 
+// R rows of bytes 0x88 (re = im = 0): no power, so they add nothing to the sums.
+template <int R>
+__device__ __forceinline__ void fill_zero_power_rows(uint2 (&b)[R])
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        b[r] = make_uint2(0x88888888u, 0x88888888u);
+}
+
 // Fast path: time-major, N % 8 == 0, M % (R*S) == 0, 8-byte aligned rows.
 // Every load stays inside rows 0..M-1 of a frame below f_end.  Rows stream
 // through a ring of S register batches of R rows: batch g is loaded right after
@@ -44,7 +53,9 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
     if (ok) {
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-            if constexpr (NC > 0) {
+            if (!SK_DBG_IN(it, fp + (int64_t)j * R * N, (R - 1) * N + 8)) {
+                fill_zero_power_rows<R>(buf[j]);
+            } else if constexpr (NC > 0) {
                 load_rows_imm<NC>(buf[j], fp + (int64_t)j * R * NC,
                                   std::make_integer_sequence<int, R>{});
             } else {
@@ -102,7 +113,9 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
                         flush(acc, s1, s2);
                 }
                 if (lok) {
-                    if constexpr (NC > 0) {
+                    if (!SK_DBG_IN(it, pn + (int64_t)j * R * N, (R - 1) * N + 8)) {
+                        fill_zero_power_rows<R>(buf[j]);
+                    } else if constexpr (NC > 0) {
                         load_rows_imm<NC>(buf[j], pn + (int64_t)j * R * NC,
                                           std::make_integer_sequence<int, R>{});
                     } else {
@@ -140,6 +153,10 @@ __device__ __forceinline__ void run_rows(const Item &it, int64_t frame, int b0, 
         acc[k] = 0u;
     auto load = [&](uint2 (&b)[R], int batch) {
         const uint8_t *p = fp + (int64_t)batch * R * N;
+        if (!SK_DBG_IN(it, p, (R - 1) * N + 8)) {
+            fill_zero_power_rows<R>(b);
+            return;
+        }
         if constexpr (NC > 0) {
             load_rows_imm<NC>(b, p, std::make_integer_sequence<int, R>{});
         } else {
@@ -187,6 +204,7 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *tm)
 
 // Register batches of a lane past the last input: bytes 0x88 (re = im = 0) have
 // no power, so the lane's sums stay zero and its inputs count for nothing.
+
 template <int S, int R>
 __device__ __forceinline__ void fill_zero_power(uint2 (&buf)[S][R])
 {
@@ -218,14 +236,14 @@ __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int c
             q += qi;
             cnt += 1;
         }
-        if (it.sk_in && col0 < it.N) {
+        if (it.sk_in && col0 < it.N && SK_DBG_OUT_IN(it, frame, col0 + k)) {
             const int64_t o = frame * it.N + col0 + k;
             it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
             if (it.mask_in)
                 it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
         }
     }
-    if (it.s1 && col0 < it.N) {
+    if (it.s1 && col0 < it.N && SK_DBG_OUT_IN(it, frame, col0 + kVec - 1)) {
         int32_t *o1 = it.s1 + frame * it.N + col0;
         int32_t *o2 = it.s2 + frame * it.N + col0;
 #pragma unroll
@@ -241,7 +259,8 @@ __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int c
 }
 
 // Warp-slice path: one-item launches and batched items with a tensor map,
-// time-major, N a multiple of 8 from 256 to 4096, 16 x 2 tiles.  The team of a
+// time-major, N a multiple of 8 from 256 to 4096, 16 x 2 tiles (8 x 2 for
+// M = 16 mod 32: 16-row turns, the 32-row prefetch box every other turn).  The team of a
 // frame is ceil(N/256) warps, each owning a 256-column slice of the team's frames
 // and running on its own: no barrier per frame.  Lane 0 of each warp asks L2 for
 // the rows the warp will load two ring turns ahead with one 2D tensor prefetch
@@ -255,7 +274,10 @@ template <int R, int S, int NC>
 __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int64_t f_end,
                                             uint32_t lb, TeamSmem &ts, const CUtensorMap *tmap)
 {
-    static_assert(R * S == 32, "one prefetch box per ring turn");
+    static_assert(R * S == 32 || R * S == 16, "ring turns of 32 or 16 rows");
+    // one 32-row prefetch box per 32 rows: every turn, or every other 16-row turn
+    constexpr int BB = 32 / R;             // batches per box
+    constexpr int PER = 32 / (R * S);      // turns per box
     const int M = it.M;
     const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
     // teams of W warps, one 256-column slice each (the last one partial when 256
@@ -272,8 +294,8 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     // lanes past N read nothing (none when N is a compiled multiple of 256)
     const bool col_ok = (NC > 0 && NC % 256 == 0) || col0 < N;
     // no tensor map when N is not a multiple of 16 (the map's row stride must
-    // be): those launches stream without the L2 prefetch
-    const bool pf = NC > 0 || it.wi != 2;
+    // be) or the plan turned the prefetch off: those launches stream without it
+    const bool pf = it.wi != 2;
     const int64_t fbytes = (int64_t)M * N;
     const int nb = M / R;
     const int64_t kmax = (f_end - f_begin + T - 1) / T;
@@ -288,6 +310,10 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     const uint8_t *fp = in + frame * fbytes + col0;
     // R rows from p, row stride N (a load immediate when NC > 0)
     auto load = [&](uint2 (&b)[R], const uint8_t *p) {
+        if (!SK_DBG_IN(it, p, (R - 1) * N + 8)) {
+            fill_zero_power_rows<R>(b);
+            return;
+        }
         if constexpr (NC > 0) {
             load_rows_imm<NC>(b, p, std::make_integer_sequence<int, R>{});
         } else {
@@ -314,12 +340,12 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
             s2[j] = 0;
         }
         for (int jb = 0; jb < nb; jb += S) {
-            if (lane == 0 && pf) {
-                const int ba = jb + 2 * S;  // two ring turns ahead
+            if (lane == 0 && pf && (jb / S) % PER == 0) {
+                const int ba = jb + 2 * BB;  // two boxes (64 rows) ahead
                 if (ba < nb) {
                     if (ok)
                         prefetch_box(tmap, xs, (int)(frame * M + ba * R));
-                } else if (nok && ba - nb + S <= nb) {
+                } else if (nok && ba - nb + BB <= nb) {
                     prefetch_box(tmap, xs, (int)(nframe * M + (ba - nb) * R));
                 }
             }
@@ -356,8 +382,8 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
 
 // Row-balanced warp-slice path (one-item time-major launches of the warp-slice
 // shapes, given the plan's scratch).  The input is one sequence of F*M rows (a
-// frame is a block of M consecutive rows), cut into TT = F*M/32 ring turns of 32
-// rows.  Team k of the grid's K teams takes the turns [TT*k/K, TT*(k+1)/K), so
+// frame is a block of M consecutive rows), cut into TT = F*M/RS ring turns of RS
+// rows (RS = R*S: 32, or 16 on the 8-row tile for M = 16 mod 32).  Team k of the grid's K teams takes the turns [TT*k/K, TT*(k+1)/K), so
 // teams differ by at most one turn whatever F is, and each of its warps runs its
 // 256-column slice of those rows.  A frame that lies inside the range goes through
 // the team's slot ring as on the warp-slice path.  A frame that a range boundary
@@ -373,7 +399,9 @@ template <int R, int S, int NC>
 __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSmem &ts,
                                             const CUtensorMap *tmap)
 {
-    static_assert(R * S == 32, "one turn per ring revolution");
+    static_assert(R * S == 32 || R * S == 16, "one turn per ring revolution");
+    constexpr int RS = R * S;         // rows per turn: 32, or 16 for M = 16 mod 32
+    constexpr int PER = 32 / RS;      // turns per 32-row prefetch box
     const int M = it.M;
     const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
     // teams of W warps (256-column slices, the last one partial when 256 does not
@@ -391,9 +419,9 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
     // lanes past N read and add nothing (none when N is a compiled multiple of 256)
     const bool col_ok = (NC > 0 && NC % 256 == 0) || col0 < N;
     // no tensor map when N is not a multiple of 16 (the map's row stride must
-    // be): those launches stream without the L2 prefetch
-    const bool pf = NC > 0 || it.wi != 2;
-    const int64_t tpf = M / 32;  // turns per frame
+    // be) or the plan turned the prefetch off: those launches stream without it
+    const bool pf = it.wi != 2;
+    const int64_t tpf = M / RS;  // turns per frame
     const int64_t TT = it.n_frames * tpf;
     const int64_t K = (int64_t)gridDim.x * T;
     const int64_t kt = (int64_t)blockIdx.x * T + team_idx;
@@ -410,6 +438,10 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
 
     // R rows from p, row stride N (a load immediate when NC > 0)
     auto load = [&](uint2 (&b)[R], const uint8_t *p) {
+        if (!SK_DBG_IN(it, p, (R - 1) * N + 8)) {
+            fill_zero_power_rows<R>(b);
+            return;
+        }
         if constexpr (NC > 0) {
             load_rows_imm<NC>(b, p, std::make_integer_sequence<int, R>{});
         } else {
@@ -424,7 +456,7 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
     if (t0 < t1 && col_ok) {
 #pragma unroll
         for (int j = 0; j < S; ++j)
-            load(buf[j], in + (t0 * 32 + j * R) * N);
+            load(buf[j], in + (t0 * RS + j * R) * N);
     }
     uint32_t acc[kVec];
     int32_t s1[kVec], s2[kVec];
@@ -439,10 +471,10 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
     int gf = (int)(t0 - frame * tpf);  // ... and turn in it (counters: no division per turn)
     int gf0 = gf;                 // first turn of the current frame part
     for (int64_t g = t0; g < t1; ++g) {
-        if (lane == 0 && pf && g + 2 < t1)
-            prefetch_box(tmap, xs, (int)((g + 2) * 32));  // two turns ahead
+        if (lane == 0 && pf && g % PER == 0 && g + 2 * PER < t1)
+            prefetch_box(tmap, xs, (int)((g + 2 * PER) * RS));  // 64 rows ahead
         const bool more = g + 1 < t1;
-        const uint8_t *pn = in + (g + 1) * 32 * N;
+        const uint8_t *pn = in + (g + 1) * RS * N;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
 #pragma unroll
@@ -472,7 +504,7 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
             // S2 <= 2^26 for M <= 4096, so the halves never carry into each other)
             const int64_t slot = ((frame * tpf + 1) * K + TT - 1) / TT;
             unsigned long long *sp = ps + slot * N + col0;
-            if (col_ok) {
+            if (col_ok && SK_DBG_SLOT(it, slot)) {
 #pragma unroll
                 for (int k = 0; k < kVec; ++k)
                     atomicAdd(sp + k,

@@ -104,3 +104,22 @@ def test_binding_rejects_buffers_before_any_call():
     finally:
         sk._plan_shape.pop(fake, None)
         sk._stream_shape.pop((fake, 3), None)
+
+
+def test_autotune_cache_lines_merge(tmp_path):
+    """The tuner's cache file: one 9-field line per shape (sk_launch_config_t order),
+    a shape's new line replacing its old one, other shapes kept."""
+    from paper_1808_10365_b300 import autotune
+
+    path = tmp_path / "tiles.txt"
+    path.write_text("# old\n2048 256 0 16 0\n256 256 0 16 0\n")
+    e = dict(N=2048, M=256, layout=0, rows=16, grid_ctas=0, path=1, team_log2=0, prefetch=1,
+             batch_path=2)
+    autotune.write_cache(str(path), [e])
+    lines = [ln.split() for ln in path.read_text().splitlines() if not ln.startswith("#")]
+    assert ["256", "256", "0", "16", "0"] in lines
+    assert ["2048", "256", "0", "16", "0", "1", "0", "1", "2"] in lines
+    assert sum(1 for ln in lines if ln[:3] == ["2048", "256", "0"]) == 1
+    cands = autotune.candidates(2048, 256, 0, 0)
+    assert cands[0]["path"] == 0 and len(cands) == 1 + 2 * (3 + 1)
+    assert len(autotune.candidates(2048, 256, 1, 8)) == 1 + 3 * 2 * 2

@@ -28,7 +28,7 @@ def _dev():
      (2048, 48, 4, 0), (256, 256, 10, 1), (2048, 128, 3, 1)],
     # input-major items only: the grouped path per M, ragged N, and the general path
     [(2048, 256, 9, 1), (256, 1024, 7, 1), (512, 512, 5, 1), (100, 128, 6, 1), (64, 64, 4, 1),
-     (2048, 128, 11, 1)],
+     (2048, 128, 11, 1), (2048, 64, 37, 1), (33, 64, 6, 1)],
     # time-major N = 2048 items of M <= 128 (the warp-slice class, one item long
     # enough that each team's slot ring wraps), beside N = 2048 items of larger M
     [(2048, 128, 19, 0), (2048, 64, 33, 0), (2048, 32, 3000, 0), (2048, 96, 7, 0),

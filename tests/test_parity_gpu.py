@@ -348,9 +348,11 @@ def test_pearson3_thresholds_and_masks_bit_exact(N, M):
 
 
 @pytest.mark.parametrize("N,M,F", [(2048, 256, 9), (256, 256, 37), (100, 128, 11), (7, 1024, 5),
-                                   (1, 128, 3), (512, 2048, 3), (4096, 128, 2), (33, 384, 6)])
+                                   (1, 128, 3), (512, 2048, 3), (4096, 128, 2), (33, 384, 6),
+                                   (2048, 64, 21), (33, 64, 9), (4096, 64, 5), (3, 64, 40)])
 def test_input_major_fast_path_bit_exact(N, M, F):
-    """Layout [frame][input][t] through the input-major path (M % 128 == 0)."""
+    """Layout [frame][input][t] through the input-major paths: grouped for M = 64 and
+    128 * 2^k (with sub-inputs above 512), per-input for other multiples of 16 G."""
     rng = np.random.default_rng(N * 3 + M * 5 + F)
     x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
     x[0, : M] = 0x88                       # input 0 of frame 0 has no power

@@ -1,6 +1,6 @@
 """Row-balanced launches: a one-item time-major launch of the warp-slice shapes
-hands every team an equal range of 32-row turns (an input-major one, of group
-rows), and frames cut by a range boundary are combined through the plan's
+hands every team an equal range of 32-row turns (16-row turns when M = 16 mod
+32; an input-major one, of group rows), and frames cut by a range boundary are combined through the plan's
 scratch in device memory.  Against the
 oracle: cut frames of every kind (a frame shared by two teams, a frame spread
 over many teams, a team inside one frame), per-input outputs written by the
@@ -53,10 +53,18 @@ def _bytes(N, M, F, seed):
     (256, 256, 64, 0),      # one-warp teams, 16 per CTA: 512 turns over 2368 teams
     (256, 128, 3001, 0),
     (264, 64, 77, 0),       # two warps, the second with one lane busy
+    # M = 16 mod 32: 16-row turns on the 8-row tile (the prefetch box every other turn)
+    (2048, 48, 301, 0),     # 3 turns per frame, frames cut in every position
+    (512, 16, 2999, 0),     # one turn per frame
+    (4096, 112, 5, 0),      # 35 turns over 148 teams: fewer turns than teams
+    (1000, 80, 61, 0),      # N = 8 mod 16: no tensor map, no prefetch
+    (2056, 48, 31, 0),
     # input-major: group rows of team*M bytes balanced over the grid (M = 128,
     # 256 and 4096; other M hand out whole frames)
     (2048, 256, 299, 1),    # 8 group rows per frame
     (2048, 4096, 3, 1),     # sub-inputs: 8 per input
+    (2048, 64, 301, 1),     # groups of 4 inputs on 4 lanes, 64-thread teams
+    (256, 64, 999, 1),
     (4096, 128, 150, 1),
     (512, 1024, 37, 1),
     (256, 512, 7, 1)])
@@ -167,7 +175,7 @@ def test_no_alloc_call_before_and_after_scratch():
 
 def test_random_balanced_shapes_sweep():
     """40 seeded random shapes on the balanced paths (N a multiple of 8 from 256 to
-    4096, M a multiple of 32, 1 to a few hundred frames, so frames cut between
+    4096, M a multiple of 32 or, every fourth case, 16 mod 32, 1 to a few hundred frames, so frames cut between
     teams in every way; some input-major with M = 128 or 256), each against the
     oracle: S1, S2, Q, N_eff, SK bits and masks."""
     dev = _dev()
@@ -176,7 +184,7 @@ def test_random_balanced_shapes_sweep():
         layout = 1 if rng.random() < 0.2 else 0
         if layout == 0:
             N = int(8 * rng.integers(32, 513))
-            M = int(32 * rng.integers(1, 33))
+            M = int(32 * rng.integers(1, 33)) if case % 4 else int(16 * (2 * rng.integers(0, 16) + 1))
         else:
             N = int(256 * rng.integers(1, 9))
             M = int(rng.choice([128, 256]))
