@@ -81,6 +81,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 return;
             }
         }
+        if constexpr (R * S == 16 && NC == 0 && !SRV) {
+            // ragged N (not a multiple of 8), balanced rows: one loop per N mod 8
+            if (single.fast == 3 && single.wi && single.rb && single.M % 16 == 0) {
+                switch (single.N & 7) {
+                case 1: run_fast_rag<1>(single, lb, ts); break;
+                case 2: run_fast_rag<2>(single, lb, ts); break;
+                case 3: run_fast_rag<3>(single, lb, ts); break;
+                case 4: run_fast_rag<4>(single, lb, ts); break;
+                case 5: run_fast_rag<5>(single, lb, ts); break;
+                case 6: run_fast_rag<6>(single, lb, ts); break;
+                default: run_fast_rag<7>(single, lb, ts); break;
+                }
+                return;
+            }
+        }
         if (fast)
             run_fast<R, S, SRV, NC>(single, fb, fe, lb, ts, parity);
         else
@@ -508,7 +523,8 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     const int64_t T = kThreads >> (it.fast == 2 ? it.imajor_team_log2 : it.team_log2);
     const int64_t gmax = grid_cap > 0 ? grid_cap : sm_count(device);
     const int nci = it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
-    const int tile = pick_tile(rows, it.M % 32 == 0);
+    // ragged N takes its balanced path on the 8-row tile (16-row turns)
+    const int tile = it.fast == 3 ? 1 : pick_tile(rows, it.M % 32 == 0);
     // the plan's requested path and prefetch (autotuned launch configuration)
     const int req = plan ? plan->path : SK_PATH_AUTO;
     const bool pf_off = plan && plan->prefetch_off;
@@ -542,8 +558,13 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // input-major teams of two or more warps combine through the same slot ring
     if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6 && req != SK_PATH_TEAM)
         run.wi = 1;
+    // ragged N: warp slices without a tensor map, given balanced rows (below)
+    const bool tm_ws = it.fast == 1 || it.fast == 3;
+    if (it.fast == 3 && warp_slice_on() && it.M % 16 == 0 &&
+        (req == SK_PATH_AUTO || req == SK_PATH_ROW_BALANCED))
+        run.wi = 2;
     // teams per CTA: 16 / ceil(N/256) on the warp-slice paths
-    const int64_t Tl = (run.wi && it.fast == 1) ? (kThreads / 32) / ((it.N + 255) / 256) : T;
+    const int64_t Tl = (run.wi && tm_ws) ? (kThreads / 32) / ((it.N + 255) / 256) : T;
     // frames per team decide the grid, unless rows are balanced over the grid
     int64_t g = std::min<int64_t>(gmax, (it.n_frames + Tl - 1) / Tl);
     std::unique_lock<std::mutex> lk;
@@ -553,7 +574,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // team*M bytes, scratch for Q and N_eff of cut frames
     int64_t units = 0;
     size_t need = 0;
-    if (run.wi && it.fast == 1) {
+    if (run.wi && tm_ws) {
         units = it.n_frames * (it.M / (tile == 0 ? 32 : 16));
         const int64_t K = std::max<int64_t>(1, std::min<int64_t>(gmax, units / Tl)) * Tl;
         const int64_t W = (it.N + 255) / 256;
@@ -579,11 +600,16 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
             lk.unlock();
         }
     }
+    if (it.fast == 3 && !rb) {
+        // ragged N without balanced rows: the general path, whole frames per team
+        run.wi = 0;
+        g = std::min<int64_t>(gmax, (it.n_frames + T - 1) / T);
+    }
     if (g < 1)
         g = 1;
 #ifdef SK_DEBUG
     // slots of the row-balancing scratch: one per team of the grid
-    run.dbg_rb_slots = rb ? g * (it.fast == 1 ? Tl : T) : 0;
+    run.dbg_rb_slots = rb ? g * (tm_ws ? Tl : T) : 0;
 #endif
     if (plan) {
         // the path the kernel takes for this item (sk_fused_kernel, sk_imajor_kernel)
@@ -592,6 +618,8 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         if ((it.fast == 1 && it.M % (tile == 0 ? 32 : 16) == 0) ||
             (it.fast == 2 && grouped && it.imajor_team_log2 >= 5))
             taken = run.wi ? (rb ? SK_PATH_ROW_BALANCED : SK_PATH_WARP_SLICE) : SK_PATH_TEAM;
+        else if (it.fast == 3 && rb)
+            taken = SK_PATH_ROW_BALANCED;
         else if (it.fast == 2 && !grouped && it.imajor_team_log2 >= 5)
             taken = SK_PATH_PER_INPUT;
         plan->last_path.store(taken, std::memory_order_relaxed);
@@ -787,7 +815,7 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.t_hi = d_t_hi;
     it.c_tab = d_c;
     it.e_tab = d_e;
-    it.fast = fast ? 1 : (imajor ? 2 : 0);
+    it.fast = fast ? 1 : (imajor ? 2 : (ragged ? 3 : 0));
     it.prefetch = 1;
     it.running_mu = (p.flags & SK_RUNNING_MU) ? 1 : 0;
     it.n_sigma = p.n_sigma;
@@ -879,6 +907,8 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
     const int32_t N = p.n_inputs, M = p.n_time;
     pl->team_log2 = ceil_log2((N + kVec - 1) / kVec);
     pl->fast = (p.layout == SK_LAYOUT_TIME_MAJOR) && (N % kVec == 0) && (M % kFlushRows == 0);
+    // time-major N not a multiple of 8: the ragged balanced path (16-row turns)
+    pl->ragged = (p.layout == SK_LAYOUT_TIME_MAJOR) && (N % kVec != 0) && (M % 16 == 0);
     const int gl = imajor_lanes(M);
     const bool grouped = imajor_shape(M) >= 0;
     pl->imajor = (p.layout == SK_LAYOUT_INPUT_MAJOR) && (grouped || M % (16 * gl) == 0);

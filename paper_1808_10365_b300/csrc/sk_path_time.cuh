@@ -219,6 +219,9 @@ __device__ __forceinline__ void fill_zero_power(uint2 (&buf)[S][R])
 // with the per-input outputs the item asks for (S1, S2, SK_i and its one-input
 // flag), and the sum over the warp of their fixed-point q_i and count.  A lane
 // past the last input (its sums zero) adds nothing and writes nothing.
+// PART: the lane may hold columns past N (ragged N), whose sums are not inputs'
+// and are left out.
+template <bool PART = false>
 __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int col0, int M,
                                             const int32_t (&s1)[kVec],
                                             const int32_t (&s2)[kVec], int64_t &q,
@@ -228,6 +231,8 @@ __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int c
     cnt = 0;
 #pragma unroll
     for (int k = 0; k < kVec; ++k) {
+        if (PART && col0 + k >= it.N)
+            continue;
         float r = 0.0f;
         int64_t qi = 0;
         const bool has = SK_EPILOGUE_ALU ? input_term_alu(s1[k], s2[k], M, r, qi)
@@ -243,11 +248,13 @@ __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int c
                 it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
         }
     }
-    if (it.s1 && col0 < it.N && SK_DBG_OUT_IN(it, frame, col0 + kVec - 1)) {
+    if (it.s1 && col0 < it.N && SK_DBG_OUT_IN(it, frame, col0)) {
         int32_t *o1 = it.s1 + frame * it.N + col0;
         int32_t *o2 = it.s2 + frame * it.N + col0;
 #pragma unroll
         for (int k = 0; k < kVec; ++k) {
+            if (PART && col0 + k >= it.N)
+                break;
             o1[k] = s1[k];
             o2[k] = s2[k];
         }
@@ -544,6 +551,193 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
                     __threadfence();
                     if (atomicAdd(parr + slot, 1) == W - 1) {
                         // the last column: the frame's outputs
+                        __threadfence();
+                        const int64_t Q = (int64_t)atomicExch(pq + slot, 0ull);
+                        const int32_t C = atomicExch(pcnt + slot, 0);
+                        atomicExch(parr + slot, 0);
+                        write_frame(it, frame, Q, C);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            acc[j] = 0u;
+            s1[j] = 0;
+            s2[j] = 0;
+        }
+        if (fend) {
+            gf = 0;
+            ++frame;
+        }
+        gf0 = gf;
+    }
+}
+
+// Ragged N (time-major, N % 8 != 0, M % 16 == 0; one-item launches given the
+// plan's scratch): the row-balanced warp-slice path above, for rows that are not
+// 8-byte aligned.  A lane's 8 bytes of row t start at a = in + t N + col0; `in`
+// is 16-byte aligned and col0 a multiple of 8, so a lies D = (t N) mod 8 bytes
+// past an 8-byte boundary, and over 16-row turns and 8-row batches D depends
+// only on the row r within its batch: D = (r NR) mod 8 with NR = N mod 8, a
+// template parameter, so every row's D is a compile-time constant.  A row takes
+// the aligned word at a - D and, when its bytes reach past it, the next one;
+// a funnel shift of each 32-bit half puts the 8 bytes in place (no shift when
+// D = 0, a swap when D = 4).  Both words start inside the row's own bytes, so no
+// load leaves the input; the last lane's bytes past column N (the next row's, or
+// beyond the input's end inside the same aligned word) are left out of the terms.
+// Rows go through L1 (ld.global.nc), where a warp's two words of a row share
+// lines.  Cut frames combine as on run_fast_rb, for the lane's columns below N.
+template <int NR>
+__device__ __forceinline__ void run_fast_rag(const Item &it, uint32_t lb, TeamSmem &ts)
+{
+    static_assert(NR >= 1 && NR <= 7, "N mod 8");
+    constexpr int R = 8, S = 2, RS = R * S;
+    const int M = it.M;
+    const int64_t N = it.N;
+    const int W = (int)((N + 255) >> 8);
+    const int T = (kThreads / 32) / W;
+    const int warp = threadIdx.x >> 5;
+    const int team_idx = warp / W;
+    if (team_idx >= T)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int c = warp - team_idx * W;
+    const int col0 = c * 256 + lane * kVec;
+    const bool col_ok = col0 < N;
+    const int keep = col_ok ? (N - col0 < kVec ? (int)(N - col0) : kVec) : 0;  // bytes of ours
+    const int64_t tpf = M / RS;  // turns per frame
+    const int64_t TT = it.n_frames * tpf;
+    const int64_t K = (int64_t)gridDim.x * T;
+    const int64_t kt = (int64_t)blockIdx.x * T + team_idx;
+    const int64_t t0 = TT * kt / K, t1 = TT * (kt + 1) / K;
+    unsigned long long *const ps = reinterpret_cast<unsigned long long *>(it.rb);
+    int32_t *const pturn = reinterpret_cast<int32_t *>(ps + K * N);
+    unsigned long long *const pq =
+        reinterpret_cast<unsigned long long *>(pturn + ((K * W + 1) & ~(int64_t)1));
+    int32_t *const pcnt = reinterpret_cast<int32_t *>(pq + K);
+    int32_t *const parr = pcnt + K;
+    WiSlot *slots = ts.wi[team_idx];
+    const uint8_t *const in = it.in + col0;
+
+    // the aligned word(s) of R rows from p (row stride N)
+    auto load = [&](uint2 (&lo)[R], uint2 (&hi)[R], const uint8_t *p) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int D = (r * NR) & 7;
+            const uint8_t *a = p + (int64_t)r * N;
+            if (!SK_DBG_IN(it, a, keep)) {
+                lo[r] = hi[r] = make_uint2(0x88888888u, 0x88888888u);
+                continue;
+            }
+            const uint2 *w = reinterpret_cast<const uint2 *>(a - D);
+            lo[r] = __ldg(w);
+            if (D > 0 && D + keep > kVec)
+                hi[r] = __ldg(w + 1);
+        }
+    };
+    // the lane's 8 bytes of a row from its aligned words
+    auto place = [](const uint2 &lo, const uint2 &hi, int D) -> uint2 {
+        const int sh = 8 * (D & 3);
+        if (D == 0)
+            return lo;
+        if (D < 4)
+            return make_uint2(__funnelshift_r(lo.x, lo.y, sh), __funnelshift_r(lo.y, hi.x, sh));
+        if (D == 4)
+            return make_uint2(lo.y, hi.x);
+        return make_uint2(__funnelshift_r(lo.y, hi.x, sh), __funnelshift_r(hi.x, hi.y, sh));
+    };
+    uint2 lo[S][R], hi[S][R];
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            lo[j][r] = hi[j][r] = make_uint2(0x88888888u, 0x88888888u);
+    if (t0 < t1 && col_ok) {
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            load(lo[j], hi[j], in + (t0 * RS + j * R) * N);
+    }
+    uint32_t acc[kVec];
+    int32_t s1[kVec], s2[kVec];
+#pragma unroll
+    for (int j = 0; j < kVec; ++j) {
+        acc[j] = 0u;
+        s1[j] = 0;
+        s2[j] = 0;
+    }
+    int64_t kk = 0;
+    int64_t frame = t0 / tpf;
+    int gf = (int)(t0 - frame * tpf);
+    int gf0 = gf;
+    for (int64_t g = t0; g < t1; ++g) {
+        const bool more = g + 1 < t1;
+        const uint8_t *pn = in + (g + 1) * RS * N;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+#pragma unroll
+            for (int r = 0; r < R; r += 2)
+                accum_pair(place(lo[j][r], hi[j][r], (r * NR) & 7),
+                           place(lo[j][r + 1], hi[j][r + 1], ((r + 1) * NR) & 7), lb, acc);
+            if (((j + 1) * R) % kFlushRows == 0)
+                flush(acc, s1, s2);
+            if (more && col_ok)
+                load(lo[j], hi[j], pn + (int64_t)j * R * N);
+        }
+        ++gf;
+        const bool fend = gf == (int)tpf;
+        if (!fend && more)
+            continue;
+        if (fend && gf0 == 0) {
+            int64_t q;
+            int32_t cnt;
+            slice_terms<true>(it, frame, col0, M, s1, s2, q, cnt);
+            if (lane == 0)
+                wi_commit(it, slots, kk, W, frame, q, cnt);
+            __syncwarp();
+            ++kk;
+        } else {
+            const int64_t slot = ((frame * tpf + 1) * K + TT - 1) / TT;
+            unsigned long long *sp = ps + slot * N + col0;
+            if (col_ok && SK_DBG_SLOT(it, slot)) {
+#pragma unroll
+                for (int k = 0; k < kVec; ++k)
+                    if (k < keep)
+                        atomicAdd(sp + k,
+                                  ((unsigned long long)(uint32_t)s2[k] << 32) | (uint32_t)s1[k]);
+            }
+            __syncwarp();
+            int fin = 0;
+            if (lane == 0) {
+                __threadfence();
+                const int part = gf - gf0;
+                fin = atomicAdd(pturn + slot * W + c, part) + part == (int)tpf;
+                if (fin)
+                    __threadfence();
+            }
+            fin = __shfl_sync(0xFFFFFFFFu, fin, 0);
+            if (fin) {
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k < kVec; ++k) {
+                    s1[k] = 0;
+                    s2[k] = 0;
+                    if (k < keep) {
+                        const unsigned long long v = atomicExch(sp + k, 0ull);
+                        s1[k] = (int32_t)(uint32_t)v;
+                        s2[k] = (int32_t)(v >> 32);
+                    }
+                }
+                int64_t q;
+                int32_t cnt;
+                slice_terms<true>(it, frame, col0, M, s1, s2, q, cnt);
+                if (lane == 0) {
+                    atomicExch(pturn + slot * W + c, 0);
+                    atomicAdd(pq + slot, (unsigned long long)q);
+                    atomicAdd(pcnt + slot, cnt);
+                    __threadfence();
+                    if (atomicAdd(parr + slot, 1) == W - 1) {
                         __threadfence();
                         const int64_t Q = (int64_t)atomicExch(pq + slot, 0ull);
                         const int32_t C = atomicExch(pcnt + slot, 0);

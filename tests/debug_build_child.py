@@ -39,6 +39,7 @@ def check_case(N, M, layout, F, cfg=None, seed=0):
         if cfg:
             sk.sk_plan_set_config(plan, **cfg)
         got = flag(plan, x, N, M, F)
+        taken = sk.sk_plan_get_config(plan)["last_path"]
         assert np.array_equal(got[1], want["mask"]), (N, M, layout, cfg)
         assert np.array_equal(got[0].view(np.uint32), want["sk"].view(np.uint32))
         # sums, Q and N_eff through sk_compute on the same plan
@@ -52,7 +53,7 @@ def check_case(N, M, layout, F, cfg=None, seed=0):
         assert np.array_equal(s1.cpu().numpy(), want["S1"]) and np.array_equal(q.cpu().numpy(), want["Q"])
         # a further call reports any failed check of the launches above
         flag(plan, x[:1], N, M, 1)
-        return sk.sk_plan_get_config(plan)["last_path"]
+        return taken
     finally:
         sk.sk_plan_destroy(plan)
 
@@ -83,7 +84,9 @@ def main():
         (2048, 48, 0, 21, dict(rows=8, path=T), T),
         (256, 256, 0, 700, None, T),
         (1000, 64, 0, 33, None, RB),
-        (2047, 256, 0, 5, None, GEN),
+        (2047, 256, 0, 5, None, RB),
+        (2047, 256, 0, 5, dict(path=T), GEN),
+        (333, 96, 0, 31, None, RB),
         (100, 100, 0, 37, None, GEN),
         (2048, 256, 1, 40, None, RB),
         (2048, 256, 1, 9, dict(path=T), T),

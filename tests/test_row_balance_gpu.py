@@ -59,6 +59,18 @@ def _bytes(N, M, F, seed):
     (4096, 112, 5, 0),      # 35 turns over 148 teams: fewer turns than teams
     (1000, 80, 61, 0),      # N = 8 mod 16: no tensor map, no prefetch
     (2056, 48, 31, 0),
+    # ragged N (not a multiple of 8): unaligned rows, two aligned words and a shift per
+    # row, one loop per N mod 8; the last lane holds columns past N
+    (2047, 256, 23, 0),     # N mod 8 = 7
+    (2049, 64, 99, 0),      # N mod 8 = 1, a last slice of one column
+    (1001, 48, 61, 0),      # 5
+    (333, 128, 77, 0),      # 5, one team of two warps
+    (98, 96, 301, 0),       # 2, one warp with 13 lanes busy
+    (4094, 16, 57, 0),      # 6, one turn per frame
+    (4093, 112, 3, 0),      # 5, fewer turns than teams
+    (3, 32, 700, 0),        # one lane, 3 inputs
+    (12, 256, 40, 0),       # 4: every other row on a 4-byte boundary
+    (2051, 32, 9, 0),       # 3
     # input-major: group rows of team*M bytes balanced over the grid (M = 128,
     # 256 and 4096; other M hand out whole frames)
     (2048, 256, 299, 1),    # 8 group rows per frame
@@ -124,11 +136,12 @@ def test_one_plan_on_two_streams():
         sk.sk_plan_destroy(plan)
 
 
-def test_captured_launch_hands_out_whole_frames():
-    """A launch captured into a CUDA graph does not use the scratch; the replayed
-    graph and the plain launch give the oracle's results."""
+@pytest.mark.parametrize("N,M,F", [(2048, 256, 299), (2047, 64, 77)])
+def test_captured_launch_hands_out_whole_frames(N, M, F):
+    """A launch captured into a CUDA graph does not use the scratch (a ragged N then
+    takes the general path); the replayed graph and the plain launch give the
+    oracle's results."""
     dev = _dev()
-    N, M, F = 2048, 256, 299
     x = _bytes(N, M, F, 5)
     want = oracle.flag(x, M, N, 3.0, 0.0)
     d_in = torch.from_numpy(x.reshape(-1)).to(dev)
