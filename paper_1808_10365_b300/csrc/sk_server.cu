@@ -156,6 +156,10 @@ struct sk_server_s {
     bool trace = false;
     double tr_n = 0, tr_frames = 0, tr_bytes = 0, tr_host_issue = 0, tr_host_total = 0,
            tr_copy = 0, tr_kernel = 0, tr_copy_to_kernel_end = 0;
+    // the slowest launches: max kernel time, host issue and issue->retire, and the
+    // launches whose kernel or issue->retire took over 500 us (SK_SERVER_TRACE)
+    double tr_kernel_max = 0, tr_issue_max = 0, tr_total_max = 0, tr_slow_kernel = 0,
+           tr_slow_total = 0;
 };
 
 static constexpr size_t kLatKeep = 1 << 20;
@@ -437,8 +441,15 @@ static void completer_main(sk_server_s *s)
             s->tr_copy += c * 1e3;
             s->tr_kernel += k * 1e3;
             s->tr_copy_to_kernel_end += ck * 1e3;
-            s->tr_host_issue += std::chrono::duration<double, std::micro>(L.t_issued - L.t_issue).count();
-            s->tr_host_total += std::chrono::duration<double, std::micro>(now - L.t_issue).count();
+            const double hi = std::chrono::duration<double, std::micro>(L.t_issued - L.t_issue).count();
+            const double ht = std::chrono::duration<double, std::micro>(now - L.t_issue).count();
+            s->tr_host_issue += hi;
+            s->tr_host_total += ht;
+            s->tr_kernel_max = std::max(s->tr_kernel_max, (double)k * 1e3);
+            s->tr_issue_max = std::max(s->tr_issue_max, hi);
+            s->tr_total_max = std::max(s->tr_total_max, ht);
+            s->tr_slow_kernel += k * 1e3 > 500.0 ? 1 : 0;
+            s->tr_slow_total += ht > 500.0 ? 1 : 0;
         }
         L.busy = false;
         L.n = 0;
@@ -576,6 +587,12 @@ extern "C" sk_status_t sk_server_destroy(sk_server_t s)
                 s->tr_host_issue / s->tr_n, s->tr_host_total / s->tr_n, s->tr_copy / s->tr_n,
                 s->tr_bytes / (s->tr_copy * 1e3 + 1e-9), s->tr_kernel / s->tr_n,
                 s->tr_copy_to_kernel_end / s->tr_n);
+    if (s->trace && s->tr_n > 0)
+        fprintf(stderr,
+                "sk_server trace: slowest kernel %.0f us, host issue %.0f us, issue->retire "
+                "%.0f us; launches over 500 us: %.0f kernels, %.0f issue->retire\n",
+                s->tr_kernel_max, s->tr_issue_max, s->tr_total_max, s->tr_slow_kernel,
+                s->tr_slow_total);
     {
         DeviceGuard dg(s->device);
         cudaStreamSynchronize(s->s_compute);
