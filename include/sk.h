@@ -45,6 +45,12 @@
  *   SK_SERVER_INJECT_FAULT=k  server (tests): launch k fails on the host, before
  *                        any CUDA call, as a failed launch would; its tickets and
  *                        the queued ones complete with SK_ERR_CUDA
+ *   SK_DEBUG_SHRINK_INPUT=k   debug build only (tests): the bounds checks take every
+ *                        input as k bytes shorter than it is, so that its last
+ *                        loads fail their checks and the plan reports it
+ * The Python binding loads the debug build of this library (every kernel load
+ * and store checked, a failed check skipped and reported as SK_ERR_CUDA by the
+ * plan's next call) instead of the release build when SK_DEBUG_LIBRARY=1.
  */
 #ifndef SK_H
 #define SK_H
@@ -144,8 +150,10 @@ sk_status_t sk_plan_offset_table(sk_plan_t plan, int64_t *e);
  * Tile choice of the fused kernel for this plan: rows_per_batch (8 or 16)
  * rows of 8 bytes each thread keeps in flight per register batch, and
  * grid_ctas (0 = one CTA per SM) for the plain launches.  Results do not
- * depend on either (exact integer combination); only speed does.  Used by
- * the autotuner.  INVALID_ARG for other values.
+ * depend on either (exact integer combination); only speed does.  The rows
+ * and grid of sk_launch_config_t (below), which carries the rest of the
+ * configuration.  Not to be called while another thread issues launches of
+ * the same plan.  INVALID_ARG for other values.
  */
 sk_status_t sk_plan_set_tiles(sk_plan_t plan, int32_t rows_per_batch,
                               int32_t grid_ctas);
@@ -205,7 +213,8 @@ typedef struct {
 } sk_launch_config_t;
 
 /* Set the plan's launch configuration (last_path is ignored).  INVALID_ARG
- * for values outside the ranges above. */
+ * for values outside the ranges above.  Like sk_plan_set_tiles, not to be
+ * called while another thread issues launches of the same plan. */
 sk_status_t sk_plan_set_config(sk_plan_t plan, const sk_launch_config_t *cfg);
 sk_status_t sk_plan_get_config(sk_plan_t plan, sk_launch_config_t *cfg);
 
