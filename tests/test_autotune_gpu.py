@@ -148,3 +148,51 @@ def test_sweep_writes_a_cache_the_plans_read(tmp_path, monkeypatch):
                 assert cfg["team_log2"] == e["team_log2"]
         finally:
             sk.sk_plan_destroy(plan)
+
+
+def test_random_configurations_stay_exact():
+    """40 seeded random shapes (both layouts, ragged N, M of any multiple of 16 and
+    others) each under a random launch configuration (path, tile rows, grid, team
+    size, prefetch): S1, S2, Q, N_eff, SK bits and masks bit-exact against the
+    oracle, whatever path the configuration leads to."""
+    dev = _dev()
+    rng = np.random.default_rng(1808_2)
+    taken = set()
+    for case in range(40):
+        layout = int(rng.integers(0, 2))
+        N = int(rng.choice([int(rng.integers(1, 4097)), int(8 * rng.integers(1, 513))]))
+        M = int(rng.choice([16, 32, 48, 64, 96, 128, 256, 512, 1024, 2048, 4096, 100, 2]))
+        F = int(rng.integers(1, 300))
+        while F > 1 and F * M * N > (12 << 20):
+            F //= 2
+        x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+        want = oracle.flag(x, M, N, 3.0, 0.01, layout=layout)
+        plan = sk.sk_plan_create(N, M, 3.0, 0.01, layout=layout)
+        try:
+            team0 = sk.sk_plan_get_config(plan)["team_log2"]
+            cfg = dict(rows=int(rng.choice([8, 16])), grid_ctas=int(rng.choice([0, 0, 37, 300])),
+                       path=int(rng.integers(0, 4)), prefetch=int(rng.integers(0, 2)))
+            if team0 and rng.random() < 0.5:
+                cfg["team_log2"] = int(min(8 if team0 <= 8 else 9, max(5, team0 + rng.integers(-1, 2))))
+            sk.sk_plan_set_config(plan, **cfg)
+            d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+            s1 = torch.full((F, N), -1, dtype=torch.int32, device=dev)
+            s2 = torch.full_like(s1, -1)
+            q = torch.full((F,), -1, dtype=torch.int64, device=dev)
+            skv = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+            ne = torch.full((F,), -1, dtype=torch.int32, device=dev)
+            mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+            sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
+            sk.sk_flag(plan, d_in, F, None, mask)
+            torch.cuda.synchronize()
+            taken.add(sk.sk_plan_get_config(plan)["last_path"])
+        finally:
+            sk.sk_plan_destroy(plan)
+        tag = f"case {case}: N={N} M={M} F={F} layout={layout} cfg={cfg}"
+        assert np.array_equal(s1.cpu().numpy(), want["S1"]), tag
+        assert np.array_equal(s2.cpu().numpy(), want["S2"]), tag
+        assert np.array_equal(q.cpu().numpy(), want["Q"]), tag
+        assert np.array_equal(ne.cpu().numpy(), want["neff"]), tag
+        assert np.array_equal(skv.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32)), tag
+        assert np.array_equal(mask.cpu().numpy(), want["mask"]), tag
+    assert len(taken) >= 4, taken
