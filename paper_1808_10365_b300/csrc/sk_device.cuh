@@ -245,15 +245,28 @@ __device__ __forceinline__ void accum_pair(uint2 w0, uint2 w1, uint32_t lb, uint
     acc[7] += lds_u32(prmt(w0.y, lb, 0x7634u)) + lds_u32(prmt(w1.y, lb, 0x7634u));
 }
 
+// Packed accumulator of 16 rows into the exact sums: S1 takes the high field
+// (acc >> 19), and s2 takes the whole packed word, so that until finish_s2 it
+// holds S2 + 2^19 S1 modulo 2^32 (one add per input instead of a mask and an add).
 __device__ __forceinline__ void flush(uint32_t (&acc)[kVec], int32_t (&s1)[kVec],
                                       int32_t (&s2)[kVec])
 {
 #pragma unroll
     for (int k = 0; k < kVec; ++k) {
         s1[k] += (int32_t)(acc[k] >> kPackShift);
-        s2[k] += (int32_t)(acc[k] & kPackMask);
+        s2[k] = (int32_t)((uint32_t)s2[k] + acc[k]);
         acc[k] = 0u;
     }
+}
+
+// The exact S2 from flush's running sum: S2 = (S2 + 2^19 S1) - 2^19 S1 modulo 2^32,
+// exact because 0 <= S2 < 2^32 (S2 <= 4096 * 128^2 = 2^26).  Once per frame part,
+// after its last flush.
+__device__ __forceinline__ void finish_s2(const int32_t (&s1)[kVec], int32_t (&s2)[kVec])
+{
+#pragma unroll
+    for (int k = 0; k < kVec; ++k)
+        s2[k] = (int32_t)((uint32_t)s2[k] - ((uint32_t)s1[k] << kPackShift));
 }
 
 // r_i scaled to 2^32 fixed point: D_i = M S2_i - S1_i^2 and S1_i^2 exact in

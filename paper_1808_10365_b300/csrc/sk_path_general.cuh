@@ -115,6 +115,7 @@ __device__ __forceinline__ void run_general(const Item &it, int64_t f_begin, int
             }
             flush(acc, s1, s2);
         }
+        finish_s2(s1, s2);
         frame_epilogue<SERVED>(it, frame, fvalid, col0, lit, team_idx, parity, s1, s2, ts);
         parity ^= 1;
         frame += fstride;

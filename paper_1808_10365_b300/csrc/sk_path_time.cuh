@@ -126,6 +126,7 @@ __device__ __forceinline__ void run_fast(const Item &it, int64_t f_begin, int64_
                 }
             }
         }
+        finish_s2(s1, s2);
         frame_epilogue<SERVED>(it, frame, fvalid, col0, lit, team_idx, parity, s1, s2, ts);
         parity ^= 1;
         frame = nframe;
@@ -181,6 +182,7 @@ __device__ __forceinline__ void run_rows(const Item &it, int64_t frame, int b0, 
                 load(buf[j], jb + S + j);
         }
     }
+    finish_s2(s1, s2);
 }
 
 // L2 prefetch of a box of the input through its tensor map (rows y .. y+31 of
@@ -374,6 +376,7 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
         }
         if (ok) {
             // the slice's terms and per-input outputs, summed over the warp
+            finish_s2(s1, s2);
             int64_t q;
             int32_t cnt;
             slice_terms(it, frame, col0, M, s1, s2, q, cnt);
@@ -496,6 +499,7 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
         const bool fend = gf == (int)tpf;
         if (!fend && more)
             continue;
+        finish_s2(s1, s2);
         if (fend && gf0 == 0) {
             // a whole frame: the slice's part goes into the team's slot ring
             int64_t q;
@@ -689,6 +693,7 @@ __device__ __forceinline__ void run_fast_rag(const Item &it, uint32_t lb, TeamSm
         const bool fend = gf == (int)tpf;
         if (!fend && more)
             continue;
+        finish_s2(s1, s2);
         if (fend && gf0 == 0) {
             int64_t q;
             int32_t cnt;
