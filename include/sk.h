@@ -503,7 +503,8 @@ sk_status_t sk_digitisation_offset(double sigma, double *delta);
  * discreteMean and normedSum2 with M S2 - S1^2 exact in int64 and one fp32
  * divide): each is compared bit for bit with CUDA's conversion intrinsics on
  * every non-negative fp32 below 2^62, on every halfway case below 2^43 and its
- * neighbours, and on hashed samples of int64 values and of (S1, S2, M).
+ * neighbours, on hashed samples of int64 values and of (S1, S2, M), and on the
+ * fp32 square of every S1 from 1 to 2^19.
  * *n_checked gets the number of cases, *n_bad the mismatches (0 expected).
  * Takes about a second.  Errors: INVALID_ARG (NULL output), CUDA.
  */

@@ -8,6 +8,7 @@
 //     neighbours; a hashed sample of 2^28 values below 2^43.
 //   input term (Eqs. discreteMean, normedSum2): a hashed sample of 2^26 valid
 //     (S1, S2, M) with M from 2 to 4096 and 0 < S1 <= 128 M, S1^2 <= M S2 <= 128 M S1.
+//   fp32(S1^2) from an exact fp32 S1 and one multiply: every S1 from 1 to 2^19.
 //
 // And a self-test of the bounded slot wait of the warp-slice combine
 // (wi_commit): one warp of a two-warp team commits frame counter 0 into a slot
@@ -73,6 +74,22 @@ __global__ void check_u43_to_f32(uint64_t n, unsigned long long *bad)
         atomicAdd(bad, nb);
 }
 
+// fp32(S1^2) as the epilogue forms it (an exact fp32 S1, one IEEE multiply) against
+// CUDA's conversion of the exact integer S1^2, for every S1 from 1 to 2^19 (the
+// largest S1: 4096 samples of power 128)
+__global__ void check_square(uint32_t n, unsigned long long *bad)
+{
+    unsigned long long nb = 0;
+    for (uint32_t s1 = 1 + blockIdx.x * blockDim.x + threadIdx.x; s1 <= n;
+         s1 += gridDim.x * blockDim.x) {
+        const float fs1 = __fsub_rn(__uint_as_float(0x4B000000u | s1), 8388608.0f);
+        nb += __float_as_uint(__fmul_rn(fs1, fs1)) !=
+              __float_as_uint(__ll2float_rn((int64_t)s1 * (int64_t)s1));
+    }
+    if (nb)
+        atomicAdd(bad, nb);
+}
+
 __global__ void check_input_term(uint64_t n, unsigned long long *bad)
 {
     unsigned long long nb = 0;
@@ -112,12 +129,14 @@ extern "C" sk_status_t sk_selftest_conversions(int device, int64_t *n_checked, i
     const uint32_t n_f32 = 0x5E800000u;  // bits of 2^62
     const uint64_t n_u43 = kSmall + kTies + kHashed;
     const uint64_t n_term = 1ull << 26;
+    const uint32_t n_square = 1u << 19;
     const int grid = sm_count(device) * 8;
     unsigned long long h_bad[3] = {0, 0, 0};
     if ((e = cudaMemset(d_bad, 0, sizeof h_bad)) == cudaSuccess) {
         check_f32_to_i64<<<grid, 256>>>(n_f32, d_bad);
         check_u43_to_f32<<<grid, 256>>>(n_u43, d_bad + 1);
         check_input_term<<<grid, 256>>>(n_term, d_bad + 2);
+        check_square<<<grid, 256>>>(n_square, d_bad + 2);
         e = cudaGetLastError();
         if (e == cudaSuccess)
             e = cudaMemcpy(h_bad, d_bad, sizeof h_bad, cudaMemcpyDeviceToHost);
@@ -125,7 +144,7 @@ extern "C" sk_status_t sk_selftest_conversions(int device, int64_t *n_checked, i
     cudaFree(d_bad);
     if (e != cudaSuccess)
         return cuda_error(e, "sk_selftest_conversions");
-    *n_checked = (int64_t)n_f32 + (int64_t)n_u43 + (int64_t)n_term;
+    *n_checked = (int64_t)n_f32 + (int64_t)n_u43 + (int64_t)n_term + (int64_t)n_square;
     *n_bad = (int64_t)(h_bad[0] + h_bad[1] + h_bad[2]);
     return SK_OK;
 }

@@ -79,7 +79,7 @@ def test_exact_conversions_match_cuda_intrinsics():
     neighbours, and hashed samples."""
     _dev()
     n, bad = sk.sk_selftest_conversions(0)
-    assert n == 0x5E800000 + (1 << 25) + 19 * (1 << 23) * 3 + (1 << 28) + (1 << 26)
+    assert n == 0x5E800000 + (1 << 25) + 19 * (1 << 23) * 3 + (1 << 28) + (1 << 26) + (1 << 19)
     assert bad == 0
 
 
