@@ -185,15 +185,53 @@ __device__ __forceinline__ uint4 ldg_stream16_at(const uint8_t *base)
     return v;
 }
 
+// Inputs between consecutive members of a segment's group.  Groups of 8 inputs on
+// 8 lanes (M >= 128) are 8 consecutive inputs: a segment reads whole 128-byte
+// lines.  Groups of 4 on 4 lanes (M = 64) are strided by 8 inputs: the 8 segments
+// of a warp share the warp's 32 consecutive inputs, segment s taking inputs s,
+// s + 8, s + 16 and s + 24, so that each warp load instruction reads 512
+// contiguous bytes (4 whole lines) instead of 8 runs of 64 bytes.
+// Both need teams of at least one warp (team_log2 >= 5, which the host keeps on
+// the grouped paths) and, when strided, whole inputs (SPLIT = 1).
+template <int G>
+__host__ __device__ constexpr int group_stride()
+{
+    return G == 4 ? 8 : 1;
+}
+
+// First (sub-)input of the group of segment seg (of nseg per team) in group row k
+// of a frame (team inputs a group row).
+template <int G>
+__device__ __forceinline__ int group_first(int k, int nseg, int seg)
+{
+    if constexpr (group_stride<G>() == 1)
+        return (k * nseg + seg) * G;
+    else
+        return k * nseg * G + (seg >> 3) * (8 * G) + (seg & 7);
+}
+
+// Members of a group below NS (sub-)inputs, 0..G.
+template <int G>
+__device__ __forceinline__ int group_live(int first, int NS)
+{
+    constexpr int IST = group_stride<G>();
+    const int r = NS - first;
+    if constexpr (IST == 1)
+        return r < 0 ? 0 : (r > G ? G : r);
+    const int n = r <= 0 ? 0 : (r + IST - 1) / IST;
+    return n > G ? G : n;
+}
+
 // Batch nb of a group on the grouped input-major path: chunk t of the batch is
-// the group's chunk g = nb KB + t, i.e. chunk g % CH of input g / CH; all offsets
-// are load immediates.
+// the group's chunk g = nb KB + t, i.e. chunk g % CH of its member g / CH; all
+// offsets are load immediates.
 template <int M, int G, int CH, int KB, int nb, int... Ts>
 __device__ __forceinline__ void load_group_imm(uint4 *buf, const uint8_t *base,
                                                std::integer_sequence<int, Ts...>)
 {
-    ((buf[Ts] = ldg_stream16_at<((nb * KB + Ts) / CH) * M + ((nb * KB + Ts) % CH) * G * 16>(
-          base)),
+    constexpr int IST = group_stride<G>();
+    ((buf[Ts] = ldg_stream16_at<((nb * KB + Ts) / CH) * IST * M +
+                                ((nb * KB + Ts) % CH) * G * 16>(base)),
      ...);
 }
 
@@ -203,11 +241,13 @@ __device__ __forceinline__ void load_group_batch(uint4 (&buf)[KB], const uint8_t
     if (live == G) {
         load_group_imm<M, G, CH, KB, nb>(buf, base, std::make_integer_sequence<int, KB>{});
     } else {
+        constexpr int IST = group_stride<G>();
 #pragma unroll
         for (int t = 0; t < KB; ++t) {
             const int g = nb * KB + t;
-            buf[t] = g / CH < live ? ldg_stream16(base + (g / CH) * M + (g % CH) * G * 16)
-                                   : make_uint4(0u, 0u, 0u, 0u);
+            buf[t] = g / CH < live
+                         ? ldg_stream16(base + (g / CH) * IST * M + (g % CH) * G * 16)
+                         : make_uint4(0u, 0u, 0u, 0u);
         }
     }
 }
@@ -242,7 +282,7 @@ __device__ __forceinline__ void group_batches(uint4 (&cur)[KB], uint4 (&nxt)[KB]
 // the G lanes leaves input j's S1, S2 in lane j (the sub-inputs of an input are
 // added), and lane j adds its input's term (Eq. normedSum2) to q, cnt and writes
 // the per-input outputs the item asks for.  i0 is the group's first sub-input in
-// the frame, M the sub-input length.
+// the frame (its members group_stride apart), M the sub-input length.
 template <int G, int SPLIT>
 __device__ __forceinline__ void group_terms(const Item &it, int32_t (&s1)[G], int32_t (&s2)[G],
                                             int j, int live, int64_t frame, int i0, int M,
@@ -268,7 +308,7 @@ __device__ __forceinline__ void group_terms(const Item &it, int32_t (&s1)[G], in
         s2[0] += __shfl_xor_sync(0xFFFFFFFFu, s2[0], o);
     }
     if (j < live && j % SPLIT == 0) {
-        const int i = (i0 + j) / SPLIT;
+        const int i = (i0 + j * group_stride<G>()) / SPLIT;
         float r = 0.0f;
         int64_t qi = 0;
         const bool has = SK_EPILOGUE_ALU ? input_term_alu(s1[0], s2[0], M * SPLIT, r, qi)
@@ -314,6 +354,7 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
     // bytes (the layout is the same bytes), whose sums are added after the
     // reduce-scatter; M here is the sub-input length
     static_assert(SPLIT >= 1 && G % SPLIT == 0, "sub-inputs of one input share a group");
+    static_assert(group_stride<G>() == 1 || SPLIT == 1, "strided groups hold whole inputs");
     constexpr int M = 16 * G * CH;
     constexpr int NB = (G * CH / 8) < 2 ? 2 : G * CH / 8;  // batches per group
     constexpr int KB = G * CH / NB;                       // chunks per batch
@@ -334,18 +375,18 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
     // through the team's slot ring instead of a barrier per frame
     const bool wi = it.wi && team >= 64;
 
+    constexpr int IST = group_stride<G>();  // inputs between a group's members
     // sub-inputs of group (frame f, k) that this segment may read: 0..G
     auto live_of = [&](int64_t f, int k) -> int {
-        const int i0 = (k * nseg + seg) * G;
-        const int r = NS - i0;
-        return (f < f_end) ? (r < 0 ? 0 : (r > G ? G : r)) : 0;
+        return (f < f_end) ? group_live<G>(group_first<G>(k, nseg, seg), NS) : 0;
     };
     auto base_of = [&](int64_t f, int k) -> const uint8_t * {
-        return it.in + f * fbytes + (int64_t)((k * nseg + seg) * G) * M + j * 16;
+        return it.in + f * fbytes + (int64_t)group_first<G>(k, nseg, seg) * M + j * 16;
     };
     // debug builds: a group whose chunks would leave the input is not read
     auto dbg_live = [&](const uint8_t *base, int live) -> int {
-        return (live > 0 && !SK_DBG_IN(it, base, (int64_t)(live - 1) * M + (CH - 1) * G * 16 + 16))
+        return (live > 0 && !SK_DBG_IN(it, base, (int64_t)(live - 1) * IST * M +
+                                                     (CH - 1) * G * 16 + 16))
                    ? 0
                    : live;
     };
@@ -364,8 +405,17 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
             const int nk = (k + 1 < NG) ? k + 1 : 0;
             const uint8_t *nxt_base = base_of(nf, nk);
             const int nxt_live = dbg_live(nxt_base, live_of(nf, nk));
-            if (PF && nxt_live > 0 && j == 0)
-                prefetch_l2(nxt_base, (uint32_t)(nxt_live * M));
+            if constexpr (PF) {
+                if (IST == 1 && nxt_live > 0 && j == 0) {
+                    prefetch_l2(nxt_base, (uint32_t)(nxt_live * M));
+                } else if (IST > 1 && j == 0 && (seg & 7) == 0 && nf < f_end) {
+                    // strided groups: the warp's first segment asks for the warp's
+                    // contiguous block of 8 G inputs
+                    const int r = NS - group_first<G>(nk, nseg, seg);
+                    if (r > 0)
+                        prefetch_l2(nxt_base, (uint32_t)((r < 8 * G ? r : 8 * G) * M));
+                }
+            }
             int32_t s1[G], s2[G];
 #pragma unroll
             for (int u = 0; u < G; ++u) {
@@ -395,7 +445,7 @@ __device__ __forceinline__ void run_imajor_grouped(const Item &it, int64_t f_beg
                 s2[0] += __shfl_xor_sync(0xFFFFFFFFu, s2[0], o);
             }
             if (j < cur_live && j % SPLIT == 0) {
-                const int i = ((k * nseg + seg) * G + j) / SPLIT;
+                const int i = (group_first<G>(k, nseg, seg) + j * IST) / SPLIT;
                 float r = 0.0f;
                 int64_t qi = 0;
                 const bool has = SK_EPILOGUE_ALU
@@ -474,6 +524,7 @@ template <int G, int CH, bool PF, int SPLIT = 1>
 __device__ __forceinline__ void run_imajor_rb(const Item &it, uint32_t lb, TeamSmem &ts)
 {
     static_assert(SPLIT >= 1 && G % SPLIT == 0, "sub-inputs of one input share a group");
+    static_assert(group_stride<G>() == 1 || SPLIT == 1, "strided groups hold whole inputs");
     constexpr int M = 16 * G * CH;
     constexpr int NB = (G * CH / 8) < 2 ? 2 : G * CH / 8;  // batches per group
     constexpr int KB = G * CH / NB;                       // chunks per batch
@@ -493,10 +544,13 @@ __device__ __forceinline__ void run_imajor_rb(const Item &it, uint32_t lb, TeamS
     const int kt = (int)blockIdx.x * T + team_idx;
     const int u0 = (int)((int64_t)TT * kt / K), u1 = (int)((int64_t)TT * (kt + 1) / K);
     const int64_t step = (int64_t)team * M;  // bytes per group row
-    const uint8_t *cur = it.in + (int64_t)u0 * step + seg * G * M + j * 16;
+    constexpr int IST = group_stride<G>();  // inputs between a group's members
+    const uint8_t *cur =
+        it.in + (int64_t)u0 * step + (int64_t)group_first<G>(0, nseg, seg) * M + j * 16;
 
     // debug builds: a group row whose chunks would leave the input is not read
-    [[maybe_unused]] const int64_t gext = (int64_t)(G - 1) * M + (CH - 1) * G * 16 + 16;
+    [[maybe_unused]] const int64_t gext =
+        (int64_t)(G - 1) * IST * M + (CH - 1) * G * 16 + 16;
     uint4 A[KB], B[KB];
     if (u0 < u1)
         load_group_batch<M, G, CH, KB, 0>(A, cur, SK_DBG_IN(it, cur, gext) ? G : 0);
@@ -508,8 +562,10 @@ __device__ __forceinline__ void run_imajor_rb(const Item &it, uint32_t lb, TeamS
     for (int u = u0; u < u1; ++u) {
         const bool more = u + 1 < u1;
         const uint8_t *nxt = more ? cur + step : cur;
-        if (PF && more && j == 0)
-            prefetch_l2(nxt, (uint32_t)(G * M));
+        // the next group row's bytes: the segment's group, or with strided groups
+        // the warp's block of 8 G inputs (from its first segment)
+        if (PF && more && j == 0 && (IST == 1 || (seg & 7) == 0))
+            prefetch_l2(nxt, (uint32_t)((IST == 1 ? G : 8 * G) * M));
         int32_t s1[G], s2[G];
 #pragma unroll
         for (int t = 0; t < G; ++t) {
@@ -519,7 +575,8 @@ __device__ __forceinline__ void run_imajor_rb(const Item &it, uint32_t lb, TeamS
         group_batches<M, G, CH, NB, KB, 0>(A, B, cur, G, nxt,
                                            (more && SK_DBG_IN(it, nxt, gext)) ? G : 0, lb, s1,
                                            s2);
-        group_terms<G, SPLIT>(it, s1, s2, j, G, frame, (ku * nseg + seg) * G, M, q, cnt);
+        group_terms<G, SPLIT>(it, s1, s2, j, G, frame, group_first<G>(ku, nseg, seg), M, q,
+                              cnt);
         cur = nxt;
         ++ku;
         const bool fend = ku == NG;
