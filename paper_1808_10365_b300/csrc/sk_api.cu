@@ -74,10 +74,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             single.fast == 1 && single.M % (R * S) == 0 && (NC == 0 || single.N == NC);
         if constexpr ((R * S == 32 || R * S == 16) && !SRV) {
             if (fast && single.wi) {
-                if (single.rb)
-                    run_fast_rb<R, S, NC>(single, lb, ts, &tmap);
-                else
-                    run_fast_wi<R, S, NC>(single, fb, fe, lb, ts, &tmap);
+                if (single.rb) {
+                    // a folded tail only where N is not a compiled multiple of 256
+                    if (NC == 0 && single.wtail)
+                        run_fast_rb<R, S, NC, true>(single, lb, ts, &tmap);
+                    else
+                        run_fast_rb<R, S, NC>(single, lb, ts, &tmap);
+                } else
+                    if (NC == 0 && single.wtail)
+                        run_fast_wi<R, S, NC, true>(single, fb, fe, lb, ts, &tmap);
+                    else
+                        run_fast_wi<R, S, NC>(single, fb, fe, lb, ts, &tmap);
                 return;
             }
         }
@@ -460,6 +467,16 @@ bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out)
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Folded tail of the warp slices (Item::wtail), on unless SK_TAIL_FOLD=0.
+static bool tail_fold_on()
+{
+    static const bool off = [] {
+        const char *v = getenv("SK_TAIL_FOLD");
+        return v && atoi(v) == 0;
+    }();
+    return !off;
+}
+
 static bool row_balance_on()
 {
     static const bool off = [] {
@@ -558,13 +575,27 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // input-major teams of two or more warps combine through the same slot ring
     if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6 && req != SK_PATH_TEAM)
         run.wi = 1;
+    // N = 256 W + 8 NT with NT of 1..min(4, W): teams of W warps, the NT groups of 8
+    // columns past the last whole slice read row-per-lane by them, one group a warp
+    // (a warp of its own would cost as much as a whole slice for NT busy lanes).
+    // Folded only where that adds a team per CTA (W = 1..5 and 8; at W = 9, N = 2312,
+    // it measured 2 % slower), and without the tensor map's L2 prefetch, which
+    // slowed folded shapes (N = 2064: 5.18 TB/s without it, 4.05 with it).
+    run.wtail = 0;
+    if (run.wi && it.fast == 1 && tail_fold_on() && it.N > 256 && (it.N & 255) <= 8 * kMaxTail &&
+        (it.N & 255) / 8 <= it.N / 256 &&
+        (kThreads / 32) / (it.N / 256) > (kThreads / 32) / (it.N / 256 + 1)) {
+        run.wtail = (it.N & 255) / 8;
+        run.wi = 2;
+    }
     // ragged N: warp slices without a tensor map, given balanced rows (below)
     const bool tm_ws = it.fast == 1 || it.fast == 3;
     if (it.fast == 3 && warp_slice_on() && it.M % 16 == 0 &&
         (req == SK_PATH_AUTO || req == SK_PATH_ROW_BALANCED))
         run.wi = 2;
     // teams per CTA: 16 / ceil(N/256) on the warp-slice paths
-    const int64_t Tl = (run.wi && tm_ws) ? (kThreads / 32) / ((it.N + 255) / 256) : T;
+    const int64_t Wl = run.wtail ? it.N / 256 : (it.N + 255) / 256;  // warps per frame
+    const int64_t Tl = (run.wi && tm_ws) ? (kThreads / 32) / Wl : T;
     // frames per team decide the grid, unless rows are balanced over the grid
     int64_t g = std::min<int64_t>(gmax, (it.n_frames + Tl - 1) / Tl);
     std::unique_lock<std::mutex> lk;
@@ -577,8 +608,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     if (run.wi && tm_ws) {
         units = it.n_frames * (it.M / (tile == 0 ? 32 : 16));
         const int64_t K = std::max<int64_t>(1, std::min<int64_t>(gmax, units / Tl)) * Tl;
-        const int64_t W = (it.N + 255) / 256;
-        need = (size_t)K * it.N * 8 + (size_t)((K * W + 1) & ~(int64_t)1) * 4 + (size_t)K * 16;
+        need = (size_t)K * it.N * 8 + (size_t)((K * Wl + 1) & ~(int64_t)1) * 4 + (size_t)K * 16;
     } else if (run.wi && it.fast == 2 && imajor_shape(it.M) >= 0 &&
                (it.M <= 256 || it.M == 4096)) {
         const int64_t split = it.M >= 1024 ? it.M / 512 : 1;
@@ -821,6 +851,7 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.n_sigma = p.n_sigma;
     it.mean_offset = p.mean_offset;
     it.wi = 0;
+    it.wtail = 0;
     it.err = d_err;
     it.tmap = nullptr;
     it.rb = nullptr;

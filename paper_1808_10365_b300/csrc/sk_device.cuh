@@ -74,6 +74,9 @@ struct Item {
     int32_t wi;              // nonzero: the warps of a frame combine through the slot ring
                              // (time-major: warp-slice path, 1 with the tensor map for
                              // the L2 prefetch, 2 without, when N % 16 != 0)
+    int32_t wtail;           // time-major warp slices: groups of 8 columns past the last
+                             // whole 256-column slice read row-per-lane by the team's
+                             // warps (1..4), or 0: the partial slice is a warp of its own
     int32_t *err;            // mapped host word: set when a bounded wait gives up
     const CUtensorMap *tmap;  // batched time-major items: the input's map in device memory
     int32_t *rb;              // row-balanced warp-slice launch: the plan's zeroed scratch
@@ -338,6 +341,7 @@ __device__ __forceinline__ bool input_term_alu(int32_t s1, int32_t s2, int32_t M
 // Per-frame accumulators of the warp-slice path: each team has a ring of kWiSlots
 // slots; slot j holds the sums of the team's frame with counter `tag`.
 constexpr int kWiSlots = 4;
+constexpr int kMaxTail = 4;  // folded 8-column groups of the warp slices (Item::wtail)
 struct WiSlot {
     unsigned long long q;
     int cnt;

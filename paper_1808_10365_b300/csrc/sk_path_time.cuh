@@ -223,14 +223,16 @@ __device__ __forceinline__ void fill_zero_power(uint2 (&buf)[S][R])
 // past the last input (its sums zero) adds nothing and writes nothing.
 // PART: the lane may hold columns past N (ragged N), whose sums are not inputs'
 // and are left out.
+// q0, cnt0: a lane's terms of other inputs (a folded tail's), added before the sum
+// over the warp.
 template <bool PART = false>
 __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int col0, int M,
                                             const int32_t (&s1)[kVec],
                                             const int32_t (&s2)[kVec], int64_t &q,
-                                            int32_t &cnt)
+                                            int32_t &cnt, int64_t q0 = 0, int32_t cnt0 = 0)
 {
-    q = 0;
-    cnt = 0;
+    q = q0;
+    cnt = cnt0;
 #pragma unroll
     for (int k = 0; k < kVec; ++k) {
         if (PART && col0 + k >= it.N)
@@ -267,11 +269,100 @@ __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int c
     }
 }
 
+// Folded tail of the warp slices (Item::wtail = NT): with N = 256 W + 8 NT and
+// NT <= W, a team is W warps instead of W + 1, since a warp with NT busy lanes
+// costs as much as a whole slice (and at W = 8 leaves a CTA's 16 warps short of a
+// second team).  Group g of the NT groups of 8 columns past the last whole slice
+// falls, for frame f, to warp (f + g) mod W of the team (on the row-balanced path
+// the same warp in every team that shares the frame).  Inside the turn loop that
+// warp loads, one turn ahead, the group's 8-byte word of each of the turn's rows
+// (lane l: row l of the turn), so that no load latency is left for the frame's
+// end; its sectors are shared with the slice loads of the same and the next row.
+// tail_turn adds one turn: the lane's 8 table values go through 3 reduce-scatter
+// steps over lane bits 4, 3 and 2, after which lane l holds input (l >> 2) & 7 of
+// the group summed over 8 rows (packed, at most 8 rows: the fields cannot carry),
+// added exactly into ts1, ts2.  Lanes that differ in bits 0 and 1 hold the input's
+// other rows.
+__device__ __forceinline__ void tail_turn(uint2 w, uint32_t lb, int32_t &ts1, int32_t &ts2)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t v[kVec];
+    v[0] = lds_u32(prmt(w.x, lb, 0x7604u));
+    v[1] = lds_u32(prmt(w.x, lb, 0x7614u));
+    v[2] = lds_u32(prmt(w.x, lb, 0x7624u));
+    v[3] = lds_u32(prmt(w.x, lb, 0x7634u));
+    v[4] = lds_u32(prmt(w.y, lb, 0x7604u));
+    v[5] = lds_u32(prmt(w.y, lb, 0x7614u));
+    v[6] = lds_u32(prmt(w.y, lb, 0x7624u));
+    v[7] = lds_u32(prmt(w.y, lb, 0x7634u));
+    // lane bit 4 keeps inputs 4..7 (set) or 0..3 and sends the other half
+    const bool b4 = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t keep = b4 ? v[k + 4] : v[k], send = b4 ? v[k] : v[k + 4];
+        v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+    }
+    const bool b3 = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const uint32_t keep = b3 ? v[k + 2] : v[k], send = b3 ? v[k] : v[k + 2];
+        v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+    }
+    const bool b2 = lane & 4;
+    const uint32_t keep = b2 ? v[1] : v[0], send = b2 ? v[0] : v[1];
+    const uint32_t t = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+    ts1 += (int32_t)(t >> kPackShift);
+    ts2 += (int32_t)(t & ((1u << kPackShift) - 1u));
+}
+
+// The folded group's input (l >> 2) & 7 at the end of a frame (part): its sums over
+// the lanes that share it, into every one of them.
+__device__ __forceinline__ void tail_reduce(int32_t &ts1, int32_t &ts2)
+{
+    ts1 += __shfl_xor_sync(0xFFFFFFFFu, ts1, 2);
+    ts2 += __shfl_xor_sync(0xFFFFFFFFu, ts2, 2);
+    ts1 += __shfl_xor_sync(0xFFFFFFFFu, ts1, 1);
+    ts2 += __shfl_xor_sync(0xFFFFFFFFu, ts2, 1);
+}
+
+// Lanes l with l % 4 == 0 form the term of input col + l / 4 (Eq. normedSum2) from
+// its totals, with the per-input outputs the item asks for, into q and cnt (which
+// slice_terms then sums over the warp with the slice's terms).
+__device__ __forceinline__ void tail_lane_term(const Item &it, int64_t frame, int col, int M,
+                                               int32_t ts1, int32_t ts2, int64_t &q,
+                                               int32_t &cnt)
+{
+    const int lane = threadIdx.x & 31;
+    if ((lane & 3) != 0)
+        return;
+    const int c = col + (lane >> 2);
+    float r = 0.0f;
+    int64_t qi = 0;
+    const bool has = SK_EPILOGUE_ALU ? input_term_alu(ts1, ts2, M, r, qi)
+                                     : input_term(ts1, ts2, M, r, qi);
+    if (has) {
+        q += qi;
+        cnt += 1;
+    }
+    if (SK_DBG_OUT_IN(it, frame, c)) {
+        const int64_t o = frame * it.N + c;
+        if (it.sk_in) {
+            it.sk_in[o] = has ? __fmul_rn(r, it.c_tab[1]) : __int_as_float(0x7FC00000);
+            if (it.mask_in)
+                it.mask_in[o] = has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+        }
+        if (it.s1) {
+            it.s1[o] = ts1;
+            it.s2[o] = ts2;
+        }
+    }
+}
+
 // Warp-slice path: one-item launches and batched items with a tensor map,
 // time-major, N a multiple of 8 from 256 to 4096, 16 x 2 tiles (8 x 2 for
 // M = 16 mod 32: 16-row turns, the 32-row prefetch box every other turn).  The team of a
-// frame is ceil(N/256) warps, each owning a 256-column slice of the team's frames
-// and running on its own: no barrier per frame.  Lane 0 of each warp asks L2 for
+// frame is ceil(N/256) warps (floor(N/256) with a folded tail, above), each owning a
+// 256-column slice of the team's frames and running on its own: no barrier per frame.  Lane 0 of each warp asks L2 for
 // the rows the warp will load two ring turns ahead with one 2D tensor prefetch
 // (32 rows x 256 bytes) through the input's tensor map (a kernel parameter of a
 // one-item launch, or the item's map in device memory; none when N % 16 != 0).  After a frame, the warp adds its
@@ -279,7 +370,7 @@ __device__ __forceinline__ void slice_terms(const Item &it, int64_t frame, int c
 // atomics); the warp that arrives last forms the frame's mask and SK and frees
 // the slot.  A team's slots form a ring of kWiSlots frames; a warp that gets
 // that far ahead of a slow one waits, bounded, for its slot.
-template <int R, int S, int NC>
+template <int R, int S, int NC, bool TAIL = false>
 __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int64_t f_end,
                                             uint32_t lb, TeamSmem &ts, const CUtensorMap *tmap)
 {
@@ -290,15 +381,21 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     const int M = it.M;
     const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
     // teams of W warps, one 256-column slice each (the last one partial when 256
-    // does not divide N); the CTA's last 16 - T W warps have nothing to do
-    const int W = (int)((N + 255) >> 8);
+    // does not divide N, unless the columns past the whole slices are folded);
+    // the CTA's last 16 - T W warps have nothing to do
+    // TAIL: NT = Item::wtail groups of 8 columns folded (NT <= W), read inside the
+    // turn loop by one warp of the team per group and frame (tail_turn)
+    constexpr int RS = R * S;  // rows per turn
+    const int NT = TAIL ? it.wtail : 0;
+    const int W = NT ? (int)(N >> 8) : (int)((N + 255) >> 8);
     const int T = (kThreads / 32) / W;
     const int warp = threadIdx.x >> 5;
     const int team_idx = warp / W;
     if (team_idx >= T)
         return;
     const int lane = threadIdx.x & 31;
-    const int xs = (warp - team_idx * W) * 256;  // the warp's first column
+    const int c = warp - team_idx * W;  // the warp's slice
+    const int xs = c * 256;             // its first column
     const int col0 = xs + lane * kVec;
     // lanes past N read nothing (none when N is a compiled multiple of 256)
     const bool col_ok = (NC > 0 && NC % 256 == 0) || col0 < N;
@@ -336,10 +433,33 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
         for (int j = 0; j < S; ++j)
             load(buf[j], fp + (int64_t)j * R * N);
     }
+    // folded tail: the first column of this warp's group of frame f, or -1
+    auto tail_col = [&](int64_t f) -> int {
+        const int gt = (c - (int)(f % W) + W) % W;
+        return gt < NT ? 256 * W + 8 * gt : -1;
+    };
+    // the group's word of row `lane` of the turn whose first row's byte col0 is at
+    // t0p (rows past the turn: no power)
+    auto tail_load = [&](const uint8_t *t0p, int tc) -> uint2 {
+        const uint8_t *p = t0p + (tc - col0) + (int64_t)lane * N;
+        return (lane < RS && SK_DBG_IN(it, p, 8)) ? ldg_stream(p)
+                                                  : make_uint2(0x88888888u, 0x88888888u);
+    };
+    [[maybe_unused]] int tcc = -1;   // this warp's group of the current frame
+    [[maybe_unused]] uint2 wt = make_uint2(0x88888888u, 0x88888888u);
+    [[maybe_unused]] int32_t ts1 = 0, ts2 = 0;
+    if constexpr (TAIL) {
+        tcc = ok ? tail_col(frame) : -1;
+        if (tcc >= 0)
+            wt = tail_load(fp, tcc);
+    }
     for (int64_t kk = 0; kk < kmax; ++kk) {
         const int64_t nframe = frame + T;
         const bool nok = nframe < f_end;
         const uint8_t *nfp = in + nframe * fbytes + col0;
+        [[maybe_unused]] int tcn = -1;  // the group of the team's next frame
+        if constexpr (TAIL)
+            tcn = nok ? tail_col(nframe) : -1;
         uint32_t acc[kVec];
         int32_t s1[kVec], s2[kVec];
 #pragma unroll
@@ -361,6 +481,13 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
             const bool same_frame = jb + S < nb;
             const uint8_t *pn = same_frame ? fp + (int64_t)(jb + S) * R * N : nfp;
             const bool lok = same_frame ? ok : nok;
+            if constexpr (TAIL) {
+                // this turn's word, then the next turn's (in flight over this turn)
+                if (tcc >= 0)
+                    tail_turn(wt, lb, ts1, ts2);
+                const int ntc = same_frame ? tcc : tcn;
+                wt = ntc >= 0 ? tail_load(pn, ntc) : make_uint2(0x88888888u, 0x88888888u);
+            }
 #pragma unroll
             for (int j = 0; j < S; ++j) {
                 if (ok) {
@@ -377,12 +504,23 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
         if (ok) {
             // the slice's terms and per-input outputs, summed over the warp
             finish_s2(s1, s2);
-            int64_t q;
-            int32_t cnt;
-            slice_terms(it, frame, col0, M, s1, s2, q, cnt);
+            int64_t q = 0, q0 = 0;
+            int32_t cnt = 0, c0 = 0;
+            if constexpr (TAIL) {
+                if (tcc >= 0) {
+                    tail_reduce(ts1, ts2);
+                    tail_lane_term(it, frame, tcc, M, ts1, ts2, q0, c0);
+                }
+            }
+            slice_terms(it, frame, col0, M, s1, s2, q, cnt, q0, c0);
             if (lane == 0)
                 wi_commit(it, slots, kk, W, frame, q, cnt);
             __syncwarp();
+        }
+        if constexpr (TAIL) {
+            ts1 = 0;
+            ts2 = 0;
+            tcc = tcn;
         }
         frame = nframe;
         fp = nfp;
@@ -405,7 +543,7 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
 // of W warps: uint64 S2:S1[K][N], int32 turns[K][W] (padded to an even count),
 // uint64 Q[K], int32 cnt[K], int32 arrive[K]; the slot of a cut frame is the
 // index of the first team boundary inside it.
-template <int R, int S, int NC>
+template <int R, int S, int NC, bool TAIL = false>
 __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSmem &ts,
                                             const CUtensorMap *tmap)
 {
@@ -415,8 +553,12 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
     const int M = it.M;
     const int64_t N = NC > 0 ? (int64_t)NC : (int64_t)it.N;
     // teams of W warps (256-column slices, the last one partial when 256 does not
-    // divide N); the CTA's last 16 - T W warps have nothing to do
-    const int W = (int)((N + 255) >> 8);
+    // divide N, unless the columns past the whole slices are folded); the CTA's
+    // last 16 - T W warps have nothing to do
+    // TAIL: NT = Item::wtail groups of 8 columns folded (NT <= W), read inside the
+    // turn loop by one warp of the team per group and frame (tail_turn)
+    const int NT = TAIL ? it.wtail : 0;
+    const int W = NT ? (int)(N >> 8) : (int)((N + 255) >> 8);
     const int T = (kThreads / 32) / W;
     const int warp = threadIdx.x >> 5;
     const int team_idx = warp / W;
@@ -480,11 +622,45 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
     int64_t frame = t0 / tpf;     // the current turn's frame ...
     int gf = (int)(t0 - frame * tpf);  // ... and turn in it (counters: no division per turn)
     int gf0 = gf;                 // first turn of the current frame part
+
+    // folded tail: the first column of this warp's group of a frame f with
+    // f mod W = fw, or -1
+    auto tail_col = [&](int fw) -> int {
+        const int gt = c >= fw ? c - fw : c - fw + W;
+        return gt < NT ? 256 * W + 8 * gt : -1;
+    };
+    // the group's word of row `lane` of the turn whose first row's byte col0 is at
+    // t0p (rows past the turn: no power)
+    auto tail_load = [&](const uint8_t *t0p, int tc) -> uint2 {
+        const uint8_t *p = t0p + (tc - col0) + (int64_t)lane * N;
+        return (lane < RS && SK_DBG_IN(it, p, 8)) ? ldg_stream(p)
+                                                  : make_uint2(0x88888888u, 0x88888888u);
+    };
+    [[maybe_unused]] int fw = 0;     // the current frame mod W (a counter)
+    [[maybe_unused]] int tcc = -1;   // this warp's group of the current frame
+    [[maybe_unused]] uint2 wt = make_uint2(0x88888888u, 0x88888888u);
+    [[maybe_unused]] int32_t ts1 = 0, ts2 = 0;
+    if constexpr (TAIL) {
+        fw = (int)(frame % W);
+        tcc = tail_col(fw);
+        if (t0 < t1 && tcc >= 0)
+            wt = tail_load(in + t0 * RS * N, tcc);
+    }
     for (int64_t g = t0; g < t1; ++g) {
         if (lane == 0 && pf && g % PER == 0 && g + 2 * PER < t1)
             prefetch_box(tmap, xs, (int)((g + 2 * PER) * RS));  // 64 rows ahead
         const bool more = g + 1 < t1;
         const uint8_t *pn = in + (g + 1) * RS * N;
+        [[maybe_unused]] int tcn = -1;  // the group of the next turn's frame
+        if constexpr (TAIL) {
+            // the next turn's word first, then this turn's
+            tcn = gf + 1 == (int)tpf ? tail_col(fw + 1 == W ? 0 : fw + 1) : tcc;
+            const uint2 wn = (more && tcn >= 0) ? tail_load(pn, tcn)
+                                                : make_uint2(0x88888888u, 0x88888888u);
+            if (tcc >= 0)
+                tail_turn(wt, lb, ts1, ts2);
+            wt = wn;
+        }
 #pragma unroll
         for (int j = 0; j < S; ++j) {
 #pragma unroll
@@ -500,11 +676,19 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
         if (!fend && more)
             continue;
         finish_s2(s1, s2);
+        if constexpr (TAIL) {
+            if (tcc >= 0)
+                tail_reduce(ts1, ts2);
+        }
         if (fend && gf0 == 0) {
             // a whole frame: the slice's part goes into the team's slot ring
-            int64_t q;
-            int32_t cnt;
-            slice_terms(it, frame, col0, M, s1, s2, q, cnt);
+            int64_t q = 0, q0 = 0;
+            int32_t cnt = 0, c0 = 0;
+            if constexpr (TAIL) {
+                if (tcc >= 0)
+                    tail_lane_term(it, frame, tcc, M, ts1, ts2, q0, c0);
+            }
+            slice_terms(it, frame, col0, M, s1, s2, q, cnt, q0, c0);
             if (lane == 0)
                 wi_commit(it, slots, kk, W, frame, q, cnt);
             __syncwarp();
@@ -520,6 +704,13 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
                 for (int k = 0; k < kVec; ++k)
                     atomicAdd(sp + k,
                               ((unsigned long long)(uint32_t)s2[k] << 32) | (uint32_t)s1[k]);
+            }
+            // this warp's folded group of the part's rows goes into the same slot
+            // (lane 4j: input j), counted with the warp's own column below
+            if constexpr (TAIL) {
+                if (tcc >= 0 && (lane & 3) == 0 && SK_DBG_SLOT(it, slot))
+                    atomicAdd(ps + slot * N + tcc + (lane >> 2),
+                              ((unsigned long long)(uint32_t)ts2 << 32) | (uint32_t)ts1);
             }
             __syncwarp();
             int fin = 0;
@@ -545,9 +736,18 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
                         s2[k] = (int32_t)(v >> 32);
                     }
                 }
-                int64_t q;
-                int32_t cnt;
-                slice_terms(it, frame, col0, M, s1, s2, q, cnt);
+                int64_t q = 0, q0 = 0;
+                int32_t cnt = 0, c0 = 0;
+                if constexpr (TAIL) {
+                    // the column's folded group: its totals (lane 4j: input j) and terms
+                    if (tcc >= 0 && (lane & 3) == 0) {
+                        const unsigned long long v =
+                            atomicExch(ps + slot * N + tcc + (lane >> 2), 0ull);
+                        tail_lane_term(it, frame, tcc, M, (int32_t)(uint32_t)v,
+                                       (int32_t)(v >> 32), q0, c0);
+                    }
+                }
+                slice_terms(it, frame, col0, M, s1, s2, q, cnt, q0, c0);
                 if (lane == 0) {
                     atomicExch(pturn + slot * W + c, 0);
                     atomicAdd(pq + slot, (unsigned long long)q);
@@ -570,6 +770,13 @@ __device__ __forceinline__ void run_fast_rb(const Item &it, uint32_t lb, TeamSme
             acc[j] = 0u;
             s1[j] = 0;
             s2[j] = 0;
+        }
+        if constexpr (TAIL) {
+            ts1 = 0;
+            ts2 = 0;
+            tcc = tcn;
+            if (fend)
+                fw = fw + 1 == W ? 0 : fw + 1;
         }
         if (fend) {
             gf = 0;

@@ -84,6 +84,10 @@ def main():
         (2048, 48, 0, 21, dict(rows=8, path=T), T),
         (256, 256, 0, 700, None, T),
         (1000, 64, 0, 33, None, RB),
+        (2056, 64, 0, 33, None, RB),             # folded tail: 8 warps + 8 columns
+        (2056, 64, 0, 7, dict(path=WS), WS),
+        (264, 96, 0, 31, None, RB),              # one warp + 1 group of 8 columns
+        (264, 96, 0, 5, dict(path=WS), WS),
         (2047, 256, 0, 5, None, RB),
         (2047, 256, 0, 5, dict(path=T), GEN),
         (333, 96, 0, 31, None, RB),

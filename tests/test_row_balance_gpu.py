@@ -4,9 +4,9 @@ hands every team an equal range of 32-row turns (16-row turns when M = 16 mod
 scratch in device memory.  Against the
 oracle: cut frames of every kind (a frame shared by two teams, a frame spread
 over many teams, a team inside one frame), per-input outputs written by the
-warp that completes a column, one plan on two streams, a captured launch (which
-hands out whole frames), and the no-allocation call before and after the plan
-has its scratch."""
+warp that completes a column, folded tails (groups of 8 columns past the last
+whole slice), one plan on two streams, a captured launch (which hands out whole
+frames), and the no-allocation call before and after the plan has its scratch."""
 
 import numpy as np
 import pytest
@@ -115,6 +115,63 @@ def test_cut_frames_bit_exact(N, M, F, layout):
         sk.sk_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("N,M,F", [
+    (2056, 256, 301),   # 8 warps and one folded group of 8 columns: two teams per CTA
+    (520, 256, 97),     # 2 warps + 1 group
+    (2064, 256, 41),    # 2 groups, with the tensor map's L2 prefetch (N = 0 mod 16)
+    (2080, 64, 61),     # 4 groups over 8 warps
+    (264, 96, 123),     # one-warp teams and one group
+    (288, 96, 123),     # 4 groups > 1 warp: not folded, a second warp of 32 columns
+    (776, 48, 77),      # 3 warps + 1 group, 16-row turns on the 8-row tile
+    (3848, 32, 9),      # 15 warps + 1 group: one team per CTA, one turn per frame
+    (264, 4096, 3),     # 1 warp + 1 group, frames spread over many teams
+])
+@pytest.mark.parametrize("path", ["balanced", "whole"])
+def test_folded_tail_bit_exact(N, M, F, path):
+    """N = 256 W + 8 NT (NT of 1..min(4, W)): teams of W warps read the NT groups
+    of 8 columns past the last whole slice row-per-lane, one warp per group and frame
+    (rotating with the frame): inside the turn loop with balanced rows (frames cut
+    between teams, the groups' sums through the scratch), at the frame's end with
+    whole frames per team.  S1, S2, Q, N_eff, SK bits, masks and the per-input
+    estimates against the oracle."""
+    dev = _dev()
+    x = _bytes(N, M, F, N + 3 * M + F)
+    want = oracle.flag(x, M, N, 3.0, 0.02)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    s1 = torch.full((F, N), -1, dtype=torch.int32, device=dev)
+    s2 = torch.full_like(s1, -1)
+    q = torch.full((F,), -1, dtype=torch.int64, device=dev)
+    skv = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+    ne = torch.full((F,), -1, dtype=torch.int32, device=dev)
+    mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.02)
+    try:
+        if path == "whole":
+            sk.sk_plan_set_config(plan, rows=16 if M % 32 == 0 else 8,
+                                  path=sk.SK_PATH_WARP_SLICE)
+        for _ in range(2):
+            sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
+            sk.sk_flag(plan, d_in, F, None, mask)
+            torch.cuda.synchronize()
+            assert np.array_equal(s1.cpu().numpy(), want["S1"])
+            assert np.array_equal(s2.cpu().numpy(), want["S2"])
+            assert np.array_equal(q.cpu().numpy(), want["Q"])
+            assert np.array_equal(ne.cpu().numpy(), want["neff"])
+            assert np.array_equal(skv.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32))
+            assert np.array_equal(mask.cpu().numpy(), want["mask"])
+        assert sk.sk_plan_get_config(plan)["last_path"] == (
+            sk.SK_PATH_ROW_BALANCED if path == "balanced" else sk.SK_PATH_WARP_SLICE)
+        wi = oracle.flag_inputs(x, M, N, 3.0, 0.02)
+        sk_in = torch.empty((F, N), dtype=torch.float32, device=dev)
+        m_in = torch.empty((F, N), dtype=torch.uint8, device=dev)
+        sk.sk_compute_inputs(plan, d_in, F, sk_in, m_in)
+        torch.cuda.synchronize()
+        assert np.array_equal(sk_in.cpu().numpy().view(np.uint32), wi["sk_in"].view(np.uint32))
+        assert np.array_equal(m_in.cpu().numpy(), wi["mask_in"])
+    finally:
+        sk.sk_plan_destroy(plan)
+
+
 def test_one_plan_on_two_streams():
     """Launches of one plan on two streams take turns on the scratch."""
     dev = _dev()
@@ -136,7 +193,7 @@ def test_one_plan_on_two_streams():
         sk.sk_plan_destroy(plan)
 
 
-@pytest.mark.parametrize("N,M,F", [(2048, 256, 299), (2047, 64, 77)])
+@pytest.mark.parametrize("N,M,F", [(2048, 256, 299), (2047, 64, 77), (2056, 64, 41)])
 def test_captured_launch_hands_out_whole_frames(N, M, F):
     """A launch captured into a CUDA graph does not use the scratch (a ragged N then
     takes the general path); the replayed graph and the plain launch give the
