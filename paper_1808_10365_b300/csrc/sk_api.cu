@@ -88,6 +88,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 return;
             }
         }
+        if constexpr (R * S == 16 && !SRV) {
+            // M not a multiple of 16 (N a multiple of 8): whole-frame warp slices whose
+            // last 16-row turn is partial
+            if (single.fast == 4 && single.wi && (NC == 0 || single.N == NC)) {
+                run_fast_wi<R, S, NC, false, true>(single, fb, fe, lb, ts, &tmap);
+                return;
+            }
+        }
         if constexpr (R * S == 16 && NC == 0 && !SRV) {
             // ragged N (not a multiple of 8), balanced rows: one loop per N mod 8
             if (single.fast == 3 && single.wi && single.rb && single.M % 16 == 0) {
@@ -572,6 +580,13 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         run.wi = (it.N % 16 != 0 || pf_off)
                      ? 2
                      : (encode_input_map(it.in, it.N, it.n_frames * it.M, &tmap) ? 1 : 0);
+    // M not a multiple of 16: whole-frame warp slices on the 8-row tile, the last turn
+    // of a frame partial, no tensor map (otherwise the general path, at a third of the
+    // rate: two loads, a shift and a mask a row)
+    const bool ws_mr = it.fast == 4 && tile == 1 && warp_slice_on() &&
+                       it.N >= 256 && it.N <= 4096 && req != SK_PATH_TEAM;
+    if (ws_mr)
+        run.wi = 2;
     // input-major teams of two or more warps combine through the same slot ring
     if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6 && req != SK_PATH_TEAM)
         run.wi = 1;
@@ -582,14 +597,15 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // it measured 2 % slower), and without the tensor map's L2 prefetch, which
     // slowed folded shapes (N = 2064: 5.18 TB/s without it, 4.05 with it).
     run.wtail = 0;
-    if (run.wi && it.fast == 1 && tail_fold_on() && it.N > 256 && (it.N & 255) <= 8 * kMaxTail &&
+    if (run.wi && it.fast == 1 && !ws_mr && tail_fold_on() && it.N > 256 &&
+        (it.N & 255) <= 8 * kMaxTail &&
         (it.N & 255) / 8 <= it.N / 256 &&
         (kThreads / 32) / (it.N / 256) > (kThreads / 32) / (it.N / 256 + 1)) {
         run.wtail = (it.N & 255) / 8;
         run.wi = 2;
     }
     // ragged N: warp slices without a tensor map, given balanced rows (below)
-    const bool tm_ws = it.fast == 1 || it.fast == 3;
+    const bool tm_ws = it.fast == 1 || it.fast == 3 || it.fast == 4;
     if (it.fast == 3 && warp_slice_on() && it.M % 16 == 0 &&
         (req == SK_PATH_AUTO || req == SK_PATH_ROW_BALANCED))
         run.wi = 2;
@@ -605,7 +621,7 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // team*M bytes, scratch for Q and N_eff of cut frames
     int64_t units = 0;
     size_t need = 0;
-    if (run.wi && tm_ws) {
+    if (run.wi && tm_ws && !ws_mr) {
         units = it.n_frames * (it.M / (tile == 0 ? 32 : 16));
         const int64_t K = std::max<int64_t>(1, std::min<int64_t>(gmax, units / Tl)) * Tl;
         need = (size_t)K * it.N * 8 + (size_t)((K * Wl + 1) & ~(int64_t)1) * 4 + (size_t)K * 16;
@@ -648,6 +664,8 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         if ((it.fast == 1 && it.M % (tile == 0 ? 32 : 16) == 0) ||
             (it.fast == 2 && grouped && it.imajor_team_log2 >= 5))
             taken = run.wi ? (rb ? SK_PATH_ROW_BALANCED : SK_PATH_WARP_SLICE) : SK_PATH_TEAM;
+        else if (ws_mr)
+            taken = SK_PATH_WARP_SLICE;
         else if (it.fast == 3 && rb)
             taken = SK_PATH_ROW_BALANCED;
         else if (it.fast == 2 && !grouped && it.imajor_team_log2 >= 5)
@@ -845,7 +863,7 @@ sk::Item sk_plan_s::item(const uint8_t *in, int64_t n_frames) const
     it.t_hi = d_t_hi;
     it.c_tab = d_c;
     it.e_tab = d_e;
-    it.fast = fast ? 1 : (imajor ? 2 : (ragged ? 3 : 0));
+    it.fast = fast ? 1 : (imajor ? 2 : (ragged ? 3 : (mr ? 4 : 0)));
     it.prefetch = 1;
     it.running_mu = (p.flags & SK_RUNNING_MU) ? 1 : 0;
     it.n_sigma = p.n_sigma;
@@ -940,6 +958,7 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
     pl->fast = (p.layout == SK_LAYOUT_TIME_MAJOR) && (N % kVec == 0) && (M % kFlushRows == 0);
     // time-major N not a multiple of 8: the ragged balanced path (16-row turns)
     pl->ragged = (p.layout == SK_LAYOUT_TIME_MAJOR) && (N % kVec != 0) && (M % 16 == 0);
+    pl->mr = (p.layout == SK_LAYOUT_TIME_MAJOR) && (N % kVec == 0) && (M % 16 != 0);
     const int gl = imajor_lanes(M);
     const bool grouped = imajor_shape(M) >= 0;
     pl->imajor = (p.layout == SK_LAYOUT_INPUT_MAJOR) && (grouped || M % (16 * gl) == 0);

@@ -114,6 +114,7 @@ struct sk_plan_s {
     bool fast = false;
     bool imajor = false;  // input-major fast path applies
     bool ragged = false;  // time-major N % 8 != 0, M % 16 == 0: ragged balanced path
+    bool mr = false;      // time-major N % 8 == 0, M % 16 != 0: partial last turn
     int rows = 16;      // register batch rows of the fast path
     int grid_ctas = 0;  // 0: one CTA per SM
     // launch configuration (sk_launch_config_t): requested read path of one-item

@@ -64,7 +64,9 @@ struct Item {
     const int64_t *e_tab;    // served: offset per power bucket [kOffsetBuckets]
     int32_t state_init;      // served: 1 on the stream's first frame
     int32_t fast;            // 1: time-major vector path, 2: input-major path, 3: time-major
-                             // ragged N (balanced rows, else general), 0: general
+                             // ragged N (balanced rows, else general), 4: time-major
+                             // M % 16 != 0 (warp slices with a partial last turn, else
+                             // general), 0: general
     float *sk_in;            // per-input SK^_i [n_frames][N] (Eq. originalSK), or null
     uint8_t *mask_in;        // per-input flag at the N_eff = 1 thresholds, or null
     int32_t prefetch;        // 1: input in device memory, L2 bulk prefetch allowed

@@ -370,7 +370,7 @@ __device__ __forceinline__ void tail_lane_term(const Item &it, int64_t frame, in
 // atomics); the warp that arrives last forms the frame's mask and SK and frees
 // the slot.  A team's slots form a ring of kWiSlots frames; a warp that gets
 // that far ahead of a slow one waits, bounded, for its slot.
-template <int R, int S, int NC, bool TAIL = false>
+template <int R, int S, int NC, bool TAIL = false, bool MR = false>
 __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int64_t f_end,
                                             uint32_t lb, TeamSmem &ts, const CUtensorMap *tmap)
 {
@@ -401,9 +401,11 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     const bool col_ok = (NC > 0 && NC % 256 == 0) || col0 < N;
     // no tensor map when N is not a multiple of 16 (the map's row stride must
     // be) or the plan turned the prefetch off: those launches stream without it
-    const bool pf = it.wi != 2;
+    const bool pf = !MR && it.wi != 2;
     const int64_t fbytes = (int64_t)M * N;
-    const int nb = M / R;
+    // MR: M not a multiple of the turn; a frame is ceil(M / RS) turns, the last one
+    // partial (rows past M read nothing and have no power)
+    const int nb = MR ? (M + RS - 1) / RS * S : M / R;
     const int64_t kmax = (f_end - f_begin + T - 1) / T;
     WiSlot *slots = ts.wi[team_idx];
     const uint8_t *const in = it.in;
@@ -414,8 +416,21 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     int64_t frame = f_begin + team_idx;
     bool ok = frame < f_end;
     const uint8_t *fp = in + frame * fbytes + col0;
-    // R rows from p, row stride N (a load immediate when NC > 0)
-    auto load = [&](uint2 (&b)[R], const uint8_t *p) {
+    // R rows from p, the frame's rows row0.., row stride N (a load immediate when
+    // NC > 0)
+    auto load = [&](uint2 (&b)[R], const uint8_t *p, int row0) {
+        if constexpr (MR) {
+            const int left = M - row0;
+            if (left < R) {
+                // the frame's last rows: loads below M only
+                const bool in = left > 0 && SK_DBG_IN(it, p, (int64_t)(left - 1) * N + 8);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    b[r] = (in && r < left) ? ldg_stream(p + (int64_t)r * N)
+                                            : make_uint2(0x88888888u, 0x88888888u);
+                return;
+            }
+        }
         if (!SK_DBG_IN(it, p, (R - 1) * N + 8)) {
             fill_zero_power_rows<R>(b);
             return;
@@ -431,7 +446,7 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     if (ok && col_ok) {
 #pragma unroll
         for (int j = 0; j < S; ++j)
-            load(buf[j], fp + (int64_t)j * R * N);
+            load(buf[j], fp + (int64_t)j * R * N, j * R);
     }
     // folded tail: the first column of this warp's group of frame f, or -1
     auto tail_col = [&](int64_t f) -> int {
@@ -491,14 +506,17 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
 #pragma unroll
             for (int j = 0; j < S; ++j) {
                 if (ok) {
+                    // MR: a batch wholly past the frame's last row adds nothing
+                    if (!MR || (jb + j) * R < M) {
 #pragma unroll
-                    for (int r = 0; r < R; r += 2)
-                        accum_pair(buf[j][r], buf[j][r + 1], lb, acc);
+                        for (int r = 0; r < R; r += 2)
+                            accum_pair(buf[j][r], buf[j][r + 1], lb, acc);
+                    }
                     if (((j + 1) * R) % kFlushRows == 0)
                         flush(acc, s1, s2);
                 }
                 if (lok && col_ok)
-                    load(buf[j], pn + (int64_t)j * R * N);
+                    load(buf[j], pn + (int64_t)j * R * N, (same_frame ? jb + S + j : j) * R);
             }
         }
         if (ok) {

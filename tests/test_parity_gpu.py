@@ -284,7 +284,7 @@ def test_full_array_workload_every_frame():
 
 @pytest.mark.parametrize("N,M,layout,F", [
     (2047, 256, 0, 23), (100, 100, 0, 301), (2056, 256, 0, 19), (520, 256, 0, 77),
-    (2048, 48, 0, 61), (2048, 64, 1, 45), (2048, 4096, 1, 3)])
+    (2048, 48, 0, 61), (2048, 100, 0, 41), (2048, 64, 1, 45), (2048, 4096, 1, 3)])
 def test_benchmarked_off_shapes_bit_exact(N, M, layout, F):
     """The shapes the benchmark times besides its own (ragged N, N = 8 mod 16, a short
     integration, input-major M = 64 and 4096), each over several CTAs' worth of
@@ -294,6 +294,49 @@ def test_benchmarked_off_shapes_bit_exact(N, M, layout, F):
     want = oracle.flag(x, M, N, 3.0, 0.0, layout=layout)
     got = run_compute(x, M, N, 3.0, 0.0, layout=layout)
     assert_parity(got, want)
+
+
+@pytest.mark.parametrize("N,M,F", [
+    (2048, 100, 61),    # 7 turns of 16 rows, the last with 4
+    (256, 100, 201),    # one-warp teams
+    (1000, 50, 77),     # N = 8 mod 16, a partial last slice
+    (4096, 24, 33),     # 16-warp teams, one per CTA
+    (512, 2, 999),      # the shortest integration: one turn of 2 rows
+    (2056, 17, 40),     # 9-warp teams (no folded tail with a partial turn)
+    (768, 200, 19),     # 13 turns, the last with 8 rows
+    (264, 7, 301),
+])
+def test_partial_last_turn_bit_exact(N, M, F):
+    """Time-major N a multiple of 8 (256..4096) with M not a multiple of 16: whole-
+    frame warp slices whose last 16-row turn is partial (rows past M read nothing);
+    the team path asked for instead takes the general path.  S1, S2, Q, N_eff, SK
+    bits, masks and the per-input estimates against the oracle."""
+    dev = _dev()
+    rng = np.random.default_rng(N * 5 + M + F)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    x[F // 2, : 3 * N] = 0x88                 # dead rows at the start of a frame
+    want = oracle.flag(x, M, N, 3.0, 0.05)
+    got = run_compute(x, M, N, 3.0, 0.05)
+    assert_parity(got, want)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    wi = oracle.flag_inputs(x, M, N, 3.0, 0.05)
+    for path, taken in ((sk.SK_PATH_AUTO, sk.SK_PATH_WARP_SLICE),
+                        (sk.SK_PATH_TEAM, sk.SK_PATH_GENERAL)):
+        plan = sk.sk_plan_create(N, M, 3.0, 0.05)
+        try:
+            sk.sk_plan_set_config(plan, rows=8, path=path)
+            sk_in = torch.empty((F, N), dtype=torch.float32, device=dev)
+            m_in = torch.empty((F, N), dtype=torch.uint8, device=dev)
+            mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+            sk.sk_compute_inputs(plan, d_in, F, sk_in, m_in)
+            sk.sk_flag(plan, d_in, F, None, mask)
+            torch.cuda.synchronize()
+            assert sk.sk_plan_get_config(plan)["last_path"] == taken
+        finally:
+            sk.sk_plan_destroy(plan)
+        assert np.array_equal(sk_in.cpu().numpy().view(np.uint32), wi["sk_in"].view(np.uint32))
+        assert np.array_equal(m_in.cpu().numpy(), wi["mask_in"])
+        assert np.array_equal(mask.cpu().numpy(), want["mask"])
 
 
 @pytest.mark.parametrize("N,M,F", [(256, 256, 40), (2048, 128, 6), (100, 64, 9)])

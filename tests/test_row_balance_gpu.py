@@ -146,9 +146,9 @@ def test_folded_tail_bit_exact(N, M, F, path):
     mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
     plan = sk.sk_plan_create(N, M, 3.0, 0.02)
     try:
-        if path == "whole":
-            sk.sk_plan_set_config(plan, rows=16 if M % 32 == 0 else 8,
-                                  path=sk.SK_PATH_WARP_SLICE)
+        sk.sk_plan_set_config(plan, rows=16 if M % 32 == 0 else 8,
+                              path=sk.SK_PATH_WARP_SLICE if path == "whole"
+                              else sk.SK_PATH_ROW_BALANCED)
         for _ in range(2):
             sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
             sk.sk_flag(plan, d_in, F, None, mask)
