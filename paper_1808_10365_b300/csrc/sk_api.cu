@@ -53,6 +53,9 @@ int sm_count(int device)
 //   3  chunk list of one-frame items, one item per CTA at a time, its rows split
 //      over the CTA's teams (served batch smaller than the GPU: more loads in
 //      flight per frame)
+//   5  one item on warp slices with a folded tail (Item::wtail) or a partial last
+//      turn (Item::fast = 4): kernels of their own, so that the extra state stays
+//      out of the register allocation of the mode-0 kernels
 template <int R, int S, bool SRV, int NC, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_fused_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
@@ -61,10 +64,29 @@ __global__ void __launch_bounds__(kThreads, 1)
 {
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     __shared__ TeamSmem ts;
-    if (MODE == 0)
+    if (MODE == 0 || MODE == 5)
         init_wi_slots(ts);  // ordered before first use by build_table's barrier
     const uint32_t lb = build_table(dyn_smem);
     int parity = 0;
+    if constexpr (MODE == 5 && (R * S == 32 || R * S == 16) && !SRV) {
+        const int64_t F = single.n_frames;
+        const int64_t G = gridDim.x;
+        const int64_t fb = F * (int64_t)blockIdx.x / G;
+        const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
+        if (single.fast == 4) {
+            // M not a multiple of 16 (N a multiple of 8): whole-frame warp slices whose
+            // last 16-row turn is partial
+            if constexpr (R * S == 16)
+                run_fast_wi<R, S, NC, false, true>(single, fb, fe, lb, ts, &tmap);
+        } else if constexpr (NC == 0) {
+            // a folded tail (N not a compiled multiple of 256)
+            if (single.rb)
+                run_fast_rb<R, S, NC, true>(single, lb, ts, &tmap);
+            else
+                run_fast_wi<R, S, NC, true>(single, fb, fe, lb, ts, &tmap);
+        }
+        return;
+    }
     if (MODE == 0) {
         const int64_t F = single.n_frames;
         const int64_t G = gridDim.x;
@@ -74,25 +96,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             single.fast == 1 && single.M % (R * S) == 0 && (NC == 0 || single.N == NC);
         if constexpr ((R * S == 32 || R * S == 16) && !SRV) {
             if (fast && single.wi) {
-                if (single.rb) {
-                    // a folded tail only where N is not a compiled multiple of 256
-                    if (NC == 0 && single.wtail)
-                        run_fast_rb<R, S, NC, true>(single, lb, ts, &tmap);
-                    else
-                        run_fast_rb<R, S, NC>(single, lb, ts, &tmap);
-                } else
-                    if (NC == 0 && single.wtail)
-                        run_fast_wi<R, S, NC, true>(single, fb, fe, lb, ts, &tmap);
-                    else
-                        run_fast_wi<R, S, NC>(single, fb, fe, lb, ts, &tmap);
-                return;
-            }
-        }
-        if constexpr (R * S == 16 && !SRV) {
-            // M not a multiple of 16 (N a multiple of 8): whole-frame warp slices whose
-            // last 16-row turn is partial
-            if (single.fast == 4 && single.wi && (NC == 0 || single.N == NC)) {
-                run_fast_wi<R, S, NC, false, true>(single, fb, fe, lb, ts, &tmap);
+                if (single.rb)
+                    run_fast_rb<R, S, NC>(single, lb, ts, &tmap);
+                else
+                    run_fast_wi<R, S, NC>(single, fb, fe, lb, ts, &tmap);
                 return;
             }
         }
@@ -293,6 +300,13 @@ static const KernelFn kSingle[2][3] = {
      sk_fused_kernel<16, 2, false, 2048, 0>},
     {sk_fused_kernel<8, 2, false, 0, 0>, sk_fused_kernel<8, 2, false, 256, 0>,
      sk_fused_kernel<8, 2, false, 2048, 0>}};
+// one-item launches with a folded tail ([tile], runtime N) or a partial last turn
+// (8-row tile, [0 -> runtime N, 1 -> N = 256, 2 -> N = 2048])
+static const KernelFn kTail[2] = {sk_fused_kernel<16, 2, false, 0, 5>,
+                                  sk_fused_kernel<8, 2, false, 0, 5>};
+static const KernelFn kPartial[3] = {sk_fused_kernel<8, 2, false, 0, 5>,
+                                     sk_fused_kernel<8, 2, false, 256, 5>,
+                                     sk_fused_kernel<8, 2, false, 2048, 5>};
 // batched launches: [tile][0 -> runtime N, 1 -> N = 256, 2 -> N = 2048] (the row
 // stride as a load immediate is worth 7-12 % here too; one kernel holding the
 // three pipelines spills, so a batch launches once per class)
@@ -414,8 +428,11 @@ sk_status_t ensure_kernel_attrs(int device)
         for (int j = 0; j < 3; ++j) {
             fns.push_back(kSingle[t][j]);
             fns.push_back(kBatched[t][j]);
+            if (t == 0)
+                fns.push_back(kPartial[j]);
         }
     }
+    fns.push_back(kTail[0]);
     for (KernelFn f : fns) {
         cudaError_t e = cudaFuncSetAttribute((const void *)f,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -598,12 +615,16 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // slowed folded shapes (N = 2064: 5.18 TB/s without it, 4.05 with it).
     run.wtail = 0;
     if (run.wi && it.fast == 1 && !ws_mr && tail_fold_on() && it.N > 256 &&
-        (it.N & 255) <= 8 * kMaxTail &&
+        (it.N & 255) != 0 && (it.N & 255) <= 8 * kMaxTail &&
         (it.N & 255) / 8 <= it.N / 256 &&
         (kThreads / 32) / (it.N / 256) > (kThreads / 32) / (it.N / 256 + 1)) {
         run.wtail = (it.N & 255) / 8;
         run.wi = 2;
     }
+    if (run.wtail)
+        fn = kTail[tile];
+    else if (ws_mr)
+        fn = kPartial[nci];
     // ragged N: warp slices without a tensor map, given balanced rows (below)
     const bool tm_ws = it.fast == 1 || it.fast == 3 || it.fast == 4;
     if (it.fast == 3 && warp_slice_on() && it.M % 16 == 0 &&

@@ -472,9 +472,6 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
         const int64_t nframe = frame + T;
         const bool nok = nframe < f_end;
         const uint8_t *nfp = in + nframe * fbytes + col0;
-        [[maybe_unused]] int tcn = -1;  // the group of the team's next frame
-        if constexpr (TAIL)
-            tcn = nok ? tail_col(nframe) : -1;
         uint32_t acc[kVec];
         int32_t s1[kVec], s2[kVec];
 #pragma unroll
@@ -497,10 +494,11 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
             const uint8_t *pn = same_frame ? fp + (int64_t)(jb + S) * R * N : nfp;
             const bool lok = same_frame ? ok : nok;
             if constexpr (TAIL) {
-                // this turn's word, then the next turn's (in flight over this turn)
+                // this turn's word, then the next turn's (in flight over this turn;
+                // past the frame's last turn, the group of the team's next frame)
                 if (tcc >= 0)
                     tail_turn(wt, lb, ts1, ts2);
-                const int ntc = same_frame ? tcc : tcn;
+                const int ntc = same_frame ? tcc : (nok ? tail_col(nframe) : -1);
                 wt = ntc >= 0 ? tail_load(pn, ntc) : make_uint2(0x88888888u, 0x88888888u);
             }
 #pragma unroll
@@ -538,7 +536,7 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
         if constexpr (TAIL) {
             ts1 = 0;
             ts2 = 0;
-            tcc = tcn;
+            tcc = nok ? tail_col(nframe) : -1;
         }
         frame = nframe;
         fp = nfp;
