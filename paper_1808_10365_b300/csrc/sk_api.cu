@@ -598,12 +598,14 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
                      ? 2
                      : (encode_input_map(it.in, it.N, it.n_frames * it.M, &tmap) ? 1 : 0);
     // M not a multiple of 16: whole-frame warp slices on the 8-row tile, the last turn
-    // of a frame partial, no tensor map (otherwise the general path, at a third of the
-    // rate: two loads, a shift and a mask a row)
+    // of a frame partial (otherwise the general path, at a third of the rate: two
+    // loads, a shift and a mask a row)
     const bool ws_mr = it.fast == 4 && tile == 1 && warp_slice_on() &&
                        it.N >= 256 && it.N <= 4096 && req != SK_PATH_TEAM;
     if (ws_mr)
-        run.wi = 2;
+        run.wi = (it.N % 16 != 0 || pf_off)
+                     ? 2
+                     : (encode_input_map(it.in, it.N, it.n_frames * it.M, &tmap) ? 1 : 2);
     // input-major teams of two or more warps combine through the same slot ring
     if (it.fast == 2 && warp_slice_on() && it.imajor_team_log2 >= 6 && req != SK_PATH_TEAM)
         run.wi = 1;

@@ -401,7 +401,16 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
     const bool col_ok = (NC > 0 && NC % 256 == 0) || col0 < N;
     // no tensor map when N is not a multiple of 16 (the map's row stride must
     // be) or the plan turned the prefetch off: those launches stream without it
-    const bool pf = !MR && it.wi != 2;
+    const bool pf = it.wi != 2;
+    // the first row of a prefetch box; MR: kept inside the input (a frame's padded last
+    // turn puts boxes past its rows)
+    auto box_row = [&](int64_t y) -> int {
+        if constexpr (MR) {
+            const int64_t last = it.n_frames * M - 32;
+            return (int)(y < last ? y : (last > 0 ? last : 0));
+        }
+        return (int)y;
+    };
     const int64_t fbytes = (int64_t)M * N;
     // MR: M not a multiple of the turn; a frame is ceil(M / RS) turns, the last one
     // partial (rows past M read nothing and have no power)
@@ -485,9 +494,9 @@ __device__ __forceinline__ void run_fast_wi(const Item &it, int64_t f_begin, int
                 const int ba = jb + 2 * BB;  // two boxes (64 rows) ahead
                 if (ba < nb) {
                     if (ok)
-                        prefetch_box(tmap, xs, (int)(frame * M + ba * R));
+                        prefetch_box(tmap, xs, box_row(frame * M + ba * R));
                 } else if (nok && ba - nb + BB <= nb) {
-                    prefetch_box(tmap, xs, (int)(nframe * M + (ba - nb) * R));
+                    prefetch_box(tmap, xs, box_row(nframe * M + (ba - nb) * R));
                 }
             }
             const bool same_frame = jb + S < nb;
