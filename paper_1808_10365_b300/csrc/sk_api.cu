@@ -53,9 +53,10 @@ int sm_count(int device)
 //   3  chunk list of one-frame items, one item per CTA at a time, its rows split
 //      over the CTA's teams (served batch smaller than the GPU: more loads in
 //      flight per frame)
-//   5  one item on warp slices with a folded tail (Item::wtail) or a partial last
-//      turn (Item::fast = 4): kernels of their own, so that the extra state stays
-//      out of the register allocation of the mode-0 kernels
+//   5  one item on warp slices with a folded tail (Item::wtail), a partial last turn
+//      (Item::fast = 4) or ragged N (Item::fast = 3, balanced rows): kernels of their
+//      own, so that the extra state stays out of the register allocation of the
+//      mode-0 kernels
 template <int R, int S, bool SRV, int NC, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     sk_fused_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
@@ -78,6 +79,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             // last 16-row turn is partial
             if constexpr (R * S == 16)
                 run_fast_wi<R, S, NC, false, true>(single, fb, fe, lb, ts, &tmap);
+        } else if (single.fast == 3) {
+            // ragged N (not a multiple of 8), balanced rows: one loop per N mod 8
+            if constexpr (R * S == 16 && NC == 0) {
+                switch (single.N & 7) {
+                case 1: run_fast_rag<1>(single, lb, ts); break;
+                case 2: run_fast_rag<2>(single, lb, ts); break;
+                case 3: run_fast_rag<3>(single, lb, ts); break;
+                case 4: run_fast_rag<4>(single, lb, ts); break;
+                case 5: run_fast_rag<5>(single, lb, ts); break;
+                case 6: run_fast_rag<6>(single, lb, ts); break;
+                default: run_fast_rag<7>(single, lb, ts); break;
+                }
+            }
         } else if constexpr (NC == 0) {
             // a folded tail (N not a compiled multiple of 256)
             if (single.rb)
@@ -100,21 +114,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     run_fast_rb<R, S, NC>(single, lb, ts, &tmap);
                 else
                     run_fast_wi<R, S, NC>(single, fb, fe, lb, ts, &tmap);
-                return;
-            }
-        }
-        if constexpr (R * S == 16 && NC == 0 && !SRV) {
-            // ragged N (not a multiple of 8), balanced rows: one loop per N mod 8
-            if (single.fast == 3 && single.wi && single.rb && single.M % 16 == 0) {
-                switch (single.N & 7) {
-                case 1: run_fast_rag<1>(single, lb, ts); break;
-                case 2: run_fast_rag<2>(single, lb, ts); break;
-                case 3: run_fast_rag<3>(single, lb, ts); break;
-                case 4: run_fast_rag<4>(single, lb, ts); break;
-                case 5: run_fast_rag<5>(single, lb, ts); break;
-                case 6: run_fast_rag<6>(single, lb, ts); break;
-                default: run_fast_rag<7>(single, lb, ts); break;
-                }
                 return;
             }
         }
@@ -300,8 +299,9 @@ static const KernelFn kSingle[2][3] = {
      sk_fused_kernel<16, 2, false, 2048, 0>},
     {sk_fused_kernel<8, 2, false, 0, 0>, sk_fused_kernel<8, 2, false, 256, 0>,
      sk_fused_kernel<8, 2, false, 2048, 0>}};
-// one-item launches with a folded tail ([tile], runtime N) or a partial last turn
-// (8-row tile, [0 -> runtime N, 1 -> N = 256, 2 -> N = 2048])
+// one-item launches with a folded tail ([tile], runtime N), a partial last turn
+// (8-row tile, [0 -> runtime N, 1 -> N = 256, 2 -> N = 2048]) or ragged N on balanced
+// rows (kPartial[0])
 static const KernelFn kTail[2] = {sk_fused_kernel<16, 2, false, 0, 5>,
                                   sk_fused_kernel<8, 2, false, 0, 5>};
 static const KernelFn kPartial[3] = {sk_fused_kernel<8, 2, false, 0, 5>,
@@ -673,6 +673,13 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
         // ragged N without balanced rows: the general path, whole frames per team
         run.wi = 0;
         g = std::min<int64_t>(gmax, (it.n_frames + T - 1) / T);
+    } else if (it.fast == 3) {
+        fn = kPartial[0];  // the ragged balanced path (mode 5, 8-row tile, runtime N)
+        // its whole-row L2 prefetch pays on long frames of teams of up to 8 warps
+        // (N = 2047: +2 % at M = 128, +7 % at 256, +11 % at 1024) and costs elsewhere
+        // (M = 64 or 48: -7 to -12 %; 9 or 16 warps: -2 to -4 %)
+        if (!(it.M >= 256 && it.N <= 2048))
+            run.prefetch = 0;
     }
     if (g < 1)
         g = 1;
