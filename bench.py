@@ -11,6 +11,8 @@ inputs resident in HBM; e2e = the same call on host (pinned) buffers with the
 host-to-device upload and the mask/SK download inside the timed region.
 After the timed steps a sustained leg streams the same launch back to back for
 a few seconds (the regime after the power cap engages: roofline.frac_sustained),
+then once more under the configuration tuned for streaming
+(tiles_b300_sustained.txt: roofline.frac_sustained_tuned),
 and the extras time off-benchmark shapes (`shapes`), the batched mixed
 workload, and the serving workload (its full 10 s paced, plus shorter legs).
 
@@ -584,6 +586,26 @@ def shapes_bench(reps: int = 10, dev_index: int = 0, target_bytes: int = 3 << 30
     return {"peak_gbs": peak, "peak_kind": f"{kind} copy bandwidth", "cases": out}
 
 
+SUSTAINED_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                               "paper_1808_10365_b300", "tiles_b300_sustained.txt")
+
+
+def sustained_config(N: int, M: int, layout: int):
+    """The launch configuration tuned for continuous streaming (autotune --sustained)
+    of (N, M, layout), as sk_plan_set_config keywords, or None without an entry."""
+    if not os.path.exists(SUSTAINED_CACHE):
+        return None
+    with open(SUSTAINED_CACHE) as f:
+        for ln in f:
+            v = ln.split()
+            if ln.startswith("#") or len(v) != 9:
+                continue
+            if (int(v[0]), int(v[1]), int(v[2])) == (N, M, layout):
+                keys = ("rows", "grid_ctas", "path", "team_log2", "prefetch", "batch_path")
+                return dict(zip(keys, (int(t) for t in v[3:])))
+    return None
+
+
 def sustained_leg(sk, plan, d_in, F, d_sk, d_mask, stream, alg_bytes, seconds, dev_index,
                   est_launch_s):
     """Back-to-back sk_flag launches of the benchmark workload for about `seconds`, as a
@@ -713,10 +735,25 @@ def run_gpu(args):
         e2e = run_e2e(sk, plan, d_in, d_mask, F, fb, bytes_per_step, e2e_steps, stream, ws)
     # the read path the benchmark launch took (sk_launch_config_t.last_path)
     taken = sk.sk_plan_get_config(plan)["last_path"]
-    sustained = None
+    sustained = sustained_tuned = None
     if args.sustained_seconds > 0:
         sustained = sustained_leg(sk, plan, d_in, F, d_sk, d_mask, stream, alg_bytes,
                                   args.sustained_seconds, dev.index, mean_launch_s)
+        # the same leg under the configuration tuned for streaming (its entry in the
+        # sustained cache, written by autotune --sustained), run after the first
+        cfg = sustained_config(N_IN, M_T, layout)
+        if cfg is not None:
+            plan_s = sk.sk_plan_create(N_IN, M_T, 3.0, delta, layout=layout, device=dev.index)
+            try:
+                sk.sk_plan_set_config(plan_s, **cfg)
+                sustained_tuned = sustained_leg(sk, plan_s, d_in, F, d_sk, d_mask, stream,
+                                                alg_bytes, args.sustained_seconds, dev.index,
+                                                mean_launch_s)
+                sustained_tuned["config"] = dict(
+                    cfg, taken=PATH_NAMES.get(sk.sk_plan_get_config(plan_s)["last_path"]),
+                    cache=os.path.basename(SUSTAINED_CACHE))
+            finally:
+                sk.sk_plan_destroy(plan_s)
     sk.sk_plan_destroy(plan)
     line_tail = dict(e2e=e2e)
     line = {
@@ -754,6 +791,9 @@ def run_gpu(args):
     if sustained is not None:
         line["roofline"]["frac_sustained"] = sustained["frac"]
         line["sustained"] = sustained
+    if sustained_tuned is not None:
+        line["roofline"]["frac_sustained_tuned"] = sustained_tuned["frac"]
+        line["sustained_tuned"] = sustained_tuned
     if ws == 1 and not args.no_extras:
         if layout == 0:
             line.update(variants_bench(d_in, F, delta, dev_index=dev.index))

@@ -19,11 +19,19 @@ Results never depend on the configuration (exact integer combination), only
 speed does; the input bytes are uniform random, since the kernel's cost does not
 depend on their values.
 
+With `sustained_s` > 0 (`--sustained SECONDS`) each configuration instead streams
+back to back for that long, the regime of a deployment that runs continuously:
+the board then sits at its power cap, and a configuration that does the same work
+with less energy runs at a higher clock.  The L2 prefetch of the warp-slice paths,
+for one, wins in short bursts and loses over seconds (N = 2048, M = 256: 0.917 of
+measured copy bandwidth without it at 1912 MHz, 0.900 with it at 1822 MHz).
+
 The winners go to the cache file that sk_plan_create reads (environment
 variable SK_AUTOTUNE_CACHE), one line per shape:
     N M layout rows grid path team_log2 prefetch batch_path
 
     python -m paper_1808_10365_b300.autotune --out tiles.txt 2048:256:0 2048:256:1
+    python -m paper_1808_10365_b300.autotune --sustained 3 --out tiles_sustained.txt 2048:256:0
 """
 
 from __future__ import annotations
@@ -97,10 +105,37 @@ def _time_round_robin(fns, reps: int, rounds: int):
     return [statistics.median(t) for t in times]
 
 
+def _time_sustained(fns, seconds: float, est_ms: float):
+    """Mean launch time (ms) of each callable over about `seconds` of back-to-back
+    launches (each launch between its own events): one callable after the other, in
+    order and then in reverse, the two means averaged, so that the board's warming
+    over the sweep falls on all of them alike."""
+    import torch
+
+    n = max(20, int(seconds * 1e3 / max(est_ms, 1e-3)))
+    sums = [0.0] * len(fns)
+    for order in (range(len(fns)), reversed(range(len(fns)))):
+        for k in order:
+            f = fns[k]
+            for _ in range(3):
+                f()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(n)]
+            for a, b in ev:
+                a.record()
+                f()
+                b.record()
+            torch.cuda.synchronize()
+            sums[k] += statistics.mean(a.elapsed_time(b) for a, b in ev)
+    return [v / 2 for v in sums]
+
+
 def tune(N: int, M: int, layout: int = 0, bytes_target: int = 3 << 30, reps: int = 5,
-         rounds: int = 4, margin: float = 0.01, device: int = 0):
+         rounds: int = 4, margin: float = 0.01, device: int = 0, sustained_s: float = 0.0):
     """Best launch configuration of sk_flag for (N, M, layout); a dict with the
-    sk_launch_config_t fields, the measured table and the chosen one's GB/s."""
+    sk_launch_config_t fields, the measured table and the chosen one's GB/s.
+    sustained_s > 0: each configuration timed over that many seconds of back-to-back
+    launches instead of short round-robin rounds."""
     import torch
 
     dev = torch.device("cuda", device)
@@ -123,7 +158,11 @@ def tune(N: int, M: int, layout: int = 0, bytes_target: int = 3 << 30, reps: int
             plans.append(p)
             sk_plan_set_config(p, **c)
             fns.append(lambda p=p: sk_flag(p, x, F, sk, mask))
-        ms = _time_round_robin(fns, reps, rounds)
+        if sustained_s > 0:
+            est = _time_round_robin(fns[:1], 2, 1)[0]
+            ms = _time_sustained(fns, sustained_s, est)
+        else:
+            ms = _time_round_robin(fns, reps, rounds)
         for p in plans[1:]:
             taken.append(sk_plan_get_config(p)["last_path"])
     finally:
@@ -136,8 +175,8 @@ def tune(N: int, M: int, layout: int = 0, bytes_target: int = 3 << 30, reps: int
         best = 0
     out = {k: cands[best][k] for k in FIELDS}
     out.update(N=N, M=M, layout=layout, ms=ms[best], gbs=F * N * M / ms[best] / 1e6,
-               default_gbs=F * N * M / ms[0] / 1e6, table=table)
-    if layout == 0 and N == 2048 and M % 32 == 0:
+               default_gbs=F * N * M / ms[0] / 1e6, table=table, sustained_s=sustained_s)
+    if layout == 0 and N == 2048 and M % 32 == 0 and sustained_s <= 0:
         out["batch_path"], out["batch_table"] = tune_batch_path(N, M, device=device,
                                                                  reps=reps, rounds=rounds,
                                                                  margin=margin)
@@ -207,13 +246,16 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("--json", help="also write every measured configuration here")
+    ap.add_argument("--sustained", type=float, default=0.0,
+                    help="time each configuration over this many seconds of back-to-back "
+                         "launches (the power-capped regime of continuous streaming)")
     ap.add_argument("shapes", nargs="+", help="N:M or N:M:layout")
     a = ap.parse_args(argv)
     entries = []
     for s in a.shapes:
         v = [int(t) for t in s.split(":")]
         N, M, layout = v[0], v[1], v[2] if len(v) > 2 else 0
-        e = tune(N, M, layout)
+        e = tune(N, M, layout, sustained_s=a.sustained)
         print(f"N={N} M={M} layout={layout}: path={PATH_NAMES[e['path']]} rows={e['rows']} "
               f"team_log2={e['team_log2']} prefetch={e['prefetch']} "
               f"batch_path={PATH_NAMES[e['batch_path']]}: {e['gbs']:.0f} GB/s "

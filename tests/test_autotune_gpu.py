@@ -150,6 +150,28 @@ def test_sweep_writes_a_cache_the_plans_read(tmp_path, monkeypatch):
             sk.sk_plan_destroy(plan)
 
 
+def test_sustained_sweep(tmp_path, monkeypatch):
+    """The sustained mode (each configuration streamed back to back, in order and in
+    reverse) times every configuration, keeps the default unless another wins, and
+    writes a cache line the plans read back."""
+    _dev()
+    monkeypatch.setenv("SK_AUTOTUNE_CACHE", str(tmp_path / "none.txt"))
+    e = autotune.tune(512, 256, 0, bytes_target=64 << 20, sustained_s=0.05)
+    assert e["sustained_s"] == 0.05 and len(e["table"]) >= 4
+    assert all(t["ms"] > 0 and t["taken"] in ("team", "warp-slice", "row-balanced")
+               for t in e["table"])
+    assert "batch_table" not in e
+    out = tmp_path / "tiles.txt"
+    autotune.write_cache(str(out), [e])
+    monkeypatch.setenv("SK_AUTOTUNE_CACHE", str(out))
+    plan = sk.sk_plan_create(512, 256, 3.0, 0.0)
+    try:
+        cfg = sk.sk_plan_get_config(plan)
+        assert (cfg["rows"], cfg["path"], cfg["prefetch"]) == (e["rows"], e["path"], e["prefetch"])
+    finally:
+        sk.sk_plan_destroy(plan)
+
+
 def test_random_configurations_stay_exact():
     """40 seeded random shapes (both layouts, ragged N, M of any multiple of 16 and
     others) each under a random launch configuration (path, tile rows, grid, team
