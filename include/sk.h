@@ -35,6 +35,10 @@
  *                        and the slot-ring combine (input-major teams of >= 2 warps)
  *   SK_ROW_BALANCE=0     warp-slice launches hand out whole frames instead of
  *                        equal row ranges (no plan scratch)
+ *   SK_TAIL_FOLD=0       time-major N = 256 W + 8 k (k of 1..min(4, W), where that
+ *                        adds a team per CTA): teams of W + 1 warps instead of W
+ *                        warps that also read the k groups of 8 columns past the
+ *                        last whole 256-column slice
  *   SK_IMAJOR_GROUPED=0  input-major: per-input path instead of the grouped one
  *   SK_IMAJOR_PREFETCH=0 input-major grouped path without the L2 prefetch
  *   SK_IMAJOR_LANES      input-major per-input path: lanes per input (2, 4, 8)
