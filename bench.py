@@ -54,7 +54,7 @@ PROFILE_SUMMARY = {0: os.path.join(ROOT, "profiles", "sk_fused_kernel_full_array
                    1: os.path.join(ROOT, "profiles", "sk_imajor_kernel_full_array.json")}
 LAYOUT_SUFFIX = {0: "", 1: ", input-major [frame][input][t]"}
 PATH_NAMES = {1: "team", 2: "warp-slice", 3: "row-balanced warp-slice", 4: "general",
-              5: "per-input"}
+              5: "per-input", 6: "stream"}
 
 
 def kernel_hash() -> str:
@@ -534,7 +534,9 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
 # own launch.
 OFF_SHAPES = [
     ("time-major N=2047 M=256 (ragged N)", 2047, 256, 0),
-    ("time-major N=100 M=100 (general path)", 100, 100, 0),
+    ("time-major N=100 M=100 (stream path)", 100, 100, 0),
+    ("time-major N=16 M=256 (stream path)", 16, 256, 0),
+    ("time-major N=99 M=101 (general path)", 99, 101, 0),
     ("time-major N=2056 M=256 (N = 8 mod 16)", 2056, 256, 0),
     ("time-major N=520 M=256 (N = 8 mod 16)", 520, 256, 0),
     ("time-major N=2048 M=48 (M = 16 mod 32)", 2048, 48, 0),
@@ -575,10 +577,11 @@ def shapes_bench(reps: int = 10, dev_index: int = 0, target_bytes: int = 3 << 30
                 sk.sk_flag(plan, d_in, F, d_sk, d_mask, st)
                 b.record(st)
             st.synchronize()
+            taken = PATH_NAMES.get(sk.sk_plan_get_config(plan)["last_path"], "?")
         finally:
             sk.sk_plan_destroy(plan)
         ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-        out.append({"shape": label, "N": N, "M": M, "layout": layout, "frames": F,
+        out.append({"shape": label, "path": taken, "N": N, "M": M, "layout": layout, "frames": F,
                     "bytes": nbytes, "ms": ms, "tb_s": nbytes / (ms * 1e-3) / 1e12,
                     "roofline_frac": (nbytes + 5 * F) / (ms * 1e-3) / 1e9 / peak})
         del d_in, d_sk, d_mask

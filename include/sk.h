@@ -172,6 +172,9 @@ sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows_per_batch,
  * (whole frames per team); ROW_BALANCED adds equal row ranges over the grid
  * through the plan's scratch.  A path the shape cannot take (or the launch:
  * a captured launch has no row balancing) falls back to the one it can.
+ * STREAM (time-major only, N / gcd(N, 16) <= 512) reads each frame as one run
+ * of 16-byte chunks, a group of lanes per frame whose byte positions keep their
+ * inputs from chunk to chunk: the path of frames of few inputs, any M.
  * Reported (sk_launch_config_t.last_path) besides those: GENERAL (any N and
  * M, either layout) and PER_INPUT (input-major lengths of the per-input path).
  */
@@ -181,7 +184,8 @@ typedef enum {
     SK_PATH_WARP_SLICE = 2,
     SK_PATH_ROW_BALANCED = 3,
     SK_PATH_GENERAL = 4,
-    SK_PATH_PER_INPUT = 5
+    SK_PATH_PER_INPUT = 5,
+    SK_PATH_STREAM = 6
 } sk_path_t;
 
 /*
@@ -193,7 +197,7 @@ typedef enum {
  *              32-row turns on 16 and, only where M = 16 mod 32, 16-row
  *              turns on 8
  *   grid_ctas  CTAs of a one-item launch (0: one per SM)
- *   path       sk_path_t requested for one-item launches (0..3)
+ *   path       sk_path_t requested for one-item launches (0..3 or 6)
  *   team_log2  input-major layout: threads per frame as a power of two,
  *              5..8 (5..9 on the per-input path); set 0 for the plan's own
  *              choice (about 2 KB of frame per thread); get returns the size

@@ -45,6 +45,7 @@ SK_PATH_WARP_SLICE = 2
 SK_PATH_ROW_BALANCED = 3
 SK_PATH_GENERAL = 4
 SK_PATH_PER_INPUT = 5
+SK_PATH_STREAM = 6
 SK_NOALLOC_MAX_BYTES = 16 * 1024 * 1024
 SK_NOALLOC_MAX_FRAMES = 65536
 

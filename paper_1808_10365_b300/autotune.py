@@ -38,14 +38,15 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 
-from . import (SK_PATH_AUTO, SK_PATH_ROW_BALANCED, SK_PATH_TEAM, SK_PATH_WARP_SLICE,
+from . import (SK_PATH_AUTO, SK_PATH_ROW_BALANCED, SK_PATH_STREAM, SK_PATH_TEAM, SK_PATH_WARP_SLICE,
                sk_batch_create, sk_batch_destroy, sk_batch_run, sk_flag, sk_plan_create,
                sk_plan_destroy, sk_plan_get_config, sk_plan_set_config)
 
-PATH_NAMES = {0: "auto", 1: "team", 2: "warp-slice", 3: "row-balanced", 4: "general",
+PATH_NAMES = {0: "auto", 1: "team", 2: "warp-slice", 3: "row-balanced", 4: "general", 6: "stream",
               5: "per-input"}
 FIELDS = ("rows", "grid_ctas", "path", "team_log2", "prefetch", "batch_path")
 
@@ -68,6 +69,10 @@ def candidates(N: int, M: int, layout: int, default_team_log2: int):
             elif M % 16 == 0:
                 for p in paths if ws else (SK_PATH_TEAM,):
                     out.append(dict(base, rows=8, path=p, prefetch=pf))
+            # the stream path: any M, N / gcd(N, 16) <= 512; tried below N = 512 (from
+            # N = 256 the warp-slice paths read whole rows)
+            if N < 512 and N // math.gcd(N, 16) <= 512:
+                out.append(dict(base, path=SK_PATH_STREAM, prefetch=pf))
     elif default_team_log2 > 0:
         teams = [t for t in (default_team_log2 - 1, default_team_log2, default_team_log2 + 1)
                  if 5 <= t <= 8]
@@ -236,7 +241,8 @@ def write_cache(path: str, entries):
     keep = [ln for ln in lines if tuple(ln.split()[:3]) not in keys]
     with open(path, "w") as f:
         f.write("# N M layout rows grid path team_log2 prefetch batch_path "
-                "(sk_launch_config_t; path 0 auto, 1 team, 2 warp-slice, 3 row-balanced)\n")
+                "(sk_launch_config_t; path 0 auto, 1 team, 2 warp-slice, 3 row-balanced, "
+                "6 stream)\n")
         f.writelines(keep)
         for e in entries:
             f.write(cache_line(e))

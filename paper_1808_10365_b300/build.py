@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsk.so")
 DEBUG_LIB = os.path.join(HERE, "libsk_debug.so")
-SOURCES = ["sk_api.cu", "sk_batch.cu", "sk_server.cu", "sk_noalloc.cu", "sk_selftest.cu"]
+SOURCES = ["sk_api.cu", "sk_batch.cu", "sk_server.cu", "sk_noalloc.cu", "sk_selftest.cu",
+           "sk_stream.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -11,6 +11,7 @@
 #include "sk_common.h"
 #include "sk_path_general.cuh"
 #include "sk_path_input.cuh"
+#include "sk_path_stream.cuh"
 #include "sk_path_time.cuh"
 
 namespace sk {
@@ -570,6 +571,17 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     // the plan's requested path and prefetch (autotuned launch configuration)
     const int req = plan ? plan->path : SK_PATH_AUTO;
     const bool pf_off = plan && plan->prefetch_off;
+    // time-major frames of few inputs: the stream path, requested or by shape
+    StreamShape ssh;
+    if (it.layout == 0 && (req == SK_PATH_STREAM || (req == SK_PATH_AUTO && stream_auto(it))) &&
+        stream_shape(it.N, it.M, &ssh)) {
+        Item run = it;
+        if (pf_off)
+            run.prefetch = 0;
+        if (plan)
+            plan->last_path.store(SK_PATH_STREAM, std::memory_order_relaxed);
+        return launch_stream(run, ssh, device, st, grid_cap);
+    }
     KernelFn fn = kSingle[tile][nci];
     if (it.fast == 2)
         fn = imajor_kernel(it.M, !pf_off);
@@ -831,7 +843,7 @@ struct CachedConfig {
 static bool config_valid(const CachedConfig &c)
 {
     return (c.rows == 8 || c.rows == 16) && c.grid >= 0 && c.grid <= 65535 && c.path >= 0 &&
-           c.path <= SK_PATH_ROW_BALANCED && (c.team_log2 == 0 ||
+           (c.path <= SK_PATH_ROW_BALANCED || c.path == SK_PATH_STREAM) && (c.team_log2 == 0 ||
                                               (c.team_log2 >= 5 && c.team_log2 <= 9)) &&
            (c.prefetch == 0 || c.prefetch == 1) && c.batch_path >= 0 &&
            c.batch_path <= SK_PATH_ROW_BALANCED;
@@ -1152,8 +1164,8 @@ extern "C" sk_status_t sk_plan_set_config(sk_plan_t plan, const sk_launch_config
     c.batch_path = cfg->batch_path;
     if (!config_valid(c) || !team_override_ok(plan, c.team_log2))
         return set_error(SK_ERR_INVALID_ARG,
-                         "sk_plan_set_config: rows 8 or 16, grid 0..65535, path and batch_path "
-                         "0..3, team_log2 0 or 5..8 (5..9 on the per-input path; input-major "
+                         "sk_plan_set_config: rows 8 or 16, grid 0..65535, path 0..3 or 6, "
+                         "batch_path 0..3, team_log2 0 or 5..8 (5..9 on the per-input path; input-major "
                          "plans only), prefetch 0 or 1");
     plan->rows = c.rows;
     plan->grid_ctas = c.grid;

@@ -49,6 +49,14 @@ bool warp_slice_shape(int N, int M);
 // Tensor map of a time-major input for the warp-slice path's prefetch: rows of N
 // bytes (N % 16 == 0), boxes of 32 rows x 256 bytes.  False if none can be made.
 bool encode_input_map(const uint8_t *in, int N, int64_t rows, CUtensorMap *out);
+// Stream path (time-major frames of few inputs, sk_path_stream.cuh): its launch
+// shape for (N, M) (false if no unit of at most 512 lanes fits), whether a launch of
+// the item takes it when the plan asks for no path, and the launch.
+struct StreamShape;
+bool stream_shape(int N, int M, StreamShape *out);
+bool stream_auto(const Item &it);
+sk_status_t launch_stream(const Item &it, const StreamShape &sh, int device, cudaStream_t st,
+                          int grid_cap);
 // SK_ERR_TIMEOUT once if a bounded wait in an earlier launch of the plan gave up.
 sk_status_t pending_fault(sk_plan_t plan, const char *who);
 // Set-up of sk_flag_host_noalloc on `device` (current): looks up the device

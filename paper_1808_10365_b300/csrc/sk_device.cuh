@@ -163,6 +163,16 @@ __device__ __forceinline__ uint2 ldg_stream(const uint8_t *p)
     return v;
 }
 
+// One 16-byte chunk, streamed like ldg_stream (p 16-byte aligned).
+__device__ __forceinline__ uint4 ldg_stream16(const uint8_t *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // Same load at base + OFF with OFF a compile-time immediate of the instruction.
 template <int OFF>
 __device__ __forceinline__ uint2 ldg_stream_at(const uint8_t *base)

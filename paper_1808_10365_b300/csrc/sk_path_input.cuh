@@ -6,15 +6,6 @@
 
 namespace sk {
 
-__device__ __forceinline__ uint4 ldg_stream16(const uint8_t *p)
-{
-    uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
-
 // 16 samples of one input (one 16-byte chunk) into one packed accumulator.
 __device__ __forceinline__ uint32_t accum16(uint4 w, uint32_t lb)
 {

@@ -1,0 +1,380 @@
+// Stream path of the fused kernel: time-major frames of few inputs (small N, any
+// M), each frame read as one flat run of bytes in aligned 16-byte chunks.
+//
+// A time-major frame is M rows of N bytes, fbytes = M N contiguous bytes, and
+// byte o of the frame belongs to input o mod N.  A unit of s lanes reads the
+// frame's 16-byte chunks round robin: lane u takes chunks u, u + s, u + 2s, ...
+// With d the frame's offset from a 16-byte boundary, byte j of lane u's chunk of
+// pass p is frame byte 16 (u + s p) + j - d.  When 16 s is a multiple of N that
+// byte belongs to input (16 u + j - d) mod N in every pass: each lane keeps one
+// packed accumulator per byte position of its chunks for the whole frame, and
+// the table path of the other read paths applies unchanged (PRMT + LDS + half an
+// IADD3 a sample, one 16-byte load a chunk), whatever N and M are.  After the
+// frame the unit's 16 s partial sums go to shared memory, and input i adds the
+// R = 16 s / N of them that hold its samples: slots x + r N, r < R, with
+// x = (i + d) mod N.  The sums are exact integers, so the order is free.
+//
+// A unit is either part of one warp (s <= 32: 32 / s units a warp, lanes past the
+// last unit idle) or W = ceil(s / 32) warps (s > 32, one named barrier per frame
+// step).  s is a multiple of N / gcd(N, 16), at least 8 so that a unit's pass
+// reads at least 128 contiguous bytes, chosen on the host by a model of the
+// instructions a frame costs.  The slots are written once per frame, lane u's 16
+// values as four 16-byte pieces rotated by u / 2, so that each group of 8 lanes
+// of a store covers all 32 banks; the units of one warp start 8 words apart
+// (modulo 32).
+#pragma once
+
+#include "sk_device.cuh"
+
+namespace sk {
+
+// Launch shape of the stream path, chosen on the host (stream_shape).
+struct StreamShape {
+    int32_t s;         // lanes per frame, a multiple of N / gcd(N, 16)
+    int32_t W;         // warps per unit: 1 (several units a warp) or ceil(s / 32)
+    int32_t per_warp;  // units per warp when W == 1
+    int32_t units;     // units (frames in flight) per CTA
+};
+
+constexpr int kStreamThreads = 512;             // 16 warps a CTA, one CTA per SM
+constexpr int kStreamWarps = kStreamThreads / 32;
+constexpr int kStreamBatch = 8;                  // passes per register batch (loads in flight)
+constexpr int kStreamLead = 2 * kStreamBatch;    // L2 prefetch distance, in passes
+// slots: 16 s x 8 B per unit, plus 8 words per unit (at most 64 units) of skew
+constexpr int kStreamPartBytes = kStreamWarps * 32 * 16 * 8 + 64 * 32;
+constexpr int kStreamSmem = kDynSmem + kStreamPartBytes;
+constexpr uint32_t kNoPower = 0x88888888u;       // bytes that decode to 0 + 0i
+
+// The 16 bytes at p (16-byte aligned) with every byte outside the frame [lo, hi)
+// replaced by 0x88 (no power).  Only bytes of the frame are read, so the chunks
+// that stick out of the frame (and of the input buffer, at its two ends) never
+// touch memory outside it.
+__device__ __forceinline__ uint4 load_clipped(const Item &it, const uint8_t *p, const uint8_t *lo,
+                                              const uint8_t *hi)
+{
+    if (p >= lo && p + 16 <= hi)
+        return SK_DBG_IN(it, p, 16) ? ldg_stream16(p) : make_uint4(kNoPower, kNoPower, kNoPower,
+                                                                   kNoPower);
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t x = kNoPower;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint8_t *q = p + 4 * k + b;
+            if (q >= lo && q < hi && SK_DBG_IN(it, q, 1))
+                x = (x & ~(0xFFu << (8 * b))) | ((uint32_t)__ldg(q) << (8 * b));
+        }
+        w[k] = x;
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// One chunk of one lane into its 16 packed accumulators (byte j of the chunk
+// into accumulator j).
+__device__ __forceinline__ void accum_chunk(uint4 a, uint32_t lb, uint32_t (&acc)[16])
+{
+    const uint32_t wa[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            acc[4 * k + j] += lds_u32(prmt(wa[k], lb, 0x7604u | ((uint32_t)j << 4)));
+}
+
+// Two chunks of one lane (same byte positions, two passes): one three-input add
+// per position.
+__device__ __forceinline__ void accum_chunk_pair(uint4 a, uint4 b, uint32_t lb,
+                                                 uint32_t (&acc)[16])
+{
+    const uint32_t wa[4] = {a.x, a.y, a.z, a.w};
+    const uint32_t wb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t sel = 0x7604u | ((uint32_t)j << 4);  // byte j of the data word
+            acc[4 * k + j] += lds_u32(prmt(wa[k], lb, sel)) + lds_u32(prmt(wb[k], lb, sel));
+        }
+}
+
+// Packed accumulators (at most 16 samples each) into the exact sums: S1 takes the
+// high field, s2 the whole word, so that s2 holds S2 + 2^19 S1 modulo 2^32 until
+// the frame ends (as in flush()).
+__device__ __forceinline__ void flush16(uint32_t (&acc)[16], int32_t (&s1)[16],
+                                        int32_t (&s2)[16])
+{
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        s1[j] += (int32_t)(acc[j] >> kPackShift);
+        s2[j] = (int32_t)((uint32_t)s2[j] + acc[j]);
+        acc[j] = 0u;
+    }
+}
+
+// Word of slot x (lane x / 16, position x % 16) in a unit's slot array: lane u's
+// piece q (positions 4q .. 4q + 3) sits at piece (q + u / 2) mod 4 of its 16 words.
+__device__ __forceinline__ int slot_word(int x)
+{
+    const int u = x >> 4, q = (x >> 2) & 3;
+    return (u << 4) | ((((q + (u >> 1)) & 3)) << 2) | (x & 3);
+}
+
+// L2 prefetch of passes [q, q + n) of a unit whose frame starts at fa, limited to
+// the frame's own 16-byte blocks (a hint: results never depend on it).
+__device__ __forceinline__ void prefetch_passes(const uint8_t *fa, int32_t fbytes, int32_t pbytes,
+                                                int32_t q, int32_t n)
+{
+    const uintptr_t a0 = (uintptr_t)fa & ~(uintptr_t)15u;
+    uintptr_t b = a0 + (uintptr_t)q * (uintptr_t)pbytes;
+    uintptr_t e = b + (uintptr_t)n * (uintptr_t)pbytes;
+    const uintptr_t lo = ((uintptr_t)fa + 15u) & ~(uintptr_t)15u;
+    const uintptr_t hi = ((uintptr_t)fa + (uintptr_t)fbytes) & ~(uintptr_t)15u;
+    b = b < lo ? lo : b;
+    e = e > hi ? hi : e;
+    if (e > b)
+        prefetch_l2((const uint8_t *)b, (uint32_t)(e - b));
+}
+
+// Passes [q, q + kStreamBatch) of the unit's run of frames (this frame, P passes,
+// then its next one, nfa, or none) into L2, kStreamLead passes ahead of the reads.
+__device__ __forceinline__ void prefetch_ahead(const uint8_t *fa, const uint8_t *nfa, int32_t P,
+                                               int32_t fbytes, int32_t pbytes, int32_t q)
+{
+    if (q < P)
+        prefetch_passes(fa, fbytes, pbytes, q, kStreamBatch);
+    if (nfa && q + kStreamBatch > P)
+        prefetch_passes(nfa, fbytes, pbytes, q > P ? q - P : 0,
+                        q > P ? kStreamBatch : q + kStreamBatch - P);
+}
+
+// Frames [f_begin, f_end) of the item on the stream path (kStreamThreads threads).
+// part: the CTA's slot area (kStreamPartBytes of shared memory, 16-byte aligned);
+// red_q, red_c: one entry per warp.
+__device__ __forceinline__ void run_stream(const Item &it, const StreamShape &sh, int64_t f_begin,
+                                           int64_t f_end, uint32_t lb, int32_t *part,
+                                           long long *red_q, int *red_c)
+{
+    const int s = sh.s;
+    const int N = it.N;
+    const int M = it.M;
+    const int32_t fbytes = M * N;  // <= 2^24 (M, N <= 4096): frame offsets fit 32 bits
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int unit, u, tsz;
+    bool active, in_unit;
+    if (sh.W == 1) {
+        const int sub = lane / s;
+        u = lane - sub * s;
+        unit = warp * sh.per_warp + sub;
+        in_unit = sub < sh.per_warp;
+        active = in_unit;
+        tsz = s;
+    } else {
+        const int team = warp / sh.W;
+        u = (int)threadIdx.x - team * 32 * sh.W;
+        unit = team;
+        in_unit = team < sh.units;
+        active = in_unit && u < s;
+        tsz = 32 * sh.W;
+        if (!in_unit)
+            return;  // whole warps past the last team: no barrier of theirs is waited on
+    }
+    // the unit's S1 slots (16 s words) and S2 slots; with several units a warp each
+    // unit's area is 8 words longer, so that neighbours start 8 words apart modulo 32
+    // and their combine reads fall in different banks
+    int32_t *const ps1 = part + unit * (32 * s + (sh.W == 1 ? 8 : 0));
+    int32_t *const ps2 = ps1 + 16 * s;
+    const int R = (16 * s) / N;
+    const int64_t nunits = sh.units;
+    const int64_t rounds = (f_end - f_begin + nunits - 1) / nunits;
+    // A pass of the unit reads pbytes = 16 s bytes.  With the frame d bytes past a
+    // 16-byte boundary its chunks cover span = fbytes + d bytes: passes p < Pe hold
+    // whole chunks of the frame in every lane (but for lane 0's chunk of pass 0 when
+    // d > 0), and at most one more pass, P = Pe or Pe + 1, ends past the frame.
+    const int32_t pbytes = 16 * s;
+    const int32_t pe0 = fbytes / pbytes;             // Pe at d = 0
+    const int32_t rem0 = fbytes - pe0 * pbytes;
+    for (int64_t k = 0; k < rounds; ++k) {
+        const int64_t frame = f_begin + k * nunits + unit;
+        const bool fvalid = in_unit && frame < f_end;
+        const bool rd = active && fvalid;
+        const uint8_t *fa = it.in + (fvalid ? frame : f_begin) * (int64_t)fbytes;
+        const int d = (int)((uintptr_t)fa & 15u);
+        const uint8_t *lp = fa - d + 16 * u;  // the lane's chunk of pass 0
+        const int32_t span = fbytes + d;
+        const int32_t nch = (span + 15) >> 4;  // chunks covering the frame
+        const int32_t Pe = pe0 + (rem0 + d >= pbytes ? 1 : 0);
+        const int32_t P = Pe + ((span - Pe * pbytes) != 0 ? 1 : 0);
+        // L2 prefetch kStreamLead passes ahead of the reads, by the unit's lane 0:
+        // a bounded amount in flight (units x kStreamLead passes a CTA)
+        const bool pf = it.prefetch && rd && u == 0;
+        const uint8_t *nfa = frame + nunits < f_end ? fa + nunits * (int64_t)fbytes : nullptr;
+        if (pf && k == 0)
+            prefetch_ahead(fa, nfa, P, fbytes, pbytes, 0);
+        if (pf && k == 0)
+            prefetch_ahead(fa, nfa, P, fbytes, pbytes, kStreamBatch);
+        uint32_t acc[16];
+        int32_t s1[16], s2[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            acc[j] = 0u;
+            s1[j] = 0;
+            s2[j] = 0;
+        }
+        const uint4 none = make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
+        int32_t p = 0;
+        int held = 0;  // samples in each packed accumulator since the last flush
+        if (d > 0) {
+            // pass 0: lane 0's chunk starts d bytes before the frame
+            accum_chunk(rd && u < nch ? load_clipped(it, lp, fa, fa + fbytes) : none, lb, acc);
+            p = 1;
+            held = 1;
+        }
+        for (; p + kStreamBatch <= Pe; p += kStreamBatch) {
+            // whole chunks of the frame: no checks, kStreamBatch loads in flight
+            if (pf)
+                prefetch_ahead(fa, nfa, P, fbytes, pbytes, p + kStreamLead);
+            uint4 v[kStreamBatch];
+#pragma unroll
+            for (int r = 0; r < kStreamBatch; ++r) {
+                const uint8_t *q = lp + (p + r) * pbytes;
+                v[r] = (rd && SK_DBG_IN(it, q, 16)) ? ldg_stream16(q) : none;
+            }
+            if (held > 16 - kStreamBatch) {
+                flush16(acc, s1, s2);
+                held = 0;
+            }
+#pragma unroll
+            for (int r = 0; r < kStreamBatch; r += 2)
+                accum_chunk_pair(v[r], v[r + 1], lb, acc);
+            held += kStreamBatch;
+        }
+        for (; p + 2 <= Pe; p += 2) {
+            const uint8_t *q = lp + p * pbytes;
+            const uint4 a = (rd && SK_DBG_IN(it, q, 16)) ? ldg_stream16(q) : none;
+            const uint4 b = (rd && SK_DBG_IN(it, q + pbytes, 16)) ? ldg_stream16(q + pbytes) : none;
+            if (held > 14) {
+                flush16(acc, s1, s2);
+                held = 0;
+            }
+            accum_chunk_pair(a, b, lb, acc);
+            held += 2;
+        }
+        if (p < Pe) {
+            const uint8_t *q = lp + p * pbytes;
+            const uint4 a = (rd && SK_DBG_IN(it, q, 16)) ? ldg_stream16(q) : none;
+            if (held > 15) {
+                flush16(acc, s1, s2);
+                held = 0;
+            }
+            accum_chunk(a, lb, acc);
+            held += 1;
+            ++p;
+        }
+        for (; p < P; ++p) {
+            // the pass that ends past the frame (its chunks clipped to the frame)
+            const int32_t c = u + s * p;
+            const uint4 a = (rd && c < nch) ? load_clipped(it, lp + p * pbytes, fa, fa + fbytes)
+                                            : none;
+            if (held > 15) {
+                flush16(acc, s1, s2);
+                held = 0;
+            }
+            accum_chunk(a, lb, acc);
+            held += 1;
+        }
+        flush16(acc, s1, s2);
+        if (rd) {
+            // the lane's 16 slots as four rotated 16-byte pieces
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int w = 16 * u + 4 * ((q + (u >> 1)) & 3);
+                *reinterpret_cast<int4 *>(ps1 + w) =
+                    make_int4(s1[4 * q], s1[4 * q + 1], s1[4 * q + 2], s1[4 * q + 3]);
+                *reinterpret_cast<int4 *>(ps2 + w) =
+                    make_int4(s2[4 * q], s2[4 * q + 1], s2[4 * q + 2], s2[4 * q + 3]);
+            }
+        }
+        if (sh.W == 1)
+            __syncwarp();
+        else
+            named_sync(1 + unit, 32 * sh.W);
+        // inputs of the frame over the unit's threads: the R slots of each, its term
+        int64_t q = 0;
+        int32_t cnt = 0;
+        if (fvalid) {
+            int dn = d;
+            while (dn >= N)
+                dn -= N;
+            for (int i = u; i < N; i += tsz) {
+                int x = i + dn;
+                if (x >= N)
+                    x -= N;
+                int32_t a1 = 0;
+                uint32_t a2 = 0;
+                for (int r = 0; r < R; ++r, x += N) {
+                    const int w = slot_word(x);
+                    a1 += ps1[w];
+                    a2 += (uint32_t)ps2[w];
+                }
+                // exact S2 from the slots' S2 + 2^19 S1 (0 <= S2 < 2^32)
+                a2 -= (uint32_t)a1 << kPackShift;
+                float rr = 0.0f;
+                int64_t qi = 0;
+                const bool has = SK_EPILOGUE_ALU ? input_term_alu(a1, (int32_t)a2, M, rr, qi)
+                                                 : input_term(a1, (int32_t)a2, M, rr, qi);
+                if (has) {
+                    q += qi;
+                    cnt += 1;
+                }
+                const int64_t o = frame * N + i;
+                if (it.s1 && SK_DBG_OUT_IN(it, frame, i)) {
+                    it.s1[o] = a1;
+                    it.s2[o] = (int32_t)a2;
+                }
+                if (it.sk_in && SK_DBG_OUT_IN(it, frame, i)) {
+                    // single-receiver estimate and its flag at the one-input thresholds
+                    it.sk_in[o] = has ? __fmul_rn(rr, it.c_tab[1]) : __int_as_float(0x7FC00000);
+                    if (it.mask_in)
+                        it.mask_in[o] =
+                            has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+                }
+            }
+        }
+        if (sh.W == 1) {
+            // sum over the unit's s lanes: segmented shuffles, lane u = 0 ends with it
+            for (int o = 1; o < s; o <<= 1) {
+                const long long qo = __shfl_down_sync(0xFFFFFFFFu, (long long)q, o);
+                const int co = __shfl_down_sync(0xFFFFFFFFu, cnt, o);
+                if (u + o < s) {
+                    q += qo;
+                    cnt += co;
+                }
+            }
+            if (fvalid && u == 0)
+                write_frame(it, frame, q, cnt);
+            __syncwarp();  // the slots are free for the next frame
+        } else {
+            for (int o = 16; o > 0; o >>= 1) {
+                q += __shfl_xor_sync(0xFFFFFFFFu, (long long)q, o);
+                cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+            }
+            if (lane == 0) {
+                red_q[warp] = q;
+                red_c[warp] = cnt;
+            }
+            named_sync(1 + unit, 32 * sh.W);
+            if (fvalid && u == 0) {
+                int64_t tq = 0;
+                int32_t tc = 0;
+                for (int w = 0; w < sh.W; ++w) {
+                    tq += red_q[unit * sh.W + w];
+                    tc += red_c[unit * sh.W + w];
+                }
+                write_frame(it, frame, tq, tc);
+            }
+        }
+    }
+}
+
+}  // namespace sk

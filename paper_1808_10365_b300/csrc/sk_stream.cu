@@ -1,0 +1,176 @@
+// Stream path kernel (time-major frames of few inputs) and its launch.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "sk_common.h"
+#include "sk_path_stream.cuh"
+
+namespace sk {
+
+__global__ void __launch_bounds__(kStreamThreads, 1) sk_stream_kernel(Item it, StreamShape sh)
+{
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ long long red_q[kStreamWarps];
+    __shared__ int red_c[kStreamWarps];
+    const uint32_t lb = build_table(dyn_smem);
+    // the table sits on a 64 KiB boundary (lb holds it and the lane's offset);
+    // the partial sums follow it, inside the kStreamSmem bytes of the launch
+    const uint32_t part_sh = (lb & ~0xFFFFu) + (uint32_t)kLutBytes;
+    int32_t *part = reinterpret_cast<int32_t *>(
+        dyn_smem + (part_sh - (uint32_t)__cvta_generic_to_shared(dyn_smem)));
+    const int64_t F = it.n_frames;
+    const int64_t G = gridDim.x;
+    const int64_t fb = F * (int64_t)blockIdx.x / G;
+    const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
+    run_stream(it, sh, fb, fe, lb, part, red_q, red_c);
+}
+
+static int gcd_int(int a, int b)
+{
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Lanes per frame override (SK_STREAM_LANES, a multiple of N / gcd(N, 16) up to
+// 512), for launch-shape sweeps; 0 = the library's choice.
+static int forced_lanes()
+{
+    static const int v = [] {
+        const char *e = getenv("SK_STREAM_LANES");
+        return e ? atoi(e) : 0;
+    }();
+    return v;
+}
+
+// Warp instructions per frame of a launch shape, a model of the two parts of the
+// path: the chunk loop (one load, 16 PRMT, 16 LDS and 8 IADD3 a pass of a warp) and
+// the combine (the slots' stores, R loads and adds per input, about 30 for the
+// term, the sums; named barriers cost units of several warps about 40 a warp).
+static double stream_cost(int N, int M, const StreamShape &c)
+{
+    const double fb = (double)M * N;
+    const double P = std::ceil(fb / (16.0 * c.s));
+    const int R = 16 * c.s / N;
+    if (c.W == 1) {
+        const double rounds = std::ceil((double)N / c.s);
+        return (P * 41.0 + 8.0 + rounds * (4.0 * R + 30.0) + 20.0) / c.per_warp;
+    }
+    const double rounds = std::ceil((double)N / (32.0 * c.W));
+    return c.W * (P * 41.0 + 8.0 + rounds * (4.0 * R + 30.0) + 15.0 + 80.0);
+}
+
+bool stream_shape(int N, int M, StreamShape *out)
+{
+    if (N < 1 || M < 1)
+        return false;
+    const int g = N / gcd_int(N, 16);  // lanes whose 16-byte chunks span whole rows
+    if (g > 512)
+        return false;
+    StreamShape best;
+    memset(&best, 0, sizeof best);
+    double best_cost = 0.0;
+    bool have = false;
+    const int want = forced_lanes();
+    for (int s = g; s <= 512; s += g) {
+        if (s < 8)
+            continue;
+        StreamShape c;
+        c.s = s;
+        if (s <= 32) {
+            c.W = 1;
+            c.per_warp = 32 / s;
+            c.units = kStreamWarps * c.per_warp;
+        } else {
+            c.W = (s + 31) / 32;
+            c.per_warp = 0;
+            c.units = kStreamWarps / c.W;
+        }
+        if (c.units < 1)
+            continue;
+        if (want > 0) {
+            if (s == want) {
+                *out = c;
+                return true;
+            }
+            continue;
+        }
+        const double cost = stream_cost(N, M, c);
+        if (!have || cost < best_cost) {
+            best = c;
+            best_cost = cost;
+            have = true;
+        }
+    }
+    if (!have)
+        return false;
+    *out = best;
+    return true;
+}
+
+// Where a plan that asks for no path takes the stream path: time-major N < 256
+// (the warp-slice paths start at 256), measured against the path the shape had
+// before (B300, 3 GB launches):
+//   general path (N % 8 != 0 and M % 16 != 0, or N % 8 == 0 below 256 with
+//   M % 16 != 0): N = 100, M = 100: 0.25 -> 0.54-0.57 of measured copy
+//   bandwidth; N = 64, M = 100: 0.30 -> 0.65-0.71; N = 120, M = 100: 0.31 -> 0.62
+//   ragged N (N % 8 != 0, M % 16 == 0): N = 100, M = 256: 0.39 -> 0.66-0.68
+//   team path at N <= 48: N = 8: 0.28 -> 0.67-0.70, N = 16: 0.45 -> 0.70-0.77,
+//   N = 24: 0.49 -> 0.59-0.63 (M = 256); from N = 64 the team path keeps up
+//   (N = 64: 0.85 against 0.80-0.85; N = 128: 0.99 against 0.78-0.83)
+// except frames that are not a multiple of 16 bytes on units of several warps
+// (N = 99, M = 101: 0.19 against 0.23 on the general path).
+bool stream_auto(const Item &it)
+{
+    if (it.layout != 0 || it.N >= 256)
+        return false;
+    if (it.fast == 1 && it.N >= 64)
+        return false;
+    StreamShape sh;
+    if (!stream_shape(it.N, it.M, &sh))
+        return false;
+    const bool clean = ((int64_t)it.M * it.N) % 16 == 0;
+    return clean || sh.W == 1;
+}
+
+sk_status_t launch_stream(const Item &it, const StreamShape &sh, int device, cudaStream_t st,
+                          int grid_cap)
+{
+    if (it.n_frames == 0)
+        return SK_OK;
+    {
+        static std::mutex mu;
+        static std::vector<int> done;
+        std::lock_guard<std::mutex> g(mu);
+        bool have = false;
+        for (int d : done)
+            have = have || d == device;
+        if (!have) {
+            cudaError_t e = cudaFuncSetAttribute((const void *)sk_stream_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kStreamSmem);
+            if (e != cudaSuccess)
+                return cuda_error(e, "cudaFuncSetAttribute (stream path)");
+            done.push_back(device);
+        }
+    }
+    const int64_t gmax = grid_cap > 0 ? grid_cap : sm_count(device);
+    int64_t g = std::min<int64_t>(gmax, (it.n_frames + sh.units - 1) / sh.units);
+    if (g < 1)
+        g = 1;
+    Item run = it;
+    sk_stream_kernel<<<(unsigned)g, kStreamThreads, kStreamSmem, st>>>(run, sh);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_error(e, "sk stream kernel launch");
+    return SK_OK;
+}
+
+}  // namespace sk

@@ -74,8 +74,8 @@ def main():
             raise AssertionError("no bounds report")
         finally:
             sk.sk_plan_destroy(plan)
-    T, WS, RB, GEN, PI = (sk.SK_PATH_TEAM, sk.SK_PATH_WARP_SLICE, sk.SK_PATH_ROW_BALANCED,
-                          sk.SK_PATH_GENERAL, sk.SK_PATH_PER_INPUT)
+    T, WS, RB, GEN, PI, ST = (sk.SK_PATH_TEAM, sk.SK_PATH_WARP_SLICE, sk.SK_PATH_ROW_BALANCED,
+                              sk.SK_PATH_GENERAL, sk.SK_PATH_PER_INPUT, sk.SK_PATH_STREAM)
     cases = [  # (N, M, layout, F, config or None, path the launch must take)
         (2048, 256, 0, 40, None, RB),
         (2048, 256, 0, 9, dict(path=WS), WS),
@@ -91,7 +91,12 @@ def main():
         (2047, 256, 0, 5, None, RB),
         (2047, 256, 0, 5, dict(path=T), GEN),
         (333, 96, 0, 31, None, RB),
-        (100, 100, 0, 37, None, GEN),
+        (100, 100, 0, 37, None, ST),             # stream path: one unit a warp
+        (100, 100, 0, 37, dict(path=T), GEN),
+        (8, 256, 0, 300, None, ST),              # four units a warp
+        (250, 200, 0, 9, None, ST),              # units of four warps
+        (99, 101, 0, 23, None, GEN),
+        (99, 101, 0, 23, dict(path=ST), ST),     # frames at every 16-byte offset
         (2048, 256, 1, 40, None, RB),
         (2048, 256, 1, 9, dict(path=T), T),
         (256, 64, 1, 30, None, T),

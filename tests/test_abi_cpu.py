@@ -123,3 +123,7 @@ def test_autotune_cache_lines_merge(tmp_path):
     cands = autotune.candidates(2048, 256, 0, 0)
     assert cands[0]["path"] == 0 and len(cands) == 1 + 2 * (3 + 1)
     assert len(autotune.candidates(2048, 256, 1, 8)) == 1 + 3 * 2 * 2
+    # small frames also try the stream path (with and without the L2 prefetch)
+    small = autotune.candidates(100, 100, 0, 0)
+    assert [c["prefetch"] for c in small if c["path"] == sk.SK_PATH_STREAM] == [0, 1]
+    assert not [c for c in autotune.candidates(2047, 256, 0, 0) if c["path"] == sk.SK_PATH_STREAM]

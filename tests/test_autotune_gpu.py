@@ -50,7 +50,10 @@ def _exact(got, want):
     (2048, 48, 0, None, sk.SK_PATH_ROW_BALANCED),
     (2047, 256, 0, None, sk.SK_PATH_ROW_BALANCED),
     (2047, 256, 0, "16 0 1 0 0 0", sk.SK_PATH_GENERAL),
-    (100, 100, 0, None, sk.SK_PATH_GENERAL),
+    (100, 100, 0, None, sk.SK_PATH_STREAM),
+    (100, 100, 0, "8 0 1 0 0 0", sk.SK_PATH_GENERAL),
+    (128, 256, 0, "16 0 6 0 0 0", sk.SK_PATH_STREAM),
+    (128, 256, 0, None, sk.SK_PATH_TEAM),
 ])
 def test_cache_entry_sets_the_path_and_results_stay_exact(tmp_path, monkeypatch, N, M, layout,
                                                           entry, taken):

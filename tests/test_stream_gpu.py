@@ -1,0 +1,157 @@
+"""Parity of the stream path (time-major frames of few inputs, SK_PATH_STREAM) with
+the oracle, through the C ABI.
+
+The stream path reads each frame as one run of 16-byte chunks.  Frames whose size
+M N is not a multiple of 16 start at every offset from a 16-byte boundary, so their
+first and last chunks hold bytes of the neighbouring frames (or lie partly outside
+the input at its two ends); units of s lanes with 16 s a multiple of N keep each
+chunk byte on one input.  Bar: S1, S2, Q, N_eff, masks and the fp32 SK bit-exact
+(Eq. 1, Eq. singlesums, Eq. final, Sec. 3.2 test), per-input SK^_i too.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1808_10365_b300 as sk  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch.device("cuda:0")
+
+
+def run_stream(x, M, N, n_sigma=2.5, delta=-0.01, grid=0, path=sk.SK_PATH_STREAM):
+    dev = _dev()
+    x = np.ascontiguousarray(x, dtype=np.uint8).reshape(-1, M * N)
+    F = x.shape[0]
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    s1 = torch.full((F, N), -1, dtype=torch.int32, device=dev)
+    s2 = torch.full_like(s1, -1)
+    q = torch.full((F,), -1, dtype=torch.int64, device=dev)
+    skv = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+    ne = torch.full((F,), -1, dtype=torch.int32, device=dev)
+    sk2 = torch.full_like(skv, -1.0)
+    mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, n_sigma, delta)
+    try:
+        sk.sk_plan_set_config(plan, rows=16 if M % 32 == 0 else 8, grid_ctas=grid, path=path)
+        sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
+        sk.sk_flag(plan, d_in, F, sk2, mask)
+        torch.cuda.synchronize()
+        taken = sk.sk_plan_get_config(plan)["last_path"]
+    finally:
+        sk.sk_plan_destroy(plan)
+    return taken, dict(S1=s1.cpu().numpy(), S2=s2.cpu().numpy(), Q=q.cpu().numpy(),
+                       neff=ne.cpu().numpy(), sk=skv.cpu().numpy(), sk_flag=sk2.cpu().numpy(),
+                       mask=mask.cpu().numpy())
+
+
+def check(got, want, label):
+    for k in ("S1", "S2", "Q", "neff", "mask"):
+        assert np.array_equal(got[k], want[k]), f"{label}: {k}"
+    assert np.array_equal(got["sk"].view(np.uint32), want["sk"].view(np.uint32)), label
+    assert np.array_equal(got["sk_flag"].view(np.uint32), want["sk"].view(np.uint32)), label
+
+
+# (N, M, F, grid): units inside one warp (N / gcd(N, 16) <= 32) and teams of several
+# warps; frames of a multiple of 16 bytes and frames at every offset from a 16-byte
+# boundary (M N odd); one round per CTA and many (small grids); frames smaller than
+# one pass of a unit.
+SHAPES = [
+    (100, 100, 37, 0), (100, 100, 200, 3), (99, 101, 23, 0), (99, 101, 90, 2),
+    (8, 256, 300, 0), (8, 256, 700, 5), (16, 64, 129, 0), (24, 256, 61, 0), (48, 256, 40, 4),
+    (64, 100, 50, 0), (96, 256, 19, 0), (120, 100, 33, 0), (127, 3, 401, 0), (200, 100, 25, 2),
+    (250, 200, 9, 0), (255, 17, 77, 1), (1, 2, 1000, 0), (1, 4096, 7, 0), (3, 17, 333, 0),
+    (5, 1000, 12, 0), (7, 3, 999, 0), (12, 33, 257, 2), (33, 64, 64, 0), (300, 64, 20, 0),
+    (500, 48, 11, 0), (512, 7, 31, 0), (1000, 16, 6, 0), (2, 2, 4097, 1),
+]
+
+
+@pytest.mark.parametrize("N,M,F,grid", SHAPES)
+def test_stream_path_bit_exact(N, M, F, grid):
+    """Random bytes (nibble 0 included) on the stream path against the oracle."""
+    rng = np.random.default_rng(N * 7919 + M * 31 + F)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    if F > 3:
+        x[1] = 0x88             # a frame without power: N_eff = 0, SK NaN, mask 1
+        x[2, ::N] = 0x88        # input 0 without power in one frame
+    want = oracle.flag(x, M, N, 2.5, -0.01)
+    taken, got = run_stream(x, M, N, grid=grid)
+    assert taken == sk.SK_PATH_STREAM
+    check(got, want, f"N={N} M={M} F={F} grid={grid}")
+
+
+def test_stream_path_synthetic_rfi():
+    """The synthetic noise and RFI model at a small array (N = 100, M = 100): masks and
+    SK bit-exact, and the injected tones flagged."""
+    import synth
+
+    ds = synth.Dataset(n_frames=256, M=100, N=100, seed=31,
+                       rfi=synth.rfi_plan(31, 256, cw_frac=0.05, pulse_frac=0.05))
+    x = ds.generate_cpu()
+    want = oracle.flag(x, 100, 100, 3.0, 0.0)
+    taken, got = run_stream(x, 100, 100, n_sigma=3.0, delta=0.0)
+    assert taken == sk.SK_PATH_STREAM
+    check(got, want, "synthetic N=100 M=100")
+    assert want["mask"].sum() > 0
+
+
+@pytest.mark.parametrize("N,M,F", [(100, 100, 21), (7, 33, 50), (64, 256, 12)])
+def test_stream_path_independent_estimates(N, M, F):
+    """sk_compute_inputs on the stream path: per-input SK^_i and flags bit-exact."""
+    dev = _dev()
+    rng = np.random.default_rng(N + 3 * M + F)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    x[1, ::N] = 0x88
+    want = oracle.flag_inputs(x, M, N, 3.0, 0.05)
+    whole = oracle.flag(x, M, N, 3.0, 0.05)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    sk_in = torch.empty((F, N), dtype=torch.float32, device=dev)
+    m_in = torch.empty((F, N), dtype=torch.uint8, device=dev)
+    skv = torch.empty(F, dtype=torch.float32, device=dev)
+    mask = torch.empty(F, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.05)
+    try:
+        sk.sk_plan_set_config(plan, rows=16 if M % 32 == 0 else 8, path=sk.SK_PATH_STREAM)
+        sk.sk_compute_inputs(plan, d_in, F, sk_in, m_in, skv, mask)
+        torch.cuda.synchronize()
+        assert sk.sk_plan_get_config(plan)["last_path"] == sk.SK_PATH_STREAM
+    finally:
+        sk.sk_plan_destroy(plan)
+    assert np.array_equal(sk_in.cpu().numpy().view(np.uint32), want["sk_in"].view(np.uint32))
+    assert np.array_equal(m_in.cpu().numpy(), want["mask_in"])
+    assert np.array_equal(mask.cpu().numpy(), whole["mask"])
+    assert np.array_equal(skv.cpu().numpy().view(np.uint32), whole["sk"].view(np.uint32))
+
+
+def test_stream_path_not_taken_where_it_cannot():
+    """N / gcd(N, 16) above 512 (N = 2047) has no stream shape: a request for it falls
+    back to the shape's own path, with the same results."""
+    rng = np.random.default_rng(5)
+    N, M, F = 2047, 32, 5
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    taken, got = run_stream(x, M, N)
+    assert taken != sk.SK_PATH_STREAM
+    check(got, oracle.flag(x, M, N, 2.5, -0.01), "N=2047 fallback")
+
+
+@pytest.mark.parametrize("N,M,F,path", [
+    (100, 100, 40, sk.SK_PATH_STREAM), (8, 256, 130, sk.SK_PATH_STREAM),
+    (100, 256, 20, sk.SK_PATH_STREAM), (64, 100, 30, sk.SK_PATH_STREAM),
+    (128, 256, 20, sk.SK_PATH_TEAM), (99, 101, 12, sk.SK_PATH_GENERAL),
+])
+def test_auto_path_choice(N, M, F, path):
+    """A plan that asks for no path takes the stream path for time-major frames of few
+    inputs where it measured faster (N < 256: the general and ragged shapes, the team
+    shapes below N = 64) and keeps the others; results bit-exact either way."""
+    rng = np.random.default_rng(N + M)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    taken, got = run_stream(x, M, N, path=sk.SK_PATH_AUTO)
+    assert taken == path
+    check(got, oracle.flag(x, M, N, 2.5, -0.01), f"auto N={N} M={M}")
