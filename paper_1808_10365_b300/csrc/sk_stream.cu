@@ -165,7 +165,12 @@ sk_status_t launch_stream(const Item &it, const StreamShape &sh, int device, cud
     int64_t g = std::min<int64_t>(gmax, (it.n_frames + sh.units - 1) / sh.units);
     if (g < 1)
         g = 1;
+    // the look-ahead L2 prefetch pays on units of several warps (N = 250, M = 200:
+    // 0.639 against 0.597 of measured copy bandwidth) and costs on one-warp units
+    // (N = 100, M = 100: 0.536 against 0.548; N = 8, 16, 120: 2-3 %)
     Item run = it;
+    if (sh.W == 1)
+        run.prefetch = 0;
     sk_stream_kernel<<<(unsigned)g, kStreamThreads, kStreamSmem, st>>>(run, sh);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
