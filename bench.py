@@ -822,6 +822,50 @@ def run_gpu(args):
     return 0
 
 
+def run_shape(args):
+    """--shape N,M[,layout]: sk_flag alone on about --shape-gb GB of random bytes of that
+    shape (a case of the off-benchmark table, or any other), `warmup` launches, then
+    `steps` launches each between its own CUDA events; one JSON line with the path the
+    plan took and the fraction of the measured copy bandwidth."""
+    import torch
+
+    import paper_1808_10365_b300 as sk
+
+    parts = [int(v) for v in args.shape.split(",")]
+    N, M = parts[0], parts[1]
+    layout = parts[2] if len(parts) > 2 else 0
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(dev)
+    peak, kind = peaks()
+    F = max(1, int(args.shape_gb * (1 << 30)) // (M * N))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1808)
+    d_in = torch.randint(0, 256, (F * M * N,), dtype=torch.uint8, device=dev, generator=gen)
+    d_sk = torch.empty(F, dtype=torch.float32, device=dev)
+    d_mask = torch.empty(F, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.0, layout=layout)
+    try:
+        for _ in range(args.warmup):
+            sk.sk_flag(plan, d_in, F, d_sk, d_mask, st)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for a, b in ev:
+            a.record(st)
+            sk.sk_flag(plan, d_in, F, d_sk, d_mask, st)
+            b.record(st)
+        st.synchronize()
+        taken = PATH_NAMES.get(sk.sk_plan_get_config(plan)["last_path"], "?")
+    finally:
+        sk.sk_plan_destroy(plan)
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev) if ev else float("nan")
+    print(json.dumps({"shape": {"N": N, "M": M, "layout": layout, "frames": F},
+                      "path": taken, "steps": args.steps, "warmup": args.warmup,
+                      "median_launch_ms": ms, "tb_s": F * M * N / (ms * 1e-3) / 1e12,
+                      "roofline_frac": (F * M * N + 5 * F) / (ms * 1e-3) / 1e9 / peak,
+                      "peak_kind": f"{kind} copy bandwidth"}))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -843,7 +887,14 @@ def main(argv=None):
                          "at most 2 s")
     ap.add_argument("--sustained-seconds", type=float, default=3.0,
                     help="seconds of back-to-back launches of the sustained leg (0: skip)")
+    ap.add_argument("--shape", default=None,
+                    help="N,M[,layout]: time sk_flag alone on that shape and print its line "
+                         "(not the benchmark workload)")
+    ap.add_argument("--shape-gb", type=float, default=3.0,
+                    help="input size of --shape, in GB (random bytes)")
     args = ap.parse_args(argv)
+    if args.shape:
+        return run_shape(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
