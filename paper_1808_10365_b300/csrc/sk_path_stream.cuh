@@ -194,6 +194,10 @@ __device__ __forceinline__ void run_stream(const Item &it, const StreamShape &sh
     const int32_t pbytes = 16 * s;
     const int32_t pe0 = fbytes / pbytes;             // Pe at d = 0
     const int32_t rem0 = fbytes - pe0 * pbytes;
+    // The next frame's first batch of chunks, loaded before this frame's combine so
+    // that its loads are in flight while the combine runs (pre: v holds it).
+    uint4 v[kStreamBatch];
+    bool pre = false;
     for (int64_t k = 0; k < rounds; ++k) {
         const int64_t frame = f_begin + k * nunits + unit;
         const bool fvalid = in_unit && frame < f_end;
@@ -234,12 +238,14 @@ __device__ __forceinline__ void run_stream(const Item &it, const StreamShape &sh
             // whole chunks of the frame: no checks, kStreamBatch loads in flight
             if (pf)
                 prefetch_ahead(fa, nfa, P, fbytes, pbytes, p + kStreamLead);
-            uint4 v[kStreamBatch];
+            if (!pre) {
 #pragma unroll
-            for (int r = 0; r < kStreamBatch; ++r) {
-                const uint8_t *q = lp + (p + r) * pbytes;
-                v[r] = (rd && SK_DBG_IN(it, q, 16)) ? ldg_stream16(q) : none;
+                for (int r = 0; r < kStreamBatch; ++r) {
+                    const uint8_t *q = lp + (p + r) * pbytes;
+                    v[r] = (rd && SK_DBG_IN(it, q, 16)) ? ldg_stream16(q) : none;
+                }
             }
+            pre = false;
             if (held > 16 - kStreamBatch) {
                 flush16(acc, s1, s2);
                 held = 0;
@@ -293,6 +299,26 @@ __device__ __forceinline__ void run_stream(const Item &it, const StreamShape &sh
                     make_int4(s1[4 * q], s1[4 * q + 1], s1[4 * q + 2], s1[4 * q + 3]);
                 *reinterpret_cast<int4 *>(ps2 + w) =
                     make_int4(s2[4 * q], s2[4 * q + 1], s2[4 * q + 2], s2[4 * q + 3]);
+            }
+        }
+        {
+            // the next round's frame: when it starts on a 16-byte boundary with a whole
+            // first batch, its first kStreamBatch passes are loaded now (the same loads
+            // its batch loop would issue: same lane, addresses and predicate)
+            const int64_t nf = frame + nunits;
+            const bool nvalid = in_unit && nf < f_end;
+            const uint8_t *na = it.in + (nvalid ? nf : f_begin) * (int64_t)fbytes;
+            const int nd = (int)((uintptr_t)na & 15u);
+            const int32_t npe = pe0 + (rem0 + nd >= pbytes ? 1 : 0);
+            if (k + 1 < rounds && nd == 0 && npe >= kStreamBatch) {
+                const bool nrd = active && nvalid;
+                const uint8_t *nlp = na + 16 * u;
+#pragma unroll
+                for (int r = 0; r < kStreamBatch; ++r) {
+                    const uint8_t *q = nlp + r * pbytes;
+                    v[r] = (nrd && SK_DBG_IN(it, q, 16)) ? ldg_stream16(q) : none;
+                }
+                pre = true;
             }
         }
         if (sh.W == 1)
