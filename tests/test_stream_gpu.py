@@ -155,3 +155,40 @@ def test_auto_path_choice(N, M, F, path):
     taken, got = run_stream(x, M, N, path=sk.SK_PATH_AUTO)
     assert taken == path
     check(got, oracle.flag(x, M, N, 2.5, -0.01), f"auto N={N} M={M}")
+
+
+def test_stream_path_graph_capture_and_host_calls():
+    """The stream path inside a captured CUDA graph (replayed twice), through the
+    host-buffer call (frames staged in chunks) and through the allocation-free host
+    call: the oracle's masks and SK every time."""
+    dev = _dev()
+    N, M, F = 100, 100, 1500
+    rng = np.random.default_rng(77)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    want = oracle.flag(x, M, N, 3.0, 0.0)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.0)
+    try:
+        m1 = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+        sk1 = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+        sk.sk_flag(plan, d_in, F, sk1, m1)  # first launch outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            sk.sk_flag(plan, d_in, F, sk1, m1, torch.cuda.current_stream())
+        for _ in range(2):
+            m1.fill_(7)
+            sk1.fill_(-1.0)
+            g.replay()
+        torch.cuda.synchronize()
+        assert sk.sk_plan_get_config(plan)["last_path"] == sk.SK_PATH_STREAM
+        assert np.array_equal(m1.cpu().numpy(), want["mask"])
+        assert np.array_equal(sk1.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32))
+        for call in (sk.sk_flag_host, sk.sk_flag_host_noalloc):
+            h_sk = np.full(F, -1.0, dtype=np.float32)
+            h_mask = np.full(F, 7, dtype=np.uint8)
+            call(plan, x, F, h_sk, h_mask)
+            assert np.array_equal(h_mask, want["mask"]), call.__name__
+            assert np.array_equal(h_sk.view(np.uint32), want["sk"].view(np.uint32)), call.__name__
+    finally:
+        sk.sk_plan_destroy(plan)
