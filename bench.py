@@ -536,6 +536,7 @@ OFF_SHAPES = [
     ("time-major N=2047 M=256 (ragged N)", 2047, 256, 0),
     ("time-major N=100 M=100 (stream path)", 100, 100, 0),
     ("time-major N=16 M=256 (stream path)", 16, 256, 0),
+    ("time-major N=500 M=100 (stream path)", 500, 100, 0),
     ("time-major N=99 M=101 (general path)", 99, 101, 0),
     ("time-major N=2056 M=256 (N = 8 mod 16)", 2056, 256, 0),
     ("time-major N=520 M=256 (N = 8 mod 16)", 520, 256, 0),

@@ -115,29 +115,34 @@ bool stream_shape(int N, int M, StreamShape *out)
     return true;
 }
 
-// Where a plan that asks for no path takes the stream path: time-major N < 256
-// (the warp-slice paths start at 256), measured against the path the shape had
-// before (B300, 3 GB launches):
-//   general path (N % 8 != 0 and M % 16 != 0, or N % 8 == 0 below 256 with
-//   M % 16 != 0): N = 100, M = 100: 0.25 -> 0.54-0.57 of measured copy
-//   bandwidth; N = 64, M = 100: 0.30 -> 0.65-0.71; N = 120, M = 100: 0.31 -> 0.62
-//   ragged N (N % 8 != 0, M % 16 == 0): N = 100, M = 256: 0.39 -> 0.66-0.68
-//   team path at N <= 48: N = 8: 0.28 -> 0.67-0.70, N = 16: 0.45 -> 0.70-0.77,
-//   N = 24: 0.49 -> 0.59-0.63 (M = 256); from N = 64 the team path keeps up
-//   (N = 64: 0.85 against 0.80-0.85; N = 128: 0.99 against 0.78-0.83)
+// Where a plan that asks for no path takes the stream path, measured against the
+// path the shape had before (B300, 3 GB launches, fraction of measured copy bandwidth):
+//   general-path shapes (time-major N % 8 != 0 and M % 16 != 0), any N: N = 100,
+//   M = 100: 0.25 -> 0.56; N = 120: 0.31 -> 0.69; N = 260: 0.17 -> 0.46; N = 300:
+//   0.19 -> 0.43; N = 500: 0.31 -> 0.61; N = 1500: 0.23 -> 0.53; N = 2044: 0.30 ->
+//   0.58 (M = 100)
+//   below N = 256 also N % 8 == 0 with M % 16 != 0 (N = 64, M = 100: 0.30 -> 0.74),
+//   ragged N (N = 100, M = 256: 0.39 -> 0.69) and the team path below N = 64 (N = 8:
+//   0.28 -> 0.69, N = 16: 0.45 -> 0.81, N = 24: 0.49 -> 0.59-0.63, M = 256); from
+//   N = 64 the team path keeps up (N = 64: 0.85, N = 128: 0.99), and from N = 256 the
+//   warp-slice paths (N = 300, M = 48 on the ragged path: 0.47 against 0.37)
 // except frames that are not a multiple of 16 bytes on units of several warps
 // (N = 99, M = 101: 0.19 against 0.23 on the general path).
 bool stream_auto(const Item &it)
 {
-    if (it.layout != 0 || it.N >= 256)
-        return false;
-    if (it.fast == 1 && it.N >= 64)
+    if (it.layout != 0)
         return false;
     StreamShape sh;
     if (!stream_shape(it.N, it.M, &sh))
         return false;
     const bool clean = ((int64_t)it.M * it.N) % 16 == 0;
-    return clean || sh.W == 1;
+    if (!clean && sh.W != 1)
+        return false;
+    if (it.fast == 0)
+        return true;
+    if (it.N >= 256)
+        return false;
+    return !(it.fast == 1 && it.N >= 64);
 }
 
 sk_status_t launch_stream(const Item &it, const StreamShape &sh, int device, cudaStream_t st,

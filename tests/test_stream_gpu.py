@@ -145,10 +145,12 @@ def test_stream_path_not_taken_where_it_cannot():
     (100, 100, 40, sk.SK_PATH_STREAM), (8, 256, 130, sk.SK_PATH_STREAM),
     (100, 256, 20, sk.SK_PATH_STREAM), (64, 100, 30, sk.SK_PATH_STREAM),
     (128, 256, 20, sk.SK_PATH_TEAM), (99, 101, 12, sk.SK_PATH_GENERAL),
+    (500, 100, 20, sk.SK_PATH_STREAM), (2044, 100, 4, sk.SK_PATH_STREAM),
+    (300, 48, 30, sk.SK_PATH_ROW_BALANCED),
 ])
 def test_auto_path_choice(N, M, F, path):
-    """A plan that asks for no path takes the stream path for time-major frames of few
-    inputs where it measured faster (N < 256: the general and ragged shapes, the team
+    """A plan that asks for no path takes the stream path where it measured faster (the
+    general path's shapes of any N; below N = 256 also the ragged shapes and the team
     shapes below N = 64) and keeps the others; results bit-exact either way."""
     rng = np.random.default_rng(N + M)
     x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
