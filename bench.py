@@ -543,6 +543,7 @@ OFF_SHAPES = [
     ("time-major N=2048 M=48 (M = 16 mod 32)", 2048, 48, 0),
     ("time-major N=2048 M=100 (M not a multiple of 16)", 2048, 100, 0),
     ("input-major N=2048 M=64", 2048, 64, 1),
+    ("input-major N=2048 M=100 (chunk path)", 2048, 100, 1),
     ("input-major N=2048 M=4096", 2048, 4096, 1),
 ]
 

@@ -582,6 +582,13 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
             plan->last_path.store(SK_PATH_STREAM, std::memory_order_relaxed);
         return launch_stream(run, ssh, device, st, grid_cap);
     }
+    // input-major frames without a fast path (M % 32 != 0 outside the grouped lengths):
+    // the chunk path, requested or by shape
+    if (it.layout == 1 && (req == SK_PATH_STREAM || (req == SK_PATH_AUTO && it.fast != 2))) {
+        if (plan)
+            plan->last_path.store(SK_PATH_STREAM, std::memory_order_relaxed);
+        return launch_imajor_chunks(it, device, st, grid_cap);
+    }
     KernelFn fn = kSingle[tile][nci];
     if (it.fast == 2)
         fn = imajor_kernel(it.M, !pf_off);

@@ -57,6 +57,10 @@ bool stream_shape(int N, int M, StreamShape *out);
 bool stream_auto(const Item &it);
 sk_status_t launch_stream(const Item &it, const StreamShape &sh, int device, cudaStream_t st,
                           int grid_cap);
+// Input-major frames of any M (run_imajor_chunks in sk_path_stream.cuh): the launch,
+// and its warps per frame for N inputs.
+sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, int grid_cap);
+int imajor_chunk_team(int N);
 // SK_ERR_TIMEOUT once if a bounded wait in an earlier launch of the plan gave up.
 sk_status_t pending_fault(sk_plan_t plan, const char *who);
 // Set-up of sk_flag_host_noalloc on `device` (current): looks up the device

@@ -403,4 +403,226 @@ __device__ __forceinline__ void run_stream(const Item &it, const StreamShape &sh
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Input-major frames of any M ([frame][input][t]: input i's M samples are the
+// bytes [i M, i M + M) of its frame).  Two lanes per input read the aligned
+// 16-byte chunks that cover the input (lane g: chunks g, g + 2, ...), with the
+// bytes of the neighbouring inputs in its first and last chunk replaced by 0x88
+// (no power).  A lane holds two inputs (i0 + j and i0 + 16 + j, j = lane / 2), so
+// that after the chunks one exchange between the two lanes of a pair leaves each
+// lane with the totals of one input: all 32 lanes then form an input term.  A
+// team of W warps takes a frame (warp w: input blocks of 32 at w, w + W, ...)
+// and combines Q and N_eff through shared memory and one named barrier when
+// W > 1.
+// ---------------------------------------------------------------------------
+
+constexpr int kImcBatch = 4;  // chunk iterations per input per register batch (8 loads)
+
+// Byte mask of the bytes [kl, kh) of word w of a 16-byte chunk (0 <= kl <= kh <= 16).
+__device__ __forceinline__ uint32_t chunk_word_mask(int kl, int kh, int w)
+{
+    const int a = max(kl - 4 * w, 0);
+    const int b = min(kh - 4 * w, 4);
+    if (b <= a)
+        return 0u;
+    const uint32_t hi = b >= 4 ? 0xFFFFFFFFu : ((1u << (8 * b)) - 1u);
+    return hi & ~((1u << (8 * a)) - 1u);
+}
+
+// The aligned chunk at p of an input whose bytes are [lo, hi): interior chunks are
+// one load; a chunk that reaches past the input (edge) keeps only the input's
+// bytes, and one that would reach past the end of the item's bytes (end) is read
+// byte by byte inside the input.
+__device__ __forceinline__ uint4 imc_load(const Item &it, const uint8_t *p, const uint8_t *lo,
+                                          const uint8_t *hi, const uint8_t *end, bool edge)
+{
+    if (!edge)
+        return SK_DBG_IN(it, p, 16) ? ldg_stream16(p)
+                                    : make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
+    if (p >= lo && p + 16 <= hi)
+        return SK_DBG_IN(it, p, 16) ? ldg_stream16(p)
+                                    : make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
+    if (p + 16 > end)
+        return load_clipped(it, p, lo, hi);
+    uint4 v = SK_DBG_IN(it, p, 16) ? ldg_stream16(p)
+                                   : make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
+    const int kl = lo > p ? (int)(lo - p) : 0;
+    const int kh = hi < p + 16 ? (int)(hi - p) : 16;
+    uint32_t m;
+    m = chunk_word_mask(kl, kh, 0);
+    v.x = (v.x & m) | (kNoPower & ~m);
+    m = chunk_word_mask(kl, kh, 1);
+    v.y = (v.y & m) | (kNoPower & ~m);
+    m = chunk_word_mask(kl, kh, 2);
+    v.z = (v.z & m) | (kNoPower & ~m);
+    m = chunk_word_mask(kl, kh, 3);
+    v.w = (v.w & m) | (kNoPower & ~m);
+    return v;
+}
+
+// One chunk of one input into its exact sums: the 16 samples through the table into
+// a packed accumulator, then split (S1 the high field, s2 the packed word: S2 +
+// 2^19 S1 modulo 2^32 until finished).
+__device__ __forceinline__ void imc_add(uint4 a, uint32_t lb, int32_t &s1, int32_t &s2)
+{
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+    uint32_t acc = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        acc += lds_u32(prmt(w[k], lb, 0x7604u)) + lds_u32(prmt(w[k], lb, 0x7614u)) +
+               lds_u32(prmt(w[k], lb, 0x7624u)) + lds_u32(prmt(w[k], lb, 0x7634u));
+    s1 += (int32_t)(acc >> kPackShift);
+    s2 = (int32_t)((uint32_t)s2 + acc);
+}
+
+// The lane's two inputs of the round at i0: bytes [lo_r, lo_r + M), chunks from base_r.
+__device__ __forceinline__ void imc_round(const uint8_t *fa, int i0, int j, int N, int M,
+                                          const uint8_t *(&lo)[2], const uint8_t *(&base)[2],
+                                          int (&nci)[2], bool (&valid)[2])
+{
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = i0 + 16 * r + j;
+        valid[r] = i < N;
+        lo[r] = fa + (int64_t)(valid[r] ? i : 0) * M;
+        base[r] = (const uint8_t *)((uintptr_t)lo[r] & ~(uintptr_t)15u);
+        nci[r] = (int)(((uintptr_t)lo[r] & 15u) + M + 15) >> 4;
+    }
+}
+
+// Chunk iterations kb .. kb + kImcBatch - 1 of the lane's two inputs into v.
+__device__ __forceinline__ void imc_batch(const Item &it, uint4 (&v)[2][kImcBatch], int kb,
+                                          int kmax, int g, bool whole,
+                                          const uint8_t *const (&lo)[2],
+                                          const uint8_t *const (&base)[2], const int (&nci)[2],
+                                          const bool (&valid)[2], int M, const uint8_t *end)
+{
+    const uint4 none = make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
+#pragma unroll
+    for (int t = 0; t < kImcBatch; ++t) {
+        // a chunk that may reach past its input: the first and the last two iterations
+        // (nci differs by one between inputs), unless inputs are whole chunks
+        const bool edge = !whole && (kb + t == 0 || kb + t >= kmax - 2);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int c = g + 2 * (kb + t);
+            v[r][t] = (valid[r] && kb + t < kmax && c < nci[r])
+                          ? imc_load(it, base[r] + 16 * c, lo[r], lo[r] + M, end, edge)
+                          : none;
+        }
+    }
+}
+
+// Frames [f_begin, f_end) of an input-major item, teams of W warps per frame.
+// red_q, red_c: one entry per warp.
+__device__ __forceinline__ void run_imajor_chunks(const Item &it, int W, int64_t f_begin,
+                                                  int64_t f_end, uint32_t lb, long long *red_q,
+                                                  int *red_c)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int team = warp / W, wt = warp - team * W;
+    const int teams = (int)(blockDim.x >> 5) / W;
+    if (team >= teams)
+        return;  // whole warps past the last team
+    const int g = lane & 1, j = lane >> 1;
+    const int N = it.N, M = it.M;
+    const int64_t fbytes = (int64_t)M * N;
+    const uint8_t *end = it.in + it.n_frames * fbytes;
+    const int kmax = (((M + 30) >> 4) + 1) >> 1;  // chunk iterations per input and lane
+    // M % 16 == 0: every input starts on a 16-byte boundary (the item's bytes do) and
+    // ends on one, so no chunk reaches past its input
+    const bool whole = (M & 15) == 0;
+    const int64_t rounds = (f_end - f_begin + teams - 1) / teams;
+    for (int64_t k = 0; k < rounds; ++k) {
+        const int64_t frame = f_begin + k * teams + team;
+        const bool fvalid = frame < f_end;
+        const uint8_t *fa = it.in + (fvalid ? frame : f_begin) * fbytes;
+        int64_t q = 0;
+        int32_t cnt = 0;
+        // a round is 32 inputs (two a lane); its first batch of chunks is loaded before
+        // the previous round's exchange and terms (pre: v holds it)
+        uint4 v[2][kImcBatch];
+        bool pre = false;
+        for (int i0 = 32 * wt; fvalid && i0 < N; i0 += 32 * W) {
+            const uint8_t *lo[2], *base[2];
+            int nci[2];
+            bool valid[2];
+            imc_round(fa, i0, j, N, M, lo, base, nci, valid);
+            int32_t s1[2] = {0, 0}, s2[2] = {0, 0};
+            for (int kb = 0; kb < kmax; kb += kImcBatch) {
+                if (!(pre && kb == 0))
+                    imc_batch(it, v, kb, kmax, g, whole, lo, base, nci, valid, M, end);
+                pre = false;
+#pragma unroll
+                for (int t = 0; t < kImcBatch; ++t)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+                        imc_add(v[r][t], lb, s1[r], s2[r]);
+            }
+            if (i0 + 32 * W < N) {
+                // the next round's first batch, in flight during this round's terms
+                const uint8_t *nlo[2], *nbase[2];
+                int nnci[2];
+                bool nvalid[2];
+                imc_round(fa, i0 + 32 * W, j, N, M, nlo, nbase, nnci, nvalid);
+                imc_batch(it, v, 0, kmax, g, whole, nlo, nbase, nnci, nvalid, M, end);
+                pre = true;
+            }
+            // the pair's sums: lane g keeps input i0 + 16 g + j
+            const int32_t k1 = g ? s1[1] : s1[0], o1 = g ? s1[0] : s1[1];
+            const int32_t k2 = g ? s2[1] : s2[0], o2 = g ? s2[0] : s2[1];
+            const int32_t a1 = k1 + __shfl_xor_sync(0xFFFFFFFFu, o1, 1);
+            const uint32_t a2 = (uint32_t)k2 + (uint32_t)__shfl_xor_sync(0xFFFFFFFFu, o2, 1) -
+                                ((uint32_t)a1 << kPackShift);  // exact S2
+            const int i = i0 + 16 * g + j;
+            if (i < N) {
+                float rr = 0.0f;
+                int64_t qi = 0;
+                const bool has = SK_EPILOGUE_ALU ? input_term_alu(a1, (int32_t)a2, M, rr, qi)
+                                                 : input_term(a1, (int32_t)a2, M, rr, qi);
+                if (has) {
+                    q += qi;
+                    cnt += 1;
+                }
+                const int64_t o = frame * N + i;
+                if (it.s1 && SK_DBG_OUT_IN(it, frame, i)) {
+                    it.s1[o] = a1;
+                    it.s2[o] = (int32_t)a2;
+                }
+                if (it.sk_in && SK_DBG_OUT_IN(it, frame, i)) {
+                    it.sk_in[o] = has ? __fmul_rn(rr, it.c_tab[1]) : __int_as_float(0x7FC00000);
+                    if (it.mask_in)
+                        it.mask_in[o] =
+                            has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            q += __shfl_xor_sync(0xFFFFFFFFu, (long long)q, o);
+            cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+        }
+        if (W == 1) {
+            if (fvalid && lane == 0)
+                write_frame(it, frame, q, cnt);
+        } else {
+            if (lane == 0) {
+                red_q[warp] = q;
+                red_c[warp] = cnt;
+            }
+            named_sync(1 + team, 32 * W);
+            if (fvalid && wt == 0 && lane == 0) {
+                int64_t tq = 0;
+                int32_t tc = 0;
+                for (int w = 0; w < W; ++w) {
+                    tq += red_q[team * W + w];
+                    tc += red_c[team * W + w];
+                }
+                write_frame(it, frame, tq, tc);
+            }
+            named_sync(1 + team, 32 * W);  // red_* free for the next frame
+        }
+    }
+}
+
 }  // namespace sk

@@ -29,6 +29,66 @@ __global__ void __launch_bounds__(kStreamThreads, 1) sk_stream_kernel(Item it, S
     run_stream(it, sh, fb, fe, lb, part, red_q, red_c);
 }
 
+// Input-major frames of any M (run_imajor_chunks): a contiguous frame range per CTA,
+// teams of W warps per frame.
+__global__ void __launch_bounds__(kThreads, 1) sk_imajor_chunk_kernel(Item it, int W)
+{
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ long long red_q[kThreads / 32];
+    __shared__ int red_c[kThreads / 32];
+    const uint32_t lb = build_table(dyn_smem);
+    const int64_t F = it.n_frames;
+    const int64_t G = gridDim.x;
+    const int64_t fb = F * (int64_t)blockIdx.x / G;
+    const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
+    run_imajor_chunks(it, W, fb, fe, lb, red_q, red_c);
+}
+
+// Warps per frame of the input-major chunk path: about four blocks of 32 inputs a
+// warp, a power of two from 1 to 16.
+int imajor_chunk_team(int N)
+{
+    const int blocks = (N + 31) / 32;
+    int W = 1;
+    while (W < 16 && blocks >= 8 * W)
+        W *= 2;
+    return W;
+}
+
+sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, int grid_cap)
+{
+    if (it.n_frames == 0)
+        return SK_OK;
+    const int W = imajor_chunk_team(it.N);
+    const int64_t teams = (kThreads / 32) / W;
+    const int64_t gmax = grid_cap > 0 ? grid_cap : sm_count(device);
+    int64_t g = std::min<int64_t>(gmax, (it.n_frames + teams - 1) / teams);
+    if (g < 1)
+        g = 1;
+    // the table's dynamic shared memory (the same attribute as the fused kernel's)
+    {
+        static std::mutex mu;
+        static std::vector<int> done;
+        std::lock_guard<std::mutex> lk(mu);
+        bool have = false;
+        for (int d : done)
+            have = have || d == device;
+        if (!have) {
+            cudaError_t e = cudaFuncSetAttribute((const void *)sk_imajor_chunk_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kDynSmem);
+            if (e != cudaSuccess)
+                return cuda_error(e, "cudaFuncSetAttribute (input-major chunk path)");
+            done.push_back(device);
+        }
+    }
+    sk_imajor_chunk_kernel<<<(unsigned)g, kThreads, kDynSmem, st>>>(it, W);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_error(e, "sk input-major chunk kernel launch");
+    return SK_OK;
+}
+
 static int gcd_int(int a, int b)
 {
     while (b) {

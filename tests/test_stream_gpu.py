@@ -194,3 +194,73 @@ def test_stream_path_graph_capture_and_host_calls():
             assert np.array_equal(h_sk.view(np.uint32), want["sk"].view(np.uint32)), call.__name__
     finally:
         sk.sk_plan_destroy(plan)
+
+
+# Input-major frames ([frame][input][t]) of any M: the chunk path (two lanes per input,
+# the aligned 16-byte chunks that cover it, neighbours' bytes masked).  (N, M, F, path
+# requested): no fast path for these M (auto), and fast-path shapes asked for it.
+IMAJOR = [
+    (100, 100, 37, 0), (2048, 100, 9, 0), (256, 48, 21, 0), (2048, 200, 5, 0),
+    (7, 3, 999, 0), (33, 17, 120, 0), (1, 2, 500, 0), (4096, 5, 40, 0), (100, 1000, 7, 0),
+    (3, 4095, 11, 0), (250, 33, 40, 0), (2047, 101, 3, 0), (31, 4096, 2, sk.SK_PATH_STREAM),
+    (64, 96, 30, sk.SK_PATH_STREAM), (2048, 256, 4, sk.SK_PATH_STREAM),
+]
+
+
+@pytest.mark.parametrize("N,M,F,path", IMAJOR)
+def test_input_major_chunk_path_bit_exact(N, M, F, path):
+    """S1, S2, Q, N_eff, SK and masks of the input-major chunk path against the oracle
+    (random bytes with nibble 0, a dead frame and a dead input)."""
+    dev = _dev()
+    rng = np.random.default_rng(N * 131 + M * 7 + F)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    if F > 3:
+        x[1] = 0x88
+        x[2, :M] = 0x88           # input 0 without power
+    want = oracle.flag(x, M, N, 2.5, -0.01, layout=1)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    s1 = torch.full((F, N), -1, dtype=torch.int32, device=dev)
+    s2 = torch.full_like(s1, -1)
+    q = torch.full((F,), -1, dtype=torch.int64, device=dev)
+    skv = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+    ne = torch.full((F,), -1, dtype=torch.int32, device=dev)
+    sk2 = torch.full_like(skv, -1.0)
+    mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, 2.5, -0.01, layout=1)
+    try:
+        if path:
+            sk.sk_plan_set_config(plan, path=path)
+        sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
+        sk.sk_flag(plan, d_in, F, sk2, mask)
+        torch.cuda.synchronize()
+        assert sk.sk_plan_get_config(plan)["last_path"] == sk.SK_PATH_STREAM
+    finally:
+        sk.sk_plan_destroy(plan)
+    got = dict(S1=s1.cpu().numpy(), S2=s2.cpu().numpy(), Q=q.cpu().numpy(),
+               neff=ne.cpu().numpy(), sk=skv.cpu().numpy(), sk_flag=sk2.cpu().numpy(),
+               mask=mask.cpu().numpy())
+    check(got, want, f"input-major N={N} M={M} F={F}")
+
+
+@pytest.mark.parametrize("N,M,F", [(100, 100, 21), (2048, 48, 3)])
+def test_input_major_chunk_path_independent_estimates(N, M, F):
+    """sk_compute_inputs on the input-major chunk path: per-input SK^_i and flags."""
+    dev = _dev()
+    rng = np.random.default_rng(N + 5 * M + F)
+    x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+    want = oracle.flag_inputs(x, M, N, 3.0, 0.05, layout=1)
+    whole = oracle.flag(x, M, N, 3.0, 0.05, layout=1)
+    d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+    sk_in = torch.empty((F, N), dtype=torch.float32, device=dev)
+    m_in = torch.empty((F, N), dtype=torch.uint8, device=dev)
+    mask = torch.empty(F, dtype=torch.uint8, device=dev)
+    plan = sk.sk_plan_create(N, M, 3.0, 0.05, layout=1)
+    try:
+        sk.sk_compute_inputs(plan, d_in, F, sk_in, m_in, None, mask)
+        torch.cuda.synchronize()
+        assert sk.sk_plan_get_config(plan)["last_path"] == sk.SK_PATH_STREAM
+    finally:
+        sk.sk_plan_destroy(plan)
+    assert np.array_equal(sk_in.cpu().numpy().view(np.uint32), want["sk_in"].view(np.uint32))
+    assert np.array_equal(m_in.cpu().numpy(), want["mask_in"])
+    assert np.array_equal(mask.cpu().numpy(), whole["mask"])
