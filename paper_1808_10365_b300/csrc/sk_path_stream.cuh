@@ -406,18 +406,19 @@ __device__ __forceinline__ void run_stream(const Item &it, const StreamShape &sh
 
 // ---------------------------------------------------------------------------
 // Input-major frames of any M ([frame][input][t]: input i's M samples are the
-// bytes [i M, i M + M) of its frame).  Two lanes per input read the aligned
-// 16-byte chunks that cover the input (lane g: chunks g, g + 2, ...), with the
-// bytes of the neighbouring inputs in its first and last chunk replaced by 0x88
-// (no power).  A lane holds two inputs (i0 + j and i0 + 16 + j, j = lane / 2), so
-// that after the chunks one exchange between the two lanes of a pair leaves each
-// lane with the totals of one input: all 32 lanes then form an input term.  A
-// team of W warps takes a frame (warp w: input blocks of 32 at w, w + W, ...)
-// and combines Q and N_eff through shared memory and one named barrier when
-// W > 1.
+// bytes [i M, i M + M) of its frame).  G lanes per input (8 for inputs of six or
+// more chunks, 4 for three to five, else 2) read the aligned 16-byte chunks that
+// cover it (lane g: chunks g, g + G, ...), so that one warp load reads 32 / G
+// neighbouring inputs' bytes as one run.  Every chunk goes through
+// a byte mask (two entries of small shared tables: the input's first chunk drops the
+// bytes before it, its last the bytes after it, the others keep all 16), which
+// replaces the neighbours' bytes by 0x88 (no power) without a branch.  A lane holds
+// G inputs (i0 + (32 / G) r + j, r < G, j = lane / G); after the chunks a
+// reduce-scatter over the G lanes of an input group leaves each lane with the
+// totals of one input, and all 32 lanes form a term.  A team of W warps takes a
+// frame (warp w: input blocks of 32 at w, w + W, ...) and combines Q and N_eff
+// through shared memory and one named barrier when W > 1.
 // ---------------------------------------------------------------------------
-
-constexpr int kImcBatch = 4;  // chunk iterations per input per register batch (8 loads)
 
 // Byte mask of the bytes [kl, kh) of word w of a 16-byte chunk (0 <= kl <= kh <= 16).
 __device__ __forceinline__ uint32_t chunk_word_mask(int kl, int kh, int w)
@@ -430,35 +431,20 @@ __device__ __forceinline__ uint32_t chunk_word_mask(int kl, int kh, int w)
     return hi & ~((1u << (8 * a)) - 1u);
 }
 
-// The aligned chunk at p of an input whose bytes are [lo, hi): interior chunks are
-// one load; a chunk that reaches past the input (edge) keeps only the input's
-// bytes, and one that would reach past the end of the item's bytes (end) is read
-// byte by byte inside the input.
-__device__ __forceinline__ uint4 imc_load(const Item &it, const uint8_t *p, const uint8_t *lo,
-                                          const uint8_t *hi, const uint8_t *end, bool edge)
+// Mask tables: head[k] keeps bytes k..15, tail[k] keeps bytes 0..k-1 (k = 0..16).
+struct ChunkMasks {
+    uint4 head[17];
+    uint4 tail[17];
+};
+
+__device__ __forceinline__ void init_chunk_masks(ChunkMasks &cm)
 {
-    if (!edge)
-        return SK_DBG_IN(it, p, 16) ? ldg_stream16(p)
-                                    : make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
-    if (p >= lo && p + 16 <= hi)
-        return SK_DBG_IN(it, p, 16) ? ldg_stream16(p)
-                                    : make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
-    if (p + 16 > end)
-        return load_clipped(it, p, lo, hi);
-    uint4 v = SK_DBG_IN(it, p, 16) ? ldg_stream16(p)
-                                   : make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
-    const int kl = lo > p ? (int)(lo - p) : 0;
-    const int kh = hi < p + 16 ? (int)(hi - p) : 16;
-    uint32_t m;
-    m = chunk_word_mask(kl, kh, 0);
-    v.x = (v.x & m) | (kNoPower & ~m);
-    m = chunk_word_mask(kl, kh, 1);
-    v.y = (v.y & m) | (kNoPower & ~m);
-    m = chunk_word_mask(kl, kh, 2);
-    v.z = (v.z & m) | (kNoPower & ~m);
-    m = chunk_word_mask(kl, kh, 3);
-    v.w = (v.w & m) | (kNoPower & ~m);
-    return v;
+    for (int k = threadIdx.x; k < 17; k += blockDim.x) {
+        cm.head[k] = make_uint4(chunk_word_mask(k, 16, 0), chunk_word_mask(k, 16, 1),
+                                chunk_word_mask(k, 16, 2), chunk_word_mask(k, 16, 3));
+        cm.tail[k] = make_uint4(chunk_word_mask(0, k, 0), chunk_word_mask(0, k, 1),
+                                chunk_word_mask(0, k, 2), chunk_word_mask(0, k, 3));
+    }
 }
 
 // One chunk of one input into its exact sums: the 16 samples through the table into
@@ -476,48 +462,25 @@ __device__ __forceinline__ void imc_add(uint4 a, uint32_t lb, int32_t &s1, int32
     s2 = (int32_t)((uint32_t)s2 + acc);
 }
 
-// The lane's two inputs of the round at i0: bytes [lo_r, lo_r + M), chunks from base_r.
-__device__ __forceinline__ void imc_round(const uint8_t *fa, int i0, int j, int N, int M,
-                                          const uint8_t *(&lo)[2], const uint8_t *(&base)[2],
-                                          int (&nci)[2], bool (&valid)[2])
+// load_clipped kept out of line: only a chunk past the end of the item's bytes takes
+// it (the last input of the last frame), and inlined it would cost the loop registers.
+static __device__ __noinline__ uint4 load_clipped_tail(const Item &it, const uint8_t *p,
+                                                const uint8_t *lo, const uint8_t *hi)
 {
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int i = i0 + 16 * r + j;
-        valid[r] = i < N;
-        lo[r] = fa + (int64_t)(valid[r] ? i : 0) * M;
-        base[r] = (const uint8_t *)((uintptr_t)lo[r] & ~(uintptr_t)15u);
-        nci[r] = (int)(((uintptr_t)lo[r] & 15u) + M + 15) >> 4;
-    }
+    return load_clipped(it, p, lo, hi);
 }
 
-// Chunk iterations kb .. kb + kImcBatch - 1 of the lane's two inputs into v.
-__device__ __forceinline__ void imc_batch(const Item &it, uint4 (&v)[2][kImcBatch], int kb,
-                                          int kmax, int g, bool whole,
-                                          const uint8_t *const (&lo)[2],
-                                          const uint8_t *const (&base)[2], const int (&nci)[2],
-                                          const bool (&valid)[2], int M, const uint8_t *end)
+__device__ __forceinline__ uint32_t keep_bytes(uint32_t v, uint32_t m)
 {
-    const uint4 none = make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
-#pragma unroll
-    for (int t = 0; t < kImcBatch; ++t) {
-        // a chunk that may reach past its input: the first and the last two iterations
-        // (nci differs by one between inputs), unless inputs are whole chunks
-        const bool edge = !whole && (kb + t == 0 || kb + t >= kmax - 2);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int c = g + 2 * (kb + t);
-            v[r][t] = (valid[r] && kb + t < kmax && c < nci[r])
-                          ? imc_load(it, base[r] + 16 * c, lo[r], lo[r] + M, end, edge)
-                          : none;
-        }
-    }
+    return (v & m) | (kNoPower & ~m);
 }
 
-// Frames [f_begin, f_end) of an input-major item, teams of W warps per frame.
-// red_q, red_c: one entry per warp.
+// Frames [f_begin, f_end) of an input-major item, G lanes per input (2, 4 or 8) and G
+// inputs a lane, teams of W warps per frame.  red_q, red_c: one entry per warp.
+template <int G>
 __device__ __forceinline__ void run_imajor_chunks(const Item &it, int W, int64_t f_begin,
-                                                  int64_t f_end, uint32_t lb, long long *red_q,
+                                                  int64_t f_end, uint32_t lb,
+                                                  const ChunkMasks &cm, long long *red_q,
                                                   int *red_c)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -525,57 +488,78 @@ __device__ __forceinline__ void run_imajor_chunks(const Item &it, int W, int64_t
     const int teams = (int)(blockDim.x >> 5) / W;
     if (team >= teams)
         return;  // whole warps past the last team
-    const int g = lane & 1, j = lane >> 1;
+    static_assert(G == 2 || G == 4 || G == 8, "lanes per input");
+    constexpr int IPW = 32 / G;  // inputs a warp load covers
+    const int g = lane & (G - 1), j = lane / G;
     const int N = it.N, M = it.M;
     const int64_t fbytes = (int64_t)M * N;
     const uint8_t *end = it.in + it.n_frames * fbytes;
-    const int kmax = (((M + 30) >> 4) + 1) >> 1;  // chunk iterations per input and lane
-    // M % 16 == 0: every input starts on a 16-byte boundary (the item's bytes do) and
-    // ends on one, so no chunk reaches past its input
-    const bool whole = (M & 15) == 0;
+    const int kmax = (((M + 30) >> 4) + G - 1) / G;  // chunk iterations per input and lane
     const int64_t rounds = (f_end - f_begin + teams - 1) / teams;
+    const uint4 none = make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
     for (int64_t k = 0; k < rounds; ++k) {
         const int64_t frame = f_begin + k * teams + team;
         const bool fvalid = frame < f_end;
         const uint8_t *fa = it.in + (fvalid ? frame : f_begin) * fbytes;
         int64_t q = 0;
         int32_t cnt = 0;
-        // a round is 32 inputs (two a lane); its first batch of chunks is loaded before
-        // the previous round's exchange and terms (pre: v holds it)
-        uint4 v[2][kImcBatch];
-        bool pre = false;
         for (int i0 = 32 * wt; fvalid && i0 < N; i0 += 32 * W) {
-            const uint8_t *lo[2], *base[2];
-            int nci[2];
-            bool valid[2];
-            imc_round(fa, i0, j, N, M, lo, base, nci, valid);
-            int32_t s1[2] = {0, 0}, s2[2] = {0, 0};
-            for (int kb = 0; kb < kmax; kb += kImcBatch) {
-                if (!(pre && kb == 0))
-                    imc_batch(it, v, kb, kmax, g, whole, lo, base, nci, valid, M, end);
-                pre = false;
+            int32_t s1[G], s2[G];
 #pragma unroll
-                for (int t = 0; t < kImcBatch; ++t)
+            for (int r = 0; r < G; ++r) {
+                s1[r] = 0;
+                s2[r] = 0;
+            }
+            for (int kb = 0; kb < kmax; ++kb) {
+                const int c = g + G * kb;  // the lane's chunk of each of its inputs
+                uint4 v[G];
 #pragma unroll
-                    for (int r = 0; r < 2; ++r)
-                        imc_add(v[r][t], lb, s1[r], s2[r]);
+                for (int r = 0; r < G; ++r) {
+                    const int i = i0 + IPW * r + j;
+                    const uint8_t *lo = fa + (int64_t)(i < N ? i : 0) * M;
+                    const uint8_t *p =
+                        (const uint8_t *)((uintptr_t)lo & ~(uintptr_t)15u) + 16 * c;
+                    const int nci = (int)(((uintptr_t)lo & 15u) + M + 15) >> 4;
+                    v[r] = none;
+                    if (i < N && c < nci) {
+                        if (p + 16 <= end)
+                            v[r] = SK_DBG_IN(it, p, 16) ? ldg_stream16(p) : none;
+                        else
+                            v[r] = load_clipped_tail(it, p, lo, lo + M);  // the item's last bytes
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < G; ++r) {
+                    const int i = i0 + IPW * r + j;
+                    const uint8_t *lo = fa + (int64_t)(i < N ? i : 0) * M;
+                    const int nci = (int)(((uintptr_t)lo & 15u) + M + 15) >> 4;
+                    const int kl = c == 0 ? (int)((uintptr_t)lo & 15u) : 0;
+                    const int kh = c == nci - 1 ? (int)(((uintptr_t)lo + M - 1) & 15u) + 1 : 16;
+                    const uint4 mh = cm.head[kl], mt = cm.tail[kh];
+                    uint4 x = v[r];
+                    x.x = keep_bytes(x.x, mh.x & mt.x);
+                    x.y = keep_bytes(x.y, mh.y & mt.y);
+                    x.z = keep_bytes(x.z, mh.z & mt.z);
+                    x.w = keep_bytes(x.w, mh.w & mt.w);
+                    imc_add(x, lb, s1[r], s2[r]);
+                }
             }
-            if (i0 + 32 * W < N) {
-                // the next round's first batch, in flight during this round's terms
-                const uint8_t *nlo[2], *nbase[2];
-                int nnci[2];
-                bool nvalid[2];
-                imc_round(fa, i0 + 32 * W, j, N, M, nlo, nbase, nnci, nvalid);
-                imc_batch(it, v, 0, kmax, g, whole, nlo, nbase, nnci, nvalid, M, end);
-                pre = true;
+            // reduce-scatter over the G lanes of each input group: lane g keeps input r = g
+#pragma unroll
+            for (int h = G / 2; h >= 1; h /= 2) {
+                const bool up = (g & h) != 0;
+#pragma unroll
+                for (int t = 0; t < h; ++t) {
+                    const int32_t k1 = up ? s1[t + h] : s1[t], o1 = up ? s1[t] : s1[t + h];
+                    const int32_t k2 = up ? s2[t + h] : s2[t], o2 = up ? s2[t] : s2[t + h];
+                    s1[t] = k1 + __shfl_xor_sync(0xFFFFFFFFu, o1, h);
+                    s2[t] = (int32_t)((uint32_t)k2 +
+                                      (uint32_t)__shfl_xor_sync(0xFFFFFFFFu, o2, h));
+                }
             }
-            // the pair's sums: lane g keeps input i0 + 16 g + j
-            const int32_t k1 = g ? s1[1] : s1[0], o1 = g ? s1[0] : s1[1];
-            const int32_t k2 = g ? s2[1] : s2[0], o2 = g ? s2[0] : s2[1];
-            const int32_t a1 = k1 + __shfl_xor_sync(0xFFFFFFFFu, o1, 1);
-            const uint32_t a2 = (uint32_t)k2 + (uint32_t)__shfl_xor_sync(0xFFFFFFFFu, o2, 1) -
-                                ((uint32_t)a1 << kPackShift);  // exact S2
-            const int i = i0 + 16 * g + j;
+            const int32_t a1 = s1[0];
+            const uint32_t a2 = (uint32_t)s2[0] - ((uint32_t)a1 << kPackShift);  // exact S2
+            const int i = i0 + IPW * g + j;
             if (i < N) {
                 float rr = 0.0f;
                 int64_t qi = 0;

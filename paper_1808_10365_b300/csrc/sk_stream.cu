@@ -31,17 +31,20 @@ __global__ void __launch_bounds__(kStreamThreads, 1) sk_stream_kernel(Item it, S
 
 // Input-major frames of any M (run_imajor_chunks): a contiguous frame range per CTA,
 // teams of W warps per frame.
+template <int G>
 __global__ void __launch_bounds__(kThreads, 1) sk_imajor_chunk_kernel(Item it, int W)
 {
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     __shared__ long long red_q[kThreads / 32];
     __shared__ int red_c[kThreads / 32];
+    __shared__ ChunkMasks cm;
+    init_chunk_masks(cm);  // ordered before use by build_table's barrier
     const uint32_t lb = build_table(dyn_smem);
     const int64_t F = it.n_frames;
-    const int64_t G = gridDim.x;
-    const int64_t fb = F * (int64_t)blockIdx.x / G;
-    const int64_t fe = F * ((int64_t)blockIdx.x + 1) / G;
-    run_imajor_chunks(it, W, fb, fe, lb, red_q, red_c);
+    const int64_t NB = gridDim.x;
+    const int64_t fb = F * (int64_t)blockIdx.x / NB;
+    const int64_t fe = F * ((int64_t)blockIdx.x + 1) / NB;
+    run_imajor_chunks<G>(it, W, fb, fe, lb, cm, red_q, red_c);
 }
 
 // Warps per frame of the input-major chunk path: about four blocks of 32 inputs a
@@ -55,6 +58,8 @@ int imajor_chunk_team(int N)
     return W;
 }
 
+typedef void (*KernelFnI)(Item, int);
+
 sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, int grid_cap)
 {
     if (it.n_frames == 0)
@@ -65,6 +70,14 @@ sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, in
     int64_t g = std::min<int64_t>(gmax, (it.n_frames + teams - 1) / teams);
     if (g < 1)
         g = 1;
+    // lanes per input by the chunks an input spans (A/B on B300, 3 GB launches: M = 48,
+    // 4 chunks: 2 lanes 0.28, 8 lanes 0.19; M = 100, 8 chunks: 2 lanes 0.27-0.32,
+    // 8 lanes 0.32-0.34)
+    const int cmax = (it.M + 30) >> 4;
+    const int G = cmax >= 6 ? 8 : (cmax >= 3 ? 4 : 2);
+    static const KernelFnI kFns[3] = {sk_imajor_chunk_kernel<2>, sk_imajor_chunk_kernel<4>,
+                                      sk_imajor_chunk_kernel<8>};
+    const KernelFnI fn = kFns[G == 2 ? 0 : (G == 4 ? 1 : 2)];
     // the table's dynamic shared memory (the same attribute as the fused kernel's)
     {
         static std::mutex mu;
@@ -74,15 +87,16 @@ sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, in
         for (int d : done)
             have = have || d == device;
         if (!have) {
-            cudaError_t e = cudaFuncSetAttribute((const void *)sk_imajor_chunk_kernel,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 kDynSmem);
-            if (e != cudaSuccess)
-                return cuda_error(e, "cudaFuncSetAttribute (input-major chunk path)");
+            for (KernelFnI f : kFns) {
+                cudaError_t e = cudaFuncSetAttribute(
+                    (const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+                if (e != cudaSuccess)
+                    return cuda_error(e, "cudaFuncSetAttribute (input-major chunk path)");
+            }
             done.push_back(device);
         }
     }
-    sk_imajor_chunk_kernel<<<(unsigned)g, kThreads, kDynSmem, st>>>(it, W);
+    fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(it, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_error(e, "sk input-major chunk kernel launch");
