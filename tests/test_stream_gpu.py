@@ -264,3 +264,49 @@ def test_input_major_chunk_path_independent_estimates(N, M, F):
     assert np.array_equal(sk_in.cpu().numpy().view(np.uint32), want["sk_in"].view(np.uint32))
     assert np.array_equal(m_in.cpu().numpy(), want["mask_in"])
     assert np.array_equal(mask.cpu().numpy(), whole["mask"])
+
+
+def test_random_stream_and_chunk_shapes():
+    """40 seeded random shapes on the stream path (time-major, N up to 600, any M,
+    frames at every 16-byte offset) and the input-major chunk path (any M not a multiple
+    of 32), random grid sizes, the path asked for or chosen by the library: S1, S2, Q,
+    N_eff, SK bits and masks bit-exact against the oracle."""
+    dev = _dev()
+    rng = np.random.default_rng(1808_10365)
+    for case in range(40):
+        layout = int(rng.integers(0, 2))
+        if layout == 0:
+            N = int(rng.integers(1, 601))
+            M = int(rng.integers(2, 400))
+        else:
+            N = int(rng.integers(1, 2500))
+            M = int(rng.integers(2, 1200))
+            if M % 32 == 0:
+                M += 1
+        F = int(rng.integers(1, 40))
+        while F > 1 and F * M * N > (8 << 20):
+            F //= 2
+        grid = int(rng.choice([0, 1, 3, 17]))
+        path = int(rng.choice([sk.SK_PATH_AUTO, sk.SK_PATH_STREAM]))
+        x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+        want = oracle.flag(x, M, N, 2.5, 0.02, layout=layout)
+        d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+        s1 = torch.full((F, N), -1, dtype=torch.int32, device=dev)
+        s2 = torch.full_like(s1, -1)
+        q = torch.full((F,), -1, dtype=torch.int64, device=dev)
+        skv = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+        ne = torch.full((F,), -1, dtype=torch.int32, device=dev)
+        mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+        plan = sk.sk_plan_create(N, M, 2.5, 0.02, layout=layout)
+        try:
+            sk.sk_plan_set_config(plan, rows=16 if M % 32 == 0 else 8, grid_ctas=grid, path=path)
+            sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
+            sk.sk_flag(plan, d_in, F, None, mask)
+            torch.cuda.synchronize()
+            taken = sk.sk_plan_get_config(plan)["last_path"]
+        finally:
+            sk.sk_plan_destroy(plan)
+        label = f"case {case}: N={N} M={M} F={F} layout={layout} grid={grid} path={path} -> {taken}"
+        for k, g in (("S1", s1), ("S2", s2), ("Q", q), ("neff", ne), ("mask", mask)):
+            assert np.array_equal(g.cpu().numpy(), want[k]), f"{label}: {k}"
+        assert np.array_equal(skv.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32)), label
