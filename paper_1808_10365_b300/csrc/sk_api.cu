@@ -1096,6 +1096,8 @@ extern "C" sk_status_t sk_plan_create(const sk_params_t *params, int device, sk_
             *pl->h_err = 0;
             st = ensure_kernel_attrs(device);
             if (st == SK_OK)
+                st = stream_kernel_attrs(device);
+            if (st == SK_OK)
                 noalloc_prepare(device);
         }
         if (st != SK_OK)

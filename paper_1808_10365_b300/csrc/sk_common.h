@@ -60,6 +60,8 @@ sk_status_t launch_stream(const Item &it, const StreamShape &sh, int device, cud
 // Input-major frames of any M (run_imajor_chunks in sk_path_stream.cuh): the launch,
 // and its warps per frame for N inputs.
 sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, int grid_cap);
+// Dynamic shared memory attributes of the stream and chunk kernels on `device` (once).
+sk_status_t stream_kernel_attrs(int device);
 int imajor_chunk_team(int N);
 // SK_ERR_TIMEOUT once if a bounded wait in an earlier launch of the plan gave up.
 sk_status_t pending_fault(sk_plan_t plan, const char *who);

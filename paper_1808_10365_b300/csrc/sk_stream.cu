@@ -59,6 +59,30 @@ int imajor_chunk_team(int N)
 }
 
 typedef void (*KernelFnI)(Item, int);
+static const KernelFnI kChunkFns[3] = {sk_imajor_chunk_kernel<2>, sk_imajor_chunk_kernel<4>,
+                                       sk_imajor_chunk_kernel<8>};
+
+// The dynamic shared memory of the stream and chunk kernels, once per device (plan
+// creation sets it, before any stream capture; the launches check it again).
+sk_status_t stream_kernel_attrs(int device)
+{
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    for (int d : done)
+        if (d == device)
+            return SK_OK;
+    cudaError_t e = cudaFuncSetAttribute((const void *)sk_stream_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kStreamSmem);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        e = cudaFuncSetAttribute((const void *)kChunkFns[k],
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+    if (e != cudaSuccess)
+        return cuda_error(e, "cudaFuncSetAttribute (stream and chunk paths)");
+    done.push_back(device);
+    return SK_OK;
+}
 
 sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, int grid_cap)
 {
@@ -75,27 +99,10 @@ sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, in
     // 8 lanes 0.32-0.34)
     const int cmax = (it.M + 30) >> 4;
     const int G = cmax >= 6 ? 8 : (cmax >= 3 ? 4 : 2);
-    static const KernelFnI kFns[3] = {sk_imajor_chunk_kernel<2>, sk_imajor_chunk_kernel<4>,
-                                      sk_imajor_chunk_kernel<8>};
-    const KernelFnI fn = kFns[G == 2 ? 0 : (G == 4 ? 1 : 2)];
-    // the table's dynamic shared memory (the same attribute as the fused kernel's)
-    {
-        static std::mutex mu;
-        static std::vector<int> done;
-        std::lock_guard<std::mutex> lk(mu);
-        bool have = false;
-        for (int d : done)
-            have = have || d == device;
-        if (!have) {
-            for (KernelFnI f : kFns) {
-                cudaError_t e = cudaFuncSetAttribute(
-                    (const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
-                if (e != cudaSuccess)
-                    return cuda_error(e, "cudaFuncSetAttribute (input-major chunk path)");
-            }
-            done.push_back(device);
-        }
-    }
+    const KernelFnI fn = kChunkFns[G == 2 ? 0 : (G == 4 ? 1 : 2)];
+    sk_status_t s = stream_kernel_attrs(device);
+    if (s != SK_OK)
+        return s;
     fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(it, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
@@ -224,22 +231,9 @@ sk_status_t launch_stream(const Item &it, const StreamShape &sh, int device, cud
 {
     if (it.n_frames == 0)
         return SK_OK;
-    {
-        static std::mutex mu;
-        static std::vector<int> done;
-        std::lock_guard<std::mutex> g(mu);
-        bool have = false;
-        for (int d : done)
-            have = have || d == device;
-        if (!have) {
-            cudaError_t e = cudaFuncSetAttribute((const void *)sk_stream_kernel,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 kStreamSmem);
-            if (e != cudaSuccess)
-                return cuda_error(e, "cudaFuncSetAttribute (stream path)");
-            done.push_back(device);
-        }
-    }
+    sk_status_t s = stream_kernel_attrs(device);
+    if (s != SK_OK)
+        return s;
     const int64_t gmax = grid_cap > 0 ? grid_cap : sm_count(device);
     int64_t g = std::min<int64_t>(gmax, (it.n_frames + sh.units - 1) / sh.units);
     if (g < 1)
