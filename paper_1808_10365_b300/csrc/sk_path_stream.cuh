@@ -495,6 +495,9 @@ __device__ __forceinline__ void run_imajor_chunks(const Item &it, int W, int64_t
     const int64_t fbytes = (int64_t)M * N;
     const uint8_t *end = it.in + it.n_frames * fbytes;
     const int kmax = (((M + 30) >> 4) + G - 1) / G;  // chunk iterations per input and lane
+    // M % 16 == 0: every input starts and ends on a 16-byte boundary (the item's bytes
+    // start on one), so no chunk holds a neighbour's bytes and none is masked
+    const bool whole = (M & 15) == 0;
     const int64_t rounds = (f_end - f_begin + teams - 1) / teams;
     const uint4 none = make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
     for (int64_t k = 0; k < rounds; ++k) {
@@ -528,21 +531,25 @@ __device__ __forceinline__ void run_imajor_chunks(const Item &it, int W, int64_t
                             v[r] = load_clipped_tail(it, p, lo, lo + M);  // the item's last bytes
                     }
                 }
+                if (!whole) {
 #pragma unroll
-                for (int r = 0; r < G; ++r) {
-                    const int i = i0 + IPW * r + j;
-                    const uint8_t *lo = fa + (int64_t)(i < N ? i : 0) * M;
-                    const int nci = (int)(((uintptr_t)lo & 15u) + M + 15) >> 4;
-                    const int kl = c == 0 ? (int)((uintptr_t)lo & 15u) : 0;
-                    const int kh = c == nci - 1 ? (int)(((uintptr_t)lo + M - 1) & 15u) + 1 : 16;
-                    const uint4 mh = cm.head[kl], mt = cm.tail[kh];
-                    uint4 x = v[r];
-                    x.x = keep_bytes(x.x, mh.x & mt.x);
-                    x.y = keep_bytes(x.y, mh.y & mt.y);
-                    x.z = keep_bytes(x.z, mh.z & mt.z);
-                    x.w = keep_bytes(x.w, mh.w & mt.w);
-                    imc_add(x, lb, s1[r], s2[r]);
+                    for (int r = 0; r < G; ++r) {
+                        const int i = i0 + IPW * r + j;
+                        const uint8_t *lo = fa + (int64_t)(i < N ? i : 0) * M;
+                        const int nci = (int)(((uintptr_t)lo & 15u) + M + 15) >> 4;
+                        const int kl = c == 0 ? (int)((uintptr_t)lo & 15u) : 0;
+                        const int kh =
+                            c == nci - 1 ? (int)(((uintptr_t)lo + M - 1) & 15u) + 1 : 16;
+                        const uint4 mh = cm.head[kl], mt = cm.tail[kh];
+                        v[r].x = keep_bytes(v[r].x, mh.x & mt.x);
+                        v[r].y = keep_bytes(v[r].y, mh.y & mt.y);
+                        v[r].z = keep_bytes(v[r].z, mh.z & mt.z);
+                        v[r].w = keep_bytes(v[r].w, mh.w & mt.w);
+                    }
                 }
+#pragma unroll
+                for (int r = 0; r < G; ++r)
+                    imc_add(v[r], lb, s1[r], s2[r]);
             }
             // reduce-scatter over the G lanes of each input group: lane g keeps input r = g
 #pragma unroll
