@@ -2,14 +2,16 @@
 // byte-balanced schedule of (item, frame range) chunks that mixes items of
 // different M (integration lengths 128..1024).  Items are split by kernel class
 // (time-major N = 2048 and N = 256 with the row stride compiled in, input-major
-// items by M on the grouped input-major path, and the rest), and each non-empty
-// class is one such launch; the launches are captured once into a CUDA graph and
-// replayed.
+// items by M on the grouped input-major path, time-major items of the stream path,
+// input-major items of the chunk path by lanes per input, and the rest), and each
+// non-empty class is one such launch; the launches are captured once into a CUDA
+// graph and replayed.
 #include <algorithm>
 #include <cstring>
 #include <new>
 
 #include "sk_common.h"
+#include "sk_path_stream.cuh"
 
 struct sk_batch_s {
     int device = 0;
@@ -23,6 +25,11 @@ struct sk_batch_s {
     sk::Chunk *d_chunks = nullptr;
     int32_t *d_cta = nullptr;
     CUtensorMap *d_maps = nullptr;  // tensor maps of the warp-slice items' inputs
+    // stream classes (time-major stream path, input-major chunk path by lanes per
+    // input): used flags and each item's stream shape, on the host and the device
+    bool sused[sk::kStreamClasses] = {};
+    std::vector<sk::StreamShape> shapes;
+    sk::StreamShape *d_shapes = nullptr;
     std::vector<sk_plan_t> plans;   // the items' plans, each once
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -36,7 +43,8 @@ namespace sk {
 // before it and b bytes of its own goes to CTA floor((c + b/2) / (total/grid)).
 // Consecutive rounds of one item on one CTA merge into one chunk.
 void build_schedule(const std::vector<Item> &items, const std::vector<int32_t> &sel, int grid,
-                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta, bool imajor)
+                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta, bool imajor,
+                    const std::vector<int64_t> *rounds)
 {
     double total = 0.0;
     for (int32_t k : sel)
@@ -50,7 +58,8 @@ void build_schedule(const std::vector<Item> &items, const std::vector<int32_t> &
     double cum = 0.0;
     for (int32_t k : sel) {
         const Item &it = items[k];
-        const int64_t T = kThreads >> (imajor ? it.imajor_team_log2 : it.team_log2);
+        const int64_t T = rounds ? (*rounds)[k]
+                                 : kThreads >> (imajor ? it.imajor_team_log2 : it.team_log2);
         const double fbytes = (double)it.M * it.N;
         for (int64_t f0 = 0; f0 < it.n_frames; f0 += T) {
             const int64_t f1 = std::min(f0 + T, it.n_frames);
@@ -166,6 +175,7 @@ static void free_batch(sk_batch_s *b)
     cudaFree(b->d_chunks);
     cudaFree(b->d_cta);
     cudaFree(b->d_maps);
+    cudaFree(b->d_shapes);
 }
 
 extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_items,
@@ -185,6 +195,9 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
     bool all_m32[kBatchClasses];
     std::fill(all_m32, all_m32 + kBatchClasses, true);
     std::vector<int32_t> sel[kBatchClasses];
+    std::vector<int32_t> ssel[kStreamClasses];
+    std::vector<int64_t> srounds(n_items, 1);
+    b->shapes.assign(n_items, StreamShape{});
     std::vector<CUtensorMap> maps;
     std::vector<int32_t> map_of;
     for (int32_t k = 0; k < n_items; ++k) {
@@ -204,6 +217,21 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
         it.mask = bi.d_mask;
         if (std::find(b->plans.begin(), b->plans.end(), bi.plan) == b->plans.end())
             b->plans.push_back(bi.plan);
+        // items without a fused-kernel fast path that the stream or chunk path takes
+        // (as a one-item launch of the plan would, when it asks for no path)
+        StreamShape ssh;
+        memset(&ssh, 0, sizeof ssh);
+        const int sc = bi.plan->batch_path == SK_PATH_AUTO ? stream_batch_class(it, &ssh) : -1;
+        if (sc >= 0) {
+            if (sc == 0 && ssh.W == 1)
+                it.prefetch = 0;  // the look-ahead prefetch pays only on multi-warp units
+            b->shapes[k] = ssh;
+            srounds[k] = stream_batch_round(it, ssh, sc);
+            b->items.push_back(it);
+            map_of.push_back(-1);
+            ssel[sc].push_back(k);
+            continue;
+        }
         int c = batch_class(it);
         // time-major N = 2048 items on 16-row tiles take the warp-slice path when
         // the plan's batch path asks for it, or by default at M <= 128 (measured
@@ -240,6 +268,20 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
         b->chunks.insert(b->chunks.end(), ch.begin(), ch.end());
         b->cta.insert(b->cta.end(), cta.begin(), cta.end());
     }
+    for (int c = 0; c < kStreamClasses; ++c) {
+        std::vector<Chunk> ch;
+        std::vector<int32_t> cta;
+        build_schedule(b->items, ssel[c], b->grid, ch, cta, false, &srounds);
+        b->sused[c] = !ch.empty();
+        const int32_t base = (int32_t)b->chunks.size();
+        for (int32_t &x : cta)
+            x += base;
+        b->chunks.insert(b->chunks.end(), ch.begin(), ch.end());
+        b->cta.insert(b->cta.end(), cta.begin(), cta.end());
+    }
+    bool any_stream = false;
+    for (int c = 0; c < kStreamClasses; ++c)
+        any_stream = any_stream || b->sused[c];
     sk_status_t s = SK_OK;
     {
         DeviceGuard dg(device);
@@ -273,8 +315,17 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
                    cudaMemcpy(b->d_cta, b->cta.data(), nt, cudaMemcpyHostToDevice) !=
                        cudaSuccess) {
             s = set_error(SK_ERR_CUDA, "batch schedule upload");
+        } else if (any_stream &&
+                   (cudaMalloc(&b->d_shapes, sizeof(StreamShape) * b->shapes.size()) !=
+                        cudaSuccess ||
+                    cudaMemcpy(b->d_shapes, b->shapes.data(),
+                               sizeof(StreamShape) * b->shapes.size(),
+                               cudaMemcpyHostToDevice) != cudaSuccess)) {
+            s = set_error(SK_ERR_OOM, "batch stream shapes");
         } else {
             s = ensure_kernel_attrs(device);
+            if (s == SK_OK)
+                s = stream_kernel_attrs(device);
         }
         if (s != SK_OK)
             free_batch(b);
@@ -311,6 +362,11 @@ extern "C" sk_status_t sk_batch_run(sk_batch_t b, sk_cuda_stream_t stream)
                 if (b->used[c])
                     s = launch_schedule(b->d_items, b->d_chunks, b->d_cta + c * (b->grid + 1),
                                         b->grid, b->tile[c], false, b->device, cs, c);
+            for (int c = 0; c < kStreamClasses && s == SK_OK; ++c)
+                if (b->sused[c])
+                    s = launch_stream_schedule(c, b->d_items, b->d_shapes, b->d_chunks,
+                                               b->d_cta + (kBatchClasses + c) * (b->grid + 1),
+                                               b->grid, b->device, cs);
             cudaGraph_t g = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(cs, &g);
             if (s == SK_OK && e2 == cudaSuccess) {
@@ -342,6 +398,9 @@ extern "C" sk_status_t sk_batch_launches(sk_batch_t b, int32_t *launches)
     if (!b->chunks.empty())
         for (int c = 0; c < kBatchClasses; ++c)
             n += b->used[c] ? 1 : 0;
+    if (!b->chunks.empty())
+        for (int c = 0; c < kStreamClasses; ++c)
+            n += b->sused[c] ? 1 : 0;
     *launches = n;
     return SK_OK;
 }

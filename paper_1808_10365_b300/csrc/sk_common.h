@@ -57,12 +57,21 @@ bool stream_shape(int N, int M, StreamShape *out);
 bool stream_auto(const Item &it);
 sk_status_t launch_stream(const Item &it, const StreamShape &sh, int device, cudaStream_t st,
                           int grid_cap);
-// Input-major frames of any M (run_imajor_chunks in sk_path_stream.cuh): the launch,
-// and its warps per frame for N inputs.
+// Input-major frames of any M (run_imajor_chunks in sk_path_stream.cuh): the launch.
 sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, int grid_cap);
 // Dynamic shared memory attributes of the stream and chunk kernels on `device` (once).
 sk_status_t stream_kernel_attrs(int device);
-int imajor_chunk_team(int N);
+// Batched launches of the stream and chunk paths (sk_batch_create / sk_batch_run): the
+// class of an item (0: time-major stream path, 1..3: input-major chunk path with 2, 4
+// or 8 lanes per input; -1: a fused-kernel class), the frames one CTA takes per round
+// (the schedule's unit), and the launch of one class over its schedule.  d_shapes
+// holds each item's stream shape (used by class 0).
+constexpr int kStreamClasses = 4;
+int stream_batch_class(const Item &it, StreamShape *sh);
+int64_t stream_batch_round(const Item &it, const StreamShape &sh, int cls);
+sk_status_t launch_stream_schedule(int cls, const Item *d_items, const StreamShape *d_shapes,
+                                   const Chunk *d_chunks, const int32_t *d_cta, int grid,
+                                   int device, cudaStream_t st);
 // SK_ERR_TIMEOUT once if a bounded wait in an earlier launch of the plan gave up.
 sk_status_t pending_fault(sk_plan_t plan, const char *who);
 // Set-up of sk_flag_host_noalloc on `device` (current): looks up the device
@@ -79,9 +88,10 @@ int sm_count(int device);
 
 // Static byte-balanced schedule of the items listed in `sel` over `grid` CTAs;
 // chunk item indices refer to `items`.  imajor: rounds follow the input-major
-// kernel's team size.
+// kernel's team size; rounds: frames per round of each item (the stream classes).
 void build_schedule(const std::vector<Item> &items, const std::vector<int32_t> &sel, int grid,
-                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta, bool imajor = false);
+                    std::vector<Chunk> &chunks, std::vector<int32_t> &cta, bool imajor = false,
+                    const std::vector<int64_t> *rounds = nullptr);
 
 // One chunk per one-frame item, round-robin over at most grid_max CTAs (the
 // served launch that splits each frame's rows over a CTA); returns the grid.

@@ -475,6 +475,26 @@ __device__ __forceinline__ uint32_t keep_bytes(uint32_t v, uint32_t m)
     return (v & m) | (kNoPower & ~m);
 }
 
+// Warps per frame of the input-major chunk path: about four blocks of 32 inputs a
+// warp, a power of two from 1 to 16.
+__host__ __device__ __forceinline__ int imajor_chunk_team(int N)
+{
+    const int blocks = (N + 31) / 32;
+    int W = 1;
+    while (W < 16 && blocks >= 8 * W)
+        W *= 2;
+    return W;
+}
+
+// Lanes per input of the chunk path by the chunks an input spans (A/B on B300, 3 GB
+// launches: M = 48, 4 chunks: 2 lanes 0.28, 8 lanes 0.19, 4 lanes 0.31; M = 100, 8
+// chunks: 2 lanes 0.27-0.32, 8 lanes 0.32-0.34).
+__host__ __device__ __forceinline__ int imajor_chunk_lanes(int M)
+{
+    const int cmax = (M + 30) >> 4;
+    return cmax >= 6 ? 8 : (cmax >= 3 ? 4 : 2);
+}
+
 // Frames [f_begin, f_end) of an input-major item, G lanes per input (2, 4 or 8) and G
 // inputs a lane, teams of W warps per frame.  red_q, red_c: one entry per warp.
 template <int G>

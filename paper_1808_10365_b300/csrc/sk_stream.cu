@@ -47,20 +47,57 @@ __global__ void __launch_bounds__(kThreads, 1) sk_imajor_chunk_kernel(Item it, i
     run_imajor_chunks<G>(it, W, fb, fe, lb, cm, red_q, red_c);
 }
 
-// Warps per frame of the input-major chunk path: about four blocks of 32 inputs a
-// warp, a power of two from 1 to 16.
-int imajor_chunk_team(int N)
+// Batched launches: one persistent grid walks a chunk schedule (item, frame range)
+// of items of the class, each with its own launch shape; the CTA's threads meet at
+// one barrier between chunks (the slots and the per-warp sums are reused).
+__global__ void __launch_bounds__(kStreamThreads, 1)
+    sk_stream_batch_kernel(const Item *__restrict__ items, const StreamShape *__restrict__ shapes,
+                           const Chunk *__restrict__ chunks, const int32_t *__restrict__ cta)
 {
-    const int blocks = (N + 31) / 32;
-    int W = 1;
-    while (W < 16 && blocks >= 8 * W)
-        W *= 2;
-    return W;
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ long long red_q[kStreamWarps];
+    __shared__ int red_c[kStreamWarps];
+    const uint32_t lb = build_table(dyn_smem);
+    const uint32_t part_sh = (lb & ~0xFFFFu) + (uint32_t)kLutBytes;
+    int32_t *part = reinterpret_cast<int32_t *>(
+        dyn_smem + (part_sh - (uint32_t)__cvta_generic_to_shared(dyn_smem)));
+    const int32_t c0 = cta[blockIdx.x], c1 = cta[blockIdx.x + 1];
+    for (int32_t c = c0; c < c1; ++c) {
+        const Chunk ch = chunks[c];
+        __syncthreads();
+        run_stream(items[ch.item], shapes[ch.item], ch.f_begin, ch.f_end, lb, part, red_q,
+                   red_c);
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads, 1)
+    sk_imajor_chunk_batch_kernel(const Item *__restrict__ items, const Chunk *__restrict__ chunks,
+                                 const int32_t *__restrict__ cta)
+{
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ long long red_q[kThreads / 32];
+    __shared__ int red_c[kThreads / 32];
+    __shared__ ChunkMasks cm;
+    init_chunk_masks(cm);
+    const uint32_t lb = build_table(dyn_smem);
+    const int32_t c0 = cta[blockIdx.x], c1 = cta[blockIdx.x + 1];
+    for (int32_t c = c0; c < c1; ++c) {
+        const Chunk ch = chunks[c];
+        __syncthreads();
+        const Item &it = items[ch.item];
+        run_imajor_chunks<G>(it, imajor_chunk_team(it.N), ch.f_begin, ch.f_end, lb, cm, red_q,
+                             red_c);
+    }
 }
 
 typedef void (*KernelFnI)(Item, int);
 static const KernelFnI kChunkFns[3] = {sk_imajor_chunk_kernel<2>, sk_imajor_chunk_kernel<4>,
                                        sk_imajor_chunk_kernel<8>};
+typedef void (*KernelFnB)(const Item *, const Chunk *, const int32_t *);
+static const KernelFnB kChunkBatchFns[3] = {sk_imajor_chunk_batch_kernel<2>,
+                                            sk_imajor_chunk_batch_kernel<4>,
+                                            sk_imajor_chunk_batch_kernel<8>};
 
 // The dynamic shared memory of the stream and chunk kernels, once per device (plan
 // creation sets it, before any stream capture; the launches check it again).
@@ -78,6 +115,12 @@ sk_status_t stream_kernel_attrs(int device)
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         e = cudaFuncSetAttribute((const void *)kChunkFns[k],
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)sk_stream_batch_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        e = cudaFuncSetAttribute((const void *)kChunkBatchFns[k],
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
     if (e != cudaSuccess)
         return cuda_error(e, "cudaFuncSetAttribute (stream and chunk paths)");
     done.push_back(device);
@@ -94,11 +137,7 @@ sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, in
     int64_t g = std::min<int64_t>(gmax, (it.n_frames + teams - 1) / teams);
     if (g < 1)
         g = 1;
-    // lanes per input by the chunks an input spans (A/B on B300, 3 GB launches: M = 48,
-    // 4 chunks: 2 lanes 0.28, 8 lanes 0.19; M = 100, 8 chunks: 2 lanes 0.27-0.32,
-    // 8 lanes 0.32-0.34)
-    const int cmax = (it.M + 30) >> 4;
-    const int G = cmax >= 6 ? 8 : (cmax >= 3 ? 4 : 2);
+    const int G = imajor_chunk_lanes(it.M);
     const KernelFnI fn = kChunkFns[G == 2 ? 0 : (G == 4 ? 1 : 2)];
     sk_status_t s = stream_kernel_attrs(device);
     if (s != SK_OK)
@@ -248,6 +287,46 @@ sk_status_t launch_stream(const Item &it, const StreamShape &sh, int device, cud
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_error(e, "sk stream kernel launch");
+    return SK_OK;
+}
+
+int stream_batch_class(const Item &it, StreamShape *sh)
+{
+    if (it.layout == 1) {
+        if (it.fast == 2)
+            return -1;
+        const int G = imajor_chunk_lanes(it.M);
+        return G == 2 ? 1 : (G == 4 ? 2 : 3);
+    }
+    if (!stream_auto(it) || !stream_shape(it.N, it.M, sh))
+        return -1;
+    return 0;
+}
+
+int64_t stream_batch_round(const Item &it, const StreamShape &sh, int cls)
+{
+    return cls == 0 ? sh.units : (kThreads / 32) / imajor_chunk_team(it.N);
+}
+
+sk_status_t launch_stream_schedule(int cls, const Item *d_items, const StreamShape *d_shapes,
+                                   const Chunk *d_chunks, const int32_t *d_cta, int grid,
+                                   int device, cudaStream_t st)
+{
+    if (grid <= 0)
+        return SK_OK;
+    NvtxRange nv("sk batched stream launch");
+    sk_status_t s = stream_kernel_attrs(device);
+    if (s != SK_OK)
+        return s;
+    if (cls == 0)
+        sk_stream_batch_kernel<<<(unsigned)grid, kStreamThreads, kStreamSmem, st>>>(
+            d_items, d_shapes, d_chunks, d_cta);
+    else
+        kChunkBatchFns[cls - 1]<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks,
+                                                                          d_cta);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_error(e, "sk batched stream kernel launch");
     return SK_OK;
 }
 

@@ -310,3 +310,52 @@ def test_random_stream_and_chunk_shapes():
         for k, g in (("S1", s1), ("S2", s2), ("Q", q), ("neff", ne), ("mask", mask)):
             assert np.array_equal(g.cpu().numpy(), want[k]), f"{label}: {k}"
         assert np.array_equal(skv.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32)), label
+
+
+def test_batch_with_stream_and_chunk_classes():
+    """A batched launch mixing items of the stream path (small and odd time-major
+    shapes), the input-major chunk path (2, 4 and 8 lanes per input) and a fused-kernel
+    class: one persistent launch per class in one graph, replayed twice, every item's
+    SK and mask bit-exact against the oracle."""
+    dev = _dev()
+    rng = np.random.default_rng(4242)
+    shapes = [  # (N, M, layout, F)
+        (100, 100, 0, 150), (8, 256, 0, 400), (500, 100, 0, 30), (99, 101, 0, 20),
+        (2048, 100, 1, 6), (256, 48, 1, 40), (33, 17, 1, 300), (2048, 256, 0, 12),
+        (16, 64, 0, 999), (7, 3, 1, 500),
+    ]
+    plans, ins, outs, wants, items = [], [], [], [], []
+    try:
+        for N, M, layout, F in shapes:
+            x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+            wants.append(oracle.flag(x, M, N, 3.0, 0.01, layout=layout))
+            plan = sk.sk_plan_create(N, M, 3.0, 0.01, layout=layout)
+            plans.append(plan)
+            d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+            d_sk = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+            d_mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+            ins.append(d_in)
+            outs.append((d_sk, d_mask))
+            items.append((plan, d_in, F, d_sk, d_mask))
+        batch = sk.sk_batch_create(items)
+        try:
+            # classes: stream (time-major small/odd), chunk G = 8 (M = 100), G = 4
+            # (M = 48, M = 17), G = 2 (M = 3), the general class (N = 99, M = 101 keeps
+            # the general path), and N = 2048 (its own fused-kernel class)
+            assert sk.sk_batch_launches(batch) >= 5
+            for _ in range(2):
+                for d_sk, d_mask in outs:
+                    d_sk.fill_(-1.0)
+                    d_mask.fill_(7)
+                sk.sk_batch_run(batch)
+                torch.cuda.synchronize()
+                for (N, M, layout, F), (d_sk, d_mask), want in zip(shapes, outs, wants):
+                    label = f"batch item N={N} M={M} layout={layout}"
+                    assert np.array_equal(d_mask.cpu().numpy(), want["mask"]), label
+                    assert np.array_equal(d_sk.cpu().numpy().view(np.uint32),
+                                          want["sk"].view(np.uint32)), label
+        finally:
+            sk.sk_batch_destroy(batch)
+    finally:
+        for p in plans:
+            sk.sk_plan_destroy(p)
