@@ -172,9 +172,13 @@ sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows_per_batch,
  * (whole frames per team); ROW_BALANCED adds equal row ranges over the grid
  * through the plan's scratch.  A path the shape cannot take (or the launch:
  * a captured launch has no row balancing) falls back to the one it can.
- * STREAM (time-major only, N / gcd(N, 16) <= 512) reads each frame as one run
- * of 16-byte chunks, a group of lanes per frame whose byte positions keep their
- * inputs from chunk to chunk: the path of frames of few inputs, any M.
+ * STREAM reads frames in aligned 16-byte chunks.  Time-major (N / gcd(N, 16) <=
+ * 512): each frame as one run, a group of lanes per frame whose byte positions
+ * keep their inputs from chunk to chunk -- the path of frames of few inputs and of
+ * the general shapes, any M.  Input-major: 2, 4 or 8 lanes per input over the
+ * chunks that cover it, the neighbours' bytes masked -- the path of lengths M
+ * without a fast path.  Batched items the library would put on it take batch
+ * classes of their own.
  * Reported (sk_launch_config_t.last_path) besides those: GENERAL (any N and
  * M, either layout) and PER_INPUT (input-major lengths of the per-input path).
  */
