@@ -451,9 +451,22 @@ def batched_bench(reps: int = 10, dev_index: int = 0, n_frames: int = 500):
             "masks_identical": same}
 
 
+def served_pools(pool: int = 32):
+    """The 32 served streams' pools of pre-generated frames (24 x N=2048 + 8 x N=256,
+    M=256, the synthetic noise and RFI model), host numpy arrays."""
+    import synth
+
+    out = []
+    for k, N in enumerate([2048] * 24 + [256] * 8):
+        s = synth.sub_seed(4, k)
+        ds = synth.Dataset(n_frames=pool, M=256, N=N, seed=s, rfi=synth.rfi_plan(s, pool))
+        out.append(ds.generate_cpu())
+    return out
+
+
 def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
                  pool: int = 32, threads: int = 0, running_mu: bool = False,
-                 by_reference: bool = False):
+                 by_reference: bool = False, pools=None, warmup_s: float = 0.0):
     """32 streams (24 x N=2048, 8 x N=256), M=256 frames arriving every 0.65536 ms per
     stream with exponential jitter (mean T/4), for `seconds` of simulated time, through
     the continuous-batching server with the running power state, driven by the
@@ -465,7 +478,10 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
     own threads -- and 8 flat out).  running_mu: the streams also normalise by the
     running power (SK_RUNNING_MU) instead of each frame's own power.  by_reference:
     frames are submitted with sk_stream_submit_ref from page-locked pools (no copy
-    into the server's ring) instead of being copied by sk_stream_submit."""
+    into the server's ring) instead of being copied by sk_stream_submit.  pools: the
+    streams' frames (numpy arrays, or page-locked tensors for by_reference; generated
+    and pinned here when None).  warmup_s: an unmeasured replay of that many seconds
+    over the same pools and server before the measured one."""
     import torch
 
     import paper_1808_10365_b300 as sk
@@ -477,17 +493,17 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
     specs = [2048] * 24 + [256] * 8
     M = 256
     T = M * 2.56e-6
-    pools = []
-    for k, N in enumerate(specs):
-        s = synth.sub_seed(4, k)
-        ds = synth.Dataset(n_frames=pool, M=M, N=N, seed=s, rfi=synth.rfi_plan(s, pool))
-        pools.append(ds.generate_cpu())
+    if pools is None:
+        pools = served_pools(pool)
+        if by_reference:
+            pools = [torch.from_numpy(p).pin_memory() for p in pools]
     n_per = int(seconds / T)
     server = sk.sk_server_create(dev_index, 8 << 30)
     flags = sk.SK_RUNNING_MU if running_mu else sk.SK_RUNNING_OFFSET
     sids = [sk.sk_stream_open(server, N, M, ring_frames=32, flags=flags) for N in specs]
-    if by_reference:
-        pools = [torch.from_numpy(p).pin_memory() for p in pools]
+    if warmup_s > 0:
+        sk.sk_server_replay(server, sids, pools, max(1, int(warmup_s / T)), T, T / 4,
+                            paced=paced, threads=threads, by_reference=by_reference)
     r = sk.sk_server_replay(server, sids, pools, n_per, T, T / 4, paced=paced, threads=threads,
                             by_reference=by_reference)
     for sid in sids:
@@ -505,6 +521,9 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
            "launches": r["launches"], "frames_per_launch": r["frames"] / max(1, r["launches"]),
            "submit_p50_us": r["submit_p50_us"], "busy_retries": r["busy_retries"],
            "load_generator": f"sk_server_replay, {threads} submitter threads"}
+    if by_reference and warmup_s > 0:
+        out["warmup"] = (f"{warmup_s:g} s unmeasured replay over the same page-locked pools "
+                         "(pinned before the first served leg) and server")
     if paced and not running_mu and not by_reference:
         # plain path on the same frames: one synchronous sk_flag_host per frame
         lat = []
@@ -808,11 +827,20 @@ def run_gpu(args):
             line["input_major"] = input_major_bench(args.freqs, d_mask, dev_index=dev.index)
         line["shapes"] = shapes_bench(dev_index=dev.index)
         line["batched"] = batched_bench(dev_index=dev.index)
-        line["served"] = served_bench(args.served_seconds, True, dev.index)
+        # the served streams' pools, generated once; the by-reference leg's page-locked
+        # copies pinned before the first served leg and reused, as a server's long-lived
+        # receive buffers would be (freshly pinned pools showed multi-millisecond p99
+        # episodes in every one of 8 runs, reused ones in a few)
+        pools = served_pools()
+        pinned = [torch.from_numpy(p).pin_memory() for p in pools]
+        line["served"] = served_bench(args.served_seconds, True, dev.index, pools=pools)
         short = min(args.served_seconds, 2.0)
-        line["served_replay"] = served_bench(min(short, 1.0), False, dev.index)
-        line["served_running_mu"] = served_bench(short, True, dev.index, running_mu=True)
-        line["served_by_reference"] = served_bench(short, True, dev.index, by_reference=True)
+        line["served_replay"] = served_bench(min(short, 1.0), False, dev.index, pools=pools)
+        line["served_running_mu"] = served_bench(short, True, dev.index, running_mu=True,
+                                                 pools=pools)
+        line["served_by_reference"] = served_bench(short, True, dev.index, by_reference=True,
+                                                   pools=pinned, warmup_s=0.5)
+        del pinned
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
