@@ -1,4 +1,6 @@
-// Stream path kernel (time-major frames of few inputs) and its launch.
+// Kernels and launches of the stream path (time-major frames of few inputs) and of the
+// chunk path (input-major frames of any M), one-item and batched, with the host-side
+// choice of their launch shapes.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
