@@ -568,11 +568,14 @@ sk_status_t launch_single(const Item &it, int rows, bool served, int device, cud
     const int nci = it.N == 256 ? 1 : (it.N == 2048 ? 2 : 0);
     // ragged N takes its balanced path on the 8-row tile (16-row turns)
     const int tile = it.fast == 3 ? 1 : pick_tile(rows, it.M % 32 == 0);
-    // the plan's requested path and prefetch (autotuned launch configuration)
-    const int req = plan ? plan->path : SK_PATH_AUTO;
+    // the plan's requested path and prefetch (autotuned launch configuration); the stream
+    // path asked for where the shape has none is the library's own choice
+    int req = plan ? plan->path : SK_PATH_AUTO;
+    StreamShape ssh;
+    if (req == SK_PATH_STREAM && it.layout == 0 && !stream_shape(it.N, it.M, &ssh))
+        req = SK_PATH_AUTO;
     const bool pf_off = plan && plan->prefetch_off;
     // time-major frames of few inputs: the stream path, requested or by shape
-    StreamShape ssh;
     if (it.layout == 0 && (req == SK_PATH_STREAM || (req == SK_PATH_AUTO && stream_auto(it))) &&
         stream_shape(it.N, it.M, &ssh)) {
         Item run = it;

@@ -131,14 +131,17 @@ def test_stream_path_independent_estimates(N, M, F):
 
 
 def test_stream_path_not_taken_where_it_cannot():
-    """N / gcd(N, 16) above 512 (N = 2047) has no stream shape: a request for it falls
-    back to the shape's own path, with the same results."""
+    """N / gcd(N, 16) above 512 (N = 2047) has no stream shape: a request for it takes
+    the path the library chooses for the shape (here the ragged row-balanced path), with
+    the same results."""
     rng = np.random.default_rng(5)
     N, M, F = 2047, 32, 5
     x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
     taken, got = run_stream(x, M, N)
-    assert taken != sk.SK_PATH_STREAM
+    _, auto = run_stream(x, M, N, path=sk.SK_PATH_AUTO)
+    assert taken == sk.SK_PATH_ROW_BALANCED
     check(got, oracle.flag(x, M, N, 2.5, -0.01), "N=2047 fallback")
+    check(auto, oracle.flag(x, M, N, 2.5, -0.01), "N=2047 auto")
 
 
 @pytest.mark.parametrize("N,M,F,path", [
