@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (fast)
             run_fast<R, S, SRV, NC>(single, fb, fe, lb, ts, parity);
         else
-            run_general<SRV>(single, fb, fe, lb, ts, parity);
+            run_general<SRV, !SRV, 8>(single, fb, fe, lb, ts, parity);
         return;
     }
     const int32_t c0 = cta_chunks[blockIdx.x], c1 = cta_chunks[blockIdx.x + 1];
