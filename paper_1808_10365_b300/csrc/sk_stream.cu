@@ -63,12 +63,20 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     const uint32_t part_sh = (lb & ~0xFFFFu) + (uint32_t)kLutBytes;
     int32_t *part = reinterpret_cast<int32_t *>(
         dyn_smem + (part_sh - (uint32_t)__cvta_generic_to_shared(dyn_smem)));
+    // each chunk's item and shape staged in shared memory: its fields are read in the
+    // frame loop, and copies in registers spilled
+    __shared__ Item s_it;
+    __shared__ StreamShape s_sh;
     const int32_t c0 = cta[blockIdx.x], c1 = cta[blockIdx.x + 1];
     for (int32_t c = c0; c < c1; ++c) {
         const Chunk ch = chunks[c];
+        __syncthreads();  // the previous chunk is done with the slots and the staged item
+        if (threadIdx.x == 0) {
+            s_it = items[ch.item];
+            s_sh = shapes[ch.item];
+        }
         __syncthreads();
-        run_stream(items[ch.item], shapes[ch.item], ch.f_begin, ch.f_end, lb, part, red_q,
-                   red_c);
+        run_stream(s_it, s_sh, ch.f_begin, ch.f_end, lb, part, red_q, red_c);
     }
 }
 
@@ -83,13 +91,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ ChunkMasks cm;
     init_chunk_masks(cm);
     const uint32_t lb = build_table(dyn_smem);
+    __shared__ Item s_it;  // each chunk's item, staged as in sk_stream_batch_kernel
     const int32_t c0 = cta[blockIdx.x], c1 = cta[blockIdx.x + 1];
     for (int32_t c = c0; c < c1; ++c) {
         const Chunk ch = chunks[c];
         __syncthreads();
-        const Item &it = items[ch.item];
-        run_imajor_chunks<G>(it, imajor_chunk_team(it.N), ch.f_begin, ch.f_end, lb, cm, red_q,
-                             red_c);
+        if (threadIdx.x == 0)
+            s_it = items[ch.item];
+        __syncthreads();
+        run_imajor_chunks<G>(s_it, imajor_chunk_team(s_it.N), ch.f_begin, ch.f_end, lb, cm,
+                             red_q, red_c);
     }
 }
 
