@@ -547,10 +547,11 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
     return out
 
 
-# Shapes off the benchmark's own: ragged N, N = 8 (mod 16), a short integration
-# (8-row tile) and input-major integration lengths at both ends.  (label, N, M,
-# layout); each runs on about 3 GB of random bytes, the size of the benchmark's
-# own launch.
+# Shapes off the benchmark's own: ragged N, small arrays and the general path's shapes
+# (the stream path), a shape the general path keeps, N = 8 (mod 16), short integrations
+# (8-row tile, a partial last turn) and input-major integration lengths at both ends and
+# without a fast path (the chunk path).  (label, N, M, layout); each runs on about 3 GB
+# of random bytes, the size of the benchmark's own launch.
 OFF_SHAPES = [
     ("time-major N=2047 M=256 (ragged N)", 2047, 256, 0),
     ("time-major N=100 M=100 (stream path)", 100, 100, 0),
