@@ -636,4 +636,203 @@ __device__ __forceinline__ void run_imajor_chunks(const Item &it, int W, int64_t
     }
 }
 
+// ---------------------------------------------------------------------------
+// Input-major frames of short inputs (M <= kStageMaxM), staged per warp.  A warp
+// takes blocks of 32 consecutive inputs of a frame: it reads the aligned 16-byte
+// chunks that cover the block's 32·M contiguous bytes, writes them to its own
+// shared buffer, and lane r then adds input i0 + r's M bytes from there, as 4-byte
+// words (a funnel shift when the input starts off a word boundary; the bytes past
+// M in its last word become 0x88, no power) or, when M % 16 == 0, as 16-byte
+// pieces.  A lane's sums are its input's: no byte masks and no exchange between
+// lanes.  The next block's chunks are loaded into registers before the current
+// block is added, so they are in flight meanwhile; the warp's own __syncwarp
+// orders its buffer's writes and reads.  Frames as on the chunk path: teams of W
+// warps, each warp the blocks wt, wt + W, ... of its team's frame.
+// ---------------------------------------------------------------------------
+constexpr int kStageMaxM = 192;
+
+// Bytes of one warp's buffer: a block's chunks (at most 32·M + 30 bytes) and the
+// word read after an input's last, rounded to 16.
+__host__ __device__ constexpr int stage_warp_bytes(int M)
+{
+    return (32 * M + 32 + 15) / 16 * 16;
+}
+
+// Chunks a lane loads per block: a block of 32 inputs starting at any offset
+// covers at most ceil((15 + 32·M) / 16) chunks.
+__host__ __device__ constexpr int stage_lane_chunks(int M)
+{
+    return ((15 + 32 * M + 15) / 16 + 31) / 32;
+}
+
+// The four samples of word w through the lane's table into one packed sum.
+__device__ __forceinline__ uint32_t lut_word(uint32_t w, uint32_t lb)
+{
+    return lds_u32(prmt(w, lb, 0x7604u)) + lds_u32(prmt(w, lb, 0x7614u)) +
+           lds_u32(prmt(w, lb, 0x7624u)) + lds_u32(prmt(w, lb, 0x7634u));
+}
+
+// Frames [f_begin, f_end) of an input-major item with M <= kStageMaxM; CH >=
+// stage_lane_chunks(M); VEC: M % 16 == 0 (16-byte pieces; every block starts on a
+// 16-byte boundary).  buf: the warp's buffer of stage_warp_bytes(M) bytes.
+template <int CH, bool VEC>
+__device__ __forceinline__ void run_imajor_staged(const Item &it, int W, int64_t f_begin,
+                                                  int64_t f_end, uint32_t lb, uint8_t *buf,
+                                                  long long *red_q, int *red_c)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int team = warp / W, wt = warp - team * W;
+    const int teams = (int)(blockDim.x >> 5) / W;
+    if (team >= teams)
+        return;  // whole warps past the last team
+    const int N = it.N, M = it.M;
+    const int64_t fbytes = (int64_t)M * N;
+    const uint8_t *end = it.in + it.n_frames * fbytes;
+    const int nblk = (N + 31) >> 5;
+    const int per = wt < nblk ? (nblk - wt + W - 1) / W : 0;  // the warp's blocks a frame
+    const int64_t rounds = (f_end - f_begin + teams - 1) / teams;
+    const uint4 none = make_uint4(kNoPower, kNoPower, kNoPower, kNoPower);
+    uint4 *buf4 = reinterpret_cast<uint4 *>(buf);
+    const uint32_t *buf32 = reinterpret_cast<const uint32_t *>(buf);
+    uint4 v[CH];
+    // the chunks of block b of `frame` into v (chunk lane + 32c of the block)
+    auto load_block = [&](int64_t frame, int b) {
+        const int i0 = 32 * b;
+        const int nb = min(32, N - i0);
+        const int64_t start = frame * fbytes + (int64_t)i0 * M;
+        const uint8_t *a0 = it.in + (start & ~(int64_t)15);  // the input is 16-byte aligned
+        const int nch = (int)(((start & 15) + (int64_t)nb * M + 15) >> 4);
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int ci = lane + 32 * c;
+            const uint8_t *p = a0 + 16 * ci;
+            v[c] = none;
+            if (ci < nch) {
+                if (p + 16 <= end)
+                    v[c] = SK_DBG_IN(it, p, 16) ? ldg_stream16(p) : none;
+                else
+                    v[c] = load_clipped_tail(it, p, it.in, end);  // the item's last bytes
+            }
+        }
+    };
+    if (per > 0 && f_begin + team < f_end)
+        load_block(f_begin + team, wt);
+    for (int64_t k = 0; k < rounds; ++k) {
+        const int64_t frame = f_begin + k * teams + team;
+        const bool fvalid = frame < f_end;
+        int64_t q = 0;
+        int32_t cnt = 0;
+        for (int jb = 0; fvalid && jb < per; ++jb) {
+            const int b = wt + jb * W;
+            const int i0 = 32 * b;
+            const int nb = min(32, N - i0);
+            const int64_t start = frame * fbytes + (int64_t)i0 * M;
+            const int s = (int)(start & 15);
+            const int nch = (s + nb * M + 15) >> 4;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (lane + 32 * c < nch)
+                    buf4[lane + 32 * c] = v[c];
+            __syncwarp();
+            // the warp's next block (this frame's, else the team's next frame's first)
+            if (jb + 1 < per)
+                load_block(frame, b + W);
+            else if (frame + teams < f_end)
+                load_block(frame + teams, wt);
+            int32_t a1 = 0;
+            uint32_t a2 = 0u;  // S2 + 2^19 S1 modulo 2^32 until finished
+            const int o = s + lane * M;  // the lane's first byte in the buffer
+            if (VEC) {
+                for (int t = 0; t < M; t += 16) {
+                    const uint4 w = buf4[(o + t) >> 4];
+                    const uint32_t acc = lut_word(w.x, lb) + lut_word(w.y, lb) +
+                                         lut_word(w.z, lb) + lut_word(w.w, lb);
+                    a1 += (int32_t)(acc >> kPackShift);
+                    a2 += acc;
+                }
+            } else {
+                const int nw = (M + 3) >> 2;  // words of the input
+                const int nwf = (M >> 4) << 2;  // words of its whole 16-sample groups
+                const int qw = o >> 2;
+                const uint32_t sh = 8u * (uint32_t)(o & 3);
+                uint32_t cur = buf32[qw];
+                int kw = 0;
+                for (; kw < nwf; kw += 4) {
+                    uint32_t acc = 0u;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint32_t nxt = buf32[qw + kw + u + 1];
+                        acc += lut_word(__funnelshift_r(cur, nxt, sh), lb);
+                        cur = nxt;
+                    }
+                    a1 += (int32_t)(acc >> kPackShift);
+                    a2 += acc;
+                }
+                if (kw < nw) {  // the last M % 16 samples (at most 4 words)
+                    uint32_t acc = 0u;
+                    for (; kw < nw; ++kw) {
+                        const uint32_t nxt = buf32[qw + kw + 1];
+                        uint32_t w = __funnelshift_r(cur, nxt, sh);
+                        cur = nxt;
+                        const int left = M - 4 * kw;  // samples from this word on
+                        if (left < 4)
+                            w = keep_bytes(w, (1u << (8 * left)) - 1u);
+                        acc += lut_word(w, lb);
+                    }
+                    a1 += (int32_t)(acc >> kPackShift);
+                    a2 += acc;
+                }
+            }
+            __syncwarp();  // the buffer is read before the next block is written
+            a2 -= (uint32_t)a1 << kPackShift;  // exact S2
+            const int i = i0 + lane;
+            if (lane < nb) {
+                float rr = 0.0f;
+                int64_t qi = 0;
+                const bool has = SK_EPILOGUE_ALU ? input_term_alu(a1, (int32_t)a2, M, rr, qi)
+                                                 : input_term(a1, (int32_t)a2, M, rr, qi);
+                if (has) {
+                    q += qi;
+                    cnt += 1;
+                }
+                const int64_t oi = frame * N + i;
+                if (it.s1 && SK_DBG_OUT_IN(it, frame, i)) {
+                    it.s1[oi] = a1;
+                    it.s2[oi] = (int32_t)a2;
+                }
+                if (it.sk_in && SK_DBG_OUT_IN(it, frame, i)) {
+                    it.sk_in[oi] = has ? __fmul_rn(rr, it.c_tab[1]) : __int_as_float(0x7FC00000);
+                    if (it.mask_in)
+                        it.mask_in[oi] =
+                            has ? ((qi > it.t_hi[1] || qi < it.t_lo[1]) ? 1 : 0) : 1;
+                }
+            }
+        }
+        for (int sft = 16; sft > 0; sft >>= 1) {
+            q += __shfl_xor_sync(0xFFFFFFFFu, (long long)q, sft);
+            cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, sft);
+        }
+        if (W == 1) {
+            if (fvalid && lane == 0)
+                write_frame(it, frame, q, cnt);
+        } else {
+            if (lane == 0) {
+                red_q[warp] = q;
+                red_c[warp] = cnt;
+            }
+            named_sync(1 + team, 32 * W);
+            if (fvalid && wt == 0 && lane == 0) {
+                int64_t tq = 0;
+                int32_t tc = 0;
+                for (int w = 0; w < W; ++w) {
+                    tq += red_q[team * W + w];
+                    tc += red_c[team * W + w];
+                }
+                write_frame(it, frame, tq, tc);
+            }
+            named_sync(1 + team, 32 * W);  // red_* free for the next frame
+        }
+    }
+}
+
 }  // namespace sk

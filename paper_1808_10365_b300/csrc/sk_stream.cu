@@ -49,6 +49,25 @@ __global__ void __launch_bounds__(kThreads, 1) sk_imajor_chunk_kernel(Item it, i
     run_imajor_chunks<G>(it, W, fb, fe, lb, cm, red_q, red_c);
 }
 
+// Input-major frames of M <= kStageMaxM: each warp's blocks of 32 inputs staged in
+// its own buffer past the table (run_imajor_staged).
+template <int CH, bool VEC>
+__global__ void __launch_bounds__(kThreads, 1) sk_imajor_staged_kernel(Item it, int W)
+{
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ long long red_q[kThreads / 32];
+    __shared__ int red_c[kThreads / 32];
+    const uint32_t lb = build_table(dyn_smem);
+    const uint32_t stage_sh = (lb & ~0xFFFFu) + (uint32_t)kLutBytes +
+                              (threadIdx.x >> 5) * (uint32_t)stage_warp_bytes(it.M);
+    uint8_t *buf = dyn_smem + (stage_sh - (uint32_t)__cvta_generic_to_shared(dyn_smem));
+    const int64_t F = it.n_frames;
+    const int64_t NB = gridDim.x;
+    const int64_t fb = F * (int64_t)blockIdx.x / NB;
+    const int64_t fe = F * ((int64_t)blockIdx.x + 1) / NB;
+    run_imajor_staged<CH, VEC>(it, W, fb, fe, lb, buf, red_q, red_c);
+}
+
 // Batched launches: one persistent grid walks a chunk schedule (item, frame range)
 // of items of the class, each with its own launch shape; the CTA's threads meet at
 // one barrier between chunks (the slots and the per-warp sums are reused).
@@ -112,6 +131,30 @@ static const KernelFnB kChunkBatchFns[3] = {sk_imajor_chunk_batch_kernel<2>,
                                             sk_imajor_chunk_batch_kernel<4>,
                                             sk_imajor_chunk_batch_kernel<8>};
 
+// Staged kernels by chunks a lane (4: M <= 62, 8: M <= 127, 13: M <= 192), 4-byte
+// words then 16-byte pieces (M % 16 == 0).
+static const KernelFnI kStagedFns[2][3] = {
+    {sk_imajor_staged_kernel<4, false>, sk_imajor_staged_kernel<8, false>,
+     sk_imajor_staged_kernel<13, false>},
+    {sk_imajor_staged_kernel<4, true>, sk_imajor_staged_kernel<8, true>,
+     sk_imajor_staged_kernel<13, true>}};
+static_assert(stage_lane_chunks(62) <= 4 && stage_lane_chunks(127) <= 8 &&
+                  stage_lane_chunks(kStageMaxM) <= 13,
+              "chunks a lane of the staged kernels");
+constexpr int kStagedSmemMax = kDynSmem + kStreamWarps * stage_warp_bytes(kStageMaxM);
+static_assert(kStreamWarps == kThreads / 32, "warps of the staged kernels");
+
+// Staged input-major kernels unless SK_IMAJOR_STAGED=0 (then the chunk kernels take
+// every M; for comparisons).
+static bool staged_on()
+{
+    static const bool v = [] {
+        const char *e = getenv("SK_IMAJOR_STAGED");
+        return !(e && e[0] == '0');
+    }();
+    return v;
+}
+
 // The dynamic shared memory of the stream and chunk kernels, once per device (plan
 // creation sets it, before any stream capture; the launches check it again).
 sk_status_t stream_kernel_attrs(int device)
@@ -134,6 +177,9 @@ sk_status_t stream_kernel_attrs(int device)
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         e = cudaFuncSetAttribute((const void *)kChunkBatchFns[k],
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        e = cudaFuncSetAttribute((const void *)kStagedFns[k / 3][k % 3],
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
     if (e != cudaSuccess)
         return cuda_error(e, "cudaFuncSetAttribute (stream and chunk paths)");
     done.push_back(device);
@@ -150,12 +196,19 @@ sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, in
     int64_t g = std::min<int64_t>(gmax, (it.n_frames + teams - 1) / teams);
     if (g < 1)
         g = 1;
-    const int G = imajor_chunk_lanes(it.M);
-    const KernelFnI fn = kChunkFns[G == 2 ? 0 : (G == 4 ? 1 : 2)];
     sk_status_t s = stream_kernel_attrs(device);
     if (s != SK_OK)
         return s;
-    fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(it, W);
+    if (it.M <= kStageMaxM && staged_on()) {
+        const int ch = stage_lane_chunks(it.M);
+        const KernelFnI fn = kStagedFns[it.M % 16 == 0][ch <= 4 ? 0 : (ch <= 8 ? 1 : 2)];
+        const int smem = kDynSmem + kStreamWarps * stage_warp_bytes(it.M);
+        fn<<<(unsigned)g, kThreads, smem, st>>>(it, W);
+    } else {
+        const int G = imajor_chunk_lanes(it.M);
+        const KernelFnI fn = kChunkFns[G == 2 ? 0 : (G == 4 ? 1 : 2)];
+        fn<<<(unsigned)g, kThreads, kDynSmem, st>>>(it, W);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_error(e, "sk input-major chunk kernel launch");

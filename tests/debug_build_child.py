@@ -104,9 +104,11 @@ def main():
         (256, 96, 1, 30, None, PI),
         (512, 2048, 1, 6, None, WS),
         (33, 384, 1, 7, None, PI),
-        (33, 100, 1, 7, None, ST),               # input-major chunk path
+        (33, 100, 1, 7, None, ST),               # input-major staged blocks (words)
         (2048, 100, 1, 3, None, ST),             # teams of 16 warps a frame
-        (256, 96, 1, 9, dict(path=ST), ST),
+        (256, 96, 1, 9, dict(path=ST), ST),      # staged 16-byte pieces
+        (40, 80, 1, 9, None, ST),
+        (100, 300, 1, 5, None, ST),              # input-major chunk path (M > 192)
     ]
     for N, M, layout, F, cfg, path in cases:
         taken = check_case(N, M, layout, F, cfg)

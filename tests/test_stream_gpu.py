@@ -207,6 +207,10 @@ IMAJOR = [
     (7, 3, 999, 0), (33, 17, 120, 0), (1, 2, 500, 0), (4096, 5, 40, 0), (100, 1000, 7, 0),
     (3, 4095, 11, 0), (250, 33, 40, 0), (2047, 101, 3, 0), (31, 4096, 2, sk.SK_PATH_STREAM),
     (64, 96, 30, sk.SK_PATH_STREAM), (2048, 256, 4, sk.SK_PATH_STREAM),
+    # staged blocks (M <= 192): 4, 8 and 13 chunks a lane, words and 16-byte pieces,
+    # a partial last block, one-warp and several-warp teams
+    (300, 127, 5, 0), (40, 80, 9, 0), (2048, 36, 3, 0), (65, 192, 4, sk.SK_PATH_STREAM),
+    (3, 191, 30, 0), (9, 112, 11, 0), (1000, 63, 6, 0),
 ]
 
 
