@@ -645,8 +645,9 @@ __device__ __forceinline__ void run_imajor_chunks(const Item &it, int W, int64_t
 // M in its last word become 0x88, no power) or, when M % 16 == 0, as 16-byte
 // pieces.  A lane's sums are its input's: no byte masks and no exchange between
 // lanes.  The next block's chunks are loaded into registers before the current
-// block is added, so they are in flight meanwhile; the warp's own __syncwarp
-// orders its buffer's writes and reads.  Frames as on the chunk path: teams of W
+// block is added, so they are in flight meanwhile; with it.prefetch, lane 0 also
+// asks L2 for the block after that.  The warp's own __syncwarp orders its buffer's
+// writes and reads.  Frames as on the chunk path: teams of W
 // warps, each warp the blocks wt, wt + W, ... of its team's frame.
 // ---------------------------------------------------------------------------
 constexpr int kStageMaxM = 192;
@@ -739,6 +740,25 @@ __device__ __forceinline__ void run_imajor_staged(const Item &it, int W, int64_t
                 load_block(frame, b + W);
             else if (frame + teams < f_end)
                 load_block(frame + teams, wt);
+            if (it.prefetch && lane == 0) {  // the block after that into L2
+                int64_t pf = frame;
+                int pj = jb + 2;
+                if (pj >= per) {
+                    pf = frame + teams;
+                    pj -= per;
+                }
+                if (pj < per && pf < f_end) {
+                    const int pi0 = 32 * (wt + pj * W);
+                    const int pnb = min(32, N - pi0);
+                    const int64_t ps = pf * fbytes + (int64_t)pi0 * M;
+                    const uint8_t *pa = it.in + (ps & ~(int64_t)15);
+                    int64_t bytes = (((ps & 15) + (int64_t)pnb * M + 15) >> 4) << 4;
+                    if (pa + bytes > end)
+                        bytes = (end - pa) & ~(int64_t)15;
+                    if (bytes > 0)
+                        prefetch_l2(pa, (uint32_t)bytes);
+                }
+            }
             int32_t a1 = 0;
             uint32_t a2 = 0u;  // S2 + 2^19 S1 modulo 2^32 until finished
             const int o = s + lane * M;  // the lane's first byte in the buffer

@@ -203,7 +203,13 @@ sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, in
         const int ch = stage_lane_chunks(it.M);
         const KernelFnI fn = kStagedFns[it.M % 16 == 0][ch <= 4 ? 0 : (ch <= 8 ? 1 : 2)];
         const int smem = kDynSmem + kStreamWarps * stage_warp_bytes(it.M);
-        fn<<<(unsigned)g, kThreads, smem, st>>>(it, W);
+        // the L2 look-ahead pays on long inputs and costs on short ones (A/B, 3 GB
+        // launches: M = 127 0.419 -> 0.448, M = 176 0.501 -> 0.577; M = 100 0.511 ->
+        // 0.504, M = 48 0.454 -> 0.408, M = 33 0.319 -> 0.280)
+        Item run = it;
+        if (it.M < 112)
+            run.prefetch = 0;
+        fn<<<(unsigned)g, kThreads, smem, st>>>(run, W);
     } else {
         const int G = imajor_chunk_lanes(it.M);
         const KernelFnI fn = kChunkFns[G == 2 ? 0 : (G == 4 ? 1 : 2)];
