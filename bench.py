@@ -550,7 +550,7 @@ def served_bench(seconds: float = 2.0, paced: bool = True, dev_index: int = 0,
 # Shapes off the benchmark's own: ragged N, small arrays and the general path's shapes
 # (the stream path), a shape the general path keeps, N = 8 (mod 16), short integrations
 # (8-row tile, a partial last turn) and input-major integration lengths at both ends and
-# without a fast path (the chunk path).  (label, N, M, layout); each runs on about 3 GB
+# without a fast path (staged blocks).  (label, N, M, layout); each runs on about 3 GB
 # of random bytes, the size of the benchmark's own launch.
 OFF_SHAPES = [
     ("time-major N=2047 M=256 (ragged N)", 2047, 256, 0),
@@ -563,7 +563,7 @@ OFF_SHAPES = [
     ("time-major N=2048 M=48 (M = 16 mod 32)", 2048, 48, 0),
     ("time-major N=2048 M=100 (M not a multiple of 16)", 2048, 100, 0),
     ("input-major N=2048 M=64", 2048, 64, 1),
-    ("input-major N=2048 M=100 (chunk path)", 2048, 100, 1),
+    ("input-major N=2048 M=100 (staged blocks)", 2048, 100, 1),
     ("input-major N=2048 M=4096", 2048, 4096, 1),
 ]
 

@@ -175,9 +175,11 @@ sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows_per_batch,
  * STREAM reads frames in aligned 16-byte chunks.  Time-major (N / gcd(N, 16) <=
  * 512): each frame as one run, a group of lanes per frame whose byte positions
  * keep their inputs from chunk to chunk -- the path of frames of few inputs and of
- * the general shapes, any M.  Input-major: 2, 4 or 8 lanes per input over the
- * chunks that cover it, the neighbours' bytes masked -- the path of lengths M
- * without a fast path.  Batched items the library would put on it take batch
+ * the general shapes, any M.  Input-major, the path of lengths M without a fast
+ * path: up to M = 192 one-item launches stage blocks of 32 inputs per warp in
+ * shared memory and each lane adds its own input; longer inputs (and batched
+ * items) take 2, 4 or 8 lanes per input over the chunks that cover it, the
+ * neighbours' bytes masked.  Batched items the library would put on it take batch
  * classes of their own.  Asked for on a time-major shape with no unit of at most
  * 512 lanes, a launch takes the path the library would choose.
  * Reported (sk_launch_config_t.last_path) besides those: GENERAL (any N and
