@@ -652,6 +652,18 @@ __device__ __forceinline__ void run_imajor_chunks(const Item &it, int W, int64_t
 // ---------------------------------------------------------------------------
 constexpr int kStageMaxM = 192;
 
+// Warps per frame of the staged blocks: about eight blocks of 32 inputs a warp, a
+// power of two from 1 to 16 (A/B, 3 GB launches, N = 2048: M = 100 0.561 -> 0.612,
+// M = 48 0.485 -> 0.559 against the chunk path's four; half the team combines).
+__host__ __device__ __forceinline__ int imajor_staged_team(int N)
+{
+    const int blocks = (N + 31) / 32;
+    int W = 1;
+    while (W < 16 && blocks >= 16 * W)
+        W *= 2;
+    return W;
+}
+
 // Bytes of one warp's buffer: a block's chunks (at most 32·M + 30 bytes) and the
 // word read after an input's last, rounded to 16.
 __host__ __device__ constexpr int stage_warp_bytes(int M)
@@ -673,10 +685,53 @@ __device__ __forceinline__ uint32_t lut_word(uint32_t w, uint32_t lb)
            lds_u32(prmt(w, lb, 0x7624u)) + lds_u32(prmt(w, lb, 0x7634u));
 }
 
+// Input r's M samples from the staged block: 4-byte words from byte o of the buffer
+// (SHIFT: o need not be a multiple of 4; each word then joins two with a funnel
+// shift), the bytes past M in the last word as 0x88.  a1 += S1, a2 += S2 + 2^19 S1.
+template <bool SHIFT>
+__device__ __forceinline__ void staged_words(const uint32_t *buf32, int o, int M, uint32_t lb,
+                                             int32_t &a1, uint32_t &a2)
+{
+    const int nw = (M + 3) >> 2;      // words of the input
+    const int nwf = (M >> 4) << 2;    // words of its whole 16-sample groups
+    const int qw = o >> 2;
+    const uint32_t sh = 8u * (uint32_t)(o & 3);
+    uint32_t cur = SHIFT ? buf32[qw] : 0u;
+    auto word = [&](int kw) {
+        if (!SHIFT)
+            return buf32[qw + kw];
+        const uint32_t nxt = buf32[qw + kw + 1];
+        const uint32_t w = __funnelshift_r(cur, nxt, sh);
+        cur = nxt;
+        return w;
+    };
+    int kw = 0;
+    for (; kw < nwf; kw += 4) {
+        uint32_t acc = 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            acc += lut_word(word(kw + u), lb);
+        a1 += (int32_t)(acc >> kPackShift);
+        a2 += acc;
+    }
+    if (kw < nw) {  // the last M % 16 samples (at most 4 words)
+        uint32_t acc = 0u;
+        for (; kw < nw; ++kw) {
+            uint32_t w = word(kw);
+            const int left = M - 4 * kw;  // samples from this word on
+            if (left < 4)
+                w = keep_bytes(w, (1u << (8 * left)) - 1u);
+            acc += lut_word(w, lb);
+        }
+        a1 += (int32_t)(acc >> kPackShift);
+        a2 += acc;
+    }
+}
+
 // Frames [f_begin, f_end) of an input-major item with M <= kStageMaxM; CH >=
 // stage_lane_chunks(M); VEC: M % 16 == 0 (16-byte pieces; every block starts on a
-// 16-byte boundary).  buf: the warp's buffer of stage_warp_bytes(M) bytes.
-template <int CH, bool VEC>
+// 16-byte boundary); SPLIT: whole blocks load without end checks.  buf: the warp's buffer of stage_warp_bytes(M) bytes.
+template <int CH, bool VEC, bool SPLIT>
 __device__ __forceinline__ void run_imajor_staged(const Item &it, int W, int64_t f_begin,
                                                   int64_t f_end, uint32_t lb, uint8_t *buf,
                                                   long long *red_q, int *red_c)
@@ -703,16 +758,25 @@ __device__ __forceinline__ void run_imajor_staged(const Item &it, int W, int64_t
         const int64_t start = frame * fbytes + (int64_t)i0 * M;
         const uint8_t *a0 = it.in + (start & ~(int64_t)15);  // the input is 16-byte aligned
         const int nch = (int)(((start & 15) + (int64_t)nb * M + 15) >> 4);
+        if (SPLIT && nb == 32 && a0 + 16 * (int64_t)nch <= end) {
+            // a whole block inside the item: no end checks, no fill of unused chunks
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int ci = lane + 32 * c;
-            const uint8_t *p = a0 + 16 * ci;
-            v[c] = none;
-            if (ci < nch) {
-                if (p + 16 <= end)
+            for (int c = 0; c < CH; ++c) {
+                const uint8_t *p = a0 + 16 * (lane + 32 * c);
+                if (lane + 32 * c < nch)
                     v[c] = SK_DBG_IN(it, p, 16) ? ldg_stream16(p) : none;
-                else
-                    v[c] = load_clipped_tail(it, p, it.in, end);  // the item's last bytes
+            }
+        } else {
+            // a frame's last, partial block, the item's last block, or every block
+            // without SPLIT
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int ci = lane + 32 * c;
+                const uint8_t *p = a0 + 16 * ci;
+                v[c] = none;
+                if (ci < nch)
+                    v[c] = p + 16 <= end ? (SK_DBG_IN(it, p, 16) ? ldg_stream16(p) : none)
+                                         : load_clipped_tail(it, p, it.in, end);
             }
         }
     };
@@ -770,38 +834,10 @@ __device__ __forceinline__ void run_imajor_staged(const Item &it, int W, int64_t
                     a1 += (int32_t)(acc >> kPackShift);
                     a2 += acc;
                 }
+            } else if (((s | M) & 3) == 0) {
+                staged_words<false>(buf32, o, M, lb, a1, a2);  // every input starts on a word
             } else {
-                const int nw = (M + 3) >> 2;  // words of the input
-                const int nwf = (M >> 4) << 2;  // words of its whole 16-sample groups
-                const int qw = o >> 2;
-                const uint32_t sh = 8u * (uint32_t)(o & 3);
-                uint32_t cur = buf32[qw];
-                int kw = 0;
-                for (; kw < nwf; kw += 4) {
-                    uint32_t acc = 0u;
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const uint32_t nxt = buf32[qw + kw + u + 1];
-                        acc += lut_word(__funnelshift_r(cur, nxt, sh), lb);
-                        cur = nxt;
-                    }
-                    a1 += (int32_t)(acc >> kPackShift);
-                    a2 += acc;
-                }
-                if (kw < nw) {  // the last M % 16 samples (at most 4 words)
-                    uint32_t acc = 0u;
-                    for (; kw < nw; ++kw) {
-                        const uint32_t nxt = buf32[qw + kw + 1];
-                        uint32_t w = __funnelshift_r(cur, nxt, sh);
-                        cur = nxt;
-                        const int left = M - 4 * kw;  // samples from this word on
-                        if (left < 4)
-                            w = keep_bytes(w, (1u << (8 * left)) - 1u);
-                        acc += lut_word(w, lb);
-                    }
-                    a1 += (int32_t)(acc >> kPackShift);
-                    a2 += acc;
-                }
+                staged_words<true>(buf32, o, M, lb, a1, a2);
             }
             __syncwarp();  // the buffer is read before the next block is written
             a2 -= (uint32_t)a1 << kPackShift;  // exact S2

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kThreads, 1) sk_imajor_chunk_kernel(Item it, i
 
 // Input-major frames of M <= kStageMaxM: each warp's blocks of 32 inputs staged in
 // its own buffer past the table (run_imajor_staged).
-template <int CH, bool VEC>
+template <int CH, bool VEC, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1) sk_imajor_staged_kernel(Item it, int W)
 {
     extern __shared__ __align__(16) uint8_t dyn_smem[];
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads, 1) sk_imajor_staged_kernel(Item it, 
     const int64_t NB = gridDim.x;
     const int64_t fb = F * (int64_t)blockIdx.x / NB;
     const int64_t fe = F * ((int64_t)blockIdx.x + 1) / NB;
-    run_imajor_staged<CH, VEC>(it, W, fb, fe, lb, buf, red_q, red_c);
+    run_imajor_staged<CH, VEC, SPLIT>(it, W, fb, fe, lb, buf, red_q, red_c);
 }
 
 // Batched launches: one persistent grid walks a chunk schedule (item, frame range)
@@ -131,13 +131,14 @@ static const KernelFnB kChunkBatchFns[3] = {sk_imajor_chunk_batch_kernel<2>,
                                             sk_imajor_chunk_batch_kernel<4>,
                                             sk_imajor_chunk_batch_kernel<8>};
 
-// Staged kernels by chunks a lane (4: M <= 62, 8: M <= 127, 13: M <= 192), 4-byte
-// words then 16-byte pieces (M % 16 == 0).
-static const KernelFnI kStagedFns[2][3] = {
-    {sk_imajor_staged_kernel<4, false>, sk_imajor_staged_kernel<8, false>,
-     sk_imajor_staged_kernel<13, false>},
-    {sk_imajor_staged_kernel<4, true>, sk_imajor_staged_kernel<8, true>,
-     sk_imajor_staged_kernel<13, true>}};
+// Staged kernels by whole-block loads without end checks (SPLIT), 4-byte words or
+// 16-byte pieces (M % 16 == 0), and chunks a lane (4: M <= 62, 8: M <= 127, 13: M <= 192).
+#define SK_STAGED3(S, V)                                                               \
+    {sk_imajor_staged_kernel<4, V, S>, sk_imajor_staged_kernel<8, V, S>,               \
+     sk_imajor_staged_kernel<13, V, S>}
+static const KernelFnI kStagedFns[2][2][3] = {{SK_STAGED3(false, false), SK_STAGED3(false, true)},
+                                              {SK_STAGED3(true, false), SK_STAGED3(true, true)}};
+#undef SK_STAGED3
 static_assert(stage_lane_chunks(62) <= 4 && stage_lane_chunks(127) <= 8 &&
                   stage_lane_chunks(kStageMaxM) <= 13,
               "chunks a lane of the staged kernels");
@@ -177,8 +178,8 @@ sk_status_t stream_kernel_attrs(int device)
     for (int k = 0; k < 3 && e == cudaSuccess; ++k)
         e = cudaFuncSetAttribute((const void *)kChunkBatchFns[k],
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
-    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
-        e = cudaFuncSetAttribute((const void *)kStagedFns[k / 3][k % 3],
+    for (int k = 0; k < 12 && e == cudaSuccess; ++k)
+        e = cudaFuncSetAttribute((const void *)kStagedFns[k / 6][(k / 3) % 2][k % 3],
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
     if (e != cudaSuccess)
         return cuda_error(e, "cudaFuncSetAttribute (stream and chunk paths)");
@@ -190,7 +191,8 @@ sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, in
 {
     if (it.n_frames == 0)
         return SK_OK;
-    const int W = imajor_chunk_team(it.N);
+    const bool staged = it.M <= kStageMaxM && staged_on();
+    const int W = staged ? imajor_staged_team(it.N) : imajor_chunk_team(it.N);
     const int64_t teams = (kThreads / 32) / W;
     const int64_t gmax = grid_cap > 0 ? grid_cap : sm_count(device);
     int64_t g = std::min<int64_t>(gmax, (it.n_frames + teams - 1) / teams);
@@ -199,9 +201,15 @@ sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, in
     sk_status_t s = stream_kernel_attrs(device);
     if (s != SK_OK)
         return s;
-    if (it.M <= kStageMaxM && staged_on()) {
+    if (staged) {
         const int ch = stage_lane_chunks(it.M);
-        const KernelFnI fn = kStagedFns[it.M % 16 == 0][ch <= 4 ? 0 : (ch <= 8 ? 1 : 2)];
+        // whole blocks without end checks pay everywhere measured but on small arrays
+        // with a partial last block (A/B, 3 GB launches: N = 2048, M = 100 0.555 ->
+        // 0.607, M = 48 0.496 -> 0.558, M = 33 0.330 -> 0.381; N = 200, M = 100 0.556
+        // -> 0.598; N = 64, M = 48 0.482 -> 0.516; N = 100, M = 100 0.480 -> 0.412)
+        const bool split = it.N % 32 == 0 || it.N >= 128;
+        const KernelFnI fn =
+            kStagedFns[split][it.M % 16 == 0][ch <= 4 ? 0 : (ch <= 8 ? 1 : 2)];
         const int smem = kDynSmem + kStreamWarps * stage_warp_bytes(it.M);
         // the L2 look-ahead pays on long inputs and costs on short ones (A/B, 3 GB
         // launches: M = 127 0.419 -> 0.448, M = 176 0.501 -> 0.577; M = 100 0.511 ->
