@@ -225,6 +225,8 @@ extern "C" sk_status_t sk_batch_create(const sk_batch_item_t *items, int32_t n_i
         if (sc >= 0) {
             if (sc == 0 && ssh.W == 1)
                 it.prefetch = 0;  // the look-ahead prefetch pays only on multi-warp units
+            if (sc == kStagedClass && it.M < 112)
+                it.prefetch = 0;  // and on the staged blocks only from M = 112
             b->shapes[k] = ssh;
             srounds[k] = stream_batch_round(it, ssh, sc);
             b->items.push_back(it);

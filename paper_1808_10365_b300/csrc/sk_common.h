@@ -63,10 +63,12 @@ sk_status_t launch_imajor_chunks(const Item &it, int device, cudaStream_t st, in
 sk_status_t stream_kernel_attrs(int device);
 // Batched launches of the stream and chunk paths (sk_batch_create / sk_batch_run): the
 // class of an item (0: time-major stream path, 1..3: input-major chunk path with 2, 4
-// or 8 lanes per input; -1: a fused-kernel class), the frames one CTA takes per round
-// (the schedule's unit), and the launch of one class over its schedule.  d_shapes
-// holds each item's stream shape (used by class 0).
-constexpr int kStreamClasses = 4;
+// or 8 lanes per input, 4: input-major staged blocks (M <= 192); -1: a fused-kernel
+// class), the frames one CTA takes per round (the schedule's unit), and the launch of
+// one class over its schedule.  d_shapes holds each item's stream shape (used by
+// class 0).
+constexpr int kStreamClasses = 5;
+constexpr int kStagedClass = 4;
 int stream_batch_class(const Item &it, StreamShape *sh);
 int64_t stream_batch_round(const Item &it, const StreamShape &sh, int cls);
 sk_status_t launch_stream_schedule(int cls, const Item *d_items, const StreamShape *d_shapes,

@@ -123,6 +123,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// Batched staged blocks: the chunks' items have their own M (at most kStageMaxM), so
+// one kernel takes every M with the largest register set, 4-byte words and whole-block
+// loads without end checks; each item's buffers follow its M.
+__global__ void __launch_bounds__(kThreads, 1)
+    sk_imajor_staged_batch_kernel(const Item *__restrict__ items,
+                                  const Chunk *__restrict__ chunks,
+                                  const int32_t *__restrict__ cta)
+{
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    __shared__ long long red_q[kThreads / 32];
+    __shared__ int red_c[kThreads / 32];
+    const uint32_t lb = build_table(dyn_smem);
+    __shared__ Item s_it;  // each chunk's item, staged as in sk_stream_batch_kernel
+    const int32_t c0 = cta[blockIdx.x], c1 = cta[blockIdx.x + 1];
+    for (int32_t c = c0; c < c1; ++c) {
+        const Chunk ch = chunks[c];
+        __syncthreads();  // the previous chunk is done with the buffers and the item
+        if (threadIdx.x == 0)
+            s_it = items[ch.item];
+        __syncthreads();
+        const uint32_t stage_sh = (lb & ~0xFFFFu) + (uint32_t)kLutBytes +
+                                  (threadIdx.x >> 5) * (uint32_t)stage_warp_bytes(s_it.M);
+        uint8_t *buf = dyn_smem + (stage_sh - (uint32_t)__cvta_generic_to_shared(dyn_smem));
+        run_imajor_staged<13, false, true>(s_it, imajor_staged_team(s_it.N), ch.f_begin,
+                                           ch.f_end, lb, buf, red_q, red_c);
+    }
+}
+
 typedef void (*KernelFnI)(Item, int);
 static const KernelFnI kChunkFns[3] = {sk_imajor_chunk_kernel<2>, sk_imajor_chunk_kernel<4>,
                                        sk_imajor_chunk_kernel<8>};
@@ -180,6 +208,9 @@ sk_status_t stream_kernel_attrs(int device)
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem);
     for (int k = 0; k < 12 && e == cudaSuccess; ++k)
         e = cudaFuncSetAttribute((const void *)kStagedFns[k / 6][(k / 3) % 2][k % 3],
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void *)sk_imajor_staged_batch_kernel,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kStagedSmemMax);
     if (e != cudaSuccess)
         return cuda_error(e, "cudaFuncSetAttribute (stream and chunk paths)");
@@ -375,6 +406,8 @@ int stream_batch_class(const Item &it, StreamShape *sh)
     if (it.layout == 1) {
         if (it.fast == 2)
             return -1;
+        if (it.M <= kStageMaxM && staged_on())
+            return kStagedClass;
         const int G = imajor_chunk_lanes(it.M);
         return G == 2 ? 1 : (G == 4 ? 2 : 3);
     }
@@ -385,6 +418,8 @@ int stream_batch_class(const Item &it, StreamShape *sh)
 
 int64_t stream_batch_round(const Item &it, const StreamShape &sh, int cls)
 {
+    if (cls == kStagedClass)
+        return (kThreads / 32) / imajor_staged_team(it.N);
     return cls == 0 ? sh.units : (kThreads / 32) / imajor_chunk_team(it.N);
 }
 
@@ -401,6 +436,9 @@ sk_status_t launch_stream_schedule(int cls, const Item *d_items, const StreamSha
     if (cls == 0)
         sk_stream_batch_kernel<<<(unsigned)grid, kStreamThreads, kStreamSmem, st>>>(
             d_items, d_shapes, d_chunks, d_cta);
+    else if (cls == kStagedClass)
+        sk_imajor_staged_batch_kernel<<<(unsigned)grid, kThreads, kStagedSmemMax, st>>>(
+            d_items, d_chunks, d_cta);
     else
         kChunkBatchFns[cls - 1]<<<(unsigned)grid, kThreads, kDynSmem, st>>>(d_items, d_chunks,
                                                                           d_cta);

@@ -113,12 +113,12 @@ def main():
     for N, M, layout, F, cfg, path in cases:
         taken = check_case(N, M, layout, F, cfg)
         assert taken == path, (N, M, layout, cfg, taken, path)
-    # a batched launch over three fused-kernel classes, the stream class and two
-    # input-major chunk classes
+    # a batched launch over three fused-kernel classes, the stream class, the staged
+    # input-major class and an input-major chunk class
     rng = np.random.default_rng(5)
     shapes = [(2048, 128, 11), (2048, 256, 9), (256, 1024, 13), (2048, 256, 7),
-              (100, 100, 40), (99, 101, 9), (2048, 100, 3), (33, 17, 50)]
-    layouts = [0, 0, 0, 1, 0, 0, 1, 1]
+              (100, 100, 40), (99, 101, 9), (2048, 100, 3), (33, 17, 50), (100, 300, 4)]
+    layouts = [0, 0, 0, 1, 0, 0, 1, 1, 1]
     xs = [rng.integers(0, 256, size=(F, M * N), dtype=np.uint8) for N, M, F in shapes]
     plans = [sk.sk_plan_create(N, M, 3.0, 0.0, layout=l) for (N, M, F), l in zip(shapes, layouts)]
     d = [torch.from_numpy(x.reshape(-1)).to(dev) for x in xs]

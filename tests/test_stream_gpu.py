@@ -321,15 +321,15 @@ def test_random_stream_and_chunk_shapes():
 
 def test_batch_with_stream_and_chunk_classes():
     """A batched launch mixing items of the stream path (small and odd time-major
-    shapes), the input-major chunk path (2, 4 and 8 lanes per input) and a fused-kernel
-    class: one persistent launch per class in one graph, replayed twice, every item's
-    SK and mask bit-exact against the oracle."""
+    shapes), input-major staged blocks (M <= 192) and chunks (8 lanes per input, longer
+    M) and a fused-kernel class: one persistent launch per class in one graph, replayed
+    twice, every item's SK and mask bit-exact against the oracle."""
     dev = _dev()
     rng = np.random.default_rng(4242)
     shapes = [  # (N, M, layout, F)
         (100, 100, 0, 150), (8, 256, 0, 400), (500, 100, 0, 30), (99, 101, 0, 20),
         (2048, 100, 1, 6), (256, 48, 1, 40), (33, 17, 1, 300), (2048, 256, 0, 12),
-        (16, 64, 0, 999), (7, 3, 1, 500),
+        (16, 64, 0, 999), (7, 3, 1, 500), (100, 300, 1, 5), (64, 1000, 1, 3),
     ]
     plans, ins, outs, wants, items = [], [], [], [], []
     try:
@@ -346,9 +346,9 @@ def test_batch_with_stream_and_chunk_classes():
             items.append((plan, d_in, F, d_sk, d_mask))
         batch = sk.sk_batch_create(items)
         try:
-            # classes: stream (time-major small/odd), chunk G = 8 (M = 100), G = 4
-            # (M = 48, M = 17), G = 2 (M = 3), the general class (N = 99, M = 101 keeps
-            # the general path), and N = 2048 (its own fused-kernel class)
+            # classes: stream (time-major small/odd), staged input-major blocks (M =
+            # 100, 48, 17, 3), chunk G = 8 (M = 300, 1000), the general class (N = 99,
+            # M = 101 keeps the general path), and N = 2048 (its own fused-kernel class)
             assert sk.sk_batch_launches(batch) >= 5
             for _ in range(2):
                 for d_sk, d_mask in outs:
