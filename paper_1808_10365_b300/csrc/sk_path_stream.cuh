@@ -647,8 +647,9 @@ __device__ __forceinline__ void run_imajor_chunks(const Item &it, int W, int64_t
 // lanes.  The next block's chunks are loaded into registers before the current
 // block is added, so they are in flight meanwhile; with it.prefetch, lane 0 also
 // asks L2 for the block after that.  The warp's own __syncwarp orders its buffer's
-// writes and reads.  Frames as on the chunk path: teams of W
-// warps, each warp the blocks wt, wt + W, ... of its team's frame.
+// writes and reads.  Frames go to teams of W warps (about eight blocks a warp,
+// imajor_staged_team), each warp taking the blocks wt, wt + W, ... of its team's
+// frame; the team combines Q and N_eff as on the chunk path.
 // ---------------------------------------------------------------------------
 constexpr int kStageMaxM = 192;
 
