@@ -319,6 +319,47 @@ def test_random_stream_and_chunk_shapes():
         assert np.array_equal(skv.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32)), label
 
 
+def test_random_staged_input_major_shapes():
+    """30 seeded random input-major shapes of M <= 192 without a fast path (the staged
+    blocks: words with and without shifts, 16-byte pieces, whole-block loads with and
+    without end checks, the L2 look-ahead from M = 112, partial last blocks), random grid
+    sizes and frame counts: S1, S2, Q, N_eff, SK bits and masks bit-exact against the
+    oracle, and the path reported as the stream path."""
+    dev = _dev()
+    rng = np.random.default_rng(2019)
+    for case in range(30):
+        N = int(rng.choice([int(rng.integers(1, 130)), int(rng.integers(130, 2500))]))
+        M = int(rng.integers(2, 193))
+        if M % 32 == 0:
+            M -= 1
+        F = int(rng.integers(1, 60))
+        while F > 1 and F * M * N > (8 << 20):
+            F //= 2
+        grid = int(rng.choice([0, 1, 3, 17]))
+        x = rng.integers(0, 256, size=(F, M * N), dtype=np.uint8)
+        want = oracle.flag(x, M, N, 2.5, 0.02, layout=1)
+        d_in = torch.from_numpy(x.reshape(-1)).to(dev)
+        s1 = torch.full((F, N), -1, dtype=torch.int32, device=dev)
+        s2 = torch.full_like(s1, -1)
+        q = torch.full((F,), -1, dtype=torch.int64, device=dev)
+        skv = torch.full((F,), -1.0, dtype=torch.float32, device=dev)
+        ne = torch.full((F,), -1, dtype=torch.int32, device=dev)
+        mask = torch.full((F,), 7, dtype=torch.uint8, device=dev)
+        plan = sk.sk_plan_create(N, M, 2.5, 0.02, layout=1)
+        try:
+            sk.sk_plan_set_config(plan, rows=8, grid_ctas=grid)
+            sk.sk_compute(plan, d_in, F, s1, s2, q, skv, ne)
+            sk.sk_flag(plan, d_in, F, None, mask)
+            torch.cuda.synchronize()
+            taken = sk.sk_plan_get_config(plan)["last_path"]
+        finally:
+            sk.sk_plan_destroy(plan)
+        label = f"case {case}: N={N} M={M} F={F} grid={grid} -> {taken}"
+        assert taken == sk.SK_PATH_STREAM, label
+        for k, g in (("S1", s1), ("S2", s2), ("Q", q), ("neff", ne), ("mask", mask)):
+            assert np.array_equal(g.cpu().numpy(), want[k]), f"{label}: {k}"
+        assert np.array_equal(skv.cpu().numpy().view(np.uint32), want["sk"].view(np.uint32)), label
+
 def test_batch_with_stream_and_chunk_classes():
     """A batched launch mixing items of the stream path (small and odd time-major
     shapes), input-major staged blocks (M <= 192) and chunks (8 lanes per input, longer
