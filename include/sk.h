@@ -179,9 +179,9 @@ sk_status_t sk_plan_get_tiles(sk_plan_t plan, int32_t *rows_per_batch,
  * path: up to M = 192 a launch stages blocks of 32 inputs per warp in shared
  * memory and each lane adds its own input; longer inputs take 2, 4 or 8 lanes per
  * input over the chunks that cover it, the neighbours' bytes masked.  Batched
- * items the library would put on it take batch
- * classes of their own.  Asked for on a time-major shape with no unit of at most
- * 512 lanes, a launch takes the path the library would choose.
+ * items the library would put on it take batch classes of their own.  Asked for
+ * on a time-major shape with no unit of at most 512 lanes, a launch takes the
+ * path the library would choose.
  * Reported (sk_launch_config_t.last_path) besides those: GENERAL (any N and
  * M, either layout) and PER_INPUT (input-major lengths of the per-input path).
  */
